@@ -1,0 +1,168 @@
+/*
+ * qhd.h -- C ABI of the GB300 QHD split-operator simulator.
+ *
+ * The library evolves the Quantum Hamiltonian Descent Schroedinger equation
+ *
+ *     i d psi/dt = [ e^{phi_t} (-1/2 Lap) + e^{chi_t} f(x) ] psi
+ *
+ * (Leng, Hickman, Li, Wu, "Quantum Hamiltonian Descent", arXiv 2303.01471,
+ * Eq. (main1) / Eq. (qhd_operator)) on the regular periodic mesh of a box
+ * [lo, hi]^d with N_d = 2^q points per axis (Sec. "Implementing QHD using
+ * product formulae", "Spatial discretization", Eq. (wave-rep)).  Time stepping
+ * is the pseudo-spectral product formula of Eqs. (prod_qhd), (prod_qhd_fft)
+ * and Algorithm 1 in its symmetric (Strang) form: per step a potential half
+ * phase, a forward FFT along every axis, the kinetic phase diagonal in Fourier
+ * space, an inverse FFT and a second potential half phase, with both schedule
+ * coefficients taken at the step midpoint.  Observables follow Eq. (expect_O)
+ * and the success criterion of the Fig. 2 caption.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Arrays are row-major with the LAST axis fastest.  The grid point with
+ *   multi-index (j_0, ..., j_{d-1}) sits at x_k = lo[k] + j_k (hi[k]-lo[k]) / n[k].
+ * - psi is complex64: interleaved (re, im) float32 pairs, batch * G values,
+ *   G = prod n[k]; instance b occupies [b*G, (b+1)*G).  The caller owns it.
+ * - Device memory (psi, workspace) and the CUDA stream belong to the caller.
+ *   The library allocates no device memory: everything it needs lives in the
+ *   caller's workspace of qhd_workspace_bytes() bytes (256-byte aligned).
+ * - All work is enqueued on the caller's stream.  qhd_set_potential*,
+ *   qhd_observables and qhd_destroy synchronise that stream; the other calls
+ *   only enqueue.
+ * - Every call returns a qhd_status; no exception crosses the ABI.  A failed
+ *   argument check leaves the context unchanged.  A CUDA error or a device
+ *   time-out makes the context sticky-failed: later calls return the same
+ *   status until qhd_destroy.  qhd_last_error() gives the message.
+ * - One context must not be used from two host threads at once.
+ */
+#ifndef QHD_H
+#define QHD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qhd_ctx qhd_ctx; /* opaque; created by qhd_init_grid, freed by qhd_destroy */
+
+typedef enum {
+    QHD_OK = 0,
+    QHD_ERR_INVALID_ARG = 1, /* a pointer, size or value is out of its documented range */
+    QHD_ERR_UNSUPPORTED = 2, /* valid request the library does not implement           */
+    QHD_ERR_STATE = 3,       /* call order violated (e.g. evolve before set_potential)  */
+    QHD_ERR_CUDA = 4,        /* a CUDA runtime call or kernel launch failed (sticky)    */
+    QHD_ERR_TIMEOUT = 5,     /* a bounded device wait gave up (sticky)                  */
+    QHD_ERR_WORKSPACE = 6    /* workspace NULL, too small or misaligned                 */
+} qhd_status;
+
+/* Damping schedule families (Eq. (qhd_operator) leaves phi_t, chi_t free). */
+typedef enum {
+    /* e^{phi_t} = c_phi / (eps + t^3), e^{chi_t} = c_chi t^3.  With c_phi = 2,
+     * eps = s = 1e-3, c_chi = 2 this is Eq. (nonconvex_QHD_h) of the paper's
+     * simulations; c_chi = 2 sigma scales the potential weight. */
+    QHD_SCHED_NESTEROV = 0,
+    /* phi(t), chi(t) piecewise linear through n_samples points (t strictly
+     * increasing), constant outside [t[0], t[n-1]]; a = e^phi, b = e^chi. */
+    QHD_SCHED_TABLE = 1
+} qhd_sched_kind;
+
+typedef struct {
+    int32_t kind;       /* qhd_sched_kind                                        */
+    double c_phi;       /* NESTEROV: > 0                                          */
+    double eps;         /* NESTEROV: >= 0; eps = 0 is allowed only if no step     */
+                        /*           midpoint is t = 0                            */
+    double c_chi;       /* NESTEROV: >= 0                                         */
+    const double *t;    /* TABLE: host arrays of n_samples values, copied by the  */
+    const double *phi;  /*        library during qhd_set_schedule                 */
+    const double *chi;
+    int64_t n_samples;  /* TABLE: 1 .. 4096                                       */
+} qhd_schedule;
+
+/* Observables of one instance (Eq. (expect_O); Fig. 2 caption). */
+typedef struct {
+    double t;          /* current simulation time                                   */
+    double norm;       /* sum_x |psi_x|^2  (l2 norm of Eq. (wave-rep); 1 ideally)   */
+    double e_f;        /* E[f] = sum_x |psi_x|^2 f(x)  (FP64 f, FP64 accumulation)  */
+    double p_succ;     /* sum of |psi_x|^2 over mesh points with |x - x*|_2 < radius */
+                       /* (Euclidean on the box, not periodic)                      */
+    double x_star[3];  /* grid minimiser of f (lowest flat index on ties); 0 beyond d */
+    int64_t steps_done;/* Strang steps taken since the last qhd_reset_state          */
+} qhd_obs;
+
+/* Bytes of device workspace a context for this grid and batch needs.
+ * Returns 0 for an unsupported shape (see qhd_init_grid). */
+size_t qhd_workspace_bytes(int ndim, const int64_t *n, int64_t batch);
+
+/*
+ * Create a context.  ndim in 1..3; every n[k] a power of two in 2..1024;
+ * lo[k] < hi[k], both finite; batch >= 1 independent instances sharing the
+ * mesh (each with its own f and schedule).  psi_dev: caller-owned device
+ * buffer of batch*G complex64, 8-byte aligned.  work_dev: caller-owned device
+ * buffer of work_bytes >= qhd_workspace_bytes(...), 256-byte aligned.
+ * stream: a cudaStream_t (NULL = legacy default stream).  Both buffers must
+ * outlive the context.  *out is set only on QHD_OK.
+ */
+qhd_status qhd_init_grid(qhd_ctx **out, int ndim, const int64_t *n, const double *lo,
+                         const double *hi, int64_t batch, void *psi_dev, void *work_dev,
+                         size_t work_bytes, void *stream);
+
+/*
+ * Load the objective sampled on the mesh (step "sample f" of Algorithm 1):
+ * f_host is host FP64, batch*G values in psi's layout.  Copies f into the
+ * workspace (FP64 for E[f], plus a 32-bit fixed-point copy with a per-instance
+ * power-of-two scale used for the potential phase), finds the grid minimiser x*.
+ * Every value must be finite and max f - min f < 2^31 per instance, else
+ * QHD_ERR_INVALID_ARG.  Synchronises the stream.
+ */
+qhd_status qhd_set_potential(qhd_ctx *ctx, const double *f_host);
+
+/* Same as qhd_set_potential with f already in device memory (FP64, batch*G). */
+qhd_status qhd_set_potential_device(qhd_ctx *ctx, const double *f_dev);
+
+/*
+ * Set the damping schedule: s points to batch schedules (one per instance).
+ * TABLE samples are copied.  Invalid parameters give QHD_ERR_INVALID_ARG.
+ */
+qhd_status qhd_set_schedule(qhd_ctx *ctx, const qhd_schedule *s);
+
+/* psi <- G^{-1/2} in every instance (uniform superposition, Algorithm 1 step 3),
+ * t <- 0, steps_done <- 0.  Enqueued on the stream. */
+qhd_status qhd_reset_state(qhd_ctx *ctx);
+
+/* Set the simulation time without touching psi (psi is the caller's buffer and
+ * may be written directly, e.g. to resume from a checkpoint). */
+qhd_status qhd_set_time(qhd_ctx *ctx, double t);
+qhd_status qhd_get_time(const qhd_ctx *ctx, double *t_out, int64_t *steps_done_out);
+
+/*
+ * Advance every instance by n = round(T/dt) Strang steps (Eq. (prod_qhd_fft)
+ * with the symmetric split): step j uses a = e^{phi}, b = e^{chi} at
+ * t_{j+1/2} = t + (j + 1/2) dt.  T/dt must be a positive integer to within
+ * 1e-9 relative; dt finite and nonzero (dt < 0 with T < 0 runs time backwards,
+ * exactly undoing a forward run up to rounding).  Requires set_potential and
+ * set_schedule.  Enqueued on the stream (asynchronous); t <- t + n dt.
+ */
+qhd_status qhd_evolve(qhd_ctx *ctx, double T, double dt);
+
+/*
+ * Observables of every instance: out_host[batch] receives qhd_obs; prob_dev
+ * (optional, NULL to skip) receives |psi|^2 as float32, batch*G values.
+ * radius > 0 (the paper's success radius is 0.1).  Synchronises the stream.
+ */
+qhd_status qhd_observables(qhd_ctx *ctx, qhd_obs *out_host, float *prob_dev, double radius);
+
+/* Kernel launches this context has issued so far (for launch accounting). */
+int64_t qhd_launch_count(const qhd_ctx *ctx);
+
+/* Synchronise the stream and free the host-side context (never the caller's
+ * buffers).  NULL is accepted. */
+qhd_status qhd_destroy(qhd_ctx *ctx);
+
+const char *qhd_status_string(qhd_status s);
+const char *qhd_last_error(const qhd_ctx *ctx); /* "" if none; ctx may be NULL */
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QHD_H */

@@ -1,0 +1,271 @@
+// qhd_device.cuh -- device building blocks of the split-operator step: complex
+// arithmetic, in-register DFTs, the two-stage shared-memory line FFT and the
+// fixed-point phase helpers.
+//
+// The kinetic factor of the pseudo-spectral product formula is diagonal in the
+// Fourier basis (Eq. (prod_qhd_fft)), so every step needs a forward and an
+// inverse DFT along each axis.  A line of N = R1 * R2 points is transformed by
+// T = N / E threads that each hold E points in registers: stage 1 is an
+// R1-point DFT done entirely in registers, a padded shared-memory exchange,
+// then twiddles and an R2-point DFT in registers (a two-stage Stockham
+// factorisation, so input and output are both in natural order).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace qhd {
+
+// ------------------------------------------------------------------ complex
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a * conj(b)
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
+    return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+// multiply by -i (forward) or +i (inverse)
+template <bool INV>
+__device__ __forceinline__ float2 mul_mi(float2 a) {
+    return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+
+// cos(2 pi k / 64), k = 0..16, correctly rounded to double.
+__host__ __device__ constexpr double cos64_q(int k) {
+    constexpr double q[17] = {1.0,
+                              0.9951847266721968862448,
+                              0.9807852804032304491262,
+                              0.9569403357322088649358,
+                              0.9238795325112867561282,
+                              0.8819212643483550297128,
+                              0.8314696123025452370788,
+                              0.7730104533627369608109,
+                              0.7071067811865475244008,
+                              0.6343932841636454982152,
+                              0.5555702330196022247428,
+                              0.4713967368259976485564,
+                              0.3826834323650897717285,
+                              0.2902846772544623676362,
+                              0.1950903220161282678483,
+                              0.0980171403295606019942,
+                              0.0};
+    return q[k];
+}
+__host__ __device__ constexpr double cos64(int k) {
+    k &= 63;
+    return k <= 16 ? cos64_q(k) : k <= 32 ? -cos64_q(32 - k) : k <= 48 ? -cos64_q(k - 32) : cos64_q(64 - k);
+}
+__host__ __device__ constexpr double sin64(int k) { return cos64(k - 16); }
+
+// v * W_R^k with W_R = exp(-2 pi i / R) (forward) or its conjugate (inverse);
+// k is a compile-time constant after unrolling, so the trivial cases fold.
+template <int R, bool INV>
+__device__ __forceinline__ float2 twiddle_const(float2 v, int k) {
+    static_assert(64 % R == 0, "in-register DFT sizes up to 64");
+    if (k == 0) return v;
+    if (4 * k == R) return mul_mi<INV>(v);
+    if (2 * k == R) return make_float2(-v.x, -v.y);
+    if (4 * k == 3 * R) return mul_mi<!INV>(v);
+    const float c = (float)cos64(k * (64 / R));
+    const float s = INV ? (float)sin64(k * (64 / R)) : -(float)sin64(k * (64 / R));
+    return make_float2(v.x * c - v.y * s, v.x * s + v.y * c);
+}
+
+// -------------------------------------------------------- in-register DFT
+// In-place R-point DFT of v[0..R) (natural order in and out), unnormalised,
+// exp(-2 pi i jk/R) forward, exp(+2 pi i jk/R) inverse.
+template <int R, bool INV>
+__device__ __forceinline__ void dft(float2 *v) {
+    if constexpr (R == 1) {
+        return;
+    } else if constexpr (R == 2) {
+        float2 a = v[0], b = v[1];
+        v[0] = cadd(a, b);
+        v[1] = csub(a, b);
+    } else if constexpr (R == 4) {
+        float2 t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+        float2 t2 = cadd(v[1], v[3]), t3 = mul_mi<INV>(csub(v[1], v[3]));
+        v[0] = cadd(t0, t2);
+        v[2] = csub(t0, t2);
+        v[1] = cadd(t1, t3);
+        v[3] = csub(t1, t3);
+    } else if constexpr (R == 8) {
+        // radix-2 split: two 4-point DFTs of the even / odd samples
+        float2 e[4], o[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            e[i] = v[2 * i];
+            o[i] = v[2 * i + 1];
+        }
+        dft<4, INV>(e);
+        dft<4, INV>(o);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            float2 w = twiddle_const<8, INV>(o[k], k);
+            v[k] = cadd(e[k], w);
+            v[k + 4] = csub(e[k], w);
+        }
+    } else {
+        // radix-4 split: four (R/4)-point DFTs of the samples r mod 4
+        constexpr int Q = R / 4;
+        float2 d[4][Q];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int i = 0; i < Q; ++i) d[r][i] = v[4 * i + r];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) dft<Q, INV>(d[r]);
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+            float2 a0 = d[0][k];
+            float2 a1 = twiddle_const<R, INV>(d[1][k], k);
+            float2 a2 = twiddle_const<R, INV>(d[2][k], 2 * k);
+            float2 a3 = twiddle_const<R, INV>(d[3][k], 3 * k);
+            float2 t0 = cadd(a0, a2), t1 = csub(a0, a2);
+            float2 t2 = cadd(a1, a3), t3 = mul_mi<INV>(csub(a1, a3));
+            v[k] = cadd(t0, t2);
+            v[k + 2 * Q] = csub(t0, t2);
+            v[k + Q] = cadd(t1, t3);
+            v[k + 3 * Q] = csub(t1, t3);
+        }
+    }
+}
+
+// ------------------------------------------------------------ line plans
+// N = R1 * R2 points per line, E points per thread, T = N / E threads per line.
+template <int N> struct Plan;
+template <> struct Plan<2>    { static constexpr int R1 = 2,  R2 = 1,  E = 2;  };
+template <> struct Plan<4>    { static constexpr int R1 = 4,  R2 = 1,  E = 4;  };
+template <> struct Plan<8>    { static constexpr int R1 = 8,  R2 = 1,  E = 8;  };
+template <> struct Plan<16>   { static constexpr int R1 = 16, R2 = 1,  E = 16; };
+template <> struct Plan<32>   { static constexpr int R1 = 4,  R2 = 8,  E = 8;  };
+template <> struct Plan<64>   { static constexpr int R1 = 8,  R2 = 8,  E = 8;  };
+template <> struct Plan<128>  { static constexpr int R1 = 8,  R2 = 16, E = 16; };
+template <> struct Plan<256>  { static constexpr int R1 = 16, R2 = 16, E = 16; };
+template <> struct Plan<512>  { static constexpr int R1 = 16, R2 = 32, E = 32; };
+template <> struct Plan<1024> { static constexpr int R1 = 32, R2 = 32, E = 32; };
+
+template <int N> struct LineCfg {
+    static constexpr int R1 = Plan<N>::R1, R2 = Plan<N>::R2, E = Plan<N>::E;
+    static constexpr int T = N / E;
+    static constexpr bool TWO_STAGE = R2 > 1;
+    static constexpr int LOG_R1 = R1 == 2 ? 1 : R1 == 4 ? 2 : R1 == 8 ? 3 : R1 == 16 ? 4 : 5;
+    static constexpr int PADDED = TWO_STAGE ? N + N / R1 : 0;  // padded line length (float2)
+    static_assert(E % R1 == 0 && E % R2 == 0 && N == R1 * R2, "bad plan");
+};
+
+__host__ __device__ constexpr int pad_index(int i, int log_r1) { return i + (i >> log_r1); }
+
+// Worst shared-memory bank conflict (8-byte words, evaluated per half warp)
+// of the two exchange patterns for a line stride S.  lanes: lane l works on
+// line (ROWMAJOR ? l / T : l % W) at thread index (ROWMAJOR ? l % T : l / W).
+template <int N>
+__host__ __device__ constexpr int conflicts(int S, bool rowmajor, int W) {
+    using C = LineCfg<N>;
+    int worst = 1;
+    for (int pass = 0; pass < 2; ++pass) {
+        const int R = pass == 0 ? C::R1 : C::R2;
+        for (int q = 0; q < C::E / R; ++q)
+            for (int m = 0; m < R; ++m)
+                for (int h = 0; h < 2; ++h) {
+                    int addr[16] = {};
+                    for (int l = 0; l < 16; ++l) {
+                        int lane = 16 * h + l;
+                        int line = rowmajor ? (C::T >= 32 ? 0 : lane / C::T) : lane % W;
+                        int t = rowmajor ? (C::T >= 32 ? lane : lane % C::T) : lane / W;
+                        if (t >= C::T) t %= C::T;
+                        int j = t + C::T * q;
+                        int i = pass == 0 ? j * C::R1 + m : j + m * C::R1;
+                        addr[l] = line * S + pad_index(i, C::LOG_R1);
+                    }
+                    int per_bank[16] = {};
+                    for (int l = 0; l < 16; ++l) {
+                        bool dup = false;
+                        for (int l2 = 0; l2 < l; ++l2) dup = dup || addr[l2] == addr[l];
+                        if (!dup) ++per_bank[addr[l] & 15];
+                    }
+                    for (int b = 0; b < 16; ++b) worst = per_bank[b] > worst ? per_bank[b] : worst;
+                }
+    }
+    return worst;
+}
+
+// Best line stride (in float2) in [PADDED, PADDED + 16] for the lane layout.
+template <int N>
+__host__ __device__ constexpr int line_stride(bool rowmajor, int W) {
+    using C = LineCfg<N>;
+    if (!C::TWO_STAGE) return 0;
+    int best = C::PADDED, best_c = 1 << 30;
+    for (int S = C::PADDED; S <= C::PADDED + 16; ++S) {
+        int c = conflicts<N>(S, rowmajor, W);
+        if (c < best_c) {
+            best_c = c;
+            best = S;
+        }
+    }
+    return best;
+}
+
+// ------------------------------------------------------------ line FFT
+// x[e] holds line element t + T*e on entry and transform element t + T*e on
+// exit.  sm: this line's shared buffer (stride-padded), tw2: stage-2 twiddles
+// tw2[m*R1 + j] = exp(-2 pi i j m / N).  SYNC() orders the exchange among
+// the T threads of the line (a warp barrier when a line lives in one warp).
+template <int N, bool INV, typename Sync>
+__device__ __forceinline__ void line_fft(float2 *x, float2 *sm, int t, const float2 *__restrict__ tw2,
+                                         Sync sync) {
+    using C = LineCfg<N>;
+    if constexpr (!C::TWO_STAGE) {
+        dft<N, INV>(x);
+    } else {
+        constexpr int R1 = C::R1, R2 = C::R2, E = C::E, T = C::T;
+#pragma unroll
+        for (int q = 0; q < E / R1; ++q) {
+            float2 v[R1];
+#pragma unroll
+            for (int m = 0; m < R1; ++m) v[m] = x[q + m * (E / R1)];
+            dft<R1, INV>(v);
+            const int j = t + T * q;
+#pragma unroll
+            for (int m = 0; m < R1; ++m) sm[pad_index(j * R1 + m, C::LOG_R1)] = v[m];
+        }
+        sync();
+#pragma unroll
+        for (int q = 0; q < E / R2; ++q) {
+            const int j = t + T * q;  // < R1
+            float2 v[R2];
+#pragma unroll
+            for (int m = 0; m < R2; ++m) v[m] = sm[pad_index(j + m * R1, C::LOG_R1)];
+#pragma unroll
+            for (int m = 1; m < R2; ++m) {
+                const float2 w = __ldg(&tw2[m * R1 + j]);
+                v[m] = INV ? cmulc(v[m], w) : cmul(v[m], w);
+            }
+            dft<R2, INV>(v);
+#pragma unroll
+            for (int m = 0; m < R2; ++m) x[q + m * (E / R2)] = v[m];
+        }
+        sync();
+    }
+}
+
+// ------------------------------------------------------- phase helpers
+// Fixed-point turns: a phase angle 2 pi u / 2^32 is carried as u (uint32).
+// hi32((c * v) mod 2^64) for a 64-bit fraction c (units of 2^-64 turns) and a
+// 32-bit integer v: the fractional turns of c*v to 2^-32, exact up to the
+// dropped low word (< 1 unit).
+__device__ __forceinline__ uint32_t turns_mul(uint64_t c, uint32_t v) {
+    const uint32_t lo = (uint32_t)c, hi = (uint32_t)(c >> 32);
+    return __umulhi(lo, v) + hi * v;
+}
+
+// exp(-2 pi i u / 2^32) in FP32.
+__device__ __forceinline__ float2 phase_from_turns(uint32_t u) {
+    const float x = (float)(int32_t)u * 4.656612873077392578125e-10f;  // 2^-31: angle = pi x
+    float s, c;
+    sincospif(x, &s, &c);
+    return make_float2(c, -s);
+}
+
+}  // namespace qhd

@@ -1,0 +1,579 @@
+// qhd_host.cu -- host side of the C ABI declared in include/qhd.h.
+//
+// Owns argument validation, the workspace layout, the per-context state and
+// the order of kernel launches of one evolve call.  Device memory and the
+// stream belong to the caller; nothing here allocates device memory.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "qhd.h"
+#include "qhd_kernels.h"
+
+using namespace qhd;
+
+namespace {
+
+constexpr int MAX_TABLE_SAMPLES = 256;
+constexpr size_t KT_BUDGET = size_t(64) << 20;  // bytes of kinetic tables per chunk
+constexpr int64_t MAX_CHUNK = 1024;
+constexpr int OBS_BLOCKS_MAX = 1024;
+constexpr int MINMAX_BLOCKS_MAX = 512;
+
+size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
+
+struct Layout {
+    size_t f64, fq, kt, pot, sched, samples, inst, tw, coord, obs_part, obs_res, mm, total;
+    int64_t chunk;
+    int obs_blocks, mm_blocks;
+};
+
+int64_t grid_points(int ndim, const int64_t *n) {
+    int64_t g = 1;
+    for (int d = 0; d < ndim; ++d) g *= n[d];
+    return g;
+}
+
+bool shape_ok(int ndim, const int64_t *n, int64_t batch) {
+    if (ndim < 1 || ndim > 3 || !n || batch < 1) return false;
+    for (int d = 0; d < ndim; ++d)
+        if (!supported_n(n[d])) return false;
+    const int64_t g = grid_points(ndim, n);
+    if (g > (int64_t(1) << 30)) return false;
+    if (batch > (int64_t(1) << 20) || g * batch > (int64_t(1) << 34)) return false;
+    return true;
+}
+
+int block_count(int64_t g, int cap) {
+    int64_t b = (g + 255) / 256;
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+Layout make_layout(int ndim, const int64_t *n, int64_t batch) {
+    Layout L{};
+    const int64_t g = grid_points(ndim, n);
+    int64_t ksum = 0;
+    for (int d = 0; d < ndim; ++d) ksum += n[d];
+    int64_t ch = (int64_t)(KT_BUDGET / ((size_t)batch * (size_t)ksum * sizeof(float2)));
+    if (ch > MAX_CHUNK) ch = MAX_CHUNK;
+    if (ch < 1) ch = 1;
+    L.chunk = ch;
+    L.obs_blocks = block_count(g, OBS_BLOCKS_MAX);
+    L.mm_blocks = block_count(g, MINMAX_BLOCKS_MAX);
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off = align_up(off + bytes);
+        return o;
+    };
+    L.f64 = take(sizeof(double) * (size_t)(g * batch));
+    L.fq = take(sizeof(uint32_t) * (size_t)(g * batch));
+    L.kt = take(sizeof(float2) * (size_t)(ch * batch * ksum));
+    L.pot = take(sizeof(uint64_t) * (size_t)((ch + 1) * batch));
+    L.sched = take(sizeof(SchedDev) * (size_t)batch);
+    L.samples = take(sizeof(double) * 3 * MAX_TABLE_SAMPLES * (size_t)batch);
+    L.inst = take(sizeof(InstDev) * (size_t)batch);
+    L.tw = take(sizeof(float2) * (size_t)(ksum));
+    L.coord = take(sizeof(double) * (size_t)ksum);
+    L.obs_part = take(sizeof(double) * 3 * (size_t)L.obs_blocks * (size_t)batch);
+    L.obs_res = take(sizeof(double) * 3 * (size_t)batch);
+    L.mm = take(sizeof(MinMaxPart) * (size_t)L.mm_blocks * (size_t)batch);
+    L.total = off;
+    return L;
+}
+
+struct SchedHost {
+    qhd_schedule s{};
+    std::vector<double> t, phi, chi;
+};
+
+}  // namespace
+
+struct qhd_ctx {
+    int ndim = 0;
+    int64_t n[3] = {1, 1, 1};
+    double lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1};
+    int64_t batch = 1, g = 1;
+    int ksum = 0, koff[3] = {0, 0, 0};
+    float2 *psi = nullptr;
+    char *work = nullptr;
+    size_t work_bytes = 0;
+    cudaStream_t stream = nullptr;
+    Layout L{};
+    // workspace views
+    double *f64 = nullptr;
+    uint32_t *fq = nullptr;
+    float2 *kt = nullptr;
+    uint64_t *pot = nullptr;
+    SchedDev *sched = nullptr;
+    double *samples = nullptr;
+    InstDev *inst = nullptr;
+    float2 *tw[3] = {nullptr, nullptr, nullptr};
+    double *coord = nullptr;
+    double *obs_part = nullptr, *obs_res = nullptr;
+    MinMaxPart *mm = nullptr;
+    // host state
+    bool have_f = false, have_sched = false;
+    double t = 0.0;
+    int64_t steps_done = 0;
+    int64_t launches = 0;
+    qhd_status sticky = QHD_OK;
+    std::string err;
+    std::vector<InstDev> inst_host;
+    std::vector<double> coord_host;
+};
+
+namespace {
+
+qhd_status fail(qhd_ctx *c, qhd_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) {
+        c->err = buf;
+        if (s == QHD_ERR_CUDA || s == QHD_ERR_TIMEOUT) c->sticky = s;
+    }
+    return s;
+}
+
+qhd_status cuda_fail(qhd_ctx *c, cudaError_t e, const char *where) {
+    return fail(c, QHD_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define QHD_CUDA(c, call)                                        \
+    do {                                                         \
+        cudaError_t e_ = (call);                                 \
+        if (e_ != cudaSuccess) return cuda_fail((c), e_, #call); \
+    } while (0)
+
+#define QHD_LAUNCH(c, call)                                      \
+    do {                                                         \
+        cudaError_t e_ = (call);                                 \
+        if (e_ != cudaSuccess) return cuda_fail((c), e_, #call); \
+        (c)->launches++;                                         \
+    } while (0)
+
+qhd_status check_ctx(qhd_ctx *c) {
+    if (!c) return QHD_ERR_INVALID_ARG;
+    if (c->sticky != QHD_OK) return c->sticky;
+    return QHD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *qhd_status_string(qhd_status s) {
+    switch (s) {
+    case QHD_OK: return "ok";
+    case QHD_ERR_INVALID_ARG: return "invalid argument";
+    case QHD_ERR_UNSUPPORTED: return "unsupported";
+    case QHD_ERR_STATE: return "bad call order";
+    case QHD_ERR_CUDA: return "CUDA error";
+    case QHD_ERR_TIMEOUT: return "device time-out";
+    case QHD_ERR_WORKSPACE: return "workspace too small or misaligned";
+    }
+    return "unknown status";
+}
+
+const char *qhd_last_error(const qhd_ctx *c) { return c ? c->err.c_str() : ""; }
+
+int64_t qhd_launch_count(const qhd_ctx *c) { return c ? c->launches : 0; }
+
+size_t qhd_workspace_bytes(int ndim, const int64_t *n, int64_t batch) {
+    if (!shape_ok(ndim, n, batch)) return 0;
+    return make_layout(ndim, n, batch).total;
+}
+
+qhd_status qhd_init_grid(qhd_ctx **out, int ndim, const int64_t *n, const double *lo, const double *hi,
+                         int64_t batch, void *psi_dev, void *work_dev, size_t work_bytes, void *stream) {
+    if (!out || !n || !lo || !hi) return QHD_ERR_INVALID_ARG;
+    if (!shape_ok(ndim, n, batch)) return QHD_ERR_INVALID_ARG;
+    for (int d = 0; d < ndim; ++d)
+        if (!std::isfinite(lo[d]) || !std::isfinite(hi[d]) || !(lo[d] < hi[d])) return QHD_ERR_INVALID_ARG;
+    if (!psi_dev || ((uintptr_t)psi_dev & 7)) return QHD_ERR_INVALID_ARG;
+    Layout L = make_layout(ndim, n, batch);
+    if (!work_dev || ((uintptr_t)work_dev & 255) || work_bytes < L.total) return QHD_ERR_WORKSPACE;
+
+    qhd_ctx *c = new qhd_ctx();
+    c->ndim = ndim;
+    c->batch = batch;
+    for (int d = 0; d < ndim; ++d) {
+        c->n[d] = n[d];
+        c->lo[d] = lo[d];
+        c->hi[d] = hi[d];
+    }
+    c->g = grid_points(ndim, n);
+    c->ksum = 0;
+    for (int d = 0; d < ndim; ++d) {
+        c->koff[d] = c->ksum;
+        c->ksum += (int)n[d];
+    }
+    c->psi = (float2 *)psi_dev;
+    c->work = (char *)work_dev;
+    c->work_bytes = work_bytes;
+    c->stream = (cudaStream_t)stream;
+    c->L = L;
+    c->f64 = (double *)(c->work + L.f64);
+    c->fq = (uint32_t *)(c->work + L.fq);
+    c->kt = (float2 *)(c->work + L.kt);
+    c->pot = (uint64_t *)(c->work + L.pot);
+    c->sched = (SchedDev *)(c->work + L.sched);
+    c->samples = (double *)(c->work + L.samples);
+    c->inst = (InstDev *)(c->work + L.inst);
+    c->coord = (double *)(c->work + L.coord);
+    c->obs_part = (double *)(c->work + L.obs_part);
+    c->obs_res = (double *)(c->work + L.obs_res);
+    c->mm = (MinMaxPart *)(c->work + L.mm);
+
+    // stage-2 twiddles per axis, tw2[m*R1 + j] = exp(-2 pi i j m / N) from FP64
+    std::vector<float2> tw((size_t)c->ksum, make_float2(0.f, 0.f));
+    for (int d = 0; d < ndim; ++d) {
+        int r1 = 0, r2 = 0;
+        plan_of((int)n[d], &r1, &r2);
+        c->tw[d] = (float2 *)(c->work + L.tw) + c->koff[d];
+        if (r2 <= 1) continue;
+        for (int m = 0; m < r2; ++m)
+            for (int j = 0; j < r1; ++j) {
+                const int64_t jm = ((int64_t)j * m) % n[d];
+                const double ang = 2.0 * 3.141592653589793238462643383279502884 * (double)jm / (double)n[d];
+                tw[(size_t)c->koff[d] + (size_t)(m * r1 + j)] = make_float2((float)cos(ang), (float)-sin(ang));
+            }
+    }
+    // mesh coordinates x = lo + (j (hi - lo)) / N
+    c->coord_host.resize((size_t)c->ksum);
+    for (int d = 0; d < ndim; ++d)
+        for (int64_t j = 0; j < n[d]; ++j)
+            c->coord_host[(size_t)(c->koff[d] + j)] = lo[d] + (double)j * (hi[d] - lo[d]) / (double)n[d];
+
+    cudaError_t e = cudaMemcpyAsync(c->work + L.tw, tw.data(), tw.size() * sizeof(float2),
+                                    cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->coord, c->coord_host.data(), c->coord_host.size() * sizeof(double),
+                            cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        delete c;
+        return QHD_ERR_CUDA;
+    }
+    c->inst_host.assign((size_t)batch, InstDev{});
+    *out = c;
+    return QHD_OK;
+}
+
+static qhd_status set_potential_common(qhd_ctx *c) {
+    const int64_t B = c->batch, G = c->g;
+    const int nb = c->L.mm_blocks;
+    QHD_LAUNCH(c, launch_minmax(c->f64, G, B, c->mm, nb, c->stream));
+    std::vector<MinMaxPart> part((size_t)(nb * B));
+    QHD_CUDA(c, cudaMemcpyAsync(part.data(), c->mm, part.size() * sizeof(MinMaxPart), cudaMemcpyDeviceToHost,
+                                c->stream));
+    QHD_CUDA(c, cudaStreamSynchronize(c->stream));
+    std::vector<InstDev> inst((size_t)B);
+    for (int64_t b = 0; b < B; ++b) {
+        double mn = INFINITY, mx = -INFINITY;
+        int64_t am = INT64_MAX, nf = 0;
+        for (int i = 0; i < nb; ++i) {
+            const MinMaxPart &p = part[(size_t)(b * nb + i)];
+            nf += p.nonfinite;
+            if (p.fmin < mn || (p.fmin == mn && p.argmin < am)) {
+                mn = p.fmin;
+                am = p.argmin;
+            }
+            if (p.fmax > mx) mx = p.fmax;
+        }
+        if (nf > 0) return fail(c, QHD_ERR_INVALID_ARG, "instance %lld: %lld non-finite f values", (long long)b,
+                                (long long)nf);
+        const double range = mx - mn;
+        if (!(range < 2147483648.0))
+            return fail(c, QHD_ERR_INVALID_ARG, "instance %lld: f range %g >= 2^31", (long long)b, range);
+        // largest power-of-two scale keeping (f - fmin) * 2^shift below 2^32 - 4096
+        int shift = 52;
+        if (range > 0.0) {
+            shift = (int)std::floor(std::log2((4294967296.0 - 4096.0) / range));
+            while (shift > 0 && std::ldexp(range, shift) >= 4294967296.0 - 4096.0) --shift;
+            if (shift > 52) shift = 52;
+        }
+        InstDev &ip = inst[(size_t)b];
+        ip.fmin = mn;
+        ip.shift = shift;
+        ip.pad_ = 0;
+        int64_t rem = am;
+        for (int d = 2; d >= 0; --d) ip.xs[d] = 0.0;
+        for (int d = c->ndim - 1; d >= 0; --d) {
+            const int64_t idx = rem % c->n[d];
+            rem /= c->n[d];
+            ip.xs[d] = c->coord_host[(size_t)(c->koff[d] + idx)];
+        }
+    }
+    QHD_CUDA(c, cudaMemcpyAsync(c->inst, inst.data(), inst.size() * sizeof(InstDev), cudaMemcpyHostToDevice,
+                                c->stream));
+    QHD_LAUNCH(c, launch_quantize(c->f64, c->fq, c->inst, G, B, c->stream));
+    QHD_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->inst_host = inst;
+    c->have_f = true;
+    return QHD_OK;
+}
+
+qhd_status qhd_set_potential(qhd_ctx *c, const double *f_host) {
+    qhd_status s = check_ctx(c);
+    if (s != QHD_OK) return s;
+    if (!f_host) return fail(c, QHD_ERR_INVALID_ARG, "f_host is NULL");
+    QHD_CUDA(c, cudaMemcpyAsync(c->f64, f_host, sizeof(double) * (size_t)(c->g * c->batch), cudaMemcpyHostToDevice,
+                                c->stream));
+    return set_potential_common(c);
+}
+
+qhd_status qhd_set_potential_device(qhd_ctx *c, const double *f_dev) {
+    qhd_status s = check_ctx(c);
+    if (s != QHD_OK) return s;
+    if (!f_dev) return fail(c, QHD_ERR_INVALID_ARG, "f_dev is NULL");
+    QHD_CUDA(c, cudaMemcpyAsync(c->f64, f_dev, sizeof(double) * (size_t)(c->g * c->batch), cudaMemcpyDeviceToDevice,
+                                c->stream));
+    return set_potential_common(c);
+}
+
+qhd_status qhd_set_schedule(qhd_ctx *c, const qhd_schedule *s) {
+    qhd_status st = check_ctx(c);
+    if (st != QHD_OK) return st;
+    if (!s) return fail(c, QHD_ERR_INVALID_ARG, "schedule is NULL");
+    const int64_t B = c->batch;
+    std::vector<SchedDev> dev((size_t)B);
+    std::vector<double> samples((size_t)(3 * MAX_TABLE_SAMPLES * B), 0.0);
+    for (int64_t b = 0; b < B; ++b) {
+        const qhd_schedule &q = s[b];
+        SchedDev &d = dev[(size_t)b];
+        d.kind = q.kind;
+        d.ns = 0;
+        d.c_phi = q.c_phi;
+        d.eps = q.eps;
+        d.c_chi = q.c_chi;
+        d.t = d.phi = d.chi = nullptr;
+        if (q.kind == QHD_SCHED_NESTEROV) {
+            if (!std::isfinite(q.c_phi) || !(q.c_phi > 0) || !std::isfinite(q.eps) || q.eps < 0 ||
+                !std::isfinite(q.c_chi) || q.c_chi < 0)
+                return fail(c, QHD_ERR_INVALID_ARG, "instance %lld: bad Nesterov schedule", (long long)b);
+        } else if (q.kind == QHD_SCHED_TABLE) {
+            if (!q.t || !q.phi || !q.chi || q.n_samples < 1 || q.n_samples > MAX_TABLE_SAMPLES)
+                return fail(c, QHD_ERR_INVALID_ARG, "instance %lld: bad table schedule", (long long)b);
+            for (int64_t i = 0; i < q.n_samples; ++i) {
+                if (!std::isfinite(q.t[i]) || !std::isfinite(q.phi[i]) || !std::isfinite(q.chi[i]))
+                    return fail(c, QHD_ERR_INVALID_ARG, "instance %lld: non-finite table sample", (long long)b);
+                if (i > 0 && !(q.t[i] > q.t[i - 1]))
+                    return fail(c, QHD_ERR_INVALID_ARG, "instance %lld: table times not increasing", (long long)b);
+            }
+            double *base = c->samples + (size_t)(3 * MAX_TABLE_SAMPLES * b);
+            d.ns = (int32_t)q.n_samples;
+            d.t = base;
+            d.phi = base + MAX_TABLE_SAMPLES;
+            d.chi = base + 2 * MAX_TABLE_SAMPLES;
+            double *hb = samples.data() + (size_t)(3 * MAX_TABLE_SAMPLES * b);
+            for (int64_t i = 0; i < q.n_samples; ++i) {
+                hb[i] = q.t[i];
+                hb[MAX_TABLE_SAMPLES + i] = q.phi[i];
+                hb[2 * MAX_TABLE_SAMPLES + i] = q.chi[i];
+            }
+        } else {
+            return fail(c, QHD_ERR_INVALID_ARG, "instance %lld: unknown schedule kind %d", (long long)b, q.kind);
+        }
+    }
+    QHD_CUDA(c, cudaMemcpyAsync(c->samples, samples.data(), samples.size() * sizeof(double), cudaMemcpyHostToDevice,
+                                c->stream));
+    QHD_CUDA(c, cudaMemcpyAsync(c->sched, dev.data(), dev.size() * sizeof(SchedDev), cudaMemcpyHostToDevice,
+                                c->stream));
+    // the host vectors die on return: wait for the copies
+    QHD_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->have_sched = true;
+    return QHD_OK;
+}
+
+qhd_status qhd_reset_state(qhd_ctx *c) {
+    qhd_status s = check_ctx(c);
+    if (s != QHD_OK) return s;
+    const float v = (float)(1.0 / std::sqrt((double)c->g));
+    QHD_LAUNCH(c, launch_uniform(c->psi, c->g * c->batch, v, c->stream));
+    c->t = 0.0;
+    c->steps_done = 0;
+    return QHD_OK;
+}
+
+qhd_status qhd_set_time(qhd_ctx *c, double t) {
+    qhd_status s = check_ctx(c);
+    if (s != QHD_OK) return s;
+    if (!std::isfinite(t)) return fail(c, QHD_ERR_INVALID_ARG, "time not finite");
+    c->t = t;
+    return QHD_OK;
+}
+
+qhd_status qhd_get_time(const qhd_ctx *c, double *t_out, int64_t *steps_out) {
+    if (!c) return QHD_ERR_INVALID_ARG;
+    if (t_out) *t_out = c->t;
+    if (steps_out) *steps_out = c->steps_done;
+    return QHD_OK;
+}
+
+qhd_status qhd_evolve(qhd_ctx *c, double T, double dt) {
+    qhd_status s = check_ctx(c);
+    if (s != QHD_OK) return s;
+    if (!std::isfinite(T) || !std::isfinite(dt) || dt == 0.0)
+        return fail(c, QHD_ERR_INVALID_ARG, "T and dt must be finite and dt nonzero");
+    const double ratio = T / dt;
+    const double nr = std::nearbyint(ratio);
+    if (!(nr >= 1.0) || std::fabs(ratio - nr) > 1e-9 * nr || nr > 1e12)
+        return fail(c, QHD_ERR_INVALID_ARG, "T/dt = %.17g is not a positive integer", ratio);
+    if (!c->have_f || !c->have_sched)
+        return fail(c, QHD_ERR_STATE, "evolve needs set_potential and set_schedule first");
+    const int64_t nsteps = (int64_t)nr;
+    const int ndim = c->ndim;
+    const int64_t B = c->batch;
+
+    PrepArgs pa{};
+    pa.sched = c->sched;
+    pa.inst = c->inst;
+    pa.pot = c->pot;
+    pa.kt = c->kt;
+    pa.t_start = c->t;
+    pa.dt = dt;
+    pa.nsteps = nsteps;
+    pa.batch = B;
+    pa.ndim = ndim;
+    for (int d = 0; d < 3; ++d) {
+        pa.n[d] = d < ndim ? (int)c->n[d] : 1;
+        pa.len[d] = d < ndim ? c->hi[d] - c->lo[d] : 1.0;
+        pa.koff[d] = d < ndim ? c->koff[d] : c->ksum;
+    }
+    pa.ksum = c->ksum;
+    pa.inv_g = 1.0 / (double)c->g;
+
+    const int64_t ch = c->L.chunk;
+    for (int64_t j0 = 0; j0 < nsteps; j0 += ch) {
+        const int64_t cnt = nsteps - j0 < ch ? nsteps - j0 : ch;
+        const bool last_chunk = j0 + cnt == nsteps;
+        pa.j0 = j0;
+        pa.cnt = cnt;
+        QHD_LAUNCH(c, launch_prep(pa, c->stream));
+        if (ndim == 1) {
+            OneDArgs o{};
+            o.psi = c->psi;
+            o.fq = c->fq;
+            o.pot = c->pot;
+            o.kt = c->kt;
+            o.tw2 = c->tw[0];
+            o.batch = B;
+            o.cnt = (int)cnt;
+            o.final_phase = last_chunk ? 1 : 0;
+            QHD_LAUNCH(c, launch_oned((int)c->n[0], o, c->stream));
+            continue;
+        }
+        const int last_ax = ndim - 1;
+        RowArgs r{};
+        r.psi = c->psi;
+        r.fq = c->fq;
+        r.tw2 = c->tw[last_ax];
+        r.rows = B * (c->g / c->n[last_ax]);
+        r.rows_per_inst = c->g / c->n[last_ax];
+        AxisArgs ax0{};
+        ax0.psi = c->psi;
+        ax0.tw2 = c->tw[0];
+        ax0.inner = c->g / c->n[0];
+        ax0.planes = B;
+        ax0.ksum = c->ksum;
+        ax0.koff1 = c->koff[1];
+        ax0.koff2 = ndim == 3 ? c->koff[2] : 0;
+        ax0.log_n2 = ndim == 3 ? (int)std::log2((double)c->n[2]) : 0;
+        ax0.ndim = ndim;
+        ax0.mode = MODE_FWD | MODE_KIN | MODE_INV;
+        AxisArgs ax1{};
+        if (ndim == 3) {
+            ax1.psi = c->psi;
+            ax1.tw2 = c->tw[1];
+            ax1.inner = c->n[2];
+            ax1.planes = B * c->n[0];
+            ax1.ndim = ndim;
+        }
+        for (int64_t jl = 0; jl < cnt; ++jl) {
+            const int64_t j = j0 + jl;
+            // row pass before step j: inverse transform of the previous step
+            // (if any), merged potential phase theta_j, forward transform
+            r.pot = c->pot + jl * B;
+            r.mode = (j == 0 ? 0 : MODE_INV) | MODE_FWD;
+            QHD_LAUNCH(c, launch_row((int)c->n[last_ax], r, c->stream));
+            if (ndim == 3) {
+                ax1.mode = MODE_FWD;
+                QHD_LAUNCH(c, launch_axis((int)c->n[1], ax1, c->stream));
+            }
+            ax0.kt = c->kt + jl * B * c->ksum;
+            QHD_LAUNCH(c, launch_axis((int)c->n[0], ax0, c->stream));
+            if (ndim == 3) {
+                ax1.mode = MODE_INV;
+                QHD_LAUNCH(c, launch_axis((int)c->n[1], ax1, c->stream));
+            }
+        }
+        if (last_chunk) {
+            r.pot = c->pot + cnt * B;
+            r.mode = MODE_INV;
+            QHD_LAUNCH(c, launch_row((int)c->n[last_ax], r, c->stream));
+        }
+    }
+    c->t = c->t + (double)nsteps * dt;
+    c->steps_done += nsteps;
+    return QHD_OK;
+}
+
+qhd_status qhd_observables(qhd_ctx *c, qhd_obs *out, float *prob_dev, double radius) {
+    qhd_status s = check_ctx(c);
+    if (s != QHD_OK) return s;
+    if (!out) return fail(c, QHD_ERR_INVALID_ARG, "out is NULL");
+    if (!std::isfinite(radius) || !(radius > 0)) return fail(c, QHD_ERR_INVALID_ARG, "radius must be > 0");
+    if (!c->have_f) return fail(c, QHD_ERR_STATE, "observables need set_potential first");
+    ObsArgs a{};
+    a.psi = c->psi;
+    a.f64 = c->f64;
+    a.inst = c->inst;
+    a.coord = c->coord;
+    a.prob = prob_dev;
+    a.partial = c->obs_part;
+    a.result = c->obs_res;
+    a.g = c->g;
+    a.ndim = c->ndim;
+    for (int d = 0; d < 3; ++d) {
+        a.n[d] = d < c->ndim ? (int)c->n[d] : 1;
+        a.log_n[d] = d < c->ndim ? (int)std::log2((double)c->n[d]) : 0;
+        a.coff[d] = d < c->ndim ? c->koff[d] : 0;
+    }
+    a.radius = radius;
+    a.nblk = c->L.obs_blocks;
+    cudaError_t e = launch_observables(a, c->batch, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "observables");
+    c->launches += 2;
+    std::vector<double> res((size_t)(3 * c->batch));
+    QHD_CUDA(c, cudaMemcpyAsync(res.data(), c->obs_res, res.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                                c->stream));
+    QHD_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (int64_t b = 0; b < c->batch; ++b) {
+        qhd_obs &o = out[b];
+        o.t = c->t;
+        o.norm = res[(size_t)(3 * b)];
+        o.e_f = res[(size_t)(3 * b + 1)];
+        o.p_succ = res[(size_t)(3 * b + 2)];
+        for (int d = 0; d < 3; ++d) o.x_star[d] = c->inst_host[(size_t)b].xs[d];
+        o.steps_done = c->steps_done;
+    }
+    return QHD_OK;
+}
+
+qhd_status qhd_destroy(qhd_ctx *c) {
+    if (!c) return QHD_OK;
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    delete c;
+    return e == cudaSuccess ? QHD_OK : QHD_ERR_CUDA;
+}
+
+}  // extern "C"

@@ -1,0 +1,260 @@
+"""Thin Python binding of the C ABI in include/qhd.h.
+
+Argument marshalling only: every step of the simulation runs in the CUDA
+kernels of libqhd.so.  PyTorch provides the device memory (psi and the
+workspace) and the stream.  There is no CPU fallback: if the library or a
+CUDA device is missing, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+from . import build as _build
+
+QHD_OK = 0
+STATUS = {0: "QHD_OK", 1: "QHD_ERR_INVALID_ARG", 2: "QHD_ERR_UNSUPPORTED", 3: "QHD_ERR_STATE",
+          4: "QHD_ERR_CUDA", 5: "QHD_ERR_TIMEOUT", 6: "QHD_ERR_WORKSPACE"}
+SCHED_NESTEROV = 0
+SCHED_TABLE = 1
+
+# Every entry point declared in include/qhd.h.
+EXPORTS = ["qhd_workspace_bytes", "qhd_init_grid", "qhd_set_potential", "qhd_set_potential_device",
+           "qhd_set_schedule", "qhd_reset_state", "qhd_set_time", "qhd_get_time", "qhd_evolve",
+           "qhd_observables", "qhd_launch_count", "qhd_destroy", "qhd_status_string",
+           "qhd_last_error"]
+
+
+class QHDError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Schedule(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("c_phi", ctypes.c_double), ("eps", ctypes.c_double),
+                ("c_chi", ctypes.c_double), ("t", ctypes.POINTER(ctypes.c_double)),
+                ("phi", ctypes.POINTER(ctypes.c_double)), ("chi", ctypes.POINTER(ctypes.c_double)),
+                ("n_samples", ctypes.c_int64)]
+
+
+class _Obs(ctypes.Structure):
+    _fields_ = [("t", ctypes.c_double), ("norm", ctypes.c_double), ("e_f", ctypes.c_double),
+                ("p_succ", ctypes.c_double), ("x_star", ctypes.c_double * 3),
+                ("steps_done", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libqhd.so (building it with nvcc first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError(f"libqhd.so not built ({_build.LIB}); run paper_2303_01471_gb300.build")
+    lib = ctypes.CDLL(_build.LIB)
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    dp = ctypes.POINTER(ctypes.c_double)
+    vp = ctypes.c_void_p
+    st = ctypes.c_int
+    lib.qhd_workspace_bytes.argtypes = [ctypes.c_int, i64p, ctypes.c_int64]
+    lib.qhd_workspace_bytes.restype = ctypes.c_size_t
+    lib.qhd_init_grid.argtypes = [ctypes.POINTER(vp), ctypes.c_int, i64p, dp, dp, ctypes.c_int64,
+                                  vp, vp, ctypes.c_size_t, vp]
+    lib.qhd_init_grid.restype = st
+    lib.qhd_set_potential.argtypes = [vp, dp]
+    lib.qhd_set_potential.restype = st
+    lib.qhd_set_potential_device.argtypes = [vp, vp]
+    lib.qhd_set_potential_device.restype = st
+    lib.qhd_set_schedule.argtypes = [vp, ctypes.POINTER(_Schedule)]
+    lib.qhd_set_schedule.restype = st
+    lib.qhd_reset_state.argtypes = [vp]
+    lib.qhd_reset_state.restype = st
+    lib.qhd_set_time.argtypes = [vp, ctypes.c_double]
+    lib.qhd_set_time.restype = st
+    lib.qhd_get_time.argtypes = [vp, dp, i64p]
+    lib.qhd_get_time.restype = st
+    lib.qhd_evolve.argtypes = [vp, ctypes.c_double, ctypes.c_double]
+    lib.qhd_evolve.restype = st
+    lib.qhd_observables.argtypes = [vp, ctypes.POINTER(_Obs), vp, ctypes.c_double]
+    lib.qhd_observables.restype = st
+    lib.qhd_launch_count.argtypes = [vp]
+    lib.qhd_launch_count.restype = ctypes.c_int64
+    lib.qhd_destroy.argtypes = [vp]
+    lib.qhd_destroy.restype = st
+    lib.qhd_status_string.argtypes = [st]
+    lib.qhd_status_string.restype = ctypes.c_char_p
+    lib.qhd_last_error.argtypes = [vp]
+    lib.qhd_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+@dataclass
+class Schedule:
+    """Damping schedule of one instance (see QHD_SCHED_* in include/qhd.h)."""
+    kind: int = SCHED_NESTEROV
+    c_phi: float = 2.0
+    eps: float = 1e-3
+    c_chi: float = 2.0
+    ts: Optional[np.ndarray] = None
+    phis: Optional[np.ndarray] = None
+    chis: Optional[np.ndarray] = None
+
+
+@dataclass
+class Observables:
+    t: float
+    norm: float
+    e_f: float
+    p_succ: float
+    x_star: tuple
+    steps_done: int
+
+
+def workspace_bytes(shape: Sequence[int], batch: int = 1) -> int:
+    lib = load()
+    n = (ctypes.c_int64 * len(shape))(*shape)
+    return int(lib.qhd_workspace_bytes(len(shape), n, int(batch)))
+
+
+class QHD:
+    """One simulation context: a mesh, `batch` instances, psi and workspace on the GPU.
+
+    psi is a torch complex64 tensor of shape (batch, *shape) owned by this
+    object (the library only borrows it); the workspace is a uint8 tensor.
+    All calls run on `stream` (default: torch's current stream at creation).
+    """
+
+    def __init__(self, shape: Sequence[int], lo=0.0, hi=1.0, batch: int = 1, device=None,
+                 stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("QHD needs a CUDA device; there is no CPU fallback")
+        self.lib = load()
+        self.shape = tuple(int(n) for n in shape)
+        self.ndim = len(self.shape)
+        self.batch = int(batch)
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.lo = np.broadcast_to(np.asarray(lo, dtype=np.float64), (self.ndim,)).copy()
+        self.hi = np.broadcast_to(np.asarray(hi, dtype=np.float64), (self.ndim,)).copy()
+        n = (ctypes.c_int64 * self.ndim)(*self.shape)
+        ws = int(self.lib.qhd_workspace_bytes(self.ndim, n, self.batch))
+        if ws == 0:
+            raise QHDError(1, f"unsupported grid {self.shape} x batch {self.batch}")
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            self.psi = torch.zeros((self.batch, *self.shape), dtype=torch.complex64, device=self.device)
+            self._work_raw = torch.empty(ws + 256, dtype=torch.uint8, device=self.device)
+        addr = self._work_raw.data_ptr()
+        off = (-addr) % 256
+        self.work_ptr = addr + off
+        self.work_bytes = ws
+        ctx = ctypes.c_void_p()
+        lo_c = (ctypes.c_double * self.ndim)(*self.lo)
+        hi_c = (ctypes.c_double * self.ndim)(*self.hi)
+        st = self.lib.qhd_init_grid(ctypes.byref(ctx), self.ndim, n, lo_c, hi_c, self.batch,
+                                    ctypes.c_void_p(self.psi.data_ptr()), ctypes.c_void_p(self.work_ptr),
+                                    ctypes.c_size_t(ws), ctypes.c_void_p(self.stream.cuda_stream))
+        if st != QHD_OK:
+            raise QHDError(st, "qhd_init_grid failed")
+        self.ctx = ctx
+
+    # -- helpers
+    def _check(self, st: int, what: str):
+        if st != QHD_OK:
+            msg = self.lib.qhd_last_error(self.ctx)
+            raise QHDError(st, f"{what}: {msg.decode() if msg else ''}")
+
+    @property
+    def grid_points(self) -> int:
+        return int(np.prod(self.shape))
+
+    # -- API
+    def set_potential(self, f) -> None:
+        """f: numpy FP64 host array (batch, *shape) or (*shape) for batch 1, or a
+        torch float64 CUDA tensor of the same size (device path)."""
+        import torch
+        if isinstance(f, torch.Tensor) and f.is_cuda:
+            ff = f.contiguous()
+            if ff.dtype != torch.float64 or ff.numel() != self.batch * self.grid_points:
+                raise ValueError("device f must be float64 with batch*G values")
+            self._check(self.lib.qhd_set_potential_device(self.ctx, ctypes.c_void_p(ff.data_ptr())),
+                        "qhd_set_potential_device")
+            return
+        arr = np.ascontiguousarray(np.asarray(f, dtype=np.float64))
+        if arr.size != self.batch * self.grid_points:
+            raise ValueError(f"f has {arr.size} values, expected {self.batch * self.grid_points}")
+        self._check(self.lib.qhd_set_potential(self.ctx, arr.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+                    "qhd_set_potential")
+
+    def set_schedule(self, sched) -> None:
+        scheds: List[Schedule] = list(sched) if isinstance(sched, (list, tuple)) else [sched] * self.batch
+        if len(scheds) != self.batch:
+            raise ValueError("one schedule per instance")
+        arr = (_Schedule * self.batch)()
+        keep = []
+        for i, s in enumerate(scheds):
+            arr[i].kind = s.kind
+            arr[i].c_phi = s.c_phi
+            arr[i].eps = s.eps
+            arr[i].c_chi = s.c_chi
+            if s.kind == SCHED_TABLE:
+                t = np.ascontiguousarray(s.ts, dtype=np.float64)
+                p = np.ascontiguousarray(s.phis, dtype=np.float64)
+                c = np.ascontiguousarray(s.chis, dtype=np.float64)
+                keep += [t, p, c]
+                dp = ctypes.POINTER(ctypes.c_double)
+                arr[i].t = t.ctypes.data_as(dp)
+                arr[i].phi = p.ctypes.data_as(dp)
+                arr[i].chi = c.ctypes.data_as(dp)
+                arr[i].n_samples = len(t)
+        self._check(self.lib.qhd_set_schedule(self.ctx, arr), "qhd_set_schedule")
+
+    def reset_state(self) -> None:
+        self._check(self.lib.qhd_reset_state(self.ctx), "qhd_reset_state")
+
+    def set_time(self, t: float) -> None:
+        self._check(self.lib.qhd_set_time(self.ctx, float(t)), "qhd_set_time")
+
+    def time(self):
+        t = ctypes.c_double()
+        s = ctypes.c_int64()
+        self._check(self.lib.qhd_get_time(self.ctx, ctypes.byref(t), ctypes.byref(s)), "qhd_get_time")
+        return t.value, s.value
+
+    def evolve(self, T: float, dt: float) -> None:
+        self._check(self.lib.qhd_evolve(self.ctx, float(T), float(dt)), "qhd_evolve")
+
+    def observables(self, radius: float = 0.1, prob=None) -> List[Observables]:
+        """prob: optional torch float32 CUDA tensor with batch*G values receiving |psi|^2."""
+        out = (_Obs * self.batch)()
+        pp = ctypes.c_void_p(prob.data_ptr()) if prob is not None else ctypes.c_void_p()
+        self._check(self.lib.qhd_observables(self.ctx, out, pp, float(radius)), "qhd_observables")
+        return [Observables(o.t, o.norm, o.e_f, o.p_succ, tuple(o.x_star), o.steps_done) for o in out]
+
+    def launch_count(self) -> int:
+        return int(self.lib.qhd_launch_count(self.ctx))
+
+    def close(self) -> None:
+        if getattr(self, "ctx", None):
+            self.lib.qhd_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

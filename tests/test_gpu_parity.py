@@ -1,0 +1,244 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (FP32 GPU vs FP64 oracle):
+  TV(|psi|^2) = 1/2 sum |p_gpu - p_oracle| <= 1e-4
+  |E[f]_gpu - E[f]_oracle| / max(|E[f]_oracle|, 1e-3 (max f - min f)) <= 1e-5
+  |sum p_gpu - 1| <= 1e-6
+and, on short runs where both trajectories are still close, element-wise
+|psi_gpu - psi_oracle| <= 2e-5 * max|psi_oracle| * sqrt(steps + 1).
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle
+import workloads
+from paper_2303_01471_gb300 import qhd
+
+TV_TOL = 1e-4
+EF_TOL = 1e-5
+NORM_TOL = 1e-6
+
+
+def to_oracle_sched(s: qhd.Schedule) -> oracle.Schedule:
+    return oracle.Schedule(kind=s.kind, c_phi=s.c_phi, eps=s.eps, c_chi=s.c_chi,
+                           ts=s.ts, phis=s.phis, chis=s.chis)
+
+
+def run_gpu(f, sched, T, dt, lo=0.0, hi=1.0, batch_f=None, t0=None, psi0=None):
+    shape = f.shape if batch_f is None else batch_f.shape[1:]
+    batch = 1 if batch_f is None else batch_f.shape[0]
+    sim = qhd.QHD(shape, lo=lo, hi=hi, batch=batch)
+    sim.set_potential(f if batch_f is None else batch_f)
+    sim.set_schedule(sched)
+    sim.reset_state()
+    if psi0 is not None:
+        sim.psi.copy_(torch.from_numpy(psi0.astype(np.complex64)).reshape(sim.psi.shape))
+    if t0 is not None:
+        sim.set_time(t0)
+    sim.evolve(T, dt)
+    obs = sim.observables(0.1)
+    psi = sim.psi.cpu().numpy().astype(np.complex128)
+    sim.close()
+    return psi, obs
+
+
+def compare(psi_g, obs_g, f, psi_o, lo=0.0, hi=1.0, steps=None, elementwise=True):
+    p_g = np.abs(psi_g) ** 2
+    ob_o = oracle.observables(f, psi_o, 0.1, lo=lo, hi=hi)
+    p_o = ob_o.prob
+    tv = 0.5 * np.abs(p_g - p_o).sum()
+    scale = max(abs(ob_o.e_f), 1e-3 * (f.max() - f.min()))
+    ef_err = abs(obs_g.e_f - ob_o.e_f) / scale
+    assert tv <= TV_TOL, f"TV {tv:.3e}"
+    assert ef_err <= EF_TOL, f"E[f] rel err {ef_err:.3e}"
+    assert abs(obs_g.norm - 1.0) <= NORM_TOL, f"norm drift {obs_g.norm - 1:.3e}"
+    assert abs(obs_g.p_succ - ob_o.p_succ) <= 2 * TV_TOL
+    assert np.allclose(obs_g.x_star[: f.ndim], ob_o.x_star[: f.ndim], rtol=0, atol=0)
+    if elementwise and steps is not None:
+        err = np.max(np.abs(psi_g - psi_o))
+        assert err <= 2e-5 * np.abs(psi_o).max() * math.sqrt(steps + 1), f"max |dpsi| {err:.3e}"
+    return tv, ef_err
+
+
+# ------------------------------------------------- every line length, 1..3-D
+
+SHAPES = [(2,), (4,), (8,), (16,), (32,), (64,), (128,), (256,), (512,), (1024,),
+          (2, 2), (4, 8), (8, 4), (16, 16), (32, 64), (64, 32), (128, 128), (256, 16),
+          (16, 512), (1024, 4), (4, 1024), (2, 1024),
+          (2, 2, 2), (4, 8, 16), (16, 8, 4), (32, 32, 32), (8, 64, 2), (2, 4, 256), (64, 16, 128)]
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "x".join(map(str, s)))
+def test_parity_short_runs_all_shapes(shape):
+    inst = workloads.gaussian_wells(11, shape, K=4)
+    sched = qhd.Schedule()
+    dt, n = 0.01, 25
+    psi_g, obs = run_gpu(inst.f, sched, n * dt, dt)
+    psi_o = oracle.evolve(inst.f, oracle.uniform_state(shape), 0.0, dt, n, to_oracle_sched(sched))
+    compare(psi_g, obs[0], inst.f, psi_o, steps=n)
+
+
+def test_parity_nonunit_box_and_table_schedule():
+    shape = (64, 32)
+    lo, hi = (-2.0, -1.0), (3.0, 1.5)
+    inst = workloads.rastrigin(3, shape, lo=0.0, hi=1.0)
+    ts = np.array([0.0, 0.3, 0.9, 2.0])
+    sched = qhd.Schedule(kind=qhd.SCHED_TABLE, ts=ts, phis=np.array([2.0, 1.0, 0.0, -1.0]),
+                         chis=np.array([-1.0, 0.0, 1.5, 2.0]))
+    dt, n = 0.005, 200
+    psi_g, obs = run_gpu(inst.f, sched, n * dt, dt, lo=lo, hi=hi)
+    psi_o = oracle.evolve(inst.f, oracle.uniform_state(shape), 0.0, dt, n, to_oracle_sched(sched),
+                          lo=np.array(lo), hi=np.array(hi))
+    compare(psi_g, obs[0], inst.f, psi_o, lo=np.array(lo), hi=np.array(hi), steps=n)
+
+
+def test_parity_batch_with_own_f_and_schedule():
+    shape = (32, 32)
+    insts = [workloads.make(fam, s, shape, draw_sigma=True)
+             for fam, s in [("wells", 1), ("rastrigin", 2), ("wells", 3)]]
+    fb = np.stack([i.f for i in insts])
+    scheds = [qhd.Schedule(c_chi=2.0 * i.sigma) for i in insts]
+    dt, n = 0.01, 100
+    psi_g, obs = run_gpu(None, scheds, n * dt, dt, batch_f=fb)
+    for b, inst in enumerate(insts):
+        psi_o = oracle.evolve(inst.f, oracle.uniform_state(shape), 0.0, dt, n, to_oracle_sched(scheds[b]))
+        compare(psi_g[b], obs[b], inst.f, psi_o, steps=n)
+
+
+# --------------------------------------------- configuration: 128^2, 1000 steps
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_parity_128sq_wells_1000_steps(seed):
+    """Plain QHD: 128x128 on [0,1]^2, K=8 wells, T=10, dt=0.01, the paper's schedule."""
+    inst = workloads.gaussian_wells(seed, (128, 128), K=8)
+    sched = qhd.Schedule()
+    psi_g, obs = run_gpu(inst.f, sched, 10.0, 0.01)
+    psi_o = oracle.evolve(inst.f, oracle.uniform_state((128, 128)), 0.0, 0.01, 1000, to_oracle_sched(sched))
+    compare(psi_g, obs[0], inst.f, psi_o, elementwise=False)
+
+
+# ------------------------------------------------------- invariants on the GPU
+
+def test_gpu_time_reversal():
+    inst = workloads.gaussian_wells(5, (64, 64), K=8)
+    sim = qhd.QHD((64, 64))
+    sim.set_potential(inst.f)
+    sim.set_schedule(qhd.Schedule())
+    sim.reset_state()
+    sim.set_time(1.0)
+    psi0 = sim.psi.clone()
+    sim.evolve(1.0, 0.01)
+    moved = (sim.psi - psi0).abs().max().item()
+    sim.evolve(-1.0, -0.01)
+    back = (sim.psi - psi0).abs().max().item()
+    t, steps = sim.time()
+    sim.close()
+    assert moved > 1e-3
+    assert back <= 1e-5 * psi0.abs().max().item() * 10
+    assert t == pytest.approx(1.0, abs=1e-12) and steps == 200
+
+
+def test_gpu_mirror_symmetry():
+    shape = (128, 64)
+    X, Y = np.meshgrid(*workloads.mesh_axes(shape), indexing="ij")
+    f = 0.5 * ((X - 0.5) ** 2 + (Y - 0.5) ** 2) - 1.2 * np.exp(-((X - 0.5) ** 2) / 0.02)
+    psi_g, _ = run_gpu(f, qhd.Schedule(), 3.0, 0.01)
+    p = np.abs(psi_g) ** 2
+    mirrored = p[(-np.arange(shape[0])) % shape[0]][:, (-np.arange(shape[1])) % shape[1]]
+    assert np.max(np.abs(p - mirrored)) <= 1e-6 * p.max()
+
+
+def test_split_evolve_matches_single_call():
+    inst = workloads.gaussian_wells(8, (64, 64), K=8)
+    a, _ = run_gpu(inst.f, qhd.Schedule(), 2.0, 0.01)
+    sim = qhd.QHD((64, 64))
+    sim.set_potential(inst.f)
+    sim.set_schedule(qhd.Schedule())
+    sim.reset_state()
+    sim.evolve(0.7, 0.01)
+    sim.evolve(1.3, 0.01)
+    b = sim.psi.cpu().numpy().astype(np.complex128)
+    sim.close()
+    assert np.max(np.abs(a - b)) <= 1e-5 * np.abs(a).max()
+
+
+def test_device_potential_matches_host_potential():
+    inst = workloads.rastrigin(4, (128, 64))
+    a, oa = run_gpu(inst.f, qhd.Schedule(), 1.0, 0.01)
+    sim = qhd.QHD((128, 64))
+    sim.set_potential(torch.from_numpy(inst.f).cuda())
+    sim.set_schedule(qhd.Schedule())
+    sim.reset_state()
+    sim.evolve(1.0, 0.01)
+    ob = sim.observables(0.1)[0]
+    b = sim.psi.cpu().numpy().astype(np.complex128)
+    sim.close()
+    assert np.array_equal(a, b)
+    assert ob.e_f == oa[0].e_f
+
+
+def test_observables_kernel_on_gpu_state():
+    """E[f], P_succ and |psi|^2 of the observable kernel vs the oracle's
+    observables evaluated on the same (GPU) state."""
+    inst = workloads.gaussian_wells(6, (64, 128), K=8)
+    sim = qhd.QHD((64, 128))
+    sim.set_potential(inst.f)
+    sim.set_schedule(qhd.Schedule())
+    sim.reset_state()
+    sim.evolve(5.0, 0.01)
+    prob = torch.empty(64 * 128, dtype=torch.float32, device="cuda")
+    ob = sim.observables(0.1, prob=prob)[0]
+    psi = sim.psi.cpu().numpy().astype(np.complex128)[0]
+    sim.close()
+    ref = oracle.observables(inst.f, psi, 0.1)
+    assert ob.norm == pytest.approx(ref.norm, rel=1e-12)
+    assert ob.e_f == pytest.approx(ref.e_f, rel=1e-12)
+    assert ob.p_succ == pytest.approx(ref.p_succ, rel=1e-12, abs=1e-15)
+    assert tuple(ob.x_star[:2]) == tuple(ref.x_star[:2])
+    assert np.allclose(prob.cpu().numpy().reshape(64, 128), ref.prob, rtol=1e-6, atol=0)
+
+
+# --------------------------------------------------------------- error paths
+
+def test_error_paths():
+    sim = qhd.QHD((16, 16))
+    with pytest.raises(qhd.QHDError) as e:
+        sim.evolve(1.0, 0.1)
+    assert e.value.status == 3
+    f = np.zeros((16, 16))
+    f[3, 3] = np.nan
+    with pytest.raises(qhd.QHDError) as e:
+        sim.set_potential(f)
+    assert e.value.status == 1
+    sim.set_potential(np.zeros((16, 16)))
+    sim.set_schedule(qhd.Schedule())
+    sim.reset_state()
+    for T, dt in [(1.0, 0.3), (1.0, 0.0), (-1.0, 0.1), (float("nan"), 0.1)]:
+        with pytest.raises(qhd.QHDError) as e:
+            sim.evolve(T, dt)
+        assert e.value.status == 1
+    with pytest.raises(qhd.QHDError):
+        sim.set_schedule(qhd.Schedule(c_phi=-1.0))
+    with pytest.raises(qhd.QHDError):
+        sim.set_schedule(qhd.Schedule(kind=qhd.SCHED_TABLE, ts=np.array([1.0, 0.5]),
+                                      phis=np.zeros(2), chis=np.zeros(2)))
+    # the context is still usable after argument errors
+    sim.evolve(0.5, 0.1)
+    assert sim.observables(0.1)[0].norm == pytest.approx(1.0, abs=1e-6)
+    sim.close()
+
+
+def test_launch_count_accounting():
+    sim = qhd.QHD((64, 64))
+    sim.set_potential(np.zeros((64, 64)))
+    sim.set_schedule(qhd.Schedule())
+    sim.reset_state()
+    before = sim.launch_count()
+    sim.evolve(0.1, 0.01)   # 10 steps: 1 prep + 11 row + 10 axis launches
+    assert sim.launch_count() - before == 1 + 11 + 10
+    sim.close()
