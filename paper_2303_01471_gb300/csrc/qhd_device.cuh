@@ -58,8 +58,25 @@ __host__ __device__ constexpr double cos64(int k) {
 }
 __host__ __device__ constexpr double sin64(int k) { return cos64(k - 16); }
 
+// v * (hi + lo) for a twiddle carried as an FP32 pair: hi is the rounded
+// value, lo the rounding residual.  The residual product is formed first and
+// folded into the two FMAs of the leading product, so the twiddle enters with
+// ~2^-48 relative precision and only the product itself is rounded.  A plain
+// FP32 twiddle would perturb the transform by the same ~2^-24 every step, an
+// error that accumulates coherently over thousands of steps.
+__device__ __forceinline__ float2 cmul_comp(float2 v, float2 hi, float2 lo) {
+    const float cre = v.x * lo.x - v.y * lo.y;
+    const float cim = v.x * lo.y + v.y * lo.x;
+    return make_float2(fmaf(v.x, hi.x, fmaf(-v.y, hi.y, cre)), fmaf(v.x, hi.y, fmaf(v.y, hi.x, cim)));
+}
+// v * conj(hi + lo)
+__device__ __forceinline__ float2 cmulc_comp(float2 v, float2 hi, float2 lo) {
+    return cmul_comp(v, make_float2(hi.x, -hi.y), make_float2(lo.x, -lo.y));
+}
+
 // v * W_R^k with W_R = exp(-2 pi i / R) (forward) or its conjugate (inverse);
-// k is a compile-time constant after unrolling, so the trivial cases fold.
+// k is a compile-time constant after unrolling, so the trivial cases fold and
+// the hi/lo split of the constant is evaluated by the compiler.
 template <int R, bool INV>
 __device__ __forceinline__ float2 twiddle_const(float2 v, int k) {
     static_assert(64 % R == 0, "in-register DFT sizes up to 64");
@@ -67,9 +84,11 @@ __device__ __forceinline__ float2 twiddle_const(float2 v, int k) {
     if (4 * k == R) return mul_mi<INV>(v);
     if (2 * k == R) return make_float2(-v.x, -v.y);
     if (4 * k == 3 * R) return mul_mi<!INV>(v);
-    const float c = (float)cos64(k * (64 / R));
-    const float s = INV ? (float)sin64(k * (64 / R)) : -(float)sin64(k * (64 / R));
-    return make_float2(v.x * c - v.y * s, v.x * s + v.y * c);
+    const double cd = cos64(k * (64 / R));
+    const double sd = INV ? sin64(k * (64 / R)) : -sin64(k * (64 / R));
+    const float ch = (float)cd, sh = (float)sd;
+    const float cl = (float)(cd - (double)ch), sl = (float)(sd - (double)sh);
+    return cmul_comp(v, make_float2(ch, sh), make_float2(cl, sl));
 }
 
 // -------------------------------------------------------- in-register DFT
@@ -210,10 +229,10 @@ __host__ __device__ constexpr int line_stride(bool rowmajor, int W) {
 // ------------------------------------------------------------ line FFT
 // x[e] holds line element t + T*e on entry and transform element t + T*e on
 // exit.  sm: this line's shared buffer (stride-padded), tw2: stage-2 twiddles
-// tw2[m*R1 + j] = exp(-2 pi i j m / N).  SYNC() orders the exchange among
+// tw2[m*R1 + j] = exp(-2 pi i j m / N) as (hi.re, hi.im, lo.re, lo.im).  SYNC() orders the exchange among
 // the T threads of the line (a warp barrier when a line lives in one warp).
 template <int N, bool INV, typename Sync>
-__device__ __forceinline__ void line_fft(float2 *x, float2 *sm, int t, const float2 *__restrict__ tw2,
+__device__ __forceinline__ void line_fft(float2 *x, float2 *sm, int t, const float4 *__restrict__ tw2,
                                          Sync sync) {
     using C = LineCfg<N>;
     if constexpr (!C::TWO_STAGE) {
@@ -239,8 +258,9 @@ __device__ __forceinline__ void line_fft(float2 *x, float2 *sm, int t, const flo
             for (int m = 0; m < R2; ++m) v[m] = sm[pad_index(j + m * R1, C::LOG_R1)];
 #pragma unroll
             for (int m = 1; m < R2; ++m) {
-                const float2 w = __ldg(&tw2[m * R1 + j]);
-                v[m] = INV ? cmulc(v[m], w) : cmul(v[m], w);
+                const float4 w = __ldg(&tw2[m * R1 + j]);
+                const float2 hi = make_float2(w.x, w.y), lo = make_float2(w.z, w.w);
+                v[m] = INV ? cmulc_comp(v[m], hi, lo) : cmul_comp(v[m], hi, lo);
             }
             dft<R2, INV>(v);
 #pragma unroll

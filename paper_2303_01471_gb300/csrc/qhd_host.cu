@@ -78,7 +78,7 @@ Layout make_layout(int ndim, const int64_t *n, int64_t batch) {
     L.sched = take(sizeof(SchedDev) * (size_t)batch);
     L.samples = take(sizeof(double) * 3 * MAX_TABLE_SAMPLES * (size_t)batch);
     L.inst = take(sizeof(InstDev) * (size_t)batch);
-    L.tw = take(sizeof(float2) * (size_t)(ksum));
+    L.tw = take(sizeof(float4) * (size_t)(ksum));
     L.coord = take(sizeof(double) * (size_t)ksum);
     L.obs_part = take(sizeof(double) * 3 * (size_t)L.obs_blocks * (size_t)batch);
     L.obs_res = take(sizeof(double) * 3 * (size_t)batch);
@@ -86,11 +86,6 @@ Layout make_layout(int ndim, const int64_t *n, int64_t batch) {
     L.total = off;
     return L;
 }
-
-struct SchedHost {
-    qhd_schedule s{};
-    std::vector<double> t, phi, chi;
-};
 
 }  // namespace
 
@@ -113,7 +108,7 @@ struct qhd_ctx {
     SchedDev *sched = nullptr;
     double *samples = nullptr;
     InstDev *inst = nullptr;
-    float2 *tw[3] = {nullptr, nullptr, nullptr};
+    float4 *tw[3] = {nullptr, nullptr, nullptr};
     double *coord = nullptr;
     double *obs_part = nullptr, *obs_res = nullptr;
     MinMaxPart *mm = nullptr;
@@ -233,18 +228,22 @@ qhd_status qhd_init_grid(qhd_ctx **out, int ndim, const int64_t *n, const double
     c->obs_res = (double *)(c->work + L.obs_res);
     c->mm = (MinMaxPart *)(c->work + L.mm);
 
-    // stage-2 twiddles per axis, tw2[m*R1 + j] = exp(-2 pi i j m / N) from FP64
-    std::vector<float2> tw((size_t)c->ksum, make_float2(0.f, 0.f));
+    // stage-2 twiddles per axis, tw2[m*R1 + j] = exp(-2 pi i j m / N) from FP64,
+    // stored as the FP32 value and its FP32 rounding residual
+    std::vector<float4> tw((size_t)c->ksum, make_float4(0.f, 0.f, 0.f, 0.f));
     for (int d = 0; d < ndim; ++d) {
         int r1 = 0, r2 = 0;
         plan_of((int)n[d], &r1, &r2);
-        c->tw[d] = (float2 *)(c->work + L.tw) + c->koff[d];
+        c->tw[d] = (float4 *)(c->work + L.tw) + c->koff[d];
         if (r2 <= 1) continue;
         for (int m = 0; m < r2; ++m)
             for (int j = 0; j < r1; ++j) {
                 const int64_t jm = ((int64_t)j * m) % n[d];
                 const double ang = 2.0 * 3.141592653589793238462643383279502884 * (double)jm / (double)n[d];
-                tw[(size_t)c->koff[d] + (size_t)(m * r1 + j)] = make_float2((float)cos(ang), (float)-sin(ang));
+                const double cr = cos(ang), ci = -sin(ang);
+                const float hr = (float)cr, hi = (float)ci;
+                tw[(size_t)c->koff[d] + (size_t)(m * r1 + j)] =
+                    make_float4(hr, hi, (float)(cr - (double)hr), (float)(ci - (double)hi));
             }
     }
     // mesh coordinates x = lo + (j (hi - lo)) / N
@@ -253,7 +252,7 @@ qhd_status qhd_init_grid(qhd_ctx **out, int ndim, const int64_t *n, const double
         for (int64_t j = 0; j < n[d]; ++j)
             c->coord_host[(size_t)(c->koff[d] + j)] = lo[d] + (double)j * (hi[d] - lo[d]) / (double)n[d];
 
-    cudaError_t e = cudaMemcpyAsync(c->work + L.tw, tw.data(), tw.size() * sizeof(float2),
+    cudaError_t e = cudaMemcpyAsync(c->work + L.tw, tw.data(), tw.size() * sizeof(float4),
                                     cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(c->coord, c->coord_host.data(), c->coord_host.size() * sizeof(double),

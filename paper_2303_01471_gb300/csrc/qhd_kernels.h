@@ -36,7 +36,7 @@ struct RowArgs {
     float2 *psi;
     const uint32_t *fq;
     const uint64_t *pot;   // potential coefficient of this pass, one per instance
-    const float2 *tw2;
+    const float4 *tw2;
     int64_t rows;          // batch * rows per instance
     int64_t rows_per_inst;
     int mode;              // MODE_INV: inverse FFT before the phase; MODE_FWD: forward after
@@ -44,7 +44,7 @@ struct RowArgs {
 
 struct AxisArgs {
     float2 *psi;
-    const float2 *tw2;
+    const float4 *tw2;
     const float2 *kt;      // kinetic tables of this step: [batch][ksum] (MODE_KIN only)
     int64_t inner;         // product of the axis lengths after this axis (line stride)
     int64_t planes;        // product of batch and the axis lengths before this axis
@@ -60,7 +60,7 @@ struct OneDArgs {
     const uint32_t *fq;
     const uint64_t *pot;   // chunk potential coefficients [cnt+1][batch]
     const float2 *kt;      // chunk kinetic tables [cnt][batch][n]
-    const float2 *tw2;
+    const float4 *tw2;
     int64_t batch;
     int cnt;
     int final_phase;       // apply pot[cnt] after the last step

@@ -5,7 +5,10 @@ Tolerances (FP32 GPU vs FP64 oracle):
   |E[f]_gpu - E[f]_oracle| / max(|E[f]_oracle|, 1e-3 (max f - min f)) <= 1e-5
   |sum p_gpu - 1| <= 1e-6
 and, on short runs where both trajectories are still close, element-wise
-|psi_gpu - psi_oracle| <= 2e-5 * max|psi_oracle| * sqrt(steps + 1).
+|psi_gpu e^{-i g} - psi_oracle| <= 2e-5 * max|psi_oracle| * sqrt(steps + 1),
+where g is the one global phase that best aligns the two states.  The GPU
+path stores f - min f in fixed point, so its psi carries the unobservable
+global phase exp(i min f sum_j theta_j) relative to the oracle.
 """
 import math
 
@@ -47,7 +50,13 @@ def run_gpu(f, sched, T, dt, lo=0.0, hi=1.0, batch_f=None, t0=None, psi0=None):
     return psi, obs
 
 
+def align_global_phase(psi_g, psi_o):
+    ov = np.vdot(psi_g.ravel(), psi_o.ravel())
+    return psi_g * (ov / abs(ov)) if abs(ov) > 0 else psi_g
+
+
 def compare(psi_g, obs_g, f, psi_o, lo=0.0, hi=1.0, steps=None, elementwise=True):
+    psi_g = psi_g.reshape(psi_o.shape)
     p_g = np.abs(psi_g) ** 2
     ob_o = oracle.observables(f, psi_o, 0.1, lo=lo, hi=hi)
     p_o = ob_o.prob
@@ -60,7 +69,7 @@ def compare(psi_g, obs_g, f, psi_o, lo=0.0, hi=1.0, steps=None, elementwise=True
     assert abs(obs_g.p_succ - ob_o.p_succ) <= 2 * TV_TOL
     assert np.allclose(obs_g.x_star[: f.ndim], ob_o.x_star[: f.ndim], rtol=0, atol=0)
     if elementwise and steps is not None:
-        err = np.max(np.abs(psi_g - psi_o))
+        err = np.max(np.abs(align_global_phase(psi_g, psi_o) - psi_o))
         assert err <= 2e-5 * np.abs(psi_o).max() * math.sqrt(steps + 1), f"max |dpsi| {err:.3e}"
     return tv, ef_err
 
@@ -148,7 +157,7 @@ def test_gpu_mirror_symmetry():
     X, Y = np.meshgrid(*workloads.mesh_axes(shape), indexing="ij")
     f = 0.5 * ((X - 0.5) ** 2 + (Y - 0.5) ** 2) - 1.2 * np.exp(-((X - 0.5) ** 2) / 0.02)
     psi_g, _ = run_gpu(f, qhd.Schedule(), 3.0, 0.01)
-    p = np.abs(psi_g) ** 2
+    p = np.abs(psi_g[0]) ** 2
     mirrored = p[(-np.arange(shape[0])) % shape[0]][:, (-np.arange(shape[1])) % shape[1]]
     assert np.max(np.abs(p - mirrored)) <= 1e-6 * p.max()
 
