@@ -1,0 +1,367 @@
+#!/usr/bin/env python3
+"""Benchmark of the QHD split-operator path on GB300.
+
+Workload (one bench step = one complete simulation of each instance, every
+row of the hot path: set f, schedule tables, uniform psi0, 10^4 Strang steps,
+observables):
+  * 2-D 1024x1024 mesh on [0,1]^2, shifted Rastrigin f (A=10, B=1, omega=5),
+  * 3-D 256^3 mesh on [0,1]^3, Gaussian-well f (K=32),
+both complex64, T = 10, dt = 1e-3, e^phi = 2/(1e-3 + t^3), e^chi = 2 t^3.
+
+Metric: grid-point Strang steps per second (sum over instances of
+G * steps / wall time of the device work), plus instances/s.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs its own replica of the workload with
+its own seeds ("replicas only": the instances are independent, no data-path
+collective); rank 0 prints the single JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+T_END, DT = 10.0, 1e-3
+NSTEPS = int(round(T_END / DT))
+METRIC = "grid-point Strang steps/s"
+WORKLOAD = ("QHD at scale, complex64, T=10, dt=1e-3 (10^4 Strang steps each): "
+            "2-D 1024^2 shifted Rastrigin (A=10,B=1,omega=5) + 3-D 256^3 Gaussian wells (K=32), "
+            "paper schedule e^phi=2/(1e-3+t^3), e^chi=2t^3, uniform psi0")
+# algorithmic bytes per grid point per launch of each pass (psi read+write,
+# plus the 32-bit fixed-point potential in the pass that applies it)
+BYTES_PER_POINT = {"row": 20, "axis1_fwd": 16, "axis0": 16, "axis1_inv": 16}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def cases_for_rank(rank: int):
+    return [("rastrigin", 1000 * rank + 0, (1024, 1024), {}),
+            ("wells", 1000 * rank + 1, (256, 256, 256), {"K": 32})]
+
+
+def make_instances(rank: int):
+    out = []
+    for fam, seed, shape, kw in cases_for_rank(rank):
+        out.append(workloads.make(fam, seed, shape, **kw))
+    return out
+
+
+# ------------------------------------------------------------- clocks sampler
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------- CPU oracle leg
+def oracle_sample(insts, budget_s: float = 15.0, max_steps=(400, 40)):
+    """Time the FP64 oracle on a bounded number of Strang steps of each instance
+    (the same workload, truncated); returns (grid-point steps/s, cores, text)."""
+    import oracle
+    cores = oracle.max_threads()
+    tot_pts, tot_t, parts = 0.0, 0.0, []
+    per = budget_s / len(insts)
+    for inst, cap in zip(insts, max_steps):
+        psi = oracle.uniform_state(inst.shape)
+        steps, t_used = 0, 0.0
+        chunk = 1
+        while steps < cap and t_used < per:
+            t0 = time.perf_counter()
+            psi = oracle.evolve(inst.f, psi, steps * DT, DT, chunk, oracle.Schedule())
+            t_used += time.perf_counter() - t0
+            steps += chunk
+        g = int(np.prod(inst.shape))
+        tot_pts += g * steps
+        tot_t += t_used
+        parts.append(f"{'x'.join(map(str, inst.shape))} {inst.family}: {steps} steps in {t_used:.1f}s")
+    return tot_pts / tot_t, cores, "; ".join(parts)
+
+
+# -------------------------------------------------------------------- our arm
+def run_ours(args, rank, world, local_rank, dist):
+    import torch
+    from paper_2303_01471_gb300 import qhd
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    qhd.load()
+    insts = make_instances(rank)
+    sims, f_dev = [], []
+    for inst in insts:
+        sim = qhd.QHD(inst.shape, batch=1, device=dev)
+        sim.set_schedule(qhd.Schedule())
+        sims.append(sim)
+        f_dev.append(torch.from_numpy(inst.f).to(dev))
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)  # > L2 (126 MB)
+    prob = [torch.empty(int(np.prod(i.shape)), dtype=torch.float32, device=dev) for i in insts]
+    prob_host = [torch.empty(int(np.prod(i.shape)), dtype=torch.float32).pin_memory() for i in insts]
+    pts_per_step = sum(int(np.prod(i.shape)) * NSTEPS for i in insts)
+
+    def one_step(device_inputs=True):
+        obs = []
+        for k, sim in enumerate(sims):
+            if device_inputs:
+                sim.set_potential(f_dev[k])
+            else:
+                sim.set_potential(insts[k].f)        # host FP64 -> device inside the call
+            sim.reset_state()
+            sim.evolve(T_END, DT)
+            obs.append(sim.observables(0.1, prob=prob[k])[0])
+            if not device_inputs:
+                prob_host[k].copy_(prob[k], non_blocking=False)
+        return obs
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+
+    # ---------------- timed region: device-resident inputs
+    for sim in sims:
+        sim.timing_read(reset=True)
+        sim.timing_enable(16)
+    launches0 = sum(s.launch_count() for s in sims)
+    step_ms = []
+    barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    with Clocks(local_rank) as clk:
+        for _ in range(args.steps):
+            flush.random_(0, 255)             # evict psi/f of the previous step from L2
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            obs = one_step()
+            e1.record()
+            torch.cuda.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+    barrier()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    launches = sum(s.launch_count() for s in sims) - launches0
+    timing = [s.timing_read(reset=True) for s in sims]
+    for sim in sims:
+        sim.timing_enable(0)
+    total_ms = float(sum(step_ms))
+    if dist is not None:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = pts_per_step * world / (ms_per_step / 1e3)
+
+    # ---------------- e2e: host inputs and host result through the C ABI
+    e2e_ms = []
+    for _ in range(args.steps):
+        flush.random_(0, 255)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        one_step(device_inputs=False)
+        torch.cuda.synchronize()
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_step = statistics.mean(e2e_ms)
+    if dist is not None:
+        t = torch.tensor([e2e_step], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_step = float(t.item())
+    h2d = sum(8 * int(np.prod(i.shape)) for i in insts)
+    d2h = sum(4 * int(np.prod(i.shape)) + 64 for i in insts)
+
+    # ---------------- roofline of the dominant kernel class
+    peak, peak_src = peaks()
+    kernels = []
+    for inst, tm in zip(insts, timing):
+        g = int(np.prod(inst.shape))
+        for cls, (ms, cnt) in tm.items():
+            if cnt == 0:
+                continue
+            avg_ms = ms / cnt
+            bpp = BYTES_PER_POINT.get(cls)
+            row = {"instance": "x".join(map(str, inst.shape)), "kernel": cls, "timed_launches": cnt,
+                   "avg_us": round(avg_ms * 1e3, 3), "share_est": None}
+            if bpp is not None:
+                row["bytes_per_launch"] = bpp * g
+                row["gbs"] = round(bpp * g / (avg_ms * 1e-3) / 1e9, 1)
+            kernels.append(row)
+    # share of device time per class, scaling sampled launches to all steps
+    est = []
+    for row in kernels:
+        n_launch = NSTEPS + (1 if row["kernel"] == "row" else 0) if row["kernel"] != "prep" else None
+        if n_launch is None:
+            n_launch = row["timed_launches"] / args.steps
+        est.append(row["avg_us"] * 1e-3 * n_launch)
+    tot = sum(est)
+    for row, e in zip(kernels, est):
+        row["share_est"] = round(e / tot, 4) if tot > 0 else None
+    dom = max((r for r in kernels if "gbs" in r), key=lambda r: r["share_est"] or 0)
+    roofline = {"bound": "hbm", "kernel": f"{dom['kernel']} pass, {dom['instance']}",
+                "achieved": dom["gbs"], "peak": peak, "unit": "GB/s",
+                "frac": round(dom["gbs"] / peak, 4), "peak_source": peak_src,
+                "traffic": None,
+                "algorithmic_bytes_per_launch": dom["bytes_per_launch"]}
+
+    result = {
+        "metric": METRIC, "value": value, "unit": "grid-point Strang steps/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded Rastrigin / Gaussian wells)",
+        "instances_per_s": len(insts) * world / (ms_per_step / 1e3),
+        "config": {"workload": WORKLOAD, "instances_per_rank": len(insts),
+                   "grid_points_x_steps_per_step": pts_per_step, "parallelism": f"replicas x{world}",
+                   "l2": "psi+f of the 256^3 instance exceed L2; a 512 MiB write flushes L2 between timed steps"},
+        "e2e": {"value": pts_per_step * world / (e2e_step / 1e3), "unit": "grid-point Strang steps/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "ms_per_step": e2e_step},
+        "gpu_launches": launches,
+        "roofline": roofline,
+        "kernels": kernels,
+        "clocks": clk.summary(),
+        "wall_s_timed_region": wall,
+        "observables": [{"instance": "x".join(map(str, i.shape)), "norm": o.norm, "e_f": o.e_f,
+                         "p_succ": o.p_succ} for i, o in zip(insts, obs)],
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, cores, sample = oracle_sample(insts, budget_s=args.cpu_budget)
+        result["cpu_baseline"] = {"value": v, "unit": "grid-point Strang steps/s", "cores": cores,
+                                  "kind": "oracle", "sample": sample}
+    for sim in sims:
+        sim.close()
+    return result
+
+
+# -------------------------------------------------------------- reference arm
+def run_reference(args, rank, world):
+    """The paper ships no code; the reference arm is the FP64 oracle on the host
+    cores, each step a bounded sample of the same workload."""
+    if rank != 0:
+        return None
+    insts = make_instances(0)
+    per_step = max(2.0, args.cpu_budget / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        oracle_sample(insts, budget_s=per_step, max_steps=(2, 1))
+    vals, samples = [], []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        v, cores, sample = oracle_sample(insts, budget_s=per_step, max_steps=(400, 40))
+        vals.append(v)
+        samples.append(sample)
+    wall = time.perf_counter() - t0
+    v = statistics.mean(vals)
+    pts_per_step = sum(int(np.prod(i.shape)) * NSTEPS for i in insts)
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": "grid-point Strang steps/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": pts_per_step / v * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded Rastrigin / Gaussian wells)",
+            "config": {"workload": WORKLOAD, "instances_per_rank": len(insts),
+                       "note": "FP64 CPU oracle timed on a bounded prefix of the 10^4 steps"},
+            "cpu_baseline": {"value": v, "unit": "grid-point Strang steps/s", "cores": cores,
+                             "kind": "oracle", "sample": samples[-1]},
+            "e2e": {"value": v, "unit": "grid-point Strang steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+            "wall_s_timed_region": wall}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        backend = "nccl" if (args.impl == "ours" and torch.cuda.is_available()) else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local_rank)
+        tdist.init_process_group(backend)
+        dist = tdist
+    if args.impl == "reference":
+        res = run_reference(args, rank, world)
+    else:
+        res = run_ours(args, rank, world, local_rank, dist)
+    if rank == 0 and res is not None:
+        print(json.dumps(res), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

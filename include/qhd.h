@@ -76,7 +76,7 @@ typedef struct {
     const double *t;    /* TABLE: host arrays of n_samples values, copied by the  */
     const double *phi;  /*        library during qhd_set_schedule                 */
     const double *chi;
-    int64_t n_samples;  /* TABLE: 1 .. 4096                                       */
+    int64_t n_samples;  /* TABLE: 1 .. 256                                        */
 } qhd_schedule;
 
 /* Observables of one instance (Eq. (expect_O); Fig. 2 caption). */
@@ -108,7 +108,8 @@ qhd_status qhd_init_grid(qhd_ctx **out, int ndim, const int64_t *n, const double
                          size_t work_bytes, void *stream);
 
 /*
- * Load the objective sampled on the mesh (step "sample f" of Algorithm 1):
+ * Load the objective sampled on the mesh (the diagonal potential operator V of
+ * Algorithm 1):
  * f_host is host FP64, batch*G values in psi's layout.  Copies f into the
  * workspace (FP64 for E[f], plus a 32-bit fixed-point copy with a per-instance
  * power-of-two scale used for the potential phase), finds the grid minimiser x*.
@@ -126,7 +127,8 @@ qhd_status qhd_set_potential_device(qhd_ctx *ctx, const double *f_dev);
  */
 qhd_status qhd_set_schedule(qhd_ctx *ctx, const qhd_schedule *s);
 
-/* psi <- G^{-1/2} in every instance (uniform superposition, Algorithm 1 step 3),
+/* psi <- G^{-1/2} in every instance (the uniform superposition that Algorithm 1
+ * and Eq. (prod_qhd) start from),
  * t <- 0, steps_done <- 0.  Enqueued on the stream. */
 qhd_status qhd_reset_state(qhd_ctx *ctx);
 
@@ -154,6 +156,29 @@ qhd_status qhd_observables(qhd_ctx *ctx, qhd_obs *out_host, float *prob_dev, dou
 
 /* Kernel launches this context has issued so far (for launch accounting). */
 int64_t qhd_launch_count(const qhd_ctx *ctx);
+
+/*
+ * Device-time accounting per kernel class (instrumentation; the paper has no
+ * counterpart).  qhd_timing_enable(ctx, every) with every > 0 makes
+ * qhd_evolve record a CUDA event pair on the stream around every launch that
+ * belongs to a step j with j % every == 0 (and around the prep launch of
+ * every chunk); every = 0 turns it off.  At most 65536 pairs are kept until
+ * read.  qhd_timing_read synchronises on the recorded events and writes, per
+ * class, the summed device milliseconds and the number of timed launches
+ * into arrays of QHD_KCLASS_COUNT entries (either may be NULL), then forgets
+ * the records if reset != 0.
+ */
+enum {
+    QHD_KCLASS_PREP = 0,       /* schedule + phase tables of a chunk              */
+    QHD_KCLASS_ROW = 1,        /* fastest-axis pass with the potential phase      */
+    QHD_KCLASS_AXIS1_FWD = 2,  /* 3-D: forward transform along axis 1             */
+    QHD_KCLASS_AXIS0 = 3,      /* axis-0 pass: forward, kinetic phase, inverse    */
+    QHD_KCLASS_AXIS1_INV = 4,  /* 3-D: inverse transform along axis 1             */
+    QHD_KCLASS_ONED = 5,       /* 1-D: all steps of a chunk in one launch         */
+    QHD_KCLASS_COUNT = 6
+};
+qhd_status qhd_timing_enable(qhd_ctx *ctx, int every);
+qhd_status qhd_timing_read(qhd_ctx *ctx, double *ms_out, int64_t *launches_out, int reset);
 
 /* Synchronise the stream and free the host-side context (never the caller's
  * buffers).  NULL is accepted. */

@@ -121,6 +121,21 @@ struct qhd_ctx {
     std::string err;
     std::vector<InstDev> inst_host;
     std::vector<double> coord_host;
+    // device-time accounting (qhd_timing_*)
+    int timing_every = 0;
+    struct TimedLaunch {
+        int kclass;
+        cudaEvent_t start, stop;
+    };
+    std::vector<TimedLaunch> timed;
+    std::vector<cudaEvent_t> event_pool;
+    ~qhd_ctx() {
+        for (auto &r : timed) {
+            cudaEventDestroy(r.start);
+            cudaEventDestroy(r.stop);
+        }
+        for (auto e : event_pool) cudaEventDestroy(e);
+    }
 };
 
 namespace {
@@ -154,6 +169,42 @@ qhd_status cuda_fail(qhd_ctx *c, cudaError_t e, const char *where) {
         if (e_ != cudaSuccess) return cuda_fail((c), e_, #call); \
         (c)->launches++;                                         \
     } while (0)
+
+constexpr size_t MAX_TIMED = 65536;
+
+cudaEvent_t take_event(qhd_ctx *c) {
+    if (!c->event_pool.empty()) {
+        cudaEvent_t e = c->event_pool.back();
+        c->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+// Record an event pair around one launch when timing is on for this step.
+struct TimedScope {
+    qhd_ctx *c;
+    int kclass;
+    bool on;
+    cudaEvent_t start = nullptr, stop = nullptr;
+    TimedScope(qhd_ctx *c_, int k, bool sample) : c(c_), kclass(k), on(false) {
+        if (!sample || c->timing_every <= 0 || c->timed.size() >= MAX_TIMED) return;
+        start = take_event(c);
+        stop = take_event(c);
+        if (!start || !stop) return;
+        on = cudaEventRecord(start, c->stream) == cudaSuccess;
+    }
+    ~TimedScope() {
+        if (on && cudaEventRecord(stop, c->stream) == cudaSuccess) {
+            c->timed.push_back({kclass, start, stop});
+            return;
+        }
+        if (start) c->event_pool.push_back(start);
+        if (stop) c->event_pool.push_back(stop);
+    }
+};
 
 qhd_status check_ctx(qhd_ctx *c) {
     if (!c) return QHD_ERR_INVALID_ARG;
@@ -457,7 +508,10 @@ qhd_status qhd_evolve(qhd_ctx *c, double T, double dt) {
         const bool last_chunk = j0 + cnt == nsteps;
         pa.j0 = j0;
         pa.cnt = cnt;
-        QHD_LAUNCH(c, launch_prep(pa, c->stream));
+        {
+            TimedScope ts(c, QHD_KCLASS_PREP, true);
+            QHD_LAUNCH(c, launch_prep(pa, c->stream));
+        }
         if (ndim == 1) {
             OneDArgs o{};
             o.psi = c->psi;
@@ -468,6 +522,7 @@ qhd_status qhd_evolve(qhd_ctx *c, double T, double dt) {
             o.batch = B;
             o.cnt = (int)cnt;
             o.final_phase = last_chunk ? 1 : 0;
+            TimedScope ts(c, QHD_KCLASS_ONED, true);
             QHD_LAUNCH(c, launch_oned((int)c->n[0], o, c->stream));
             continue;
         }
@@ -499,19 +554,28 @@ qhd_status qhd_evolve(qhd_ctx *c, double T, double dt) {
         }
         for (int64_t jl = 0; jl < cnt; ++jl) {
             const int64_t j = j0 + jl;
+            const bool sample = c->timing_every > 0 && j % c->timing_every == 0;
             // row pass before step j: inverse transform of the previous step
             // (if any), merged potential phase theta_j, forward transform
             r.pot = c->pot + jl * B;
             r.mode = (j == 0 ? 0 : MODE_INV) | MODE_FWD;
-            QHD_LAUNCH(c, launch_row((int)c->n[last_ax], r, c->stream));
+            {
+                TimedScope ts(c, QHD_KCLASS_ROW, sample);
+                QHD_LAUNCH(c, launch_row((int)c->n[last_ax], r, c->stream));
+            }
             if (ndim == 3) {
                 ax1.mode = MODE_FWD;
+                TimedScope ts(c, QHD_KCLASS_AXIS1_FWD, sample);
                 QHD_LAUNCH(c, launch_axis((int)c->n[1], ax1, c->stream));
             }
             ax0.kt = c->kt + jl * B * c->ksum;
-            QHD_LAUNCH(c, launch_axis((int)c->n[0], ax0, c->stream));
+            {
+                TimedScope ts(c, QHD_KCLASS_AXIS0, sample);
+                QHD_LAUNCH(c, launch_axis((int)c->n[0], ax0, c->stream));
+            }
             if (ndim == 3) {
                 ax1.mode = MODE_INV;
+                TimedScope ts(c, QHD_KCLASS_AXIS1_INV, sample);
                 QHD_LAUNCH(c, launch_axis((int)c->n[1], ax1, c->stream));
             }
         }
@@ -564,6 +628,40 @@ qhd_status qhd_observables(qhd_ctx *c, qhd_obs *out, float *prob_dev, double rad
         o.p_succ = res[(size_t)(3 * b + 2)];
         for (int d = 0; d < 3; ++d) o.x_star[d] = c->inst_host[(size_t)b].xs[d];
         o.steps_done = c->steps_done;
+    }
+    return QHD_OK;
+}
+
+qhd_status qhd_timing_enable(qhd_ctx *c, int every) {
+    qhd_status s = check_ctx(c);
+    if (s != QHD_OK) return s;
+    if (every < 0) return fail(c, QHD_ERR_INVALID_ARG, "every must be >= 0");
+    c->timing_every = every;
+    return QHD_OK;
+}
+
+qhd_status qhd_timing_read(qhd_ctx *c, double *ms_out, int64_t *launches_out, int reset) {
+    qhd_status s = check_ctx(c);
+    if (s != QHD_OK) return s;
+    double ms[QHD_KCLASS_COUNT] = {};
+    int64_t cnt[QHD_KCLASS_COUNT] = {};
+    for (auto &r : c->timed) {
+        QHD_CUDA(c, cudaEventSynchronize(r.stop));
+        float v = 0.f;
+        QHD_CUDA(c, cudaEventElapsedTime(&v, r.start, r.stop));
+        ms[r.kclass] += v;
+        cnt[r.kclass] += 1;
+    }
+    if (ms_out)
+        for (int k = 0; k < QHD_KCLASS_COUNT; ++k) ms_out[k] = ms[k];
+    if (launches_out)
+        for (int k = 0; k < QHD_KCLASS_COUNT; ++k) launches_out[k] = cnt[k];
+    if (reset) {
+        for (auto &r : c->timed) {
+            c->event_pool.push_back(r.start);
+            c->event_pool.push_back(r.stop);
+        }
+        c->timed.clear();
     }
     return QHD_OK;
 }

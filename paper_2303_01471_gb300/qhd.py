@@ -25,8 +25,9 @@ SCHED_TABLE = 1
 # Every entry point declared in include/qhd.h.
 EXPORTS = ["qhd_workspace_bytes", "qhd_init_grid", "qhd_set_potential", "qhd_set_potential_device",
            "qhd_set_schedule", "qhd_reset_state", "qhd_set_time", "qhd_get_time", "qhd_evolve",
-           "qhd_observables", "qhd_launch_count", "qhd_destroy", "qhd_status_string",
-           "qhd_last_error"]
+           "qhd_observables", "qhd_launch_count", "qhd_timing_enable", "qhd_timing_read",
+           "qhd_destroy", "qhd_status_string", "qhd_last_error"]
+KCLASS = ["prep", "row", "axis1_fwd", "axis0", "axis1_inv", "oned"]
 
 
 class QHDError(RuntimeError):
@@ -92,6 +93,10 @@ def load(build_if_missing: bool = True):
     lib.qhd_observables.restype = st
     lib.qhd_launch_count.argtypes = [vp]
     lib.qhd_launch_count.restype = ctypes.c_int64
+    lib.qhd_timing_enable.argtypes = [vp, ctypes.c_int]
+    lib.qhd_timing_enable.restype = st
+    lib.qhd_timing_read.argtypes = [vp, dp, i64p, ctypes.c_int]
+    lib.qhd_timing_read.restype = st
     lib.qhd_destroy.argtypes = [vp]
     lib.qhd_destroy.restype = st
     lib.qhd_status_string.argtypes = [st]
@@ -247,6 +252,17 @@ class QHD:
 
     def launch_count(self) -> int:
         return int(self.lib.qhd_launch_count(self.ctx))
+
+    def timing_enable(self, every: int) -> None:
+        self._check(self.lib.qhd_timing_enable(self.ctx, int(every)), "qhd_timing_enable")
+
+    def timing_read(self, reset: bool = True) -> dict:
+        """{class: (device ms summed, timed launches)} for the sampled launches."""
+        n = len(KCLASS)
+        ms = (ctypes.c_double * n)()
+        cnt = (ctypes.c_int64 * n)()
+        self._check(self.lib.qhd_timing_read(self.ctx, ms, cnt, 1 if reset else 0), "qhd_timing_read")
+        return {KCLASS[k]: (ms[k], cnt[k]) for k in range(n)}
 
     def close(self) -> None:
         if getattr(self, "ctx", None):
