@@ -36,18 +36,23 @@ def _stale() -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and not _stale():
+def build(force: bool = False, verbose: bool = False, extra_flags=None, out: str = None) -> str:
+    """Compile libqhd.so.  extra_flags / out build a variant elsewhere (for
+    experiments); the default library is LIB."""
+    target = out or LIB
+    if not force and out is None and not extra_flags and not _stale():
         return LIB
-    os.makedirs(LIBDIR, exist_ok=True)
+    libdir = os.path.dirname(target)
+    os.makedirs(libdir, exist_ok=True)
     nvcc = _nvcc()
     flags = ["-std=c++17", "-O3", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC",
              "-I" + os.path.join(ROOT, "include"), "-I" + CSRC, "-diag-suppress", "550"]
     if verbose:
         flags += ["-Xptxas", "-v"]
+    flags += list(extra_flags or [])
 
     def compile_one(src):
-        obj = os.path.join(LIBDIR, os.path.splitext(src)[0] + ".o")
+        obj = os.path.join(libdir, os.path.splitext(src)[0] + ".o")
         cmd = [nvcc, *flags, "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -58,13 +63,13 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB + ".tmp"
+    tmp = target + ".tmp"
     cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, target)
+    return target
 
 
 if __name__ == "__main__":

@@ -288,4 +288,27 @@ __device__ __forceinline__ float2 phase_from_turns(uint32_t u) {
     return make_float2(c, -s);
 }
 
+#ifndef QHD_POT_RENORM
+#define QHD_POT_RENORM 1
+#endif
+
+// z * exp(-2 pi i u / 2^32).  The FP32 cosine/sine pair w has |w|^2 = 1 + d
+// with |d| ~ 2^-24; d is formed exactly enough from the FMA residuals of c^2
+// and s^2 (the two leading terms cancel exactly by Sterbenz), and the
+// correction -d/2 w enters as the low part of a compensated product, so the
+// phase factor is unit-modulus to ~1e-15 and only the product is rounded.
+__device__ __forceinline__ float2 apply_phase_turns(float2 z, uint32_t u) {
+    const float2 w = phase_from_turns(u);
+#if QHD_POT_RENORM
+    const float pc = w.x * w.x, ec = fmaf(w.x, w.x, -pc);
+    const float ps = w.y * w.y, es = fmaf(w.y, w.y, -ps);
+    float d = pc >= ps ? (pc - 1.0f) + ps : (ps - 1.0f) + pc;
+    d += ec + es;
+    const float h = -0.5f * d;
+    return cmul_comp(z, w, make_float2(h * w.x, h * w.y));
+#else
+    return cmul(z, w);
+#endif
+}
+
 }  // namespace qhd

@@ -59,7 +59,7 @@ Layout make_layout(int ndim, const int64_t *n, int64_t batch) {
     const int64_t g = grid_points(ndim, n);
     int64_t ksum = 0;
     for (int d = 0; d < ndim; ++d) ksum += n[d];
-    int64_t ch = (int64_t)(KT_BUDGET / ((size_t)batch * (size_t)ksum * sizeof(float2)));
+    int64_t ch = (int64_t)(KT_BUDGET / ((size_t)batch * (size_t)ksum * sizeof(float4)));
     if (ch > MAX_CHUNK) ch = MAX_CHUNK;
     if (ch < 1) ch = 1;
     L.chunk = ch;
@@ -73,7 +73,7 @@ Layout make_layout(int ndim, const int64_t *n, int64_t batch) {
     };
     L.f64 = take(sizeof(double) * (size_t)(g * batch));
     L.fq = take(sizeof(uint32_t) * (size_t)(g * batch));
-    L.kt = take(sizeof(float2) * (size_t)(ch * batch * ksum));
+    L.kt = take(sizeof(float4) * (size_t)(ch * batch * ksum));
     L.pot = take(sizeof(uint64_t) * (size_t)((ch + 1) * batch));
     L.sched = take(sizeof(SchedDev) * (size_t)batch);
     L.samples = take(sizeof(double) * 3 * MAX_TABLE_SAMPLES * (size_t)batch);
@@ -103,7 +103,7 @@ struct qhd_ctx {
     // workspace views
     double *f64 = nullptr;
     uint32_t *fq = nullptr;
-    float2 *kt = nullptr;
+    float4 *kt = nullptr;
     uint64_t *pot = nullptr;
     SchedDev *sched = nullptr;
     double *samples = nullptr;
@@ -269,7 +269,7 @@ qhd_status qhd_init_grid(qhd_ctx **out, int ndim, const int64_t *n, const double
     c->L = L;
     c->f64 = (double *)(c->work + L.f64);
     c->fq = (uint32_t *)(c->work + L.fq);
-    c->kt = (float2 *)(c->work + L.kt);
+    c->kt = (float4 *)(c->work + L.kt);
     c->pot = (uint64_t *)(c->work + L.pot);
     c->sched = (SchedDev *)(c->work + L.sched);
     c->samples = (double *)(c->work + L.samples);

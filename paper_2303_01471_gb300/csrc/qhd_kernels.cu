@@ -62,8 +62,7 @@ __global__ void __launch_bounds__(ROW_THREADS) k_row(RowArgs a) {
     const uint64_t c = a.pot[r / a.rows_per_inst];
 #pragma unroll
     for (int e = 0; e < E; ++e) {
-        const uint32_t u = turns_mul(c, __ldg(&fq[t + T * e]));
-        x[e] = cmul(x[e], phase_from_turns(u));
+        x[e] = apply_phase_turns(x[e], turns_mul(c, __ldg(&fq[t + T * e])));
     }
     if (a.mode & MODE_FWD) line_fft<N, false>(x, sm, t, a.tw2, WarpSync{});
     if (valid) {
@@ -93,17 +92,22 @@ __global__ void __launch_bounds__(W * LineCfg<N>::T) k_axis(AxisArgs a) {
     float2 *sm = smem + (C::TWO_STAGE ? c * S : 0);
     if (a.mode & MODE_FWD) line_fft<N, false>(x, sm, t, a.tw2, BlockSync{});
     if (a.mode & MODE_KIN) {
-        // axis 0 pass: plane index o is the instance
-        const float2 *kb = a.kt + o * a.ksum;
-        float2 kc;
-        if (a.ndim == 2) {
-            kc = __ldg(&kb[a.koff1 + ci]);
-        } else {
-            const int64_t i1 = ci >> a.log_n2, i2 = ci & ((1 << a.log_n2) - 1);
-            kc = cmul(__ldg(&kb[a.koff1 + i1]), __ldg(&kb[a.koff2 + i2]));
-        }
+        // axis 0 pass: plane index o is the instance.  Each per-axis factor is
+        // an FP32 hi/lo pair applied with a compensated product: a table entry
+        // is shared by every point with the same frequency index, so a plain
+        // FP32 rounding of it would perturb the norm coherently.
+        const float4 *kb = a.kt + o * a.ksum;
+        const float4 k1 = __ldg(&kb[a.koff1 + (a.ndim == 2 ? ci : (ci >> a.log_n2))]);
+        float4 k2 = make_float4(1.f, 0.f, 0.f, 0.f);
+        if (a.ndim == 3) k2 = __ldg(&kb[a.koff2 + (ci & ((1 << a.log_n2) - 1))]);
 #pragma unroll
-        for (int e = 0; e < E; ++e) x[e] = cmul(x[e], cmul(__ldg(&kb[t + T * e]), kc));
+        for (int e = 0; e < E; ++e) {
+            const float4 k0 = __ldg(&kb[t + T * e]);
+            float2 y = cmul_comp(x[e], make_float2(k0.x, k0.y), make_float2(k0.z, k0.w));
+            y = cmul_comp(y, make_float2(k1.x, k1.y), make_float2(k1.z, k1.w));
+            if (a.ndim == 3) y = cmul_comp(y, make_float2(k2.x, k2.y), make_float2(k2.z, k2.w));
+            x[e] = y;
+        }
     }
     if (a.mode & MODE_INV) line_fft<N, true>(x, sm, t, a.tw2, BlockSync{});
 #pragma unroll
@@ -135,17 +139,20 @@ __global__ void __launch_bounds__(ROW_THREADS) k_oned(OneDArgs a) {
     for (int j = 0; j < a.cnt; ++j) {
         const uint64_t c = a.pot[(int64_t)j * a.batch + b];
 #pragma unroll
-        for (int e = 0; e < E; ++e) x[e] = cmul(x[e], phase_from_turns(turns_mul(c, fv[e])));
+        for (int e = 0; e < E; ++e) x[e] = apply_phase_turns(x[e], turns_mul(c, fv[e]));
         line_fft<N, false>(x, sm, t, a.tw2, WarpSync{});
-        const float2 *kb = a.kt + ((int64_t)j * a.batch + b) * N;
+        const float4 *kb = a.kt + ((int64_t)j * a.batch + b) * N;
 #pragma unroll
-        for (int e = 0; e < E; ++e) x[e] = cmul(x[e], __ldg(&kb[t + T * e]));
+        for (int e = 0; e < E; ++e) {
+            const float4 k0 = __ldg(&kb[t + T * e]);
+            x[e] = cmul_comp(x[e], make_float2(k0.x, k0.y), make_float2(k0.z, k0.w));
+        }
         line_fft<N, true>(x, sm, t, a.tw2, WarpSync{});
     }
     if (a.final_phase) {
         const uint64_t c = a.pot[(int64_t)a.cnt * a.batch + b];
 #pragma unroll
-        for (int e = 0; e < E; ++e) x[e] = cmul(x[e], phase_from_turns(turns_mul(c, fv[e])));
+        for (int e = 0; e < E; ++e) x[e] = apply_phase_turns(x[e], turns_mul(c, fv[e]));
     }
     if (valid) {
 #pragma unroll
@@ -200,7 +207,6 @@ __global__ void k_prep(PrepArgs a) {
     const int64_t jl = blockIdx.x;  // local step 0..cnt (cnt is the extra potential entry)
     const int64_t b = blockIdx.y;
     const int64_t j = a.j0 + jl;    // global step index
-    __shared__ double s_a;
     __shared__ uint64_t s_k[3];
     if (threadIdx.x == 0) {
         const SchedDev &sd = a.sched[b];
@@ -221,7 +227,6 @@ __global__ void k_prep(PrepArgs a) {
         // turns per unit of the fixed-point potential: theta / (2 pi) * 2^-shift
         const double y = ldexp(theta / (2.0 * PI), -shift);
         a.pot[jl * a.batch + b] = frac_to_u64(y);
-        s_a = a_p;
         for (int d = 0; d < a.ndim; ++d) {
             // turns per unit m^2: dt * a * |2 pi m / L|^2 / 2 / (2 pi) = dt a pi m^2 / L^2
             const double kap = __ddiv_rn(__dmul_rn(__dmul_rn(a.dt, a_p), PI), __dmul_rn(a.len[d], a.len[d]));
@@ -230,7 +235,7 @@ __global__ void k_prep(PrepArgs a) {
     }
     __syncthreads();
     if (jl >= a.cnt) return;
-    float2 *out = a.kt + (jl * a.batch + b) * a.ksum;
+    float4 *out = a.kt + (jl * a.batch + b) * a.ksum;
     for (int i = threadIdx.x; i < a.ksum; i += blockDim.x) {
         int d = 0;
         while (d + 1 < a.ndim && i >= a.koff[d + 1]) ++d;
@@ -240,8 +245,10 @@ __global__ void k_prep(PrepArgs a) {
         const uint32_t u = turns_mul(s_k[d], (uint32_t)(m * m));
         double s, c;
         sincospi((double)(int32_t)u * 4.656612873077392578125e-10, &s, &c);
-        const double scale = d == 0 ? a.inv_g : 1.0;
-        out[i] = make_float2((float)(c * scale), (float)(-s * scale));
+        const double scale = d == 0 ? a.inv_g : 1.0;  // exact power of two
+        const double cr = c * scale, ci = -s * scale;
+        const float hr = (float)cr, hi = (float)ci;
+        out[i] = make_float4(hr, hi, (float)(cr - (double)hr), (float)(ci - (double)hi));
     }
 }
 

@@ -45,7 +45,7 @@ struct RowArgs {
 struct AxisArgs {
     float2 *psi;
     const float4 *tw2;
-    const float2 *kt;      // kinetic tables of this step: [batch][ksum] (MODE_KIN only)
+    const float4 *kt;      // kinetic tables of this step: [batch][ksum] (MODE_KIN only)
     int64_t inner;         // product of the axis lengths after this axis (line stride)
     int64_t planes;        // product of batch and the axis lengths before this axis
     int ksum;              // sum of the axis lengths
@@ -59,7 +59,7 @@ struct OneDArgs {
     float2 *psi;
     const uint32_t *fq;
     const uint64_t *pot;   // chunk potential coefficients [cnt+1][batch]
-    const float2 *kt;      // chunk kinetic tables [cnt][batch][n]
+    const float4 *kt;      // chunk kinetic tables [cnt][batch][n]
     const float4 *tw2;
     int64_t batch;
     int cnt;
@@ -70,7 +70,7 @@ struct PrepArgs {
     const SchedDev *sched;
     const InstDev *inst;
     uint64_t *pot;         // [cnt+1][batch]
-    float2 *kt;            // [cnt][batch][ksum]
+    float4 *kt;            // [cnt][batch][ksum], (hi.re, hi.im, lo.re, lo.im)
     double t_start, dt;
     int64_t j0, cnt, nsteps, batch;
     int ndim;
