@@ -288,6 +288,19 @@ __device__ __forceinline__ float2 phase_from_turns(uint32_t u) {
     return make_float2(c, -s);
 }
 
+// Per-step dither: a pseudo-random global phase (in turns, 2^-32 units) added
+// to the potential phase of every point.  A global phase changes no
+// observable, but it changes the FP32 values every later operation rounds, so
+// the rounding errors of consecutive steps decorrelate.  Without it a state
+// that varies slowly from step to step (late, nearly adiabatic evolution)
+// repeats the same rounding errors and its norm drifts coherently.
+__host__ __device__ inline uint32_t step_dither(uint64_t step) {
+    uint64_t z = step + 0x9E3779B97F4A7C15ull;  // splitmix64 finaliser
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return (uint32_t)((z ^ (z >> 31)) >> 32);
+}
+
 #ifndef QHD_POT_RENORM
 #define QHD_POT_RENORM 1
 #endif

@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "qhd.h"
+#include "qhd_device.cuh"
 #include "qhd_kernels.h"
 
 using namespace qhd;
@@ -522,6 +523,7 @@ qhd_status qhd_evolve(qhd_ctx *c, double T, double dt) {
             o.batch = B;
             o.cnt = (int)cnt;
             o.final_phase = last_chunk ? 1 : 0;
+            o.dither_base = (uint64_t)(c->steps_done + j0);
             TimedScope ts(c, QHD_KCLASS_ONED, true);
             QHD_LAUNCH(c, launch_oned((int)c->n[0], o, c->stream));
             continue;
@@ -559,6 +561,7 @@ qhd_status qhd_evolve(qhd_ctx *c, double T, double dt) {
             // (if any), merged potential phase theta_j, forward transform
             r.pot = c->pot + jl * B;
             r.mode = (j == 0 ? 0 : MODE_INV) | MODE_FWD;
+            r.dither = step_dither((uint64_t)(c->steps_done + j));
             {
                 TimedScope ts(c, QHD_KCLASS_ROW, sample);
                 QHD_LAUNCH(c, launch_row((int)c->n[last_ax], r, c->stream));
@@ -582,6 +585,7 @@ qhd_status qhd_evolve(qhd_ctx *c, double T, double dt) {
         if (last_chunk) {
             r.pot = c->pot + cnt * B;
             r.mode = MODE_INV;
+            r.dither = 0;
             QHD_LAUNCH(c, launch_row((int)c->n[last_ax], r, c->stream));
         }
     }

@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(ROW_THREADS) k_row(RowArgs a) {
     const uint64_t c = a.pot[r / a.rows_per_inst];
 #pragma unroll
     for (int e = 0; e < E; ++e) {
-        x[e] = apply_phase_turns(x[e], turns_mul(c, __ldg(&fq[t + T * e])));
+        x[e] = apply_phase_turns(x[e], turns_mul(c, __ldg(&fq[t + T * e])) + a.dither);
     }
     if (a.mode & MODE_FWD) line_fft<N, false>(x, sm, t, a.tw2, WarpSync{});
     if (valid) {
@@ -138,8 +138,9 @@ __global__ void __launch_bounds__(ROW_THREADS) k_oned(OneDArgs a) {
     float2 *sm = smem + (C::TWO_STAGE ? line * S : 0);
     for (int j = 0; j < a.cnt; ++j) {
         const uint64_t c = a.pot[(int64_t)j * a.batch + b];
+        const uint32_t dz = step_dither(a.dither_base + (uint64_t)j);
 #pragma unroll
-        for (int e = 0; e < E; ++e) x[e] = apply_phase_turns(x[e], turns_mul(c, fv[e]));
+        for (int e = 0; e < E; ++e) x[e] = apply_phase_turns(x[e], turns_mul(c, fv[e]) + dz);
         line_fft<N, false>(x, sm, t, a.tw2, WarpSync{});
         const float4 *kb = a.kt + ((int64_t)j * a.batch + b) * N;
 #pragma unroll

@@ -40,6 +40,7 @@ struct RowArgs {
     int64_t rows;          // batch * rows per instance
     int64_t rows_per_inst;
     int mode;              // MODE_INV: inverse FFT before the phase; MODE_FWD: forward after
+    uint32_t dither;       // global phase of this pass in 2^-32 turns (step_dither)
 };
 
 struct AxisArgs {
@@ -64,6 +65,7 @@ struct OneDArgs {
     int64_t batch;
     int cnt;
     int final_phase;       // apply pot[cnt] after the last step
+    uint64_t dither_base;  // global step index of the chunk's first step
 };
 
 struct PrepArgs {

@@ -144,7 +144,10 @@ def test_gpu_time_reversal():
     sim.evolve(1.0, 0.01)
     moved = (sim.psi - psi0).abs().max().item()
     sim.evolve(-1.0, -0.01)
-    back = (sim.psi - psi0).abs().max().item()
+    # every step carries a pseudo-random global phase (rounding dither), so the
+    # state returns up to one global phase
+    ov = torch.vdot(sim.psi.flatten(), psi0.flatten())
+    back = (sim.psi * (ov / ov.abs()) - psi0).abs().max().item()
     t, steps = sim.time()
     sim.close()
     assert moved > 1e-3
@@ -173,7 +176,7 @@ def test_split_evolve_matches_single_call():
     sim.evolve(1.3, 0.01)
     b = sim.psi.cpu().numpy().astype(np.complex128)
     sim.close()
-    assert np.max(np.abs(a - b)) <= 1e-5 * np.abs(a).max()
+    assert np.max(np.abs(align_global_phase(b, a) - a)) <= 1e-5 * np.abs(a).max()
 
 
 def test_device_potential_matches_host_potential():
