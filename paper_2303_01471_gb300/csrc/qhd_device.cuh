@@ -304,6 +304,9 @@ __host__ __device__ inline uint32_t step_dither(uint64_t step) {
 #ifndef QHD_POT_RENORM
 #define QHD_POT_RENORM 1
 #endif
+#ifndef QHD_POT_FP64
+#define QHD_POT_FP64 0
+#endif
 
 // z * exp(-2 pi i u / 2^32).  The FP32 cosine/sine pair w has |w|^2 = 1 + d
 // with |d| ~ 2^-24; d is formed exactly enough from the FMA residuals of c^2
@@ -311,6 +314,11 @@ __host__ __device__ inline uint32_t step_dither(uint64_t step) {
 // correction -d/2 w enters as the low part of a compensated product, so the
 // phase factor is unit-modulus to ~1e-15 and only the product is rounded.
 __device__ __forceinline__ float2 apply_phase_turns(float2 z, uint32_t u) {
+#if QHD_POT_FP64
+    double sd, cd;
+    sincospi((double)(int32_t)u * 4.656612873077392578125e-10, &sd, &cd);
+    return make_float2((float)((double)z.x * cd + (double)z.y * sd), (float)((double)z.y * cd - (double)z.x * sd));
+#endif
     const float2 w = phase_from_turns(u);
 #if QHD_POT_RENORM
     const float pc = w.x * w.x, ec = fmaf(w.x, w.x, -pc);

@@ -62,7 +62,11 @@ __global__ void __launch_bounds__(ROW_THREADS) k_row(RowArgs a) {
     const uint64_t c = a.pot[r / a.rows_per_inst];
 #pragma unroll
     for (int e = 0; e < E; ++e) {
+#ifdef QHD_NO_DITHER
+        x[e] = apply_phase_turns(x[e], turns_mul(c, __ldg(&fq[t + T * e])));
+#else
         x[e] = apply_phase_turns(x[e], turns_mul(c, __ldg(&fq[t + T * e])) + a.dither);
+#endif
     }
     if (a.mode & MODE_FWD) line_fft<N, false>(x, sm, t, a.tw2, WarpSync{});
     if (valid) {
