@@ -154,6 +154,43 @@ qhd_status qhd_evolve(qhd_ctx *ctx, double T, double dt);
  */
 qhd_status qhd_observables(qhd_ctx *ctx, qhd_obs *out_host, float *prob_dev, double radius);
 
+/*
+ * qhd_observables_static -- observables of states the caller already holds,
+ * with no context, no workspace and no device allocation.  The paper has no
+ * counterpart; this exists for callers that cannot call cudaMalloc where they
+ * need the observables: e.g. an application whose device memory is entirely
+ * reserved by another allocator, where one more allocation would fail or
+ * fragment that pool, or a latency-critical caller that must not pay for
+ * cudaMalloc, which can synchronise the device.
+ *
+ * The reduction scratch is a fixed array of QHD_STATIC_SCRATCH_BYTES inside the
+ * library; every GPU that loads the library holds that much memory until the
+ * process exits.  Limits: batch <= 32 instances, every n[k] a power of two in
+ * 2..1024, ndim 1..3.  Larger requests return QHD_ERR_INVALID_ARG.
+ *
+ * Inputs (device pointers on the current device): psi_dev, batch*G complex64
+ * in the layout of qhd_init_grid; f_dev, batch*G FP64 objective values.
+ * x_star: host array of batch*3 doubles, the minimiser coordinates used for
+ * the success probability (entries beyond ndim ignored).  radius > 0.
+ * Outputs: out_dev, a device array of batch*3 doubles receiving per instance
+ * (sum |psi|^2, sum |psi|^2 f, sum of |psi|^2 within radius of x_star), the
+ * same quantities and accumulation order as qhd_observables; prob_dev
+ * (optional, NULL to skip) receives |psi|^2 as float32.  Everything is
+ * enqueued on `stream` (a cudaStream_t, NULL = legacy default stream); the
+ * call does not synchronise.
+ *
+ * The first call on a device looks up the device address of the scratch
+ * array with that device current; make that first call before any stream
+ * capture.  All calls share the one array and each call overwrites every part
+ * of it it reads, so nothing needs clearing, but calls whose work overlaps on
+ * the GPU (e.g. on two streams, or from two host threads) race on it.
+ */
+#define QHD_STATIC_SCRATCH_BYTES (1u << 20)
+qhd_status qhd_observables_static(int ndim, const int64_t *n, const double *lo, const double *hi,
+                                  int64_t batch, const void *psi_dev, const double *f_dev,
+                                  const double *x_star, double radius, double *out_dev,
+                                  float *prob_dev, void *stream);
+
 /* Kernel launches this context has issued so far (for launch accounting). */
 int64_t qhd_launch_count(const qhd_ctx *ctx);
 

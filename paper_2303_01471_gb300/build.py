@@ -16,7 +16,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libqhd.so")
-SOURCES = ["qhd_kernels.cu", "qhd_host.cu"]
+SOURCES = ["qhd_kernels.cu", "qhd_host.cu", "qhd_static.cu"]
 HEADERS = ["qhd_device.cuh", "qhd_kernels.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

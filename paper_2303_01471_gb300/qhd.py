@@ -26,7 +26,7 @@ SCHED_TABLE = 1
 EXPORTS = ["qhd_workspace_bytes", "qhd_init_grid", "qhd_set_potential", "qhd_set_potential_device",
            "qhd_set_schedule", "qhd_reset_state", "qhd_set_time", "qhd_get_time", "qhd_evolve",
            "qhd_observables", "qhd_launch_count", "qhd_timing_enable", "qhd_timing_read",
-           "qhd_destroy", "qhd_status_string", "qhd_last_error"]
+           "qhd_destroy", "qhd_status_string", "qhd_last_error", "qhd_observables_static"]
 KCLASS = ["prep", "row", "axis1_fwd", "axis0", "axis1_inv", "oned"]
 
 
@@ -97,6 +97,9 @@ def load(build_if_missing: bool = True):
     lib.qhd_timing_enable.restype = st
     lib.qhd_timing_read.argtypes = [vp, dp, i64p, ctypes.c_int]
     lib.qhd_timing_read.restype = st
+    lib.qhd_observables_static.argtypes = [ctypes.c_int, i64p, dp, dp, ctypes.c_int64, vp, vp, dp,
+                                           ctypes.c_double, vp, vp, vp]
+    lib.qhd_observables_static.restype = st
     lib.qhd_destroy.argtypes = [vp]
     lib.qhd_destroy.restype = st
     lib.qhd_status_string.argtypes = [st]
