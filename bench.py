@@ -43,7 +43,7 @@ WORKLOAD = ("QHD at scale, complex64, T=10, dt=1e-3 (10^4 Strang steps each): "
             "paper schedule e^phi=2/(1e-3+t^3), e^chi=2t^3, uniform psi0")
 # algorithmic bytes per grid point per launch of each pass (psi read+write,
 # plus the 32-bit fixed-point potential in the pass that applies it)
-BYTES_PER_POINT = {"row": 20, "axis1_fwd": 16, "axis0": 16, "axis1_inv": 16}
+BYTES_PER_POINT = {"row": 20, "axis1_fwd": 16, "axis0": 16, "axis1_inv": 16, "plane": 20}
 
 
 def peaks():

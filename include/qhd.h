@@ -212,7 +212,11 @@ enum {
     QHD_KCLASS_AXIS0 = 3,      /* axis-0 pass: forward, kinetic phase, inverse    */
     QHD_KCLASS_AXIS1_INV = 4,  /* 3-D: inverse transform along axis 1             */
     QHD_KCLASS_ONED = 5,       /* 1-D: all steps of a chunk in one launch         */
-    QHD_KCLASS_COUNT = 6
+    QHD_KCLASS_PLANE = 6,      /* 3-D: cluster pass over axes 1 and 2 with the    */
+                               /*      potential phase                           */
+    QHD_KCLASS_WHOLE = 7,      /* 2-D: all steps of a chunk, instance resident in */
+                               /*      one thread-block cluster                   */
+    QHD_KCLASS_COUNT = 8
 };
 qhd_status qhd_timing_enable(qhd_ctx *ctx, int every);
 qhd_status qhd_timing_read(qhd_ctx *ctx, double *ms_out, int64_t *launches_out, int reset);

@@ -16,8 +16,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libqhd.so")
-SOURCES = ["qhd_kernels.cu", "qhd_host.cu", "qhd_static.cu"]
-HEADERS = ["qhd_device.cuh", "qhd_kernels.h"]
+SOURCES = ["qhd_kernels.cu", "qhd_plane.cu", "qhd_host.cu", "qhd_static.cu"]
+HEADERS = ["qhd_device.cuh", "qhd_kernels.h", "qhd_plane.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -27,7 +27,7 @@ constexpr int MINMAX_BLOCKS_MAX = 512;
 size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
 
 struct Layout {
-    size_t f64, fq, kt, pot, sched, samples, inst, tw, coord, obs_part, obs_res, mm, total;
+    size_t f64, fq, kt, pot, sched, samples, inst, tw, twx, coord, obs_part, obs_res, mm, total;
     int64_t chunk;
     int obs_blocks, mm_blocks;
 };
@@ -80,6 +80,7 @@ Layout make_layout(int ndim, const int64_t *n, int64_t batch) {
     L.samples = take(sizeof(double) * 3 * MAX_TABLE_SAMPLES * (size_t)batch);
     L.inst = take(sizeof(InstDev) * (size_t)batch);
     L.tw = take(sizeof(float4) * (size_t)(ksum));
+    L.twx = take(sizeof(float4) * (size_t)(ksum));
     L.coord = take(sizeof(double) * (size_t)ksum);
     L.obs_part = take(sizeof(double) * 3 * (size_t)L.obs_blocks * (size_t)batch);
     L.obs_res = take(sizeof(double) * 3 * (size_t)batch);
@@ -110,6 +111,8 @@ struct qhd_ctx {
     double *samples = nullptr;
     InstDev *inst = nullptr;
     float4 *tw[3] = {nullptr, nullptr, nullptr};
+    float4 *twx = nullptr;  // exchange twiddles of the cluster-distributed axis
+    int plane_mode = 0;     // 0 generic passes, 2 whole-run 2-D clusters, 3 3-D plane pass
     double *coord = nullptr;
     double *obs_part = nullptr, *obs_res = nullptr;
     MinMaxPart *mm = nullptr;
@@ -298,6 +301,29 @@ qhd_status qhd_init_grid(qhd_ctx **out, int ndim, const int64_t *n, const double
                     make_float4(hr, hi, (float)(cr - (double)hr), (float)(ci - (double)hi));
             }
     }
+    // cluster plane engine: 2-D grids with both axes in 32..256 stay resident in
+    // one cluster per instance; 3-D grids whose last two axes fit use plane passes
+    c->twx = (float4 *)(c->work + L.twx);
+    int dist_axis = -1;
+    if (ndim == 2 && plane_supported((int)n[0], (int)n[1])) {
+        c->plane_mode = 2;
+        dist_axis = 0;
+    } else if (ndim == 3 && plane_supported((int)n[1], (int)n[2])) {
+        c->plane_mode = 3;
+        dist_axis = 1;
+    }
+    std::vector<float4> twx((size_t)c->ksum, make_float4(0.f, 0.f, 0.f, 0.f));
+    if (dist_axis >= 0) {
+        const int n1 = (int)n[dist_axis], cc = plane_cluster(n1), rr = n1 / cc;
+        for (int q = 0; q < cc; ++q)
+            for (int j = 0; j < rr; ++j) {
+                const double ang = 2.0 * 3.141592653589793238462643383279502884 * (double)(((int64_t)j * q) % n1) /
+                                   (double)n1;
+                const double cr = cos(ang), ci = -sin(ang);
+                const float hr = (float)cr, hi = (float)ci;
+                twx[(size_t)(q * rr + j)] = make_float4(hr, hi, (float)(cr - (double)hr), (float)(ci - (double)hi));
+            }
+    }
     // mesh coordinates x = lo + (j (hi - lo)) / N
     c->coord_host.resize((size_t)c->ksum);
     for (int d = 0; d < ndim; ++d)
@@ -306,6 +332,8 @@ qhd_status qhd_init_grid(qhd_ctx **out, int ndim, const int64_t *n, const double
 
     cudaError_t e = cudaMemcpyAsync(c->work + L.tw, tw.data(), tw.size() * sizeof(float4),
                                     cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->twx, twx.data(), twx.size() * sizeof(float4), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(c->coord, c->coord_host.data(), c->coord_host.size() * sizeof(double),
                             cudaMemcpyHostToDevice, c->stream);
@@ -528,6 +556,23 @@ qhd_status qhd_evolve(qhd_ctx *c, double T, double dt) {
             QHD_LAUNCH(c, launch_oned((int)c->n[0], o, c->stream));
             continue;
         }
+        if (c->plane_mode == 2) {
+            PlaneArgs w{};
+            w.psi = c->psi;
+            w.fq = c->fq;
+            w.pot = c->pot;
+            w.kt = c->kt;
+            w.tw_row = c->tw[1];
+            w.twx = c->twx;
+            w.batch = B;
+            w.cnt = (int)cnt;
+            w.final_phase = last_chunk ? 1 : 0;
+            w.ksum = c->ksum;
+            w.dither_base = (uint64_t)(c->steps_done + j0);
+            TimedScope ts(c, QHD_KCLASS_WHOLE, true);
+            QHD_LAUNCH(c, launch_plane_whole((int)c->n[0], (int)c->n[1], w, c->stream));
+            continue;
+        }
         const int last_ax = ndim - 1;
         RowArgs r{};
         r.psi = c->psi;
@@ -546,6 +591,19 @@ qhd_status qhd_evolve(qhd_ctx *c, double T, double dt) {
         ax0.log_n2 = ndim == 3 ? (int)std::log2((double)c->n[2]) : 0;
         ax0.ndim = ndim;
         ax0.mode = MODE_FWD | MODE_KIN | MODE_INV;
+        PlaneArgs pl{};
+        if (c->plane_mode == 3) {
+            pl.psi = c->psi;
+            pl.fq = c->fq;
+            pl.tw_row = c->tw[2];
+            pl.twx = c->twx;
+            pl.planes = B * c->n[0];
+            pl.planes_per_inst = c->n[0];
+            pl.batch = B;
+            const int cc = plane_cluster((int)c->n[1]);
+            ax0.perm1_r = (int)c->n[1] / cc;
+            ax0.perm1_c = cc;
+        }
         AxisArgs ax1{};
         if (ndim == 3) {
             ax1.psi = c->psi;
@@ -559,6 +617,21 @@ qhd_status qhd_evolve(qhd_ctx *c, double T, double dt) {
             const bool sample = c->timing_every > 0 && j % c->timing_every == 0;
             // row pass before step j: inverse transform of the previous step
             // (if any), merged potential phase theta_j, forward transform
+            if (c->plane_mode == 3) {
+                // plane pass over axes 1, 2 (inverse of the previous step, potential
+                // phase, forward), then the axis-0 pass with the kinetic phase
+                pl.pot = c->pot + jl * B;
+                pl.mode = (j == 0 ? 0 : MODE_INV) | MODE_FWD;
+                pl.dither = step_dither((uint64_t)(c->steps_done + j));
+                {
+                    TimedScope ts(c, QHD_KCLASS_PLANE, sample);
+                    QHD_LAUNCH(c, launch_plane_pass((int)c->n[1], (int)c->n[2], pl, c->stream));
+                }
+                ax0.kt = c->kt + jl * B * c->ksum;
+                TimedScope ts(c, QHD_KCLASS_AXIS0, sample);
+                QHD_LAUNCH(c, launch_axis((int)c->n[0], ax0, c->stream));
+                continue;
+            }
             r.pot = c->pot + jl * B;
             r.mode = (j == 0 ? 0 : MODE_INV) | MODE_FWD;
             r.dither = step_dither((uint64_t)(c->steps_done + j));
@@ -583,10 +656,17 @@ qhd_status qhd_evolve(qhd_ctx *c, double T, double dt) {
             }
         }
         if (last_chunk) {
-            r.pot = c->pot + cnt * B;
-            r.mode = MODE_INV;
-            r.dither = 0;
-            QHD_LAUNCH(c, launch_row((int)c->n[last_ax], r, c->stream));
+            if (c->plane_mode == 3) {
+                pl.pot = c->pot + cnt * B;
+                pl.mode = MODE_INV;
+                pl.dither = 0;
+                QHD_LAUNCH(c, launch_plane_pass((int)c->n[1], (int)c->n[2], pl, c->stream));
+            } else {
+                r.pot = c->pot + cnt * B;
+                r.mode = MODE_INV;
+                r.dither = 0;
+                QHD_LAUNCH(c, launch_row((int)c->n[last_ax], r, c->stream));
+            }
         }
     }
     c->t = c->t + (double)nsteps * dt;

@@ -101,7 +101,9 @@ __global__ void __launch_bounds__(W * LineCfg<N>::T) k_axis(AxisArgs a) {
         // is shared by every point with the same frequency index, so a plain
         // FP32 rounding of it would perturb the norm coherently.
         const float4 *kb = a.kt + o * a.ksum;
-        const float4 k1 = __ldg(&kb[a.koff1 + (a.ndim == 2 ? ci : (ci >> a.log_n2))]);
+        int64_t i1 = a.ndim == 2 ? ci : (ci >> a.log_n2);
+        if (a.perm1_r) i1 = i1 / a.perm1_r + (int64_t)a.perm1_c * (i1 % a.perm1_r);
+        const float4 k1 = __ldg(&kb[a.koff1 + i1]);
         float4 k2 = make_float4(1.f, 0.f, 0.f, 0.f);
         if (a.ndim == 3) k2 = __ldg(&kb[a.koff2 + (ci & ((1 << a.log_n2) - 1))]);
 #pragma unroll

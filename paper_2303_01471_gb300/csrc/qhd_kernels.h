@@ -54,6 +54,27 @@ struct AxisArgs {
     int log_n2;            // log2 n[2] (3-D only)
     int ndim;
     int mode;
+    int perm1_r, perm1_c;  // 3-D after a plane pass: stored axis-1 row s holds
+                           // frequency s / perm1_r + perm1_c * (s % perm1_r); 0 = natural
+};
+
+// Plane engine (qhd_plane.cu): N1 distributed over a cluster, N2 per row.
+struct PlaneArgs {
+    float2 *psi;
+    const uint32_t *fq;
+    const uint64_t *pot;     // pass: coefficients of this pass [batch]; whole: chunk [cnt+1][batch]
+    const float4 *kt;        // whole: chunk kinetic tables [cnt][batch][ksum]
+    const float4 *tw_row;    // stage-2 twiddles of the row length
+    const float4 *twx;       // exchange twiddles twx[q*R + n2] = exp(-2 pi i n2 q / N1), (hi, lo)
+    int64_t planes;          // pass: batch * n0 planes
+    int64_t planes_per_inst; // pass: n0
+    int64_t batch;
+    int mode;                // pass: MODE_INV (previous step's inverse first), MODE_FWD
+    uint32_t dither;         // pass: global phase of this step
+    int cnt;                 // whole: steps in the chunk
+    int final_phase;         // whole: apply pot[cnt] at the end
+    int ksum;
+    uint64_t dither_base;    // whole: global index of the chunk's first step
 };
 
 struct OneDArgs {
@@ -111,6 +132,10 @@ cudaError_t launch_minmax(const double *f, int64_t g, int64_t batch, MinMaxPart 
 cudaError_t launch_quantize(const double *f, uint32_t *fq, const InstDev *inst, int64_t g,
                             int64_t batch, cudaStream_t s);
 cudaError_t launch_observables(const ObsArgs &a, int64_t batch, cudaStream_t s);
+cudaError_t launch_plane_pass(int n1, int n2, const PlaneArgs &a, cudaStream_t s);
+cudaError_t launch_plane_whole(int n1, int n2, const PlaneArgs &a, cudaStream_t s);
+bool plane_supported(int n1, int n2);
+int plane_cluster(int n1);
 
 // Plans shared with the host (twiddle tables are built on the host).
 void plan_of(int n, int *r1, int *r2);

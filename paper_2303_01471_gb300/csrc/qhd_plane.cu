@@ -1,0 +1,161 @@
+// qhd_plane.cu -- kernels built on the cluster-resident plane engine.
+//
+// k_plane_pass: one fused pass over the last two axes of a 3-D grid (for
+//   every (instance, i0) plane): inverse transform of the previous step along
+//   axes 2 and 1, potential phase, forward transform along axes 1 and 2.  With
+//   the axis-0 pass (forward, kinetic phase, inverse) a 3-D Strang step then
+//   reads and writes psi twice instead of four times.
+// k_plane_whole: a whole 2-D instance resident in one cluster for every step
+//   of a chunk: per step the cross-cluster exchange with the potential phase,
+//   then the local transforms with the kinetic phase in between.  psi touches
+//   global memory only at the chunk's start and end.
+#include "qhd_kernels.h"
+#include "qhd_plane.cuh"
+
+namespace qhd {
+
+template <int N1, int N2, int C>
+__global__ void __launch_bounds__(PLANE_THREADS) k_plane_pass(PlaneArgs a) {
+    using P = PlaneCfg<N1, N2, C>;
+    extern __shared__ __align__(16) float2 tile[];
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    const int64_t plane = blockIdx.x / C;
+    float2 *tiles[C];
+#pragma unroll
+    for (int q = 0; q < C; ++q) tiles[q] = cluster.map_shared_rank(tile, q);
+    float2 *g = a.psi + plane * (int64_t)N1 * N2 + (int64_t)rank * P::R * N2;
+    const bool inv = a.mode & MODE_INV, fwd = a.mode & MODE_FWD;
+
+    plane_copy<N1, N2, C, true>(tile, g);
+    __syncthreads();
+    if (inv) {
+        plane_rows<N1, N2, C, 1>(tile, a.tw_row, nullptr, nullptr, rank);
+        __syncthreads();
+        plane_columns<N1, N2, C, true>(tile);
+    }
+    cluster.sync();
+    const uint64_t coef = a.pot[plane / a.planes_per_inst];
+    plane_exchange<N1, N2, C>(tiles, rank, inv, true, fwd, a.twx, a.fq + plane * (int64_t)N1 * N2, coef, a.dither);
+    cluster.sync();
+    if (fwd) {
+        plane_columns<N1, N2, C, false>(tile);
+        __syncthreads();
+        plane_rows<N1, N2, C, 0>(tile, a.tw_row, nullptr, nullptr, rank);
+        __syncthreads();
+    }
+    plane_copy<N1, N2, C, false>(tile, g);
+}
+
+template <int N1, int N2, int C>
+__global__ void __launch_bounds__(PLANE_THREADS) k_plane_whole(PlaneArgs a) {
+    using P = PlaneCfg<N1, N2, C>;
+    extern __shared__ __align__(16) float2 tile[];
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    const int64_t b = blockIdx.x / C;  // instance
+    float2 *tiles[C];
+#pragma unroll
+    for (int q = 0; q < C; ++q) tiles[q] = cluster.map_shared_rank(tile, q);
+    float2 *g = a.psi + b * (int64_t)N1 * N2 + (int64_t)rank * P::R * N2;
+    const uint32_t *fq = a.fq + b * (int64_t)N1 * N2;
+
+    plane_copy<N1, N2, C, true>(tile, g);
+    cluster.sync();
+#pragma unroll 1
+    for (int j = 0; j < a.cnt; ++j) {
+        const uint64_t coef = a.pot[(int64_t)j * a.batch + b];
+        plane_exchange<N1, N2, C>(tiles, rank, j > 0, true, true, a.twx, fq, coef,
+                                  step_dither(a.dither_base + (uint64_t)j));
+        cluster.sync();
+        plane_columns<N1, N2, C, false>(tile);
+        __syncthreads();
+        const float4 *kb = a.kt + ((int64_t)j * a.batch + b) * a.ksum;
+        plane_rows<N1, N2, C, 2>(tile, a.tw_row, kb, kb + N1, rank);
+        __syncthreads();
+        plane_columns<N1, N2, C, true>(tile);
+        cluster.sync();
+    }
+    const uint64_t coef = a.pot[(int64_t)a.cnt * a.batch + b];
+    plane_exchange<N1, N2, C>(tiles, rank, a.cnt > 0, a.final_phase != 0, false, a.twx, fq, coef, 0u);
+    cluster.sync();
+    plane_copy<N1, N2, C, false>(tile, g);
+}
+
+// ---------------------------------------------------------------- launchers
+template <typename K>
+static cudaError_t launch_cluster(K kernel, int64_t clusters, int c, size_t smem, const PlaneArgs &a,
+                                  cudaStream_t s, bool &attr_done) {
+    if (!attr_done) {
+        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_done = true;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(clusters * c), 1, 1);
+    cfg.blockDim = dim3(PLANE_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)c;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, a);
+}
+
+// The shared-memory attribute is a per-device property of the kernel; it is set
+// on the first launch of each instantiation (one device per process here).
+template <int N1, int N2, int C>
+static cudaError_t plane_pass_impl(const PlaneArgs &a, cudaStream_t s) {
+    static bool attr_done = false;
+    return launch_cluster(k_plane_pass<N1, N2, C>, a.planes, C, PlaneCfg<N1, N2, C>::SMEM, a, s, attr_done);
+}
+
+template <int N1, int N2, int C>
+static cudaError_t plane_whole_impl(const PlaneArgs &a, cudaStream_t s) {
+    static bool attr_done = false;
+    return launch_cluster(k_plane_whole<N1, N2, C>, a.batch, C, PlaneCfg<N1, N2, C>::SMEM, a, s, attr_done);
+}
+
+// Cluster size per distributed-axis length: R = 32 rows per CTA (16 for 32).
+__host__ __device__ constexpr int plane_c(int n1) { return n1 >= 256 ? 8 : n1 >= 128 ? 4 : n1 >= 64 ? 2 : n1 >= 32 ? 2 : 0; }
+
+bool plane_supported(int n1, int n2) {
+    return (n1 == 32 || n1 == 64 || n1 == 128 || n1 == 256) && (n2 == 32 || n2 == 64 || n2 == 128 || n2 == 256);
+}
+
+int plane_cluster(int n1) { return plane_c(n1); }
+
+#define QHD_PLANE_DISPATCH(fn)                                                        \
+    switch (n1 * 1000 + n2) {                                                         \
+    case 32032: return fn<32, 32, plane_c(32)>(a, s);                                 \
+    case 32064: return fn<32, 64, plane_c(32)>(a, s);                                 \
+    case 32128: return fn<32, 128, plane_c(32)>(a, s);                                \
+    case 32256: return fn<32, 256, plane_c(32)>(a, s);                                \
+    case 64032: return fn<64, 32, plane_c(64)>(a, s);                                 \
+    case 64064: return fn<64, 64, plane_c(64)>(a, s);                                 \
+    case 64128: return fn<64, 128, plane_c(64)>(a, s);                                \
+    case 64256: return fn<64, 256, plane_c(64)>(a, s);                                \
+    case 128032: return fn<128, 32, plane_c(128)>(a, s);                              \
+    case 128064: return fn<128, 64, plane_c(128)>(a, s);                              \
+    case 128128: return fn<128, 128, plane_c(128)>(a, s);                             \
+    case 128256: return fn<128, 256, plane_c(128)>(a, s);                             \
+    case 256032: return fn<256, 32, plane_c(256)>(a, s);                              \
+    case 256064: return fn<256, 64, plane_c(256)>(a, s);                              \
+    case 256128: return fn<256, 128, plane_c(256)>(a, s);                             \
+    case 256256: return fn<256, 256, plane_c(256)>(a, s);                             \
+    default: return cudaErrorInvalidValue;                                            \
+    }
+
+cudaError_t launch_plane_pass(int n1, int n2, const PlaneArgs &a, cudaStream_t s) {
+    QHD_PLANE_DISPATCH(plane_pass_impl)
+}
+
+cudaError_t launch_plane_whole(int n1, int n2, const PlaneArgs &a, cudaStream_t s) {
+    QHD_PLANE_DISPATCH(plane_whole_impl)
+}
+
+}  // namespace qhd

@@ -1,0 +1,161 @@
+// qhd_plane.cuh -- cluster-resident plane engine.
+//
+// A plane of N1 x N2 points (the last two axes of a 3-D grid for one index of
+// axis 0, or a whole 2-D instance) is held in the shared memory of a cluster of
+// C CTAs: CTA r owns R = N1 / C consecutive rows.  The row transforms (axis of
+// length N2) run locally with the line engine; the transform along the
+// distributed axis is a four-step factorisation N1 = C * R:
+//
+//   forward  y[k1][n2] = W_N1^{n2 k1} sum_{n1} x[R n1 + n2] W_C^{n1 k1}   (across the cluster)
+//            X[k1 + C k2] = sum_{n2} y[k1][n2] W_R^{n2 k2}                 (local, CTA k1, row k2)
+//   inverse  the same two steps in reverse order with conjugate factors.
+//
+// So in Fourier space CTA r's local row k2 holds frequency r + C k2 along the
+// distributed axis.  The cross-cluster step reads the C values at one local
+// position (n2, c) from every CTA through distributed shared memory, and one
+// thread owns each position cluster-wide, so the inverse step, the potential
+// phase (diagonal in position space) and the forward step are fused with no
+// barrier between them: two cluster barriers per Strang step.
+#pragma once
+#include <cooperative_groups.h>
+
+#include "qhd_device.cuh"
+
+namespace qhd {
+
+namespace cg = cooperative_groups;
+
+constexpr int PLANE_THREADS = 256;
+
+template <int N1, int N2, int C> struct PlaneCfg {
+    static constexpr int R = N1 / C;                      // rows per CTA
+    using RowC = LineCfg<N2>;
+    static constexpr int S = line_stride<N2>(true, 0);     // row stride in float2 (>= padded row)
+    static constexpr int T2 = RowC::T, E2 = RowC::E;
+    static constexpr int ROWS_PER_ITER = PLANE_THREADS / T2;
+    static constexpr int PAIRS = (R / C) * N2;            // exchange positions owned per CTA
+    static constexpr size_t SMEM = (size_t)R * S * sizeof(float2);
+    static_assert(RowC::TWO_STAGE, "rows of at least 32 points");
+    static_assert(N1 % C == 0 && R % C == 0, "R rows per CTA, R/C exchange rows per CTA");
+    static_assert(N2 <= PLANE_THREADS, "one thread per column in the column phase");
+    static_assert(R <= 32, "local column transform held in registers");
+    static_assert((R * T2) % 32 == 0, "whole warps in the row phase");
+    static_assert(S % 2 == 0, "16-byte aligned rows");
+};
+
+// Global <-> shared copy of this CTA's R rows (contiguous in global memory).
+template <int N1, int N2, int C, bool TO_SHARED>
+__device__ __forceinline__ void plane_copy(float2 *tile, float2 *g) {
+    using P = PlaneCfg<N1, N2, C>;
+    constexpr int Q = P::R * N2 / 2;  // float4 chunks
+    for (int i = threadIdx.x; i < Q; i += PLANE_THREADS) {
+        const int row = (2 * i) / N2, col = (2 * i) % N2;
+        float4 *s = reinterpret_cast<float4 *>(tile + row * P::S + col);
+        float4 *d = reinterpret_cast<float4 *>(g + (int64_t)row * N2 + col);
+        if (TO_SHARED) *s = *d;
+        else *d = *s;
+    }
+}
+
+// Local transform along the distributed axis: each column of the CTA's R rows.
+template <int N1, int N2, int C, bool INV>
+__device__ __forceinline__ void plane_columns(float2 *tile) {
+    using P = PlaneCfg<N1, N2, C>;
+    const int c = threadIdx.x;
+    if (c < N2) {
+        float2 v[P::R];
+#pragma unroll
+        for (int r = 0; r < P::R; ++r) v[r] = tile[r * P::S + c];
+        dft<P::R, INV>(v);
+#pragma unroll
+        for (int r = 0; r < P::R; ++r) tile[r * P::S + c] = v[r];
+    }
+}
+
+// Row transforms along N2.  KIN: forward, kinetic phase, inverse (2-D whole
+// run); otherwise one direction.  The row's own storage is the exchange buffer
+// of the line engine (its content is in registers at that point).
+struct WarpSyncP {
+    __device__ __forceinline__ void operator()() const { __syncwarp(); }
+};
+
+template <int N1, int N2, int C, int DIR>  // DIR: 0 forward, 1 inverse, 2 forward-kinetic-inverse
+__device__ __forceinline__ void plane_rows(float2 *tile, const float4 *__restrict__ tw_row, const float4 *kt0,
+                                           const float4 *kt1, int rank) {
+    using P = PlaneCfg<N1, N2, C>;
+    constexpr int T2 = P::T2, E2 = P::E2;
+    const int t = threadIdx.x % T2;
+#pragma unroll 1
+    for (int base = 0; base < P::R; base += P::ROWS_PER_ITER) {
+        const int row = base + threadIdx.x / T2;
+        if (row < P::R) {
+            float2 *rp = tile + row * P::S;
+            float2 x[E2];
+#pragma unroll
+            for (int e = 0; e < E2; ++e) x[e] = rp[t + T2 * e];
+            __syncwarp();
+            if (DIR == 1) {
+                line_fft<N2, true>(x, rp, t, tw_row, WarpSyncP{});
+            } else {
+                line_fft<N2, false>(x, rp, t, tw_row, WarpSyncP{});
+                if (DIR == 2) {
+                    // this local row holds frequency rank + C * row along the distributed axis
+                    const float4 k0 = __ldg(&kt0[rank + C * row]);
+#pragma unroll
+                    for (int e = 0; e < E2; ++e) {
+                        const float4 k1 = __ldg(&kt1[t + T2 * e]);
+                        float2 y = cmul_comp(x[e], make_float2(k0.x, k0.y), make_float2(k0.z, k0.w));
+                        x[e] = cmul_comp(y, make_float2(k1.x, k1.y), make_float2(k1.z, k1.w));
+                    }
+                    line_fft<N2, true>(x, rp, t, tw_row, WarpSyncP{});
+                }
+            }
+#pragma unroll
+            for (int e = 0; e < E2; ++e) rp[t + T2 * e] = x[e];
+        }
+    }
+}
+
+// The cross-cluster step at the positions this CTA owns: optional inverse
+// four-step half, potential phase, optional forward half.  tiles[q] is CTA
+// q's tile in the distributed shared-memory window.
+template <int N1, int N2, int C>
+__device__ __forceinline__ void plane_exchange(float2 *const *tiles, int rank, bool inv, bool phase, bool fwd,
+                                               const float4 *__restrict__ twx, const uint32_t *__restrict__ fq,
+                                               uint64_t coef, uint32_t dither) {
+    using P = PlaneCfg<N1, N2, C>;
+    constexpr int R = P::R;
+#pragma unroll 1
+    for (int p = threadIdx.x; p < P::PAIRS; p += PLANE_THREADS) {
+        const int n2 = rank * (R / C) + p / N2;
+        const int c = p % N2;
+        float2 v[C];
+#pragma unroll
+        for (int q = 0; q < C; ++q) v[q] = tiles[q][n2 * P::S + c];
+        if (inv) {
+#pragma unroll
+            for (int q = 1; q < C; ++q) {
+                const float4 w = __ldg(&twx[q * R + n2]);
+                v[q] = cmulc_comp(v[q], make_float2(w.x, w.y), make_float2(w.z, w.w));
+            }
+            dft<C, true>(v);
+        }
+        if (phase) {
+#pragma unroll
+            for (int q = 0; q < C; ++q)
+                v[q] = apply_phase_turns(v[q], turns_mul(coef, __ldg(&fq[(R * q + n2) * N2 + c])) + dither);
+        }
+        if (fwd) {
+            dft<C, false>(v);
+#pragma unroll
+            for (int q = 1; q < C; ++q) {
+                const float4 w = __ldg(&twx[q * R + n2]);
+                v[q] = cmul_comp(v[q], make_float2(w.x, w.y), make_float2(w.z, w.w));
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < C; ++q) tiles[q][n2 * P::S + c] = v[q];
+    }
+}
+
+}  // namespace qhd

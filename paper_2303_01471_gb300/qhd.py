@@ -27,7 +27,7 @@ EXPORTS = ["qhd_workspace_bytes", "qhd_init_grid", "qhd_set_potential", "qhd_set
            "qhd_set_schedule", "qhd_reset_state", "qhd_set_time", "qhd_get_time", "qhd_evolve",
            "qhd_observables", "qhd_launch_count", "qhd_timing_enable", "qhd_timing_read",
            "qhd_destroy", "qhd_status_string", "qhd_last_error", "qhd_observables_static"]
-KCLASS = ["prep", "row", "axis1_fwd", "axis0", "axis1_inv", "oned"]
+KCLASS = ["prep", "row", "axis1_fwd", "axis0", "axis1_inv", "oned", "plane", "whole"]
 
 
 class QHDError(RuntimeError):

@@ -85,9 +85,15 @@ def compare(psi_g, obs_g, f, psi_o, lo=0.0, hi=1.0, steps=None, elementwise=True
 # ------------------------------------------------- every line length, 1..3-D
 
 SHAPES = [(2,), (4,), (8,), (16,), (32,), (64,), (128,), (256,), (512,), (1024,),
-          (2, 2), (4, 8), (8, 4), (16, 16), (32, 64), (64, 32), (128, 128), (256, 16),
-          (16, 512), (1024, 4), (4, 1024), (2, 1024),
-          (2, 2, 2), (4, 8, 16), (16, 8, 4), (32, 32, 32), (8, 64, 2), (2, 4, 256), (64, 16, 128)]
+          # generic row + column passes
+          (2, 2), (4, 8), (8, 4), (16, 16), (256, 16), (16, 512), (1024, 4), (4, 1024), (2, 1024),
+          (512, 64), (1024, 32),
+          # 2-D instance resident in one cluster (both axes in 32..256)
+          (32, 32), (32, 64), (64, 32), (128, 128), (256, 256), (128, 256), (256, 32), (32, 256), (64, 128),
+          # 3-D generic passes
+          (2, 2, 2), (4, 8, 16), (16, 8, 4), (8, 64, 2), (2, 4, 256), (64, 16, 128),
+          # 3-D plane pass over the last two axes + axis-0 pass
+          (32, 32, 32), (2, 256, 256), (4, 64, 128), (8, 128, 32), (16, 32, 64), (4, 256, 64)]
 
 
 @pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "x".join(map(str, s)))
@@ -114,8 +120,8 @@ def test_parity_nonunit_box_and_table_schedule():
     compare(psi_g, obs[0], inst.f, psi_o, lo=np.array(lo), hi=np.array(hi), steps=n)
 
 
-def test_parity_batch_with_own_f_and_schedule():
-    shape = (32, 32)
+@pytest.mark.parametrize("shape", [(32, 32), (16, 16), (8, 64, 32)], ids=lambda s: "x".join(map(str, s)))
+def test_parity_batch_with_own_f_and_schedule(shape):
     insts = [workloads.make(fam, s, shape, draw_sigma=True)
              for fam, s in [("wells", 1), ("rastrigin", 2), ("wells", 3)]]
     fb = np.stack([i.f for i in insts])
@@ -274,12 +280,18 @@ def test_error_paths():
     sim.close()
 
 
-def test_launch_count_accounting():
-    sim = qhd.QHD((64, 64))
-    sim.set_potential(np.zeros((64, 64)))
+@pytest.mark.parametrize("shape,launches", [
+    ((1024, 64), 1 + 11 + 10),        # prep + row passes + axis-0 passes
+    ((64, 64), 1 + 1),                # prep + one cluster-resident launch for all steps
+    ((4, 8, 16), 1 + 11 + 3 * 10),    # prep + x passes + (y, z, y) per step
+    ((4, 32, 32), 1 + 11 + 10),       # prep + plane passes + axis-0 passes
+])
+def test_launch_count_accounting(shape, launches):
+    sim = qhd.QHD(shape)
+    sim.set_potential(np.zeros(shape))
     sim.set_schedule(qhd.Schedule())
     sim.reset_state()
     before = sim.launch_count()
-    sim.evolve(0.1, 0.01)   # 10 steps: 1 prep + 11 row + 10 axis launches
-    assert sim.launch_count() - before == 1 + 11 + 10
+    sim.evolve(0.1, 0.01)   # 10 steps
+    assert sim.launch_count() - before == launches
     sim.close()
