@@ -28,15 +28,17 @@ __global__ void __launch_bounds__(PLANE_THREADS) k_plane_pass(PlaneArgs a) {
     const bool inv = a.mode & MODE_INV, fwd = a.mode & MODE_FWD;
 
     plane_copy<N1, N2, C, true>(tile, g);
-    __syncthreads();
+    PlaneFq<N1, N2, C> fqr;
+    plane_load_fq<N1, N2, C>(fqr, a.fq + plane * (int64_t)N1 * N2, rank);
+    const uint64_t coef = a.pot[plane / a.planes_per_inst];
+    plane_copy_wait();
     if (inv) {
         plane_rows<N1, N2, C, 1>(tile, a.tw_row, nullptr, nullptr, rank);
         __syncthreads();
         plane_columns<N1, N2, C, true>(tile);
     }
     cluster.sync();
-    const uint64_t coef = a.pot[plane / a.planes_per_inst];
-    plane_exchange<N1, N2, C>(tiles, rank, inv, true, fwd, a.twx, a.fq + plane * (int64_t)N1 * N2, coef, a.dither);
+    plane_exchange<N1, N2, C>(tiles, rank, inv, true, fwd, a.twx, fqr, coef, a.dither);
     cluster.sync();
     if (fwd) {
         plane_columns<N1, N2, C, false>(tile);
@@ -58,14 +60,14 @@ __global__ void __launch_bounds__(PLANE_THREADS) k_plane_whole(PlaneArgs a) {
 #pragma unroll
     for (int q = 0; q < C; ++q) tiles[q] = cluster.map_shared_rank(tile, q);
     float2 *g = a.psi + b * (int64_t)N1 * N2 + (int64_t)rank * P::R * N2;
-    const uint32_t *fq = a.fq + b * (int64_t)N1 * N2;
-
+    const uint32_t *fqr = a.fq + b * (int64_t)N1 * N2;
     plane_copy<N1, N2, C, true>(tile, g);
+    plane_copy_wait();
     cluster.sync();
 #pragma unroll 1
     for (int j = 0; j < a.cnt; ++j) {
         const uint64_t coef = a.pot[(int64_t)j * a.batch + b];
-        plane_exchange<N1, N2, C>(tiles, rank, j > 0, true, true, a.twx, fq, coef,
+        plane_exchange<N1, N2, C>(tiles, rank, j > 0, true, true, a.twx, fqr, coef,
                                   step_dither(a.dither_base + (uint64_t)j));
         cluster.sync();
         plane_columns<N1, N2, C, false>(tile);
@@ -77,7 +79,7 @@ __global__ void __launch_bounds__(PLANE_THREADS) k_plane_whole(PlaneArgs a) {
         cluster.sync();
     }
     const uint64_t coef = a.pot[(int64_t)a.cnt * a.batch + b];
-    plane_exchange<N1, N2, C>(tiles, rank, a.cnt > 0, a.final_phase != 0, false, a.twx, fq, coef, 0u);
+    plane_exchange<N1, N2, C>(tiles, rank, a.cnt > 0, a.final_phase != 0, false, a.twx, fqr, coef, 0u);
     cluster.sync();
     plane_copy<N1, N2, C, false>(tile, g);
 }

@@ -18,6 +18,7 @@
 // barrier between them: two cluster barriers per Strang step.
 #pragma once
 #include <cooperative_groups.h>
+#include <type_traits>
 
 #include "qhd_device.cuh"
 
@@ -44,17 +45,30 @@ template <int N1, int N2, int C> struct PlaneCfg {
 };
 
 // Global <-> shared copy of this CTA's R rows (contiguous in global memory).
+// Global -> shared uses 16-byte asynchronous copies so that the whole tile is
+// in flight at once; the caller waits with plane_copy_wait().
 template <int N1, int N2, int C, bool TO_SHARED>
 __device__ __forceinline__ void plane_copy(float2 *tile, float2 *g) {
     using P = PlaneCfg<N1, N2, C>;
     constexpr int Q = P::R * N2 / 2;  // float4 chunks
+#pragma unroll 4
     for (int i = threadIdx.x; i < Q; i += PLANE_THREADS) {
         const int row = (2 * i) / N2, col = (2 * i) % N2;
-        float4 *s = reinterpret_cast<float4 *>(tile + row * P::S + col);
-        float4 *d = reinterpret_cast<float4 *>(g + (int64_t)row * N2 + col);
-        if (TO_SHARED) *s = *d;
-        else *d = *s;
+        float2 *s = tile + row * P::S + col;
+        float2 *d = g + (int64_t)row * N2 + col;
+        if (TO_SHARED) {
+            const unsigned sa = (unsigned)__cvta_generic_to_shared(s);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(d) : "memory");
+        } else {
+            *reinterpret_cast<float4 *>(d) = *reinterpret_cast<const float4 *>(s);
+        }
     }
+    if (TO_SHARED) asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void plane_copy_wait() {
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    __syncthreads();
 }
 
 // Local transform along the distributed axis: each column of the CTA's R rows.
@@ -119,42 +133,93 @@ __device__ __forceinline__ void plane_rows(float2 *tile, const float4 *__restric
 // The cross-cluster step at the positions this CTA owns: optional inverse
 // four-step half, potential phase, optional forward half.  tiles[q] is CTA
 // q's tile in the distributed shared-memory window.
+// Fixed-point potential at the positions this thread owns in the exchange
+// (PAIRS_PER_THREAD positions x C rows), loaded once into registers.
+template <int N1, int N2, int C> struct PlaneFq {
+    static constexpr int PPT = (PlaneCfg<N1, N2, C>::PAIRS + PLANE_THREADS - 1) / PLANE_THREADS;
+    uint32_t v[PPT][C];
+};
+
 template <int N1, int N2, int C>
-__device__ __forceinline__ void plane_exchange(float2 *const *tiles, int rank, bool inv, bool phase, bool fwd,
-                                               const float4 *__restrict__ twx, const uint32_t *__restrict__ fq,
-                                               uint64_t coef, uint32_t dither) {
+__device__ __forceinline__ void plane_load_fq(PlaneFq<N1, N2, C> &f, const uint32_t *__restrict__ fq, int rank) {
     using P = PlaneCfg<N1, N2, C>;
     constexpr int R = P::R;
+#pragma unroll
+    for (int k = 0; k < PlaneFq<N1, N2, C>::PPT; ++k) {
+        const int p = threadIdx.x + k * PLANE_THREADS;
+        const int pp = p < P::PAIRS ? p : 0;
+        const int n2 = rank * (R / C) + pp / N2, c = pp % N2;
+#pragma unroll
+        for (int q = 0; q < C; ++q) f.v[k][q] = __ldg(&fq[(R * q + n2) * N2 + c]);
+    }
+}
+
+// FQ is either PlaneFq (values prefetched into registers, for a single pass)
+// or a const uint32_t * to the plane's fixed-point potential (read through the
+// cache each step, for the whole-run kernel, where registers are scarcer).
+template <int N1, int N2, int C> __device__ __forceinline__ uint32_t fq_at(const PlaneFq<N1, N2, C> &f, int k, int q,
+                                                                          int, int) {
+    return f.v[k][q];
+}
+template <int N1, int N2, int C> __device__ __forceinline__ uint32_t fq_at(const uint32_t *f, int, int q, int n2,
+                                                                          int c) {
+    return __ldg(&f[(PlaneCfg<N1, N2, C>::R * q + n2) * N2 + c]);
+}
+
+template <int N1, int N2, int C, typename FQ>
+__device__ __forceinline__ void plane_exchange_at(float2 *const *tiles, int rank, int k, int p, bool inv, bool phase,
+                                                  bool fwd, const float4 *__restrict__ twx, const FQ &fqr,
+                                                  uint64_t coef, uint32_t dither) {
+    using P = PlaneCfg<N1, N2, C>;
+    constexpr int R = P::R;
+    const int n2 = rank * (R / C) + p / N2;
+    const int c = p % N2;
+    float2 v[C];
+#pragma unroll
+    for (int q = 0; q < C; ++q) v[q] = tiles[q][n2 * P::S + c];
+    if (inv) {
+#pragma unroll
+        for (int q = 1; q < C; ++q) {
+            const float4 w = __ldg(&twx[q * R + n2]);
+            v[q] = cmulc_comp(v[q], make_float2(w.x, w.y), make_float2(w.z, w.w));
+        }
+        dft<C, true>(v);
+    }
+    if (phase) {
+#pragma unroll
+        for (int q = 0; q < C; ++q)
+            v[q] = apply_phase_turns(v[q], turns_mul(coef, fq_at<N1, N2, C>(fqr, k, q, n2, c)) + dither);
+    }
+    if (fwd) {
+        dft<C, false>(v);
+#pragma unroll
+        for (int q = 1; q < C; ++q) {
+            const float4 w = __ldg(&twx[q * R + n2]);
+            v[q] = cmul_comp(v[q], make_float2(w.x, w.y), make_float2(w.z, w.w));
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < C; ++q) tiles[q][n2 * P::S + c] = v[q];
+}
+
+template <int N1, int N2, int C, typename FQ>
+__device__ __forceinline__ void plane_exchange(float2 *const *tiles, int rank, bool inv, bool phase, bool fwd,
+                                               const float4 *__restrict__ twx, const FQ &fqr, uint64_t coef,
+                                               uint32_t dither) {
+    using P = PlaneCfg<N1, N2, C>;
+    constexpr int PPT = PlaneFq<N1, N2, C>::PPT;
+    if constexpr (std::is_pointer<FQ>::value) {
 #pragma unroll 1
-    for (int p = threadIdx.x; p < P::PAIRS; p += PLANE_THREADS) {
-        const int n2 = rank * (R / C) + p / N2;
-        const int c = p % N2;
-        float2 v[C];
-#pragma unroll
-        for (int q = 0; q < C; ++q) v[q] = tiles[q][n2 * P::S + c];
-        if (inv) {
-#pragma unroll
-            for (int q = 1; q < C; ++q) {
-                const float4 w = __ldg(&twx[q * R + n2]);
-                v[q] = cmulc_comp(v[q], make_float2(w.x, w.y), make_float2(w.z, w.w));
-            }
-            dft<C, true>(v);
+        for (int k = 0; k < PPT; ++k) {
+            const int p = threadIdx.x + k * PLANE_THREADS;
+            if (p < P::PAIRS) plane_exchange_at<N1, N2, C>(tiles, rank, k, p, inv, phase, fwd, twx, fqr, coef, dither);
         }
-        if (phase) {
+    } else {
 #pragma unroll
-            for (int q = 0; q < C; ++q)
-                v[q] = apply_phase_turns(v[q], turns_mul(coef, __ldg(&fq[(R * q + n2) * N2 + c])) + dither);
+        for (int k = 0; k < PPT; ++k) {
+            const int p = threadIdx.x + k * PLANE_THREADS;
+            if (p < P::PAIRS) plane_exchange_at<N1, N2, C>(tiles, rank, k, p, inv, phase, fwd, twx, fqr, coef, dither);
         }
-        if (fwd) {
-            dft<C, false>(v);
-#pragma unroll
-            for (int q = 1; q < C; ++q) {
-                const float4 w = __ldg(&twx[q * R + n2]);
-                v[q] = cmul_comp(v[q], make_float2(w.x, w.y), make_float2(w.z, w.w));
-            }
-        }
-#pragma unroll
-        for (int q = 0; q < C; ++q) tiles[q][n2 * P::S + c] = v[q];
     }
 }
 
