@@ -280,56 +280,43 @@ __device__ __forceinline__ uint32_t turns_mul(uint64_t c, uint32_t v) {
     return __umulhi(lo, v) + hi * v;
 }
 
-// exp(-2 pi i u / 2^32) in FP32.
-__device__ __forceinline__ float2 phase_from_turns(uint32_t u) {
-    const float x = (float)(int32_t)u * 4.656612873077392578125e-10f;  // 2^-31: angle = pi x
-    float s, c;
-    sincospif(x, &s, &c);
-    return make_float2(c, -s);
+// Potential phase factor exp(-2 pi i u / 2^32) applied to z.
+// u = 2^24 k + r with k = round(u / 2^24) mod 256 and r in [-2^23, 2^23):
+// exp(-2 pi i u/2^32) = T[k] (1 + eps), T[k] = exp(-2 pi i k/256) an FP32
+// hi/lo pair from FP64, and eps = exp(-i delta) - 1, delta = 2 pi r / 2^32,
+// |delta| <= pi/256, from its Taylor series (truncation < 3e-12).  eps is
+// small, so it is formed in FP32 to ~1e-9 absolute and |T (1 + eps)| = 1 to
+// ~1e-9; the whole factor enters as hi + lo of one compensated product, so
+// only the product is rounded.  tab: the 256-entry table in shared memory.
+constexpr int PHASE_TAB = 256;
+
+__device__ __forceinline__ float2 apply_phase_tab(float2 z, uint32_t u, const float4 *tab) {
+    const uint32_t k = ((u + (1u << 23)) >> 24) & (PHASE_TAB - 1);
+    const int32_t r = (int32_t)(u - (k << 24));
+    const float d = (float)r * 1.4629180792671596e-09f;  // 2 pi / 2^32
+    const float d2 = d * d;
+    const float cm1 = d2 * fmaf(d2, 1.0f / 24.0f, -0.5f);  // cos d - 1
+    const float sn = d * fmaf(d2, -1.0f / 6.0f, 1.0f);     // sin d
+    const float4 t = tab[k];
+    // lo = T_lo + T_hi * eps, eps = (cm1, -sn)
+    const float2 lo = make_float2(fmaf(t.x, cm1, fmaf(t.y, sn, t.z)), fmaf(t.y, cm1, fmaf(-t.x, sn, t.w)));
+    return cmul_comp(z, make_float2(t.x, t.y), lo);
+}
+
+// Copy the phase table (global, PHASE_TAB float4) into shared memory.
+__device__ __forceinline__ void load_phase_tab(float4 *dst, const float4 *__restrict__ src) {
+    for (int i = threadIdx.x; i < PHASE_TAB; i += blockDim.x) dst[i] = __ldg(&src[i]);
 }
 
 // Per-step dither: a pseudo-random global phase (in turns, 2^-32 units) added
 // to the potential phase of every point.  A global phase changes no
 // observable, but it changes the FP32 values every later operation rounds, so
-// the rounding errors of consecutive steps decorrelate.  Without it a state
-// that varies slowly from step to step (late, nearly adiabatic evolution)
-// repeats the same rounding errors and its norm drifts coherently.
+// the rounding errors of consecutive steps decorrelate.
 __host__ __device__ inline uint32_t step_dither(uint64_t step) {
     uint64_t z = step + 0x9E3779B97F4A7C15ull;  // splitmix64 finaliser
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
     return (uint32_t)((z ^ (z >> 31)) >> 32);
-}
-
-#ifndef QHD_POT_RENORM
-#define QHD_POT_RENORM 1
-#endif
-#ifndef QHD_POT_FP64
-#define QHD_POT_FP64 0
-#endif
-
-// z * exp(-2 pi i u / 2^32).  The FP32 cosine/sine pair w has |w|^2 = 1 + d
-// with |d| ~ 2^-24; d is formed exactly enough from the FMA residuals of c^2
-// and s^2 (the two leading terms cancel exactly by Sterbenz), and the
-// correction -d/2 w enters as the low part of a compensated product, so the
-// phase factor is unit-modulus to ~1e-15 and only the product is rounded.
-__device__ __forceinline__ float2 apply_phase_turns(float2 z, uint32_t u) {
-#if QHD_POT_FP64
-    double sd, cd;
-    sincospi((double)(int32_t)u * 4.656612873077392578125e-10, &sd, &cd);
-    return make_float2((float)((double)z.x * cd + (double)z.y * sd), (float)((double)z.y * cd - (double)z.x * sd));
-#endif
-    const float2 w = phase_from_turns(u);
-#if QHD_POT_RENORM
-    const float pc = w.x * w.x, ec = fmaf(w.x, w.x, -pc);
-    const float ps = w.y * w.y, es = fmaf(w.y, w.y, -ps);
-    float d = pc >= ps ? (pc - 1.0f) + ps : (ps - 1.0f) + pc;
-    d += ec + es;
-    const float h = -0.5f * d;
-    return cmul_comp(z, w, make_float2(h * w.x, h * w.y));
-#else
-    return cmul(z, w);
-#endif
 }
 
 }  // namespace qhd

@@ -27,7 +27,7 @@ constexpr int MINMAX_BLOCKS_MAX = 512;
 size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
 
 struct Layout {
-    size_t f64, fq, kt, pot, sched, samples, inst, tw, twx, coord, obs_part, obs_res, mm, total;
+    size_t f64, fq, kt, pot, sched, samples, inst, tw, twx, ptab, coord, obs_part, obs_res, mm, total;
     int64_t chunk;
     int obs_blocks, mm_blocks;
 };
@@ -81,6 +81,7 @@ Layout make_layout(int ndim, const int64_t *n, int64_t batch) {
     L.inst = take(sizeof(InstDev) * (size_t)batch);
     L.tw = take(sizeof(float4) * (size_t)(ksum));
     L.twx = take(sizeof(float4) * (size_t)(ksum));
+    L.ptab = take(sizeof(float4) * (size_t)PHASE_TAB);
     L.coord = take(sizeof(double) * (size_t)ksum);
     L.obs_part = take(sizeof(double) * 3 * (size_t)L.obs_blocks * (size_t)batch);
     L.obs_res = take(sizeof(double) * 3 * (size_t)batch);
@@ -112,6 +113,7 @@ struct qhd_ctx {
     InstDev *inst = nullptr;
     float4 *tw[3] = {nullptr, nullptr, nullptr};
     float4 *twx = nullptr;  // exchange twiddles of the cluster-distributed axis
+    float4 *ptab = nullptr; // potential phase table exp(-2 pi i k / PHASE_TAB), hi/lo
     int plane_mode = 0;     // 0 generic passes, 2 whole-run 2-D clusters, 3 3-D plane pass
     double *coord = nullptr;
     double *obs_part = nullptr, *obs_res = nullptr;
@@ -324,6 +326,15 @@ qhd_status qhd_init_grid(qhd_ctx **out, int ndim, const int64_t *n, const double
                 twx[(size_t)(q * rr + j)] = make_float4(hr, hi, (float)(cr - (double)hr), (float)(ci - (double)hi));
             }
     }
+    // potential phase table
+    c->ptab = (float4 *)(c->work + L.ptab);
+    std::vector<float4> ptab((size_t)PHASE_TAB);
+    for (int k = 0; k < PHASE_TAB; ++k) {
+        const double ang = 2.0 * 3.141592653589793238462643383279502884 * (double)k / (double)PHASE_TAB;
+        const double cr = cos(ang), ci = -sin(ang);
+        const float hr = (float)cr, hi = (float)ci;
+        ptab[(size_t)k] = make_float4(hr, hi, (float)(cr - (double)hr), (float)(ci - (double)hi));
+    }
     // mesh coordinates x = lo + (j (hi - lo)) / N
     c->coord_host.resize((size_t)c->ksum);
     for (int d = 0; d < ndim; ++d)
@@ -334,6 +345,8 @@ qhd_status qhd_init_grid(qhd_ctx **out, int ndim, const int64_t *n, const double
                                     cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(c->twx, twx.data(), twx.size() * sizeof(float4), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->ptab, ptab.data(), ptab.size() * sizeof(float4), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(c->coord, c->coord_host.data(), c->coord_host.size() * sizeof(double),
                             cudaMemcpyHostToDevice, c->stream);
@@ -552,6 +565,7 @@ qhd_status qhd_evolve(qhd_ctx *c, double T, double dt) {
             o.cnt = (int)cnt;
             o.final_phase = last_chunk ? 1 : 0;
             o.dither_base = (uint64_t)(c->steps_done + j0);
+            o.ptab = c->ptab;
             TimedScope ts(c, QHD_KCLASS_ONED, true);
             QHD_LAUNCH(c, launch_oned((int)c->n[0], o, c->stream));
             continue;
@@ -569,6 +583,7 @@ qhd_status qhd_evolve(qhd_ctx *c, double T, double dt) {
             w.final_phase = last_chunk ? 1 : 0;
             w.ksum = c->ksum;
             w.dither_base = (uint64_t)(c->steps_done + j0);
+            w.ptab = c->ptab;
             TimedScope ts(c, QHD_KCLASS_WHOLE, true);
             QHD_LAUNCH(c, launch_plane_whole((int)c->n[0], (int)c->n[1], w, c->stream));
             continue;
@@ -580,6 +595,7 @@ qhd_status qhd_evolve(qhd_ctx *c, double T, double dt) {
         r.tw2 = c->tw[last_ax];
         r.rows = B * (c->g / c->n[last_ax]);
         r.rows_per_inst = c->g / c->n[last_ax];
+        r.ptab = c->ptab;
         AxisArgs ax0{};
         ax0.psi = c->psi;
         ax0.tw2 = c->tw[0];
@@ -600,6 +616,7 @@ qhd_status qhd_evolve(qhd_ctx *c, double T, double dt) {
             pl.planes = B * c->n[0];
             pl.planes_per_inst = c->n[0];
             pl.batch = B;
+            pl.ptab = c->ptab;
             const int cc = plane_cluster((int)c->n[1]);
             ax0.perm1_r = (int)c->n[1] / cc;
             ax0.perm1_c = cc;

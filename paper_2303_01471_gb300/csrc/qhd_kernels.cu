@@ -46,7 +46,11 @@ __global__ void __launch_bounds__(ROW_THREADS) k_row(RowArgs a) {
     using C = LineCfg<N>;
     constexpr int E = C::E, T = C::T;
     constexpr int S = line_stride<N>(true, 0);
-    extern __shared__ float2 smem[];
+    extern __shared__ __align__(16) float4 smem4[];
+    float4 *ptab = smem4;
+    float2 *smem = reinterpret_cast<float2 *>(smem4 + PHASE_TAB);
+    load_phase_tab(ptab, a.ptab);
+    __syncthreads();
     const int lpb = blockDim.x / T;
     const int line = threadIdx.x / T, t = threadIdx.x % T;
     const int64_t row = (int64_t)blockIdx.x * lpb + line;
@@ -62,11 +66,7 @@ __global__ void __launch_bounds__(ROW_THREADS) k_row(RowArgs a) {
     const uint64_t c = a.pot[r / a.rows_per_inst];
 #pragma unroll
     for (int e = 0; e < E; ++e) {
-#ifdef QHD_NO_DITHER
-        x[e] = apply_phase_turns(x[e], turns_mul(c, __ldg(&fq[t + T * e])));
-#else
-        x[e] = apply_phase_turns(x[e], turns_mul(c, __ldg(&fq[t + T * e])) + a.dither);
-#endif
+        x[e] = apply_phase_tab(x[e], turns_mul(c, __ldg(&fq[t + T * e])) + a.dither, ptab);
     }
     if (a.mode & MODE_FWD) line_fft<N, false>(x, sm, t, a.tw2, WarpSync{});
     if (valid) {
@@ -126,7 +126,11 @@ __global__ void __launch_bounds__(ROW_THREADS) k_oned(OneDArgs a) {
     using C = LineCfg<N>;
     constexpr int E = C::E, T = C::T;
     constexpr int S = line_stride<N>(true, 0);
-    extern __shared__ float2 smem[];
+    extern __shared__ __align__(16) float4 smem4[];
+    float4 *ptab = smem4;
+    float2 *smem = reinterpret_cast<float2 *>(smem4 + PHASE_TAB);
+    load_phase_tab(ptab, a.ptab);
+    __syncthreads();
     const int lpb = blockDim.x / T;
     const int line = threadIdx.x / T, t = threadIdx.x % T;
     const int64_t row = (int64_t)blockIdx.x * lpb + line;
@@ -146,7 +150,7 @@ __global__ void __launch_bounds__(ROW_THREADS) k_oned(OneDArgs a) {
         const uint64_t c = a.pot[(int64_t)j * a.batch + b];
         const uint32_t dz = step_dither(a.dither_base + (uint64_t)j);
 #pragma unroll
-        for (int e = 0; e < E; ++e) x[e] = apply_phase_turns(x[e], turns_mul(c, fv[e]) + dz);
+        for (int e = 0; e < E; ++e) x[e] = apply_phase_tab(x[e], turns_mul(c, fv[e]) + dz, ptab);
         line_fft<N, false>(x, sm, t, a.tw2, WarpSync{});
         const float4 *kb = a.kt + ((int64_t)j * a.batch + b) * N;
 #pragma unroll
@@ -159,7 +163,7 @@ __global__ void __launch_bounds__(ROW_THREADS) k_oned(OneDArgs a) {
     if (a.final_phase) {
         const uint64_t c = a.pot[(int64_t)a.cnt * a.batch + b];
 #pragma unroll
-        for (int e = 0; e < E; ++e) x[e] = apply_phase_turns(x[e], turns_mul(c, fv[e]));
+        for (int e = 0; e < E; ++e) x[e] = apply_phase_tab(x[e], turns_mul(c, fv[e]), ptab);
     }
     if (valid) {
 #pragma unroll
@@ -398,7 +402,7 @@ static cudaError_t row_impl(const RowArgs &a, cudaStream_t s) {
     constexpr int S = line_stride<N>(true, 0);
     const int lpb = ROW_THREADS / C::T;
     const int64_t blocks = (a.rows + lpb - 1) / lpb;
-    const size_t sm = C::TWO_STAGE ? (size_t)lpb * S * sizeof(float2) : 0;
+    const size_t sm = PHASE_TAB * sizeof(float4) + (C::TWO_STAGE ? (size_t)lpb * S * sizeof(float2) : 0);
     k_row<N><<<(unsigned)blocks, ROW_THREADS, sm, s>>>(a);
     return cudaGetLastError();
 }
@@ -430,7 +434,7 @@ static cudaError_t oned_impl(const OneDArgs &a, cudaStream_t s) {
     constexpr int S = line_stride<N>(true, 0);
     const int lpb = ROW_THREADS / C::T;
     const int64_t blocks = (a.batch + lpb - 1) / lpb;
-    const size_t sm = C::TWO_STAGE ? (size_t)lpb * S * sizeof(float2) : 0;
+    const size_t sm = PHASE_TAB * sizeof(float4) + (C::TWO_STAGE ? (size_t)lpb * S * sizeof(float2) : 0);
     k_oned<N><<<(unsigned)blocks, ROW_THREADS, sm, s>>>(a);
     return cudaGetLastError();
 }

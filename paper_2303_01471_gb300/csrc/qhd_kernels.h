@@ -41,6 +41,7 @@ struct RowArgs {
     int64_t rows_per_inst;
     int mode;              // MODE_INV: inverse FFT before the phase; MODE_FWD: forward after
     uint32_t dither;       // global phase of this pass in 2^-32 turns (step_dither)
+    const float4 *ptab;    // potential phase table (PHASE_TAB hi/lo entries)
 };
 
 struct AxisArgs {
@@ -75,6 +76,7 @@ struct PlaneArgs {
     int final_phase;         // whole: apply pot[cnt] at the end
     int ksum;
     uint64_t dither_base;    // whole: global index of the chunk's first step
+    const float4 *ptab;      // potential phase table
 };
 
 struct OneDArgs {
@@ -87,6 +89,7 @@ struct OneDArgs {
     int cnt;
     int final_phase;       // apply pot[cnt] after the last step
     uint64_t dither_base;  // global step index of the chunk's first step
+    const float4 *ptab;    // potential phase table
 };
 
 struct PrepArgs {

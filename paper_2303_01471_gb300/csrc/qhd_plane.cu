@@ -17,7 +17,9 @@ namespace qhd {
 template <int N1, int N2, int C>
 __global__ void __launch_bounds__(PLANE_THREADS) k_plane_pass(PlaneArgs a) {
     using P = PlaneCfg<N1, N2, C>;
-    extern __shared__ __align__(16) float2 tile[];
+    extern __shared__ __align__(16) float4 smem4[];
+    float4 *ptab = smem4;
+    float2 *tile = reinterpret_cast<float2 *>(smem4 + PHASE_TAB);
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
     const int64_t plane = blockIdx.x / C;
@@ -28,6 +30,7 @@ __global__ void __launch_bounds__(PLANE_THREADS) k_plane_pass(PlaneArgs a) {
     const bool inv = a.mode & MODE_INV, fwd = a.mode & MODE_FWD;
 
     plane_copy<N1, N2, C, true>(tile, g);
+    load_phase_tab(ptab, a.ptab);
     PlaneFq<N1, N2, C> fqr;
     plane_load_fq<N1, N2, C>(fqr, a.fq + plane * (int64_t)N1 * N2, rank);
     const uint64_t coef = a.pot[plane / a.planes_per_inst];
@@ -38,7 +41,7 @@ __global__ void __launch_bounds__(PLANE_THREADS) k_plane_pass(PlaneArgs a) {
         plane_columns<N1, N2, C, true>(tile);
     }
     cluster.sync();
-    plane_exchange<N1, N2, C>(tiles, rank, inv, true, fwd, a.twx, fqr, coef, a.dither);
+    plane_exchange<N1, N2, C>(tiles, rank, inv, true, fwd, a.twx, fqr, coef, a.dither, ptab);
     cluster.sync();
     if (fwd) {
         plane_columns<N1, N2, C, false>(tile);
@@ -52,7 +55,9 @@ __global__ void __launch_bounds__(PLANE_THREADS) k_plane_pass(PlaneArgs a) {
 template <int N1, int N2, int C>
 __global__ void __launch_bounds__(PLANE_THREADS) k_plane_whole(PlaneArgs a) {
     using P = PlaneCfg<N1, N2, C>;
-    extern __shared__ __align__(16) float2 tile[];
+    extern __shared__ __align__(16) float4 smem4[];
+    float4 *ptab = smem4;
+    float2 *tile = reinterpret_cast<float2 *>(smem4 + PHASE_TAB);
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
     const int64_t b = blockIdx.x / C;  // instance
@@ -62,13 +67,14 @@ __global__ void __launch_bounds__(PLANE_THREADS) k_plane_whole(PlaneArgs a) {
     float2 *g = a.psi + b * (int64_t)N1 * N2 + (int64_t)rank * P::R * N2;
     const uint32_t *fqr = a.fq + b * (int64_t)N1 * N2;
     plane_copy<N1, N2, C, true>(tile, g);
+    load_phase_tab(ptab, a.ptab);
     plane_copy_wait();
     cluster.sync();
 #pragma unroll 1
     for (int j = 0; j < a.cnt; ++j) {
         const uint64_t coef = a.pot[(int64_t)j * a.batch + b];
         plane_exchange<N1, N2, C>(tiles, rank, j > 0, true, true, a.twx, fqr, coef,
-                                  step_dither(a.dither_base + (uint64_t)j));
+                                  step_dither(a.dither_base + (uint64_t)j), ptab);
         cluster.sync();
         plane_columns<N1, N2, C, false>(tile);
         __syncthreads();
@@ -79,7 +85,7 @@ __global__ void __launch_bounds__(PLANE_THREADS) k_plane_whole(PlaneArgs a) {
         cluster.sync();
     }
     const uint64_t coef = a.pot[(int64_t)a.cnt * a.batch + b];
-    plane_exchange<N1, N2, C>(tiles, rank, a.cnt > 0, a.final_phase != 0, false, a.twx, fqr, coef, 0u);
+    plane_exchange<N1, N2, C>(tiles, rank, a.cnt > 0, a.final_phase != 0, false, a.twx, fqr, coef, 0u, ptab);
     cluster.sync();
     plane_copy<N1, N2, C, false>(tile, g);
 }

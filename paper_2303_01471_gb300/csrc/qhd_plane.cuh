@@ -35,7 +35,7 @@ template <int N1, int N2, int C> struct PlaneCfg {
     static constexpr int T2 = RowC::T, E2 = RowC::E;
     static constexpr int ROWS_PER_ITER = PLANE_THREADS / T2;
     static constexpr int PAIRS = (R / C) * N2;            // exchange positions owned per CTA
-    static constexpr size_t SMEM = (size_t)R * S * sizeof(float2);
+    static constexpr size_t SMEM = PHASE_TAB * sizeof(float4) + (size_t)R * S * sizeof(float2);
     static_assert(RowC::TWO_STAGE, "rows of at least 32 points");
     static_assert(N1 % C == 0 && R % C == 0, "R rows per CTA, R/C exchange rows per CTA");
     static_assert(N2 <= PLANE_THREADS, "one thread per column in the column phase");
@@ -169,7 +169,7 @@ template <int N1, int N2, int C> __device__ __forceinline__ uint32_t fq_at(const
 template <int N1, int N2, int C, typename FQ>
 __device__ __forceinline__ void plane_exchange_at(float2 *const *tiles, int rank, int k, int p, bool inv, bool phase,
                                                   bool fwd, const float4 *__restrict__ twx, const FQ &fqr,
-                                                  uint64_t coef, uint32_t dither) {
+                                                  uint64_t coef, uint32_t dither, const float4 *ptab) {
     using P = PlaneCfg<N1, N2, C>;
     constexpr int R = P::R;
     const int n2 = rank * (R / C) + p / N2;
@@ -188,7 +188,7 @@ __device__ __forceinline__ void plane_exchange_at(float2 *const *tiles, int rank
     if (phase) {
 #pragma unroll
         for (int q = 0; q < C; ++q)
-            v[q] = apply_phase_turns(v[q], turns_mul(coef, fq_at<N1, N2, C>(fqr, k, q, n2, c)) + dither);
+            v[q] = apply_phase_tab(v[q], turns_mul(coef, fq_at<N1, N2, C>(fqr, k, q, n2, c)) + dither, ptab);
     }
     if (fwd) {
         dft<C, false>(v);
@@ -205,20 +205,20 @@ __device__ __forceinline__ void plane_exchange_at(float2 *const *tiles, int rank
 template <int N1, int N2, int C, typename FQ>
 __device__ __forceinline__ void plane_exchange(float2 *const *tiles, int rank, bool inv, bool phase, bool fwd,
                                                const float4 *__restrict__ twx, const FQ &fqr, uint64_t coef,
-                                               uint32_t dither) {
+                                               uint32_t dither, const float4 *ptab) {
     using P = PlaneCfg<N1, N2, C>;
     constexpr int PPT = PlaneFq<N1, N2, C>::PPT;
     if constexpr (std::is_pointer<FQ>::value) {
 #pragma unroll 1
         for (int k = 0; k < PPT; ++k) {
             const int p = threadIdx.x + k * PLANE_THREADS;
-            if (p < P::PAIRS) plane_exchange_at<N1, N2, C>(tiles, rank, k, p, inv, phase, fwd, twx, fqr, coef, dither);
+            if (p < P::PAIRS) plane_exchange_at<N1, N2, C>(tiles, rank, k, p, inv, phase, fwd, twx, fqr, coef, dither, ptab);
         }
     } else {
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
             const int p = threadIdx.x + k * PLANE_THREADS;
-            if (p < P::PAIRS) plane_exchange_at<N1, N2, C>(tiles, rank, k, p, inv, phase, fwd, twx, fqr, coef, dither);
+            if (p < P::PAIRS) plane_exchange_at<N1, N2, C>(tiles, rank, k, p, inv, phase, fwd, twx, fqr, coef, dither, ptab);
         }
     }
 }
