@@ -310,10 +310,13 @@ qhd_status qhd_init_grid(qhd_ctx **out, int ndim, const int64_t *n, const double
     if (ndim == 2 && plane_supported((int)n[0], (int)n[1])) {
         c->plane_mode = 2;
         dist_axis = 0;
-    } else if (ndim == 3 && plane_supported((int)n[1], (int)n[2])) {
+    }
+#ifndef QHD_NO_PLANE3D
+    else if (ndim == 3 && plane_supported((int)n[1], (int)n[2])) {
         c->plane_mode = 3;
         dist_axis = 1;
     }
+#endif
     std::vector<float4> twx((size_t)c->ksum, make_float4(0.f, 0.f, 0.f, 0.f));
     if (dist_axis >= 0) {
         const int n1 = (int)n[dist_axis], cc = plane_cluster(n1), rr = n1 / cc;

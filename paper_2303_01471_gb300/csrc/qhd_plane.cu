@@ -12,10 +12,14 @@
 #include "qhd_kernels.h"
 #include "qhd_plane.cuh"
 
+#ifndef QHD_PLANE_MINB
+#define QHD_PLANE_MINB 1
+#endif
+
 namespace qhd {
 
 template <int N1, int N2, int C>
-__global__ void __launch_bounds__(PLANE_THREADS) k_plane_pass(PlaneArgs a) {
+__global__ void __launch_bounds__(PLANE_THREADS, QHD_PLANE_MINB) k_plane_pass(PlaneArgs a) {
     using P = PlaneCfg<N1, N2, C>;
     extern __shared__ __align__(16) float4 smem4[];
     float4 *ptab = smem4;
