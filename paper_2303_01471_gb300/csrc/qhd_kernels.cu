@@ -41,11 +41,8 @@ __host__ __device__ constexpr int axis_w(int n) {
 }
 
 // --------------------------------------------------------------- row pass
-#ifndef QHD_ROW_MINB
-#define QHD_ROW_MINB 1
-#endif
 template <int N>
-__global__ void __launch_bounds__(ROW_THREADS, QHD_ROW_MINB) k_row(RowArgs a) {
+__global__ void __launch_bounds__(ROW_THREADS) k_row(RowArgs a) {
     using C = LineCfg<N>;
     constexpr int E = C::E, T = C::T;
     constexpr int S = line_stride<N>(true, 0);
@@ -82,11 +79,11 @@ __global__ void __launch_bounds__(ROW_THREADS, QHD_ROW_MINB) k_row(RowArgs a) {
 // Lines of length N at stride `inner`; a block owns W adjacent lines (columns)
 // of one plane, lanes run along the columns so each global access moves W
 // consecutive complex values per row.
-#ifndef QHD_AXIS_MINB
-#define QHD_AXIS_MINB 1
-#endif
+// Strided passes over lines up to 256 points are compiled for 4 resident blocks
+// per SM (issue-bound, latency hidden by warps); longer lines keep their
+// registers (32 points per thread).
 template <int N, int W>
-__global__ void __launch_bounds__(W * LineCfg<N>::T, QHD_AXIS_MINB) k_axis(AxisArgs a) {
+__global__ void __launch_bounds__(W * LineCfg<N>::T, N <= 256 ? 4 : 1) k_axis(AxisArgs a) {
     using C = LineCfg<N>;
     constexpr int E = C::E, T = C::T;
     constexpr int S = line_stride<N>(false, W);

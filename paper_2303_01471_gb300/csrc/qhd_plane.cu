@@ -12,14 +12,18 @@
 #include "qhd_kernels.h"
 #include "qhd_plane.cuh"
 
-#ifndef QHD_PLANE_MINB
-#define QHD_PLANE_MINB 1
-#endif
-
 namespace qhd {
 
+// Resident CTAs per SM the pass is compiled for: as many as the tile's shared
+// memory allows, at most 3 (the pass is issue-bound; more warps hide latency).
+template <int N1, int N2, int C> constexpr int plane_min_blocks() {
+    constexpr size_t smem = PlaneCfg<N1, N2, C>::SMEM;
+    constexpr int by_smem = (int)((227 * 1024) / smem);
+    return by_smem >= 3 ? 3 : by_smem < 1 ? 1 : by_smem;
+}
+
 template <int N1, int N2, int C>
-__global__ void __launch_bounds__(PLANE_THREADS, QHD_PLANE_MINB) k_plane_pass(PlaneArgs a) {
+__global__ void __launch_bounds__(PLANE_THREADS, plane_min_blocks<N1, N2, C>()) k_plane_pass(PlaneArgs a) {
     using P = PlaneCfg<N1, N2, C>;
     extern __shared__ __align__(16) float4 smem4[];
     float4 *ptab = smem4;
