@@ -148,6 +148,8 @@ def run_ours(args, rank, world, local_rank, dist):
     import torch
     from paper_2303_01471_gb300 import qhd
 
+    t_end = args.profile_T if args.profile_T is not None else T_END
+    nsteps = int(round(t_end / DT))
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     qhd.load()
@@ -161,7 +163,7 @@ def run_ours(args, rank, world, local_rank, dist):
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)  # > L2 (126 MB)
     prob = [torch.empty(int(np.prod(i.shape)), dtype=torch.float32, device=dev) for i in insts]
     prob_host = [torch.empty(int(np.prod(i.shape)), dtype=torch.float32).pin_memory() for i in insts]
-    pts_per_step = sum(int(np.prod(i.shape)) * NSTEPS for i in insts)
+    pts_per_step = sum(int(np.prod(i.shape)) * nsteps for i in insts)
 
     def one_step(device_inputs=True):
         obs = []
@@ -171,7 +173,7 @@ def run_ours(args, rank, world, local_rank, dist):
             else:
                 sim.set_potential(insts[k].f)        # host FP64 -> device inside the call
             sim.reset_state()
-            sim.evolve(T_END, DT)
+            sim.evolve(t_end, DT)
             obs.append(sim.observables(0.1, prob=prob[k])[0])
             if not device_inputs:
                 prob_host[k].copy_(prob[k], non_blocking=False)
@@ -256,7 +258,7 @@ def run_ours(args, rank, world, local_rank, dist):
     # share of device time per class, scaling sampled launches to all steps
     est = []
     for row in kernels:
-        n_launch = NSTEPS + (1 if row["kernel"] == "row" else 0) if row["kernel"] != "prep" else None
+        n_launch = nsteps + (1 if row["kernel"] in ("row", "plane") else 0) if row["kernel"] != "prep" else None
         if n_launch is None:
             n_launch = row["timed_launches"] / args.steps
         est.append(row["avg_us"] * 1e-3 * n_launch)
@@ -290,6 +292,8 @@ def run_ours(args, rank, world, local_rank, dist):
         "observables": [{"instance": "x".join(map(str, i.shape)), "norm": o.norm, "e_f": o.e_f,
                          "p_succ": o.p_succ} for i, o in zip(insts, obs)],
     }
+    if args.profile_T is not None:
+        result["profiling_run"] = f"evolutions shortened to T={t_end}: not a bench value"
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, cores, sample = oracle_sample(insts, budget_s=args.cpu_budget)
         result["cpu_baseline"] = {"value": v, "unit": "grid-point Strang steps/s", "cores": cores,
@@ -339,6 +343,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-T", type=float, default=None,
+                    help="shorten each evolution to this simulated time (profiling runs only; "
+                         "the printed line is then not a bench value)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
