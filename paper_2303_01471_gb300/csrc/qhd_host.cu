@@ -28,7 +28,8 @@ size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
 
 struct Layout {
     size_t f64, fq, kt, pot, sched, samples, inst, tw, twx, ptab, coord, obs_part, obs_res, mm, total;
-    int64_t chunk;
+    int64_t chunk;         // steps per chunk with one kinetic table per instance
+    int64_t chunk_shared;  // steps per chunk when all instances share the kinetic table
     int obs_blocks, mm_blocks;
 };
 
@@ -60,10 +61,16 @@ Layout make_layout(int ndim, const int64_t *n, int64_t batch) {
     const int64_t g = grid_points(ndim, n);
     int64_t ksum = 0;
     for (int d = 0; d < ndim; ++d) ksum += n[d];
-    int64_t ch = (int64_t)(KT_BUDGET / ((size_t)batch * (size_t)ksum * sizeof(float4)));
-    if (ch > MAX_CHUNK) ch = MAX_CHUNK;
-    if (ch < 1) ch = 1;
-    L.chunk = ch;
+    // kinetic tables: at most KT_BUDGET bytes, enough for MAX_CHUNK steps of one
+    // table per instance when that fits
+    const size_t per_step_all = (size_t)batch * (size_t)ksum * sizeof(float4);
+    size_t kt_bytes = (size_t)MAX_CHUNK * per_step_all;
+    if (kt_bytes > KT_BUDGET) kt_bytes = KT_BUDGET;
+    if (kt_bytes < per_step_all) kt_bytes = per_step_all;
+    int64_t ch = (int64_t)(kt_bytes / per_step_all);
+    L.chunk = ch > MAX_CHUNK ? MAX_CHUNK : ch;
+    int64_t chs = (int64_t)(kt_bytes / ((size_t)ksum * sizeof(float4)));
+    L.chunk_shared = chs > MAX_CHUNK ? MAX_CHUNK : chs;
     L.obs_blocks = block_count(g, OBS_BLOCKS_MAX);
     L.mm_blocks = block_count(g, MINMAX_BLOCKS_MAX);
     size_t off = 0;
@@ -74,8 +81,8 @@ Layout make_layout(int ndim, const int64_t *n, int64_t batch) {
     };
     L.f64 = take(sizeof(double) * (size_t)(g * batch));
     L.fq = take(sizeof(uint32_t) * (size_t)(g * batch));
-    L.kt = take(sizeof(float4) * (size_t)(ch * batch * ksum));
-    L.pot = take(sizeof(uint64_t) * (size_t)((ch + 1) * batch));
+    L.kt = take(kt_bytes);
+    L.pot = take(sizeof(uint64_t) * (size_t)((MAX_CHUNK + 1) * batch));
     L.sched = take(sizeof(SchedDev) * (size_t)batch);
     L.samples = take(sizeof(double) * 3 * MAX_TABLE_SAMPLES * (size_t)batch);
     L.inst = take(sizeof(InstDev) * (size_t)batch);
@@ -120,6 +127,7 @@ struct qhd_ctx {
     MinMaxPart *mm = nullptr;
     // host state
     bool have_f = false, have_sched = false;
+    bool kt_shared = false;  // every instance has the same kinetic schedule
     double t = 0.0;
     int64_t steps_done = 0;
     int64_t launches = 0;
@@ -485,6 +493,19 @@ qhd_status qhd_set_schedule(qhd_ctx *c, const qhd_schedule *s) {
                                 c->stream));
     // the host vectors die on return: wait for the copies
     QHD_CUDA(c, cudaStreamSynchronize(c->stream));
+    // One kinetic table serves every instance when the kinetic weights e^{phi}
+    // agree (e.g. instances that differ only in the potential scale).
+    bool shared = true;
+    for (int64_t b = 1; b < B && shared; ++b) {
+        const qhd_schedule &p = s[0], &q = s[b];
+        if (p.kind != q.kind) shared = false;
+        else if (p.kind == QHD_SCHED_NESTEROV) shared = p.c_phi == q.c_phi && p.eps == q.eps;
+        else {
+            shared = p.n_samples == q.n_samples;
+            for (int64_t i = 0; shared && i < p.n_samples; ++i) shared = p.t[i] == q.t[i] && p.phi[i] == q.phi[i];
+        }
+    }
+    c->kt_shared = shared;
     c->have_sched = true;
     return QHD_OK;
 }
@@ -547,7 +568,9 @@ qhd_status qhd_evolve(qhd_ctx *c, double T, double dt) {
     pa.ksum = c->ksum;
     pa.inv_g = 1.0 / (double)c->g;
 
-    const int64_t ch = c->L.chunk;
+    const int64_t ch = c->kt_shared ? c->L.chunk_shared : c->L.chunk;
+    const int64_t ktb = c->kt_shared ? 1 : B;
+    pa.kt_batch = ktb;
     for (int64_t j0 = 0; j0 < nsteps; j0 += ch) {
         const int64_t cnt = nsteps - j0 < ch ? nsteps - j0 : ch;
         const bool last_chunk = j0 + cnt == nsteps;
@@ -569,6 +592,7 @@ qhd_status qhd_evolve(qhd_ctx *c, double T, double dt) {
             o.final_phase = last_chunk ? 1 : 0;
             o.dither_base = (uint64_t)(c->steps_done + j0);
             o.ptab = c->ptab;
+            o.kt_batch = ktb;
             TimedScope ts(c, QHD_KCLASS_ONED, true);
             QHD_LAUNCH(c, launch_oned((int)c->n[0], o, c->stream));
             continue;
@@ -587,6 +611,7 @@ qhd_status qhd_evolve(qhd_ctx *c, double T, double dt) {
             w.ksum = c->ksum;
             w.dither_base = (uint64_t)(c->steps_done + j0);
             w.ptab = c->ptab;
+            w.kt_batch = ktb;
             TimedScope ts(c, QHD_KCLASS_WHOLE, true);
             QHD_LAUNCH(c, launch_plane_whole((int)c->n[0], (int)c->n[1], w, c->stream));
             continue;
@@ -609,6 +634,7 @@ qhd_status qhd_evolve(qhd_ctx *c, double T, double dt) {
         ax0.koff2 = ndim == 3 ? c->koff[2] : 0;
         ax0.log_n2 = ndim == 3 ? (int)std::log2((double)c->n[2]) : 0;
         ax0.ndim = ndim;
+        ax0.kt_batch = ktb;
         ax0.mode = MODE_FWD | MODE_KIN | MODE_INV;
         PlaneArgs pl{};
         if (c->plane_mode == 3) {
@@ -647,7 +673,7 @@ qhd_status qhd_evolve(qhd_ctx *c, double T, double dt) {
                     TimedScope ts(c, QHD_KCLASS_PLANE, sample);
                     QHD_LAUNCH(c, launch_plane_pass((int)c->n[1], (int)c->n[2], pl, c->stream));
                 }
-                ax0.kt = c->kt + jl * B * c->ksum;
+                ax0.kt = c->kt + jl * ktb * c->ksum;
                 TimedScope ts(c, QHD_KCLASS_AXIS0, sample);
                 QHD_LAUNCH(c, launch_axis((int)c->n[0], ax0, c->stream));
                 continue;
@@ -664,7 +690,7 @@ qhd_status qhd_evolve(qhd_ctx *c, double T, double dt) {
                 TimedScope ts(c, QHD_KCLASS_AXIS1_FWD, sample);
                 QHD_LAUNCH(c, launch_axis((int)c->n[1], ax1, c->stream));
             }
-            ax0.kt = c->kt + jl * B * c->ksum;
+            ax0.kt = c->kt + jl * ktb * c->ksum;
             {
                 TimedScope ts(c, QHD_KCLASS_AXIS0, sample);
                 QHD_LAUNCH(c, launch_axis((int)c->n[0], ax0, c->stream));

@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(W * LineCfg<N>::T, N <= 256 ? 4 : 1) k_axis(Ax
         // an FP32 hi/lo pair applied with a compensated product: a table entry
         // is shared by every point with the same frequency index, so a plain
         // FP32 rounding of it would perturb the norm coherently.
-        const float4 *kb = a.kt + o * a.ksum;
+        const float4 *kb = a.kt + (a.kt_batch == 1 ? 0 : o) * a.ksum;
         int64_t i1 = a.ndim == 2 ? ci : (ci >> a.log_n2);
         if (a.perm1_r) i1 = i1 / a.perm1_r + (int64_t)a.perm1_c * (i1 % a.perm1_r);
         const float4 k1 = __ldg(&kb[a.koff1 + i1]);
@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(ROW_THREADS) k_oned(OneDArgs a) {
 #pragma unroll
         for (int e = 0; e < E; ++e) x[e] = apply_phase_tab(x[e], turns_mul(c, fv[e]) + dz, ptab);
         line_fft<N, false>(x, sm, t, a.tw2, WarpSync{});
-        const float4 *kb = a.kt + ((int64_t)j * a.batch + b) * N;
+        const float4 *kb = a.kt + ((int64_t)j * a.kt_batch + (a.kt_batch == 1 ? 0 : b)) * N;
 #pragma unroll
         for (int e = 0; e < E; ++e) {
             const float4 k0 = __ldg(&kb[t + T * e]);
@@ -248,8 +248,8 @@ __global__ void k_prep(PrepArgs a) {
         }
     }
     __syncthreads();
-    if (jl >= a.cnt) return;
-    float4 *out = a.kt + (jl * a.batch + b) * a.ksum;
+    if (jl >= a.cnt || b >= a.kt_batch) return;
+    float4 *out = a.kt + (jl * a.kt_batch + b) * a.ksum;
     for (int i = threadIdx.x; i < a.ksum; i += blockDim.x) {
         int d = 0;
         while (d + 1 < a.ndim && i >= a.koff[d + 1]) ++d;

@@ -55,6 +55,7 @@ struct AxisArgs {
     int log_n2;            // log2 n[2] (3-D only)
     int ndim;
     int mode;
+    int64_t kt_batch;      // 1: every instance shares the kinetic table; else batch
     int perm1_r, perm1_c;  // 3-D after a plane pass: stored axis-1 row s holds
                            // frequency s / perm1_r + perm1_c * (s % perm1_r); 0 = natural
 };
@@ -77,6 +78,7 @@ struct PlaneArgs {
     int ksum;
     uint64_t dither_base;    // whole: global index of the chunk's first step
     const float4 *ptab;      // potential phase table
+    int64_t kt_batch;        // whole: 1 = shared kinetic table, else batch
 };
 
 struct OneDArgs {
@@ -90,13 +92,15 @@ struct OneDArgs {
     int final_phase;       // apply pot[cnt] after the last step
     uint64_t dither_base;  // global step index of the chunk's first step
     const float4 *ptab;    // potential phase table
+    int64_t kt_batch;      // 1: shared kinetic table; else batch
 };
 
 struct PrepArgs {
     const SchedDev *sched;
     const InstDev *inst;
     uint64_t *pot;         // [cnt+1][batch]
-    float4 *kt;            // [cnt][batch][ksum], (hi.re, hi.im, lo.re, lo.im)
+    float4 *kt;            // [cnt][kt_batch][ksum], (hi.re, hi.im, lo.re, lo.im)
+    int64_t kt_batch;      // 1 when every instance has the same kinetic schedule
     double t_start, dt;
     int64_t j0, cnt, nsteps, batch;
     int ndim;

@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(PLANE_THREADS) k_plane_whole(PlaneArgs a) {
         cluster.sync();
         plane_columns<N1, N2, C, false>(tile);
         __syncthreads();
-        const float4 *kb = a.kt + ((int64_t)j * a.batch + b) * a.ksum;
+        const float4 *kb = a.kt + ((int64_t)j * a.kt_batch + (a.kt_batch == 1 ? 0 : b)) * a.ksum;
         plane_rows<N1, N2, C, 2>(tile, a.tw_row, kb, kb + N1, rank);
         __syncthreads();
         plane_columns<N1, N2, C, true>(tile);

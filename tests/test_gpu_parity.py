@@ -120,12 +120,16 @@ def test_parity_nonunit_box_and_table_schedule():
     compare(psi_g, obs[0], inst.f, psi_o, lo=np.array(lo), hi=np.array(hi), steps=n)
 
 
-@pytest.mark.parametrize("shape", [(32, 32), (16, 16), (8, 64, 32)], ids=lambda s: "x".join(map(str, s)))
-def test_parity_batch_with_own_f_and_schedule(shape):
+@pytest.mark.parametrize("own_kinetic", [False, True], ids=["shared-kinetic", "own-kinetic"])
+@pytest.mark.parametrize("shape", [(32, 32), (16, 16), (8, 64, 32), (64,)], ids=lambda s: "x".join(map(str, s)))
+def test_parity_batch_with_own_f_and_schedule(shape, own_kinetic):
+    """Instances with their own f and potential scale sigma share one kinetic table;
+    instances whose kinetic weight differs (c_phi) each get their own."""
     insts = [workloads.make(fam, s, shape, draw_sigma=True)
              for fam, s in [("wells", 1), ("rastrigin", 2), ("wells", 3)]]
     fb = np.stack([i.f for i in insts])
-    scheds = [qhd.Schedule(c_chi=2.0 * i.sigma) for i in insts]
+    scheds = [qhd.Schedule(c_chi=2.0 * i.sigma, c_phi=(1.0 + 0.5 * b) if own_kinetic else 2.0)
+              for b, i in enumerate(insts)]
     dt, n = 0.01, 100
     psi_g, obs = run_gpu(None, scheds, n * dt, dt, batch_f=fb)
     for b, inst in enumerate(insts):

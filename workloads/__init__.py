@@ -102,6 +102,39 @@ def ragged_batch_spec(count: int = 4096, seed0: int = 0):
     return spec
 
 
+def batch_on_device(spec, shape, device, K: int = 8, lo: float = 0.0, hi: float = 1.0):
+    """FP64 objective values of many same-shape instances, evaluated on a torch
+    device with the same seeded draws and formulas as gaussian_wells / rastrigin.
+    spec: list of (family, seed).  Returns (f of shape (B, *shape), sigmas)."""
+    import torch
+    shape = tuple(int(n) for n in shape)
+    d = len(shape)
+    axes = [torch.as_tensor(a, dtype=torch.float64, device=device) for a in mesh_axes(shape, lo, hi)]
+    grids = torch.meshgrid(*axes, indexing="ij")
+    out = torch.empty((len(spec),) + shape, dtype=torch.float64, device=device)
+    sig = []
+    for i, (fam, seed) in enumerate(spec):
+        rng = np.random.default_rng(seed)
+        if fam == "wells":
+            centres = rng.uniform(0.0, 1.0, size=(K, d))
+            widths = rng.uniform(0.05, 0.2, size=K)
+            depths = rng.uniform(0.5, 2.0, size=K)
+            sig.append(float(rng.uniform(0.5, 2.0)))
+            f = 0.5 * sum((g - 0.5) ** 2 for g in grids)
+            for k in range(K):
+                d2 = sum((g - centres[k, ax]) ** 2 for ax, g in enumerate(grids))
+                f = f - depths[k] * torch.exp(-d2 / (2.0 * widths[k] ** 2))
+        else:
+            s = rng.uniform(0.2, 0.8, size=d)
+            sig.append(float(rng.uniform(0.5, 2.0)))
+            f = 0.0
+            for ax, g in enumerate(grids):
+                u = g - s[ax]
+                f = f + (10.0 * u * u - 1.0 * torch.cos(2.0 * np.pi * 5.0 * u))
+        out[i] = f
+    return out, sig
+
+
 def make(family: str, seed: int, shape, **kw) -> Instance:
     if family == "wells":
         return gaussian_wells(seed, shape, **kw)
