@@ -119,6 +119,22 @@ class Clocks:
                 "samples": len(sm)}
 
 
+# ------------------------------------------------------------ multi-rank logic
+def max_over_ranks(value: float, dist, device=None) -> float:
+    """Maximum of a per-rank timing over all ranks (every rank gets the result)."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, seconds_max: float) -> float:
+    """Whole-job throughput of weak-scaled replicas: all ranks' units over the slowest rank's time."""
+    return units_per_rank * world / seconds_max
+
+
 # --------------------------------------------------------------- CPU oracle leg
 def oracle_sample(insts, budget_s: float = 15.0, max_steps=(400, 40)):
     """Time the FP64 oracle on a bounded number of Strang steps of each instance
@@ -214,13 +230,9 @@ def run_ours(args, rank, world, local_rank, dist):
     timing = [s.timing_read(reset=True) for s in sims]
     for sim in sims:
         sim.timing_enable(0)
-    total_ms = float(sum(step_ms))
-    if dist is not None:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(float(sum(step_ms)), dist, dev)
     ms_per_step = total_ms / args.steps
-    value = pts_per_step * world / (ms_per_step / 1e3)
+    value = whole_job_rate(pts_per_step, world, ms_per_step / 1e3)
 
     # ---------------- e2e: host inputs and host result through the C ABI
     e2e_ms = []
@@ -231,11 +243,7 @@ def run_ours(args, rank, world, local_rank, dist):
         one_step(device_inputs=False)
         torch.cuda.synchronize()
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
-    e2e_step = statistics.mean(e2e_ms)
-    if dist is not None:
-        t = torch.tensor([e2e_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_step = float(t.item())
+    e2e_step = max_over_ranks(statistics.mean(e2e_ms), dist, dev)
     h2d = sum(8 * int(np.prod(i.shape)) for i in insts)
     d2h = sum(4 * int(np.prod(i.shape)) + 64 for i in insts)
 
@@ -281,7 +289,7 @@ def run_ours(args, rank, world, local_rank, dist):
         "config": {"workload": WORKLOAD, "instances_per_rank": len(insts),
                    "grid_points_x_steps_per_step": pts_per_step, "parallelism": f"replicas x{world}",
                    "l2": "psi+f of the 256^3 instance exceed L2; a 512 MiB write flushes L2 between timed steps"},
-        "e2e": {"value": pts_per_step * world / (e2e_step / 1e3), "unit": "grid-point Strang steps/s",
+        "e2e": {"value": whole_job_rate(pts_per_step, world, e2e_step / 1e3), "unit": "grid-point Strang steps/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": e2e_step},
         "gpu_launches": launches,
@@ -361,12 +369,8 @@ def run_ragged(args, rank, world, local_rank, dist):
             torch.cuda.synchronize()
             times.append(time.perf_counter() - t0)
     launches = sum(s.launch_count() for s in sims) - launches0
-    step_s = statistics.mean(times)
-    if dist is not None:
-        t = torch.tensor([step_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        step_s = float(t.item())
-    inst_per_s = count * world / step_s
+    step_s = max_over_ranks(statistics.mean(times), dist, dev)
+    inst_per_s = whole_job_rate(count, world, step_s)
     pts = sum(int(np.prod(sh)) * len(sp) for sh, sp in classes.items()) * nsteps
 
     # one context per instance (a launch sequence per instance), on a sample

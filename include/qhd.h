@@ -148,6 +148,30 @@ qhd_status qhd_get_time(const qhd_ctx *ctx, double *t_out, int64_t *steps_done_o
 qhd_status qhd_evolve(qhd_ctx *ctx, double T, double dt);
 
 /*
+ * Trajectory of the observables (the loss E[f](t) of Eq. (expect_O) and the
+ * success probability of the Fig. 2 caption along the evolution): advances by
+ * n = round(T/dt) steps like qhd_evolve and, after every `every` steps, writes
+ * (sum |psi|^2, E[f], P_succ) of every instance into traj_dev, a caller-owned
+ * device array of (n/every) * batch * 3 doubles: point k, instance b at
+ * traj_dev[(k*batch + b)*3 + 0..2].  every >= 1 must divide n.  Asynchronous
+ * on the stream (no host synchronisation between points).
+ */
+qhd_status qhd_evolve_trajectory(qhd_ctx *ctx, double T, double dt, int64_t every, double radius,
+                                 double *traj_dev);
+
+/*
+ * Time-stepping formula used by qhd_evolve (default QHD_SPLIT_STRANG).
+ * QHD_SPLIT_STRANG: P(dt/2) F^-1 K(dt) F P(dt/2) with a, b at the step midpoint
+ *   (second order).
+ * QHD_SPLIT_LIE_TROTTER: the first-order product formula exactly as printed in
+ *   Eq. (prod_qhd) / Algorithm 1: psi_{j+1} = F^-1 K(dt a_j) F P(dt b_j) psi_j with
+ *   a_j = e^{phi(t_j)}, b_j = e^{chi(t_j)}, t_j = t + j dt (left end point).
+ * Unknown kinds give QHD_ERR_INVALID_ARG.  Applies to later qhd_evolve calls.
+ */
+enum { QHD_SPLIT_STRANG = 0, QHD_SPLIT_LIE_TROTTER = 1 };
+qhd_status qhd_set_splitting(qhd_ctx *ctx, int kind);
+
+/*
  * Observables of every instance: out_host[batch] receives qhd_obs; prob_dev
  * (optional, NULL to skip) receives |psi|^2 as float32, batch*G values.
  * radius > 0 (the paper's success radius is 0.1).  Synchronises the stream.

@@ -128,6 +128,7 @@ struct qhd_ctx {
     // host state
     bool have_f = false, have_sched = false;
     bool kt_shared = false;  // every instance has the same kinetic schedule
+    int split = QHD_SPLIT_STRANG;
     double t = 0.0;
     int64_t steps_done = 0;
     int64_t launches = 0;
@@ -567,6 +568,7 @@ qhd_status qhd_evolve(qhd_ctx *c, double T, double dt) {
     }
     pa.ksum = c->ksum;
     pa.inv_g = 1.0 / (double)c->g;
+    pa.split = c->split == QHD_SPLIT_LIE_TROTTER ? 1 : 0;
 
     const int64_t ch = c->kt_shared ? c->L.chunk_shared : c->L.chunk;
     const int64_t ktb = c->kt_shared ? 1 : B;
@@ -759,6 +761,61 @@ qhd_status qhd_observables(qhd_ctx *c, qhd_obs *out, float *prob_dev, double rad
         for (int d = 0; d < 3; ++d) o.x_star[d] = c->inst_host[(size_t)b].xs[d];
         o.steps_done = c->steps_done;
     }
+    return QHD_OK;
+}
+
+qhd_status qhd_evolve_trajectory(qhd_ctx *c, double T, double dt, int64_t every, double radius,
+                                 double *traj_dev) {
+    qhd_status s = check_ctx(c);
+    if (s != QHD_OK) return s;
+    if (!traj_dev) return fail(c, QHD_ERR_INVALID_ARG, "traj_dev is NULL");
+    if (!std::isfinite(radius) || !(radius > 0)) return fail(c, QHD_ERR_INVALID_ARG, "radius must be > 0");
+    if (!std::isfinite(T) || !std::isfinite(dt) || dt == 0.0)
+        return fail(c, QHD_ERR_INVALID_ARG, "T and dt must be finite and dt nonzero");
+    const double ratio = T / dt;
+    const double nr = std::nearbyint(ratio);
+    if (!(nr >= 1.0) || std::fabs(ratio - nr) > 1e-9 * nr || nr > 1e12)
+        return fail(c, QHD_ERR_INVALID_ARG, "T/dt = %.17g is not a positive integer", ratio);
+    const int64_t nsteps = (int64_t)nr;
+    if (every < 1 || nsteps % every != 0)
+        return fail(c, QHD_ERR_INVALID_ARG, "every = %lld must divide the %lld steps", (long long)every,
+                    (long long)nsteps);
+    if (!c->have_f || !c->have_sched)
+        return fail(c, QHD_ERR_STATE, "evolve needs set_potential and set_schedule first");
+    const int64_t npts = nsteps / every;
+    ObsArgs a{};
+    a.psi = c->psi;
+    a.f64 = c->f64;
+    a.inst = c->inst;
+    a.coord = c->coord;
+    a.prob = nullptr;
+    a.partial = c->obs_part;
+    a.g = c->g;
+    a.ndim = c->ndim;
+    for (int d = 0; d < 3; ++d) {
+        a.n[d] = d < c->ndim ? (int)c->n[d] : 1;
+        a.log_n[d] = d < c->ndim ? (int)std::log2((double)c->n[d]) : 0;
+        a.coff[d] = d < c->ndim ? c->koff[d] : 0;
+    }
+    a.radius = radius;
+    a.nblk = c->L.obs_blocks;
+    for (int64_t k = 0; k < npts; ++k) {
+        s = qhd_evolve(c, (double)every * dt, dt);
+        if (s != QHD_OK) return s;
+        a.result = traj_dev + k * c->batch * 3;
+        cudaError_t e = launch_observables(a, c->batch, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "trajectory observables");
+        c->launches += 2;
+    }
+    return QHD_OK;
+}
+
+qhd_status qhd_set_splitting(qhd_ctx *c, int kind) {
+    qhd_status s = check_ctx(c);
+    if (s != QHD_OK) return s;
+    if (kind != QHD_SPLIT_STRANG && kind != QHD_SPLIT_LIE_TROTTER)
+        return fail(c, QHD_ERR_INVALID_ARG, "unknown splitting %d", kind);
+    c->split = kind;
     return QHD_OK;
 }
 

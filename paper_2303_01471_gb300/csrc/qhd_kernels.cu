@@ -225,18 +225,25 @@ __global__ void k_prep(PrepArgs a) {
     if (threadIdx.x == 0) {
         const SchedDev &sd = a.sched[b];
         const double PI = 3.141592653589793238462643383279502884;
-        // midpoints t_{j-1/2} and t_{j+1/2}
-        double a_m = 0, b_m = 0, a_p = 0, b_p = 0;
-        if (j >= 1) {
-            const double tm = __dadd_rn(a.t_start, __dmul_rn((double)(j - 1) + 0.5, a.dt));
-            sched_eval_dev(sd, tm, &a_m, &b_m);
+        double a_m = 0, b_m = 0, a_p = 0, b_p = 0, theta = 0;
+        if (a.split == 0) {
+            // Strang: midpoints t_{j-1/2} and t_{j+1/2}; merged half steps
+            if (j >= 1) {
+                const double tm = __dadd_rn(a.t_start, __dmul_rn((double)(j - 1) + 0.5, a.dt));
+                sched_eval_dev(sd, tm, &a_m, &b_m);
+            }
+            if (j < a.nsteps) {
+                const double tp = __dadd_rn(a.t_start, __dmul_rn((double)j + 0.5, a.dt));
+                sched_eval_dev(sd, tp, &a_p, &b_p);
+            }
+            theta = __dmul_rn(a.dt, __dadd_rn(j >= 1 ? b_m : 0.0, j < a.nsteps ? b_p : 0.0)) * 0.5;
+        } else if (j < a.nsteps) {
+            // first-order product formula of Eq. (prod_qhd): a_j, b_j at t_j = t + j dt,
+            // one potential phase dt b_j per step and none after the last
+            const double tj = __dadd_rn(a.t_start, __dmul_rn((double)j, a.dt));
+            sched_eval_dev(sd, tj, &a_p, &b_p);
+            theta = __dmul_rn(a.dt, b_p);
         }
-        if (j < a.nsteps) {
-            const double tp = __dadd_rn(a.t_start, __dmul_rn((double)j + 0.5, a.dt));
-            sched_eval_dev(sd, tp, &a_p, &b_p);
-        }
-        // merged potential coefficient theta_j (radians per unit f)
-        const double theta = __dmul_rn(a.dt, __dadd_rn(j >= 1 ? b_m : 0.0, j < a.nsteps ? b_p : 0.0)) * 0.5;
         const int shift = a.inst[b].shift;
         // turns per unit of the fixed-point potential: theta / (2 pi) * 2^-shift
         const double y = ldexp(theta / (2.0 * PI), -shift);

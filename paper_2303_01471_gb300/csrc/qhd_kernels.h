@@ -109,6 +109,7 @@ struct PrepArgs {
     int koff[3];
     int ksum;
     double inv_g;          // 1/G (exact power of two)
+    int split;             // 0 Strang (midpoint, merged halves), 1 first-order Lie-Trotter
 };
 
 struct ObsArgs {

@@ -26,7 +26,10 @@ SCHED_TABLE = 1
 EXPORTS = ["qhd_workspace_bytes", "qhd_init_grid", "qhd_set_potential", "qhd_set_potential_device",
            "qhd_set_schedule", "qhd_reset_state", "qhd_set_time", "qhd_get_time", "qhd_evolve",
            "qhd_observables", "qhd_launch_count", "qhd_timing_enable", "qhd_timing_read",
-           "qhd_destroy", "qhd_status_string", "qhd_last_error", "qhd_observables_static"]
+           "qhd_destroy", "qhd_status_string", "qhd_last_error", "qhd_observables_static",
+           "qhd_set_splitting", "qhd_evolve_trajectory"]
+SPLIT_STRANG = 0
+SPLIT_LIE_TROTTER = 1
 KCLASS = ["prep", "row", "axis1_fwd", "axis0", "axis1_inv", "oned", "plane", "whole"]
 
 
@@ -100,6 +103,11 @@ def load(build_if_missing: bool = True):
     lib.qhd_observables_static.argtypes = [ctypes.c_int, i64p, dp, dp, ctypes.c_int64, vp, vp, dp,
                                            ctypes.c_double, vp, vp, vp]
     lib.qhd_observables_static.restype = st
+    lib.qhd_evolve_trajectory.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_int64,
+                                          ctypes.c_double, vp]
+    lib.qhd_evolve_trajectory.restype = st
+    lib.qhd_set_splitting.argtypes = [vp, ctypes.c_int]
+    lib.qhd_set_splitting.restype = st
     lib.qhd_destroy.argtypes = [vp]
     lib.qhd_destroy.restype = st
     lib.qhd_status_string.argtypes = [st]
@@ -234,6 +242,10 @@ class QHD:
     def reset_state(self) -> None:
         self._check(self.lib.qhd_reset_state(self.ctx), "qhd_reset_state")
 
+    def set_splitting(self, kind: int) -> None:
+        """SPLIT_STRANG (default) or SPLIT_LIE_TROTTER (Eq. (prod_qhd) as printed)."""
+        self._check(self.lib.qhd_set_splitting(self.ctx, int(kind)), "qhd_set_splitting")
+
     def set_time(self, t: float) -> None:
         self._check(self.lib.qhd_set_time(self.ctx, float(t)), "qhd_set_time")
 
@@ -245,6 +257,18 @@ class QHD:
 
     def evolve(self, T: float, dt: float) -> None:
         self._check(self.lib.qhd_evolve(self.ctx, float(T), float(dt)), "qhd_evolve")
+
+    def evolve_trajectory(self, T: float, dt: float, every: int, radius: float = 0.1):
+        """Evolve and record (norm, E[f], P_succ) every `every` steps; returns a torch
+        float64 CUDA tensor of shape (n/every, batch, 3)."""
+        import torch
+        n = int(round(T / dt))
+        if every < 1 or n % every:
+            raise ValueError("every must divide the number of steps")
+        traj = torch.empty((n // every, self.batch, 3), dtype=torch.float64, device=self.device)
+        self._check(self.lib.qhd_evolve_trajectory(self.ctx, float(T), float(dt), int(every), float(radius),
+                                                   ctypes.c_void_p(traj.data_ptr())), "qhd_evolve_trajectory")
+        return traj
 
     def observables(self, radius: float = 0.1, prob=None) -> List[Observables]:
         """prob: optional torch float32 CUDA tensor with batch*G values receiving |psi|^2."""

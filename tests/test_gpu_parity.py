@@ -137,6 +137,49 @@ def test_parity_batch_with_own_f_and_schedule(shape, own_kinetic):
         compare(psi_g[b], obs[b], inst.f, psi_o, steps=n)
 
 
+@pytest.mark.parametrize("shape", [(128,), (64, 64), (512, 64), (4, 32, 32), (4, 8, 16)],
+                         ids=lambda s: "x".join(map(str, s)))
+def test_parity_lie_trotter_matches_oracle(shape):
+    """Eq. (prod_qhd) as printed: first order, left-end-point coefficients."""
+    inst = workloads.gaussian_wells(12, shape, K=4)
+    sim = qhd.QHD(shape)
+    sim.set_potential(inst.f)
+    sim.set_schedule(qhd.Schedule())
+    sim.set_splitting(qhd.SPLIT_LIE_TROTTER)
+    sim.reset_state()
+    sim.set_time(0.5)
+    sim.evolve(0.5, 0.01)
+    obs = sim.observables(0.1)
+    psi_g = sim.psi.cpu().numpy().astype(np.complex128)
+    sim.close()
+    psi_o = oracle.evolve_trotter(inst.f, oracle.uniform_state(shape), 0.5, 0.01, 50)
+    compare(psi_g, obs[0], inst.f, psi_o, steps=50)
+    # and it is a different map from the default Strang form
+    psi_s = oracle.evolve(inst.f, oracle.uniform_state(shape), 0.5, 0.01, 50, oracle.Schedule())
+    assert np.abs(np.abs(psi_s) ** 2 - np.abs(psi_o) ** 2).max() > 1e-4 * (np.abs(psi_o) ** 2).max()
+
+
+def test_trajectory_matches_oracle_loss_curve():
+    """E[f](t) and P_succ(t) every 100 steps (the paper's loss / success curves)."""
+    shape = (64, 64)
+    inst = workloads.gaussian_wells(13, shape, K=8)
+    sim = qhd.QHD(shape)
+    sim.set_potential(inst.f)
+    sim.set_schedule(qhd.Schedule())
+    sim.reset_state()
+    traj = sim.evolve_trajectory(5.0, 0.01, 100).cpu().numpy()
+    sim.close()
+    assert traj.shape == (5, 1, 3)
+    psi = oracle.uniform_state(shape)
+    for k in range(5):
+        psi = oracle.evolve(inst.f, psi, k * 1.0, 0.01, 100, oracle.Schedule())
+        ob = oracle.observables(inst.f, psi)
+        scale = max(abs(ob.e_f), 1e-3 * np.ptp(inst.f))
+        assert abs(traj[k, 0, 0] - 1.0) <= 4e-6
+        assert abs(traj[k, 0, 1] - ob.e_f) / scale <= EF_TOL
+        assert abs(traj[k, 0, 2] - ob.p_succ) <= 2 * TV_TOL
+
+
 # --------------------------------------------- configuration: 128^2, 1000 steps
 
 _CFG0 = {}
