@@ -36,24 +36,26 @@ def _stale() -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=None, out: str = None) -> str:
-    """Compile libqhd.so.  extra_flags / out build a variant elsewhere (for
-    experiments); the default library is LIB."""
+def build(force: bool = False, verbose: bool = False, extra_flags=None, out: str = None,
+          csrc: str = None) -> str:
+    """Compile libqhd.so.  extra_flags / out / csrc build a variant elsewhere (for
+    experiments); the default library is LIB from CSRC."""
     target = out or LIB
+    src_dir = csrc or CSRC
     if not force and out is None and not extra_flags and not _stale():
         return LIB
     libdir = os.path.dirname(target)
     os.makedirs(libdir, exist_ok=True)
     nvcc = _nvcc()
     flags = ["-std=c++17", "-O3", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC",
-             "-I" + os.path.join(ROOT, "include"), "-I" + CSRC, "-diag-suppress", "550"]
+             "-I" + os.path.join(ROOT, "include"), "-I" + src_dir, "-diag-suppress", "550"]
     if verbose:
         flags += ["-Xptxas", "-v"]
     flags += list(extra_flags or [])
 
     def compile_one(src):
         obj = os.path.join(libdir, os.path.splitext(src)[0] + ".o")
-        cmd = [nvcc, *flags, "-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [nvcc, *flags, "-c", os.path.join(src_dir, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")

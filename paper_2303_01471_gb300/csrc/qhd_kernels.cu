@@ -503,7 +503,7 @@ static cudaError_t axis_w_impl(const AxisArgs &a, cudaStream_t s) {
     constexpr int S = line_stride<N>(false, W);
     const int64_t blocks = a.planes * (a.inner / W);
     const size_t xch = C::TWO_STAGE ? (size_t)W * S * sizeof(float2) : 0;
-#ifndef QHD_NO_AXIS_PIPE
+#ifdef QHD_AXIS_PIPE
     if constexpr (W >= 2) {
         if (((uintptr_t)a.psi & 15) == 0) {
             // persistent grid: resident blocks per SM x SMs, never more than tiles
