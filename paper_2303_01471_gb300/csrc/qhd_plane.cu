@@ -31,16 +31,15 @@ __global__ void __launch_bounds__(PLANE_THREADS, plane_min_blocks<N1, N2, C>()) 
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
     const int64_t plane = blockIdx.x / C;
-    float2 *tiles[C];
+    uint32_t tiles[C];
 #pragma unroll
-    for (int q = 0; q < C; ++q) tiles[q] = cluster.map_shared_rank(tile, q);
+    for (int q = 0; q < C; ++q) tiles[q] = cluster_addr(tile, (uint32_t)q);
     float2 *g = a.psi + plane * (int64_t)N1 * N2 + (int64_t)rank * P::R * N2;
     const bool inv = a.mode & MODE_INV, fwd = a.mode & MODE_FWD;
 
     plane_copy<N1, N2, C, true>(tile, g);
     load_phase_tab(ptab, a.ptab);
-    PlaneFq<N1, N2, C> fqr;
-    plane_load_fq<N1, N2, C>(fqr, a.fq + plane * (int64_t)N1 * N2, rank);
+    const uint32_t *fqr = a.fq + plane * (int64_t)N1 * N2;
     const uint64_t coef = a.pot[plane / a.planes_per_inst];
     plane_copy_wait();
     if (inv) {
@@ -61,7 +60,7 @@ __global__ void __launch_bounds__(PLANE_THREADS, plane_min_blocks<N1, N2, C>()) 
 }
 
 template <int N1, int N2, int C>
-__global__ void __launch_bounds__(PLANE_THREADS) k_plane_whole(PlaneArgs a) {
+__global__ void __launch_bounds__(PLANE_THREADS, 2) k_plane_whole(PlaneArgs a) {
     using P = PlaneCfg<N1, N2, C>;
     extern __shared__ __align__(16) float4 smem4[];
     float4 *ptab = smem4;
@@ -69,9 +68,9 @@ __global__ void __launch_bounds__(PLANE_THREADS) k_plane_whole(PlaneArgs a) {
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
     const int64_t b = blockIdx.x / C;  // instance
-    float2 *tiles[C];
+    uint32_t tiles[C];
 #pragma unroll
-    for (int q = 0; q < C; ++q) tiles[q] = cluster.map_shared_rank(tile, q);
+    for (int q = 0; q < C; ++q) tiles[q] = cluster_addr(tile, (uint32_t)q);
     float2 *g = a.psi + b * (int64_t)N1 * N2 + (int64_t)rank * P::R * N2;
     const uint32_t *fqr = a.fq + b * (int64_t)N1 * N2;
     plane_copy<N1, N2, C, true>(tile, g);

@@ -130,53 +130,35 @@ __device__ __forceinline__ void plane_rows(float2 *tile, const float4 *__restric
     }
 }
 
-// The cross-cluster step at the positions this CTA owns: optional inverse
-// four-step half, potential phase, optional forward half.  tiles[q] is CTA
-// q's tile in the distributed shared-memory window.
-// Fixed-point potential at the positions this thread owns in the exchange
-// (PAIRS_PER_THREAD positions x C rows), loaded once into registers.
-template <int N1, int N2, int C> struct PlaneFq {
-    static constexpr int PPT = (PlaneCfg<N1, N2, C>::PAIRS + PLANE_THREADS - 1) / PLANE_THREADS;
-    uint32_t v[PPT][C];
-};
+// Number of exchange positions (n2, c) each thread owns.
+template <int N1, int N2, int C> __host__ __device__ constexpr int plane_ppt() {
+    return (PlaneCfg<N1, N2, C>::PAIRS + PLANE_THREADS - 1) / PLANE_THREADS;
+}
 
+// Distributed shared memory through explicit cluster addresses: mapa gives the
+// address of the same shared location in CTA `rank`; ld/st.shared::cluster
+// access it without the generic-address path.
+__device__ __forceinline__ uint32_t cluster_addr(const void *local, uint32_t rank) {
+    uint32_t r;
+    asm("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"((uint32_t)__cvta_generic_to_shared(local)), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ float2 ld_cluster(uint32_t addr) {
+    float2 v;
+    asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_cluster(uint32_t addr, float2 v) {
+    asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(addr), "f"(v.x), "f"(v.y) : "memory");
+}
+
+// One exchange position (n2, c): the C values are in v, the fixed-point
+// potential of the C rows in fv.
 template <int N1, int N2, int C>
-__device__ __forceinline__ void plane_load_fq(PlaneFq<N1, N2, C> &f, const uint32_t *__restrict__ fq, int rank) {
-    using P = PlaneCfg<N1, N2, C>;
-    constexpr int R = P::R;
-#pragma unroll
-    for (int k = 0; k < PlaneFq<N1, N2, C>::PPT; ++k) {
-        const int p = threadIdx.x + k * PLANE_THREADS;
-        const int pp = p < P::PAIRS ? p : 0;
-        const int n2 = rank * (R / C) + pp / N2, c = pp % N2;
-#pragma unroll
-        for (int q = 0; q < C; ++q) f.v[k][q] = __ldg(&fq[(R * q + n2) * N2 + c]);
-    }
-}
-
-// FQ is either PlaneFq (values prefetched into registers, for a single pass)
-// or a const uint32_t * to the plane's fixed-point potential (read through the
-// cache each step, for the whole-run kernel, where registers are scarcer).
-template <int N1, int N2, int C> __device__ __forceinline__ uint32_t fq_at(const PlaneFq<N1, N2, C> &f, int k, int q,
-                                                                          int, int) {
-    return f.v[k][q];
-}
-template <int N1, int N2, int C> __device__ __forceinline__ uint32_t fq_at(const uint32_t *f, int, int q, int n2,
-                                                                          int c) {
-    return __ldg(&f[(PlaneCfg<N1, N2, C>::R * q + n2) * N2 + c]);
-}
-
-template <int N1, int N2, int C, typename FQ>
-__device__ __forceinline__ void plane_exchange_at(float2 *const *tiles, int rank, int k, int p, bool inv, bool phase,
-                                                  bool fwd, const float4 *__restrict__ twx, const FQ &fqr,
-                                                  uint64_t coef, uint32_t dither, const float4 *ptab) {
-    using P = PlaneCfg<N1, N2, C>;
-    constexpr int R = P::R;
-    const int n2 = rank * (R / C) + p / N2;
-    const int c = p % N2;
-    float2 v[C];
-#pragma unroll
-    for (int q = 0; q < C; ++q) v[q] = tiles[q][n2 * P::S + c];
+__device__ __forceinline__ void plane_exchange_math(float2 *v, const uint32_t *fv, int n2, bool inv, bool phase,
+                                                    bool fwd, const float4 *__restrict__ twx, uint64_t coef,
+                                                    uint32_t dither, const float4 *ptab) {
+    constexpr int R = PlaneCfg<N1, N2, C>::R;
     if (inv) {
 #pragma unroll
         for (int q = 1; q < C; ++q) {
@@ -188,7 +170,7 @@ __device__ __forceinline__ void plane_exchange_at(float2 *const *tiles, int rank
     if (phase) {
 #pragma unroll
         for (int q = 0; q < C; ++q)
-            v[q] = apply_phase_tab(v[q], turns_mul(coef, fq_at<N1, N2, C>(fqr, k, q, n2, c)) + dither, ptab);
+            v[q] = apply_phase_tab(v[q], turns_mul(coef, fv[q]) + dither, ptab);
     }
     if (fwd) {
         dft<C, false>(v);
@@ -198,27 +180,51 @@ __device__ __forceinline__ void plane_exchange_at(float2 *const *tiles, int rank
             v[q] = cmul_comp(v[q], make_float2(w.x, w.y), make_float2(w.z, w.w));
         }
     }
-#pragma unroll
-    for (int q = 0; q < C; ++q) tiles[q][n2 * P::S + c] = v[q];
 }
 
-template <int N1, int N2, int C, typename FQ>
-__device__ __forceinline__ void plane_exchange(float2 *const *tiles, int rank, bool inv, bool phase, bool fwd,
-                                               const float4 *__restrict__ twx, const FQ &fqr, uint64_t coef,
-                                               uint32_t dither, const float4 *ptab) {
+// The cross-cluster step over the positions this CTA owns, INF positions at a
+// time (two for clusters of up to 4 CTAs, one for 8, by register budget) so
+// that their INF C remote loads (and potential loads) are in flight before the
+// arithmetic.  base[q] = cluster address of CTA q's tile; fq: this
+// plane's fixed-point potential.
+template <int N1, int N2, int C>
+__device__ __forceinline__ void plane_exchange(const uint32_t *base, int rank, bool inv, bool phase, bool fwd,
+                                               const float4 *__restrict__ twx, const uint32_t *__restrict__ fq,
+                                               uint64_t coef, uint32_t dither, const float4 *ptab) {
     using P = PlaneCfg<N1, N2, C>;
-    constexpr int PPT = PlaneFq<N1, N2, C>::PPT;
-    if constexpr (std::is_pointer<FQ>::value) {
-#pragma unroll 1
-        for (int k = 0; k < PPT; ++k) {
-            const int p = threadIdx.x + k * PLANE_THREADS;
-            if (p < P::PAIRS) plane_exchange_at<N1, N2, C>(tiles, rank, k, p, inv, phase, fwd, twx, fqr, coef, dither, ptab);
-        }
-    } else {
+    constexpr int R = P::R;
+    constexpr int PPT = plane_ppt<N1, N2, C>();
+    constexpr int INF = C >= 8 ? 1 : 2;
 #pragma unroll
-        for (int k = 0; k < PPT; ++k) {
+    for (int k0 = 0; k0 < PPT; k0 += INF) {
+        float2 v[INF][C];
+        uint32_t fv[INF][C];
+        int n2[INF], c[INF];
+        bool live[INF];
+#pragma unroll
+        for (int h = 0; h < INF; ++h) {
+            const int k = k0 + h;
             const int p = threadIdx.x + k * PLANE_THREADS;
-            if (p < P::PAIRS) plane_exchange_at<N1, N2, C>(tiles, rank, k, p, inv, phase, fwd, twx, fqr, coef, dither, ptab);
+            live[h] = k < PPT && p < P::PAIRS;
+            n2[h] = rank * (R / C) + (live[h] ? p : 0) / N2;
+            c[h] = (live[h] ? p : 0) % N2;
+            if (live[h]) {
+                const uint32_t off = (uint32_t)((n2[h] * P::S + c[h]) * sizeof(float2));
+#pragma unroll
+                for (int q = 0; q < C; ++q) v[h][q] = ld_cluster(base[q] + off);
+                if (phase) {
+#pragma unroll
+                    for (int q = 0; q < C; ++q) fv[h][q] = __ldg(&fq[(R * q + n2[h]) * N2 + c[h]]);
+                }
+            }
+        }
+#pragma unroll
+        for (int h = 0; h < INF; ++h) {
+            if (!live[h]) continue;
+            plane_exchange_math<N1, N2, C>(v[h], fv[h], n2[h], inv, phase, fwd, twx, coef, dither, ptab);
+            const uint32_t off = (uint32_t)((n2[h] * P::S + c[h]) * sizeof(float2));
+#pragma unroll
+            for (int q = 0; q < C; ++q) st_cluster(base[q] + off, v[h][q]);
         }
     }
 }
