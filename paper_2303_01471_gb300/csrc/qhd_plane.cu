@@ -48,7 +48,7 @@ __global__ void __launch_bounds__(PLANE_THREADS, plane_min_blocks<N1, N2, C>()) 
         plane_columns<N1, N2, C, true>(tile);
     }
     cluster.sync();
-    plane_exchange<N1, N2, C>(tiles, rank, inv, true, fwd, a.twx, fqr, coef, a.dither, ptab);
+    plane_exchange<N1, N2, C, (C >= 8 ? 1 : 2)>(tiles, rank, inv, true, fwd, a.twx, fqr, coef, a.dither, ptab);
     cluster.sync();
     if (fwd) {
         plane_columns<N1, N2, C, false>(tile);
@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(PLANE_THREADS, 2) k_plane_whole(PlaneArgs a) {
 #pragma unroll 1
     for (int j = 0; j < a.cnt; ++j) {
         const uint64_t coef = a.pot[(int64_t)j * a.batch + b];
-        plane_exchange<N1, N2, C>(tiles, rank, j > 0, true, true, a.twx, fqr, coef,
+        plane_exchange<N1, N2, C, 1>(tiles, rank, j > 0, true, true, a.twx, fqr, coef,
                                   step_dither(a.dither_base + (uint64_t)j), ptab);
         cluster.sync();
         plane_columns<N1, N2, C, false>(tile);
@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(PLANE_THREADS, 2) k_plane_whole(PlaneArgs a) {
         cluster.sync();
     }
     const uint64_t coef = a.pot[(int64_t)a.cnt * a.batch + b];
-    plane_exchange<N1, N2, C>(tiles, rank, a.cnt > 0, a.final_phase != 0, false, a.twx, fqr, coef, 0u, ptab);
+    plane_exchange<N1, N2, C, 1>(tiles, rank, a.cnt > 0, a.final_phase != 0, false, a.twx, fqr, coef, 0u, ptab);
     cluster.sync();
     plane_copy<N1, N2, C, false>(tile, g);
 }

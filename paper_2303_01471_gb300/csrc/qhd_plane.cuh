@@ -183,18 +183,16 @@ __device__ __forceinline__ void plane_exchange_math(float2 *v, const uint32_t *f
 }
 
 // The cross-cluster step over the positions this CTA owns, INF positions at a
-// time (two for clusters of up to 4 CTAs, one for 8, by register budget) so
-// that their INF C remote loads (and potential loads) are in flight before the
-// arithmetic.  base[q] = cluster address of CTA q's tile; fq: this
+// time so that their INF * C remote loads (and potential loads) are in flight
+// before the arithmetic (INF is chosen per kernel by register budget).  base[q] = cluster address of CTA q's tile; fq: this
 // plane's fixed-point potential.
-template <int N1, int N2, int C>
+template <int N1, int N2, int C, int INF>
 __device__ __forceinline__ void plane_exchange(const uint32_t *base, int rank, bool inv, bool phase, bool fwd,
                                                const float4 *__restrict__ twx, const uint32_t *__restrict__ fq,
                                                uint64_t coef, uint32_t dither, const float4 *ptab) {
     using P = PlaneCfg<N1, N2, C>;
     constexpr int R = P::R;
     constexpr int PPT = plane_ppt<N1, N2, C>();
-    constexpr int INF = C >= 8 ? 1 : 2;
 #pragma unroll
     for (int k0 = 0; k0 < PPT; k0 += INF) {
         float2 v[INF][C];
