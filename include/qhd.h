@@ -172,6 +172,44 @@ enum { QHD_SPLIT_STRANG = 0, QHD_SPLIT_LIE_TROTTER = 1 };
 qhd_status qhd_set_splitting(qhd_ctx *ctx, int kind);
 
 /*
+ * Transform used by qhd_evolve for the per-axis DFTs of the kinetic step
+ * (Eq. prod_qhd_fft).  QHD_TRANSFORM_FFT (default): the shared-memory FFT
+ * passes.  QHD_TRANSFORM_TC_DFT: each axis transform is a dense product with
+ * the n x n DFT matrix on the tensor cores, FP16 operands with FP32
+ * accumulation (cuBLAS GEMMs; the phases, transposes and operand splits run
+ * in this library's kernels, with the same fixed-point phase arguments as the
+ * FFT path).  products selects the operand form:
+ *   3: data and DFT matrix as FP16 hi + lo (hi*hi + hi*lo + lo*hi);
+ *   5: the DFT matrix to ~33 bits (two more correction products);
+ *  10: fixed-point slices on a per-instance power-of-two scale (data to 2^-28
+ *      of the instance maximum, DFT matrix 29 bits) whose slice-level sums
+ *      are integers the FP32 accumulator holds exactly (n <= 512).
+ * The tensor cores' FP32 accumulation is biased towards zero over long K
+ * loops, so the 3- and 5-product forms lose norm steadily (measured ~2e-4 per
+ * 100 steps at 64^2..512^2); the 10-product form does not.
+ *
+ * Requires ndim == 2 and n[0] == n[1], a power of two in 64..1024 (64..512 for
+ * products = 10), and batch <= 65535 (else QHD_ERR_UNSUPPORTED;
+ * qhd_tc_workspace_bytes returns 0 for these and for other products).
+ * tc_work_dev: caller-owned device buffer, 256-byte aligned, of at least
+ * qhd_tc_workspace_bytes(...) bytes, kept until the transform is changed or
+ * the context destroyed (else QHD_ERR_WORKSPACE); it holds the DFT matrices,
+ * the FP16 operands, the FP32 products and cuBLAS's workspace.  Creating the
+ * cuBLAS handle is the only device allocation (made by cuBLAS, freed by
+ * qhd_destroy or the next qhd_set_transform).  transform = QHD_TRANSFORM_FFT
+ * frees it and ignores the other arguments.  Unknown transforms or products
+ * other than 3, 5, 10 give QHD_ERR_INVALID_ARG.  Synchronises the stream
+ * (uploads the DFT matrices).
+ */
+enum { QHD_TRANSFORM_FFT = 0, QHD_TRANSFORM_TC_DFT = 1 };
+size_t qhd_tc_workspace_bytes(int ndim, const int64_t *n, int64_t batch, int products);
+qhd_status qhd_set_transform(qhd_ctx *ctx, int transform, int products, void *tc_work_dev,
+                             size_t tc_work_bytes);
+
+/* cuBLAS GEMM calls this context has issued so far (tensor-core transform). */
+int64_t qhd_library_call_count(const qhd_ctx *ctx);
+
+/*
  * Observables of every instance: out_host[batch] receives qhd_obs; prob_dev
  * (optional, NULL to skip) receives |psi|^2 as float32, batch*G values.
  * radius > 0 (the paper's success radius is 0.1).  Synchronises the stream.
@@ -240,7 +278,10 @@ enum {
                                /*      potential phase                           */
     QHD_KCLASS_WHOLE = 7,      /* 2-D: all steps of a chunk, instance resident in */
                                /*      one thread-block cluster                   */
-    QHD_KCLASS_COUNT = 8
+    QHD_KCLASS_TC_SPLIT = 8,   /* tensor-core transform: phase / transpose and    */
+                               /*      FP16 split kernels                         */
+    QHD_KCLASS_TC_GEMM = 9,    /* tensor-core transform: cuBLAS GEMM calls        */
+    QHD_KCLASS_COUNT = 10
 };
 qhd_status qhd_timing_enable(qhd_ctx *ctx, int every);
 qhd_status qhd_timing_read(qhd_ctx *ctx, double *ms_out, int64_t *launches_out, int reset);

@@ -2,7 +2,8 @@
 
 The translation units compile in parallel; the result is
 paper_2303_01471_gb300/_lib/libqhd.so, a plain C ABI (include/qhd.h) with
-the CUDA runtime linked statically.
+the CUDA runtime linked statically and cuBLAS (the tensor-core transform's
+GEMMs) linked dynamically from the toolkit.
 """
 from __future__ import annotations
 
@@ -16,13 +17,17 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libqhd.so")
-SOURCES = ["qhd_kernels.cu", "qhd_plane.cu", "qhd_host.cu", "qhd_static.cu"]
-HEADERS = ["qhd_device.cuh", "qhd_kernels.h", "qhd_plane.cuh"]
+SOURCES = ["qhd_kernels.cu", "qhd_plane.cu", "qhd_host.cu", "qhd_static.cu", "qhd_tcdft.cu"]
+HEADERS = ["qhd_device.cuh", "qhd_kernels.h", "qhd_plane.cuh", "qhd_tcdft.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
+def _cuda_home() -> str:
+    return os.environ.get("CUDA_HOME", "/usr/local/cuda")
+
+
 def _nvcc() -> str:
-    cand = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "bin", "nvcc")
+    cand = os.path.join(_cuda_home(), "bin", "nvcc")
     return cand if os.path.exists(cand) else "nvcc"
 
 
@@ -66,7 +71,9 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None, out: str
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = target + ".tmp"
-    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static"]
+    cudalib = os.path.join(_cuda_home(), "lib64")
+    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static", "-L" + cudalib, "-lcublas",
+           "-Xlinker", "-rpath," + cudalib]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

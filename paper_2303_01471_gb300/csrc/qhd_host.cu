@@ -13,6 +13,7 @@
 #include "qhd.h"
 #include "qhd_device.cuh"
 #include "qhd_kernels.h"
+#include "qhd_tcdft.h"
 
 using namespace qhd;
 
@@ -137,6 +138,9 @@ struct qhd_ctx {
     std::vector<InstDev> inst_host;
     std::vector<double> coord_host;
     // device-time accounting (qhd_timing_*)
+    // tensor-core transform (qhd_set_transform)
+    TcState *tc = nullptr;
+    int64_t lib_calls = 0;
     int timing_every = 0;
     struct TimedLaunch {
         int kclass;
@@ -150,6 +154,7 @@ struct qhd_ctx {
             cudaEventDestroy(r.stop);
         }
         for (auto e : event_pool) cudaEventDestroy(e);
+        tc_destroy(tc);
     }
 };
 
@@ -536,6 +541,64 @@ qhd_status qhd_get_time(const qhd_ctx *c, double *t_out, int64_t *steps_out) {
     return QHD_OK;
 }
 
+namespace {
+
+// One chunk of steps with the tensor-core transform: per step a potential
+// split, W along axis 1, a transposing split, W along axis 0, the kinetic
+// split, conj W along axis 0, a transposing split, conj W along axis 1.  The
+// state stays in the transform's product buffer between steps and chunks.
+qhd_status evolve_tc_chunk(qhd_ctx *c, int64_t j0, int64_t cnt, bool last_chunk, int64_t ktb) {
+    const int64_t B = c->batch;
+    TcPhaseArgs ta{};
+    ta.psi = c->psi;
+    ta.fq = c->fq;
+    ta.ptab = c->ptab;
+    ta.ksum = c->ksum;
+    ta.kt_batch = ktb;
+    auto gemm = [&](bool inv, bool sample) -> qhd_status {
+        TimedScope ts(c, QHD_KCLASS_TC_GEMM, sample);
+        cudaError_t e = tc_gemm(c->tc, inv, &c->lib_calls);
+        if (e != cudaSuccess) return fail(c, QHD_ERR_CUDA, "tensor-core GEMM failed: %s", cudaGetErrorString(e));
+        return QHD_OK;
+    };
+    for (int64_t jl = 0; jl < cnt; ++jl) {
+        const int64_t j = j0 + jl;
+        const bool sample = c->timing_every > 0 && j % c->timing_every == 0;
+        ta.pot = c->pot + jl * B;
+        ta.dither = step_dither((uint64_t)(c->steps_done + j));
+        ta.kt = c->kt + jl * ktb * c->ksum;
+        qhd_status s;
+        {
+            TimedScope ts(c, QHD_KCLASS_TC_SPLIT, sample);
+            QHD_CUDA(c, tc_split_potential(c->tc, ta, j == 0, c->stream, &c->launches));
+        }
+        if ((s = gemm(false, sample)) != QHD_OK) return s;
+        {
+            TimedScope ts(c, QHD_KCLASS_TC_SPLIT, sample);
+            QHD_CUDA(c, tc_split_transpose(c->tc, c->stream, &c->launches));
+        }
+        if ((s = gemm(false, sample)) != QHD_OK) return s;
+        {
+            TimedScope ts(c, QHD_KCLASS_TC_SPLIT, sample);
+            QHD_CUDA(c, tc_split_kinetic(c->tc, ta, c->stream, &c->launches));
+        }
+        if ((s = gemm(true, sample)) != QHD_OK) return s;
+        {
+            TimedScope ts(c, QHD_KCLASS_TC_SPLIT, sample);
+            QHD_CUDA(c, tc_split_transpose(c->tc, c->stream, &c->launches));
+        }
+        if ((s = gemm(true, sample)) != QHD_OK) return s;
+    }
+    if (last_chunk) {
+        ta.pot = c->pot + cnt * B;
+        ta.dither = 0;
+        QHD_CUDA(c, tc_finish(c->tc, ta, true, c->stream, &c->launches));
+    }
+    return QHD_OK;
+}
+
+}  // namespace
+
 qhd_status qhd_evolve(qhd_ctx *c, double T, double dt) {
     qhd_status s = check_ctx(c);
     if (s != QHD_OK) return s;
@@ -597,6 +660,11 @@ qhd_status qhd_evolve(qhd_ctx *c, double T, double dt) {
             o.kt_batch = ktb;
             TimedScope ts(c, QHD_KCLASS_ONED, true);
             QHD_LAUNCH(c, launch_oned((int)c->n[0], o, c->stream));
+            continue;
+        }
+        if (c->tc) {
+            s = evolve_tc_chunk(c, j0, cnt, last_chunk, ktb);
+            if (s != QHD_OK) return s;
             continue;
         }
         if (c->plane_mode == 2) {
@@ -818,6 +886,45 @@ qhd_status qhd_set_splitting(qhd_ctx *c, int kind) {
     c->split = kind;
     return QHD_OK;
 }
+
+size_t qhd_tc_workspace_bytes(int ndim, const int64_t *n, int64_t batch, int products) {
+    if (!shape_ok(ndim, n, batch) || ndim != 2 || !tc_supported((int)n[0], (int)n[1], batch)) return 0;
+    if (!tc_products_ok((int)n[0], products)) return 0;
+    return tc_workspace_bytes((int)n[0], batch, products);
+}
+
+qhd_status qhd_set_transform(qhd_ctx *c, int transform, int products, void *tc_work_dev, size_t tc_work_bytes) {
+    qhd_status s = check_ctx(c);
+    if (s != QHD_OK) return s;
+    if (transform == QHD_TRANSFORM_FFT) {
+        if (c->tc) {
+            QHD_CUDA(c, cudaStreamSynchronize(c->stream));
+            tc_destroy(c->tc);
+            c->tc = nullptr;
+        }
+        return QHD_OK;
+    }
+    if (transform != QHD_TRANSFORM_TC_DFT) return fail(c, QHD_ERR_INVALID_ARG, "unknown transform %d", transform);
+    if (products != 3 && products != 5 && products != 10)
+        return fail(c, QHD_ERR_INVALID_ARG, "products must be 3, 5 or 10");
+    if (c->ndim != 2 || !tc_supported((int)c->n[0], (int)c->n[1], c->batch) ||
+        !tc_products_ok((int)c->n[0], products))
+        return fail(c, QHD_ERR_UNSUPPORTED,
+                    "tensor-core transform needs a square 2-D grid, n a power of two in 64..1024 (64..512 for "
+                    "10 products), batch <= 65535");
+    if (!tc_work_dev || ((uintptr_t)tc_work_dev & 255) ||
+        tc_work_bytes < tc_workspace_bytes((int)c->n[0], c->batch, products))
+        return fail(c, QHD_ERR_WORKSPACE, "tensor-core workspace too small or not 256-byte aligned");
+    QHD_CUDA(c, cudaStreamSynchronize(c->stream));
+    tc_destroy(c->tc);
+    c->tc = nullptr;
+    const char *why = nullptr;
+    c->tc = tc_create((int)c->n[0], c->batch, products, tc_work_dev, tc_work_bytes, c->stream, &why);
+    if (!c->tc) return fail(c, QHD_ERR_CUDA, "%s", why ? why : "tensor-core transform set-up failed");
+    return QHD_OK;
+}
+
+int64_t qhd_library_call_count(const qhd_ctx *c) { return c ? c->lib_calls : 0; }
 
 qhd_status qhd_timing_enable(qhd_ctx *c, int every) {
     qhd_status s = check_ctx(c);

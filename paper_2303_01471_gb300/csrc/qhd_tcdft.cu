@@ -1,0 +1,585 @@
+// qhd_tcdft.cu -- tensor-core DFT form of the 2-D step.
+//
+// The per-axis transforms of the pseudo-spectral step (Eq. prod_qhd_fft) are
+// dense matrix products on the tensor cores.  B instances of n x n points are
+// a matrix of B*n rows of n complex values, stored per row as [re | im]; one
+// axis transform is the product of that matrix with the real block form of
+// the DFT matrix,
+//     [xr | xi] . [[Wr, Wi], [-Wi, Wr]] = [Xr | Xi],   W_jk = exp(-+2 pi i jk / n).
+// W is symmetric, so the transform along axis 0 is the same right product
+// after each instance is transposed; a step is
+//     potential phase -> W (axis 1) -> transpose -> W (axis 0) -> kinetic phase
+//     -> conj W (axis 0) -> transpose -> conj W (axis 1)
+// and ends in natural layout, ready for the next step's potential phase.  The
+// state stays in the FP32 product buffer between steps; psi is read at the
+// start of an evolve call and written at its end.  The kernels here apply the
+// phases, transpose and split the operands; the GEMMs are cuBLAS FP16 GEMMs
+// with FP32 accumulation.
+//
+// Two operand forms.
+//
+// Floating hi/lo (3 or 5 products).  A value x (FP32) is split a = fp16(x),
+// c = fp16(x - a), and b = fp16(2^-11 a), d = fp16(2^-11 c) feed the
+// correction terms; W = W_hi + 2^-11 W_mid + 2^-22 W_lo with the parts FP16
+// numbers of about |W|.  One GEMM over concatenated K segments:
+//   3 products: [a | c | b]         . [W_hi; W_hi; W_mid]
+//   5 products: [a | c | b | b | d] . [W_hi; W_hi; W_mid; 2^-11 W_lo; W_mid]
+// Every stage is unitary up to a known power of two, so a fixed scale keeps
+// the operands in range: psi is scaled by 2^14, each GEMM by alpha = 2^-h
+// (2^h >= sqrt n), and the kinetic split takes out the 1/n^2 its table
+// carries.  The tensor cores' FP32 accumulation is not round-to-nearest: the
+// result of a long K loop is biased towards zero (about -1e-9 K relative per
+// GEMM, measured), and over hundreds of steps that bias, not the operand
+// precision, decides the error of this form.
+//
+// Fixed-point slices (10 products, an error-free splitting in the manner of
+// Ozaki et al.).  Each instance is scaled by a power of two 2^(7-e) with
+// 2^e > max |z| over the instance, and every real value u (|u| <= 2^7) is
+// cut into integer slices u = a0 + 2^-7 a1 + 2^-14 a2 + 2^-21 a3, each
+// |a_i| <= 2^7 (this holds the FP32 value to 2^-28 of the instance maximum);
+// 2^7 W likewise into integer slices w0..w3 (29 bits).  A GEMM of one slice
+// level sums integers that the FP32 accumulator holds exactly whatever its
+// rounding (below 2^24 for levels 0 and 1; levels 2 and 3 are ~2^-14 and
+// ~2^-21 corrections), so no bias enters:
+//   level L: [a0 | .. | aL] . [wL; ..; w0]        (K = 2n (L + 1))
+// and the levels are combined smallest first through the GEMM epilogue
+// (C = alpha acc + beta C in FP32, alpha = 2^-7L).  A per-instance
+// power-of-two exponent E (true value = buffer * 2^E) follows the scales and
+// is read back at the end.
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+#include <cublas_v2.h>
+#include <cuda_fp16.h>
+
+#include "qhd_device.cuh"
+#include "qhd_tcdft.h"
+
+namespace qhd {
+
+namespace {
+
+constexpr int TC_S = 14;               // log2 of the operand scale, floating form
+constexpr int TC_THREADS = 256;
+constexpr int TC_TR = 64, TC_TC = 32;  // transpose tile: input rows x input columns
+constexpr int TC_FIXED = 10;           // products of the fixed-point form
+constexpr size_t TC_CUBLAS_WS = size_t(32) << 20;
+
+struct SplitOut {
+    __half *a;     // B*n rows of segments of 2n FP16
+    int64_t kp;    // row length in halves
+    int n;
+};
+
+// Per-instance scale state of the fixed-point form.
+struct FixedScale {
+    const unsigned *maxin;  // max |z|^2 of the split's input, per instance (float bits)
+    unsigned *maxclr;       // the other max buffer, cleared for the next transform
+    int *e;                 // per-instance exponent: true value = buffer * 2^E
+    int e_add;              // extra exponent of this split (-2 log2 n for the kinetic split)
+    int from_psi;           // E restarts at this split
+};
+
+// ---------------------------------------------------------- floating hi/lo
+// Split of two neighbouring values (columns col, col+1 of one row half) into
+// every segment.
+template <int P>
+__device__ __forceinline__ void put_pair(const SplitOut &o, int64_t row, int col, float x0, float x1) {
+    const __half a0 = __float2half_rn(x0), a1 = __float2half_rn(x1);
+    const __half c0 = __float2half_rn(x0 - __half2float(a0)), c1 = __float2half_rn(x1 - __half2float(a1));
+    const float sd = 1.0f / 2048.0f;
+    const __half2 A = __halves2half2(a0, a1);
+    const __half2 Cc = __halves2half2(c0, c1);
+    const __half2 Bb = __floats2half2_rn(__half2float(a0) * sd, __half2float(a1) * sd);
+    const int m = 2 * o.n;
+    __half2 *dst = reinterpret_cast<__half2 *>(o.a + row * o.kp + col);
+    dst[0] = A;
+    dst[m / 2] = Cc;
+    dst[m] = Bb;
+    if (P == 5) {
+        const __half2 D = __floats2half2_rn(__half2float(c0) * sd, __half2float(c1) * sd);
+        dst[3 * m / 2] = Bb;
+        dst[2 * m] = D;
+    }
+}
+
+// Fixed-point slices of two neighbouring values u0, u1 (|u| <= 2^7):
+// segments [a0 | a1 | a2 | a3].  Each subtraction and power-of-two product is
+// exact in FP32; only the last slice rounds (below 2^-21).
+__device__ __forceinline__ void put_fixed_pair(const SplitOut &o, int64_t row, int col, float u0, float u1) {
+    const int m = 2 * o.n;
+    __half2 *dst = reinterpret_cast<__half2 *>(o.a + row * o.kp + col);
+    float r0 = u0, r1 = u1;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float p = rintf(r0), q = rintf(r1);
+        dst[k * (m / 2)] = __floats2half2_rn(p, q);
+        r0 = (r0 - p) * 128.f;
+        r1 = (r1 - q) * 128.f;
+    }
+}
+
+// Exponent e with 2^e > max |z| of an instance (max |z|^2 given as float bits).
+__device__ __forceinline__ int tc_exponent(unsigned m2bits) {
+    const float m2 = __uint_as_float(m2bits);
+    if (!(m2 > 0.f)) return 0;
+    int e;
+    frexpf(sqrtf(m2), &e);
+    return e;
+}
+
+template <int P>
+__device__ __forceinline__ void put_two(const SplitOut &o, int64_t row, int col, float x0, float x1) {
+    if (P == TC_FIXED) put_fixed_pair(o, row, col, x0, x1);
+    else put_pair<P>(o, row, col, x0, x1);
+}
+
+// mode 0: potential phase, input psi (interleaved); 1: potential phase, input
+// the product buffer; 2: kinetic phase, input the product buffer (rows hold
+// frequency k1 of axis 1, columns frequency k0 of axis 0).  One thread per two
+// neighbouring columns of one row.  scale: the floating form's fixed scale.
+template <int P, int MODE>
+__global__ void __launch_bounds__(TC_THREADS) k_tc_split(SplitOut o, const float *cbuf, TcPhaseArgs a,
+                                                         int64_t rows, float scale, FixedScale fs) {
+    __shared__ float4 ptab[PHASE_TAB];
+    if (MODE != 2) {
+        load_phase_tab(ptab, a.ptab);
+        __syncthreads();
+    }
+    const int n = o.n, half = n / 2;
+    const int64_t total = rows * half;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = i / half;
+        const int col = 2 * (int)(i - row * half);
+        const int64_t b = row / n;
+        float sc = scale;
+        if (P == TC_FIXED) {
+            const int e = tc_exponent(fs.maxin[b]);
+            sc = ldexpf(scale, 7 - e);
+            if (row == b * n && col == 0) {  // one thread per instance
+                fs.e[b] = (fs.from_psi ? 0 : fs.e[b]) + e - 14 + fs.e_add;
+                fs.maxclr[b] = 0u;
+            }
+        }
+        float2 z0, z1;
+        if (MODE == 0) {
+            const float4 v = *reinterpret_cast<const float4 *>(a.psi + row * n + col);
+            z0 = make_float2(v.x * sc, v.y * sc);
+            z1 = make_float2(v.z * sc, v.w * sc);
+        } else {
+            const float2 re = *reinterpret_cast<const float2 *>(cbuf + row * 2 * n + col);
+            const float2 im = *reinterpret_cast<const float2 *>(cbuf + row * 2 * n + n + col);
+            z0 = make_float2(re.x * sc, im.x * sc);
+            z1 = make_float2(re.y * sc, im.y * sc);
+        }
+        if (MODE == 2) {
+            // kinetic factor of (k0, k1): axis 0 first, then axis 1
+            const float4 *kb = a.kt + (a.kt_batch == 1 ? 0 : b) * a.ksum;
+            const int k1 = (int)(row - b * n);
+            const float4 f1 = __ldg(&kb[n + k1]);
+            const float4 f0a = __ldg(&kb[col]), f0b = __ldg(&kb[col + 1]);
+            z0 = cmul_comp(z0, make_float2(f0a.x, f0a.y), make_float2(f0a.z, f0a.w));
+            z0 = cmul_comp(z0, make_float2(f1.x, f1.y), make_float2(f1.z, f1.w));
+            z1 = cmul_comp(z1, make_float2(f0b.x, f0b.y), make_float2(f0b.z, f0b.w));
+            z1 = cmul_comp(z1, make_float2(f1.x, f1.y), make_float2(f1.z, f1.w));
+        } else {
+            const uint64_t coef = a.pot[b];
+            const uint2 f = *reinterpret_cast<const uint2 *>(a.fq + row * n + col);
+            z0 = apply_phase_tab(z0, turns_mul(coef, f.x) + a.dither, ptab);
+            z1 = apply_phase_tab(z1, turns_mul(coef, f.y) + a.dither, ptab);
+        }
+        put_two<P>(o, row, col, z0.x, z1.x);
+        put_two<P>(o, row, n + col, z0.y, z1.y);
+    }
+}
+
+// Product buffer rows (b, r), columns c -> split rows (b, c), columns r.
+// Tile: TC_TR input rows x TC_TC input columns, block (32, 8).
+template <int P>
+__global__ void __launch_bounds__(TC_THREADS) k_tc_split_t(SplitOut o, const float *cbuf, FixedScale fs) {
+    __shared__ float tr[TC_TR][TC_TC + 1], ti[TC_TR][TC_TC + 1];
+    const int n = o.n;
+    const int64_t b = blockIdx.z;
+    const int r0 = blockIdx.y * TC_TR, c0 = blockIdx.x * TC_TC;
+    float sc = 1.f;
+    if (P == TC_FIXED) {
+        const int e = tc_exponent(fs.maxin[b]);
+        sc = ldexpf(1.f, 7 - e);
+        if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
+            fs.e[b] = fs.e[b] + e - 14;
+            fs.maxclr[b] = 0u;
+        }
+    }
+    const float *base = cbuf + b * (int64_t)n * 2 * n;
+    for (int k = threadIdx.y; k < TC_TR; k += blockDim.y) {
+        const float *rp = base + (int64_t)(r0 + k) * 2 * n + c0 + threadIdx.x;
+        tr[k][threadIdx.x] = rp[0] * sc;
+        ti[k][threadIdx.x] = rp[n] * sc;
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < TC_TC; k += blockDim.y) {
+        const int64_t row = b * n + c0 + k;
+        const int r = 2 * threadIdx.x;
+        put_two<P>(o, row, r0 + r, tr[r][k], tr[r + 1][k]);
+        put_two<P>(o, row, n + r0 + r, ti[r][k], ti[r + 1][k]);
+    }
+}
+
+// Per-instance max |z|^2 of psi (interleaved) or of the product buffer
+// (rows of [re | im]); grid (blocks per instance, B).
+template <bool INTERLEAVED>
+__global__ void __launch_bounds__(TC_THREADS) k_tc_absmax(const float *in, int n, unsigned *maxbits) {
+    const int64_t b = blockIdx.y;
+    const int64_t g = (int64_t)n * n;
+    const float *base = in + b * g * 2;
+    const int half = n / 2;
+    float m = 0.f;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < g / 2; p += (int64_t)gridDim.x * blockDim.x) {
+        if (INTERLEAVED) {
+            const float4 v = reinterpret_cast<const float4 *>(base)[p];
+            m = fmaxf(m, fmaxf(v.x * v.x + v.y * v.y, v.z * v.z + v.w * v.w));
+        } else {
+            const int64_t row = p / half;
+            const int col = 2 * (int)(p - row * half);
+            const float2 re = *reinterpret_cast<const float2 *>(base + row * 2 * n + col);
+            const float2 im = *reinterpret_cast<const float2 *>(base + row * 2 * n + n + col);
+            m = fmaxf(m, fmaxf(re.x * re.x + im.x * im.x, re.y * re.y + im.y * im.y));
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    __shared__ float wm[TC_THREADS / 32];
+    if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < TC_THREADS / 32; ++w) m = fmaxf(m, wm[w]);
+        atomicMax(&maxbits[b], __float_as_uint(m));
+    }
+}
+
+// Product buffer (natural layout) -> psi, with the final potential phase.
+// Floating form: a fixed scale; fixed-point form: 2^E per instance.
+__global__ void __launch_bounds__(TC_THREADS) k_tc_finish(const float *cbuf, TcPhaseArgs a, int n, int64_t rows,
+                                                         float scale, const int *e, int phase) {
+    __shared__ float4 ptab[PHASE_TAB];
+    load_phase_tab(ptab, a.ptab);
+    __syncthreads();
+    const int half = n / 2;
+    const int64_t total = rows * half;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = i / half;
+        const int col = 2 * (int)(i - row * half);
+        const int64_t b = row / n;
+        const float sc = e ? ldexpf(1.f, e[b]) : scale;
+        const float2 re = *reinterpret_cast<const float2 *>(cbuf + row * 2 * n + col);
+        const float2 im = *reinterpret_cast<const float2 *>(cbuf + row * 2 * n + n + col);
+        float2 z0 = make_float2(re.x * sc, im.x * sc), z1 = make_float2(re.y * sc, im.y * sc);
+        if (phase) {
+            const uint64_t coef = a.pot[b];
+            const uint2 f = *reinterpret_cast<const uint2 *>(a.fq + row * n + col);
+            z0 = apply_phase_tab(z0, turns_mul(coef, f.x), ptab);
+            z1 = apply_phase_tab(z1, turns_mul(coef, f.y), ptab);
+        }
+        *reinterpret_cast<float4 *>(a.psi + row * n + col) = make_float4(z0.x, z0.y, z1.x, z1.y);
+    }
+}
+
+size_t tc_align(size_t v) { return (v + 255) & ~size_t(255); }
+
+int log2i(int n) {
+    int l = 0;
+    while ((1 << l) < n) ++l;
+    return l;
+}
+
+// K extent (in units of 2n) of the DFT-matrix buffers of one direction, and
+// the row length (in units of 2n) of the split operands.
+int w_segments(int products) { return products == TC_FIXED ? 1 + 2 + 3 + 4 : products; }
+int a_segments(int products) { return products == TC_FIXED ? 4 : products; }
+
+}  // namespace
+
+struct TcState {
+    int n = 0, products = 5, h = 0, l = 0;
+    int64_t batch = 0;
+    cublasHandle_t handle = nullptr;
+    __half *w[2] = {nullptr, nullptr};  // forward, inverse; fixed form: levels 0 | 1 | 2 | 3 back to back
+    __half *a = nullptr;                // B*n rows of split operands
+    float *c = nullptr;                 // B*n x 2n products
+    unsigned *maxbits = nullptr;        // fixed form: 2 x B max |z|^2 buffers
+    int *e = nullptr;                   // fixed form: B exponents
+    int cur = 0;                        // max buffer of the next split
+    int grid = 0;
+};
+
+bool tc_supported(int n0, int n1, int64_t batch) {
+    // transpose grids index instances by blockIdx.z; cuBLAS takes B*n rows as int
+    return n0 == n1 && n0 >= 64 && n0 <= 1024 && (n0 & (n0 - 1)) == 0 && batch >= 1 && batch <= 65535;
+}
+
+bool tc_products_ok(int n, int products) {
+    // the fixed-point level-0 and level-1 sums stay below 2^24 for K = 2n <= 1024
+    return products == 3 || products == 5 || (products == TC_FIXED && n <= 512);
+}
+
+size_t tc_workspace_bytes(int n, int64_t batch, int products) {
+    const size_t m = 2 * (size_t)n, rows = (size_t)batch * (size_t)n;
+    size_t t = 0;
+    t += 2 * tc_align((size_t)w_segments(products) * m * m * sizeof(__half));
+    t += tc_align(rows * (size_t)a_segments(products) * m * sizeof(__half));
+    t += tc_align(rows * m * sizeof(float));
+    t += tc_align(2 * (size_t)batch * sizeof(unsigned));
+    t += tc_align((size_t)batch * sizeof(int));
+    t += TC_CUBLAS_WS;
+    return t;
+}
+
+int tc_products(const TcState *t) { return t ? t->products : 0; }
+
+// Real block form [[Wr, Wi], [-Wi, Wr]] of W (d = 0) or conj W (d = 1), entry (row, col).
+static double dft_block(int n, int d, size_t row, size_t col) {
+    const size_t j = row % n, k = col % n;
+    const double ang = 2.0 * 3.141592653589793238462643383279502884 * (double)((j * k) % n) / (double)n;
+    const double wr = cos(ang), wi = (d == 0 ? -1.0 : 1.0) * sin(ang);
+    const int q = (int)(row / n) * 2 + (int)(col / n);
+    return q == 0 || q == 3 ? wr : (q == 1 ? wi : -wi);
+}
+
+TcState *tc_create(int n, int64_t batch, int products, void *ws, size_t ws_bytes, cudaStream_t s, const char **why) {
+    *why = nullptr;
+    if (!tc_products_ok(n, products)) {
+        *why = "unsupported number of products for this n";
+        return nullptr;
+    }
+    if (!ws || ((uintptr_t)ws & 255) || ws_bytes < tc_workspace_bytes(n, batch, products)) {
+        *why = "tensor-core workspace too small or not 256-byte aligned";
+        return nullptr;
+    }
+    TcState *t = new TcState();
+    t->n = n;
+    t->batch = batch;
+    t->products = products;
+    t->l = log2i(n);
+    t->h = (t->l + 1) / 2;
+    const size_t m = 2 * (size_t)n, rows = (size_t)batch * (size_t)n;
+    const size_t wseg = (size_t)w_segments(products);
+    char *p = (char *)ws;
+    t->w[0] = (__half *)p;
+    p += tc_align(wseg * m * m * sizeof(__half));
+    t->w[1] = (__half *)p;
+    p += tc_align(wseg * m * m * sizeof(__half));
+    t->a = (__half *)p;
+    p += tc_align(rows * (size_t)a_segments(products) * m * sizeof(__half));
+    t->c = (float *)p;
+    p += tc_align(rows * m * sizeof(float));
+    t->maxbits = (unsigned *)p;
+    p += tc_align(2 * (size_t)batch * sizeof(unsigned));
+    t->e = (int *)p;
+    p += tc_align((size_t)batch * sizeof(int));
+    void *cublas_ws = p;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    t->grid = (sms > 0 ? sms : 152) * 8;
+
+    // W and conj W from FP64, split on the host
+    std::vector<__half> host(wseg * m * m);
+    for (int d = 0; d < 2; ++d) {
+        for (size_t row = 0; row < m; ++row)
+            for (size_t col = 0; col < m; ++col) {
+                const double v = dft_block(n, d, row, col);
+                if (products != TC_FIXED) {
+                    // hi, mid, lo of about |W| each; the lo part is paired with
+                    // b = 2^-11 a, so it carries 2^11 (v - hi - 2^-11 mid) = r1 - mid
+                    const __half hi = __double2half(v);
+                    const double r1 = (v - (double)__half2float(hi)) * 2048.0;
+                    const __half mid = __double2half(r1);
+                    const __half lo = __double2half(r1 - (double)__half2float(mid));
+                    const __half part[3] = {hi, mid, lo};
+                    const int seg3[3] = {0, 0, 1}, seg5[5] = {0, 0, 1, 2, 1};
+                    const int *seg = products == 3 ? seg3 : seg5;
+                    for (int sidx = 0; sidx < products; ++sidx) host[(sidx * m + row) * m + col] = part[seg[sidx]];
+                } else {
+                    // integer slices of 2^7 v: w0 + 2^-7 w1 + 2^-14 w2 + 2^-21 w3
+                    double r = v * 128.0, w[4];
+                    for (int k = 0; k < 4; ++k) {
+                        w[k] = std::nearbyint(r);
+                        r = (r - w[k]) * 128.0;
+                    }
+                    // level L pairs [a0 | .. | aL] with [wL; ..; w0]
+                    int sidx = 0;
+                    for (int lev = 0; lev < 4; ++lev)
+                        for (int i = 0; i <= lev; ++i) host[(sidx++ * m + row) * m + col] = __double2half(w[lev - i]);
+                }
+            }
+        if (cudaMemcpyAsync(t->w[d], host.data(), host.size() * sizeof(__half), cudaMemcpyHostToDevice, s) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+            *why = "copy of the DFT matrices failed";
+            delete t;
+            return nullptr;
+        }
+    }
+    if (cublasCreate(&t->handle) != CUBLAS_STATUS_SUCCESS) {
+        *why = "cublasCreate failed";
+        t->handle = nullptr;
+        delete t;
+        return nullptr;
+    }
+    if (cublasSetStream(t->handle, s) != CUBLAS_STATUS_SUCCESS ||
+        cublasSetWorkspace(t->handle, cublas_ws, TC_CUBLAS_WS) != CUBLAS_STATUS_SUCCESS ||
+        cublasSetMathMode(t->handle, CUBLAS_DEFAULT_MATH) != CUBLAS_STATUS_SUCCESS) {
+        *why = "cuBLAS stream / workspace set-up failed";
+        cublasDestroy(t->handle);
+        delete t;
+        return nullptr;
+    }
+    return t;
+}
+
+void tc_destroy(TcState *t) {
+    if (!t) return;
+    if (t->handle) cublasDestroy(t->handle);
+    delete t;
+}
+
+static SplitOut split_out(TcState *t) {
+    SplitOut o;
+    o.a = t->a;
+    o.kp = (int64_t)a_segments(t->products) * 2 * t->n;
+    o.n = t->n;
+    return o;
+}
+
+// Fixed form: the max pass over the split's input, and the scale state the
+// split reads (the current max buffer) and prepares (the other one).
+static cudaError_t fixed_prepare(TcState *t, const float *in, bool interleaved, int e_add, bool from_psi,
+                                 cudaStream_t s, FixedScale *fs, int64_t *launches) {
+    if (from_psi) {
+        cudaError_t e = cudaMemsetAsync(t->maxbits, 0, 2 * (size_t)t->batch * sizeof(unsigned), s);
+        if (e != cudaSuccess) return e;
+        t->cur = 0;
+    }
+    unsigned *mcur = t->maxbits + (size_t)t->cur * t->batch;
+    const int64_t pairs = (int64_t)t->n * t->n / 2;
+    int per = (int)((pairs + TC_THREADS - 1) / TC_THREADS);
+    const int cap = (int)((t->grid + t->batch - 1) / t->batch) * 2;
+    if (per > cap) per = cap;
+    if (per < 1) per = 1;
+    const dim3 grid((unsigned)per, (unsigned)t->batch);
+    if (interleaved) k_tc_absmax<true><<<grid, TC_THREADS, 0, s>>>(in, t->n, mcur);
+    else k_tc_absmax<false><<<grid, TC_THREADS, 0, s>>>(in, t->n, mcur);
+    ++*launches;
+    fs->maxin = mcur;
+    fs->maxclr = t->maxbits + (size_t)(t->cur ^ 1) * t->batch;
+    fs->e = t->e;
+    fs->e_add = e_add;
+    fs->from_psi = from_psi ? 1 : 0;
+    t->cur ^= 1;
+    return cudaGetLastError();
+}
+
+cudaError_t tc_split_potential(TcState *t, const TcPhaseArgs &a, bool from_psi, cudaStream_t s, int64_t *launches) {
+    const int64_t rows = t->batch * t->n;
+    const SplitOut o = split_out(t);
+    FixedScale fs{};
+    if (t->products == TC_FIXED) {
+        cudaError_t e = fixed_prepare(t, from_psi ? reinterpret_cast<const float *>(a.psi) : t->c, from_psi, 0,
+                                      from_psi, s, &fs, launches);
+        if (e != cudaSuccess) return e;
+        if (from_psi) k_tc_split<TC_FIXED, 0><<<t->grid, TC_THREADS, 0, s>>>(o, t->c, a, rows, 1.f, fs);
+        else k_tc_split<TC_FIXED, 1><<<t->grid, TC_THREADS, 0, s>>>(o, t->c, a, rows, 1.f, fs);
+    } else {
+        // scale to 2^14 |psi|: psi directly, or the product buffer 2^(14 - 4h) n^2 psi
+        const float scale = from_psi ? ldexpf(1.f, TC_S) : ldexpf(1.f, 4 * t->h - 2 * t->l);
+        if (t->products == 3) {
+            if (from_psi) k_tc_split<3, 0><<<t->grid, TC_THREADS, 0, s>>>(o, t->c, a, rows, scale, fs);
+            else k_tc_split<3, 1><<<t->grid, TC_THREADS, 0, s>>>(o, t->c, a, rows, scale, fs);
+        } else {
+            if (from_psi) k_tc_split<5, 0><<<t->grid, TC_THREADS, 0, s>>>(o, t->c, a, rows, scale, fs);
+            else k_tc_split<5, 1><<<t->grid, TC_THREADS, 0, s>>>(o, t->c, a, rows, scale, fs);
+        }
+    }
+    ++*launches;
+    return cudaGetLastError();
+}
+
+cudaError_t tc_split_kinetic(TcState *t, const TcPhaseArgs &a, cudaStream_t s, int64_t *launches) {
+    const int64_t rows = t->batch * t->n;
+    const SplitOut o = split_out(t);
+    // the axis-0 kinetic factors carry the inverse transform's 1 / n^2; the
+    // unnormalised conj W products restore it, so it is taken out here
+    const float scale = ldexpf(1.f, 2 * t->l);
+    FixedScale fs{};
+    if (t->products == TC_FIXED) {
+        cudaError_t e = fixed_prepare(t, t->c, false, -2 * t->l, false, s, &fs, launches);
+        if (e != cudaSuccess) return e;
+        k_tc_split<TC_FIXED, 2><<<t->grid, TC_THREADS, 0, s>>>(o, t->c, a, rows, scale, fs);
+    } else if (t->products == 3) {
+        k_tc_split<3, 2><<<t->grid, TC_THREADS, 0, s>>>(o, t->c, a, rows, scale, fs);
+    } else {
+        k_tc_split<5, 2><<<t->grid, TC_THREADS, 0, s>>>(o, t->c, a, rows, scale, fs);
+    }
+    ++*launches;
+    return cudaGetLastError();
+}
+
+cudaError_t tc_split_transpose(TcState *t, cudaStream_t s, int64_t *launches) {
+    const dim3 grid((unsigned)(t->n / TC_TC), (unsigned)(t->n / TC_TR), (unsigned)t->batch), block(32, 8);
+    const SplitOut o = split_out(t);
+    FixedScale fs{};
+    if (t->products == TC_FIXED) {
+        cudaError_t e = fixed_prepare(t, t->c, false, 0, false, s, &fs, launches);
+        if (e != cudaSuccess) return e;
+        k_tc_split_t<TC_FIXED><<<grid, block, 0, s>>>(o, t->c, fs);
+    } else if (t->products == 3) {
+        k_tc_split_t<3><<<grid, block, 0, s>>>(o, t->c, fs);
+    } else {
+        k_tc_split_t<5><<<grid, block, 0, s>>>(o, t->c, fs);
+    }
+    ++*launches;
+    return cudaGetLastError();
+}
+
+// One cuBLAS GEMM: row-major C[rows][m] = alpha A[rows][:k] . W[k][m] + beta C,
+// A with row length lda; in cuBLAS's column-major terms C^T = W^T A^T.
+static cublasStatus_t gemm_call(TcState *t, const __half *w, int k, int lda, float alpha, float beta) {
+    const int m = 2 * t->n;
+    const int rows = (int)(t->batch * t->n);
+    return cublasGemmEx(t->handle, CUBLAS_OP_N, CUBLAS_OP_N, m, rows, k, &alpha, w, CUDA_R_16F, m, t->a, CUDA_R_16F,
+                        lda, &beta, t->c, CUDA_R_32F, m, CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT);
+}
+
+cudaError_t tc_gemm(TcState *t, bool inverse, int64_t *calls) {
+    const int m = 2 * t->n;
+    const __half *w = t->w[inverse ? 1 : 0];
+    cublasStatus_t st;
+    if (t->products == TC_FIXED) {
+        const int lda = 4 * m;
+        const size_t mm = (size_t)m * m;
+        // levels smallest first, combined in the epilogue: C = 2^-7L level_L + C
+        const size_t off[4] = {0, 1, 3, 6};
+        st = CUBLAS_STATUS_SUCCESS;
+        for (int lev = 3; lev >= 0 && st == CUBLAS_STATUS_SUCCESS; --lev)
+            st = gemm_call(t, w + off[lev] * mm, (lev + 1) * m, lda, ldexpf(1.f, -7 * lev), lev == 3 ? 0.f : 1.f);
+        *calls += 4;
+    } else {
+        const int kp = t->products * m;
+        st = gemm_call(t, w, kp, kp, ldexpf(1.f, -t->h), 0.f);
+        *calls += 1;
+    }
+    if (st != CUBLAS_STATUS_SUCCESS) return cudaErrorLaunchFailure;
+    return cudaGetLastError();
+}
+
+cudaError_t tc_finish(TcState *t, const TcPhaseArgs &a, bool phase, cudaStream_t s, int64_t *launches) {
+    const int64_t rows = t->batch * t->n;
+    const float scale = ldexpf(1.f, 4 * t->h - 2 * t->l - TC_S);
+    k_tc_finish<<<t->grid, TC_THREADS, 0, s>>>(t->c, a, t->n, rows, scale,
+                                               t->products == TC_FIXED ? t->e : nullptr, phase ? 1 : 0);
+    ++*launches;
+    return cudaGetLastError();
+}
+
+}  // namespace qhd

@@ -27,10 +27,13 @@ EXPORTS = ["qhd_workspace_bytes", "qhd_init_grid", "qhd_set_potential", "qhd_set
            "qhd_set_schedule", "qhd_reset_state", "qhd_set_time", "qhd_get_time", "qhd_evolve",
            "qhd_observables", "qhd_launch_count", "qhd_timing_enable", "qhd_timing_read",
            "qhd_destroy", "qhd_status_string", "qhd_last_error", "qhd_observables_static",
-           "qhd_set_splitting", "qhd_evolve_trajectory"]
+           "qhd_set_splitting", "qhd_evolve_trajectory", "qhd_tc_workspace_bytes", "qhd_set_transform",
+           "qhd_library_call_count"]
 SPLIT_STRANG = 0
 SPLIT_LIE_TROTTER = 1
-KCLASS = ["prep", "row", "axis1_fwd", "axis0", "axis1_inv", "oned", "plane", "whole"]
+KCLASS = ["prep", "row", "axis1_fwd", "axis0", "axis1_inv", "oned", "plane", "whole", "tc_split", "tc_gemm"]
+TRANSFORM_FFT = 0
+TRANSFORM_TC_DFT = 1
 
 
 class QHDError(RuntimeError):
@@ -108,6 +111,12 @@ def load(build_if_missing: bool = True):
     lib.qhd_evolve_trajectory.restype = st
     lib.qhd_set_splitting.argtypes = [vp, ctypes.c_int]
     lib.qhd_set_splitting.restype = st
+    lib.qhd_tc_workspace_bytes.argtypes = [ctypes.c_int, i64p, ctypes.c_int64, ctypes.c_int]
+    lib.qhd_tc_workspace_bytes.restype = ctypes.c_size_t
+    lib.qhd_set_transform.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, ctypes.c_size_t]
+    lib.qhd_set_transform.restype = st
+    lib.qhd_library_call_count.argtypes = [vp]
+    lib.qhd_library_call_count.restype = ctypes.c_int64
     lib.qhd_destroy.argtypes = [vp]
     lib.qhd_destroy.restype = st
     lib.qhd_status_string.argtypes = [st]
@@ -246,6 +255,32 @@ class QHD:
         """SPLIT_STRANG (default) or SPLIT_LIE_TROTTER (Eq. (prod_qhd) as printed)."""
         self._check(self.lib.qhd_set_splitting(self.ctx, int(kind)), "qhd_set_splitting")
 
+    def set_transform(self, kind: int, products: int = 5) -> None:
+        """TRANSFORM_FFT (default) or TRANSFORM_TC_DFT (dense DFT GEMMs on the tensor
+        cores on FP16 operands: `products` = 3 or 5 floating hi/lo partial products,
+        or 10 fixed-point slice products); the tensor-core workspace is allocated
+        here and kept with this object."""
+        import torch
+        if kind == TRANSFORM_FFT:
+            self._check(self.lib.qhd_set_transform(self.ctx, 0, 0, None, 0), "qhd_set_transform")
+            self._tc_raw = None
+            return
+        n = (ctypes.c_int64 * self.ndim)(*self.shape)
+        ws = int(self.lib.qhd_tc_workspace_bytes(self.ndim, n, self.batch, int(products)))
+        if ws == 0:
+            raise QHDError(2, f"tensor-core transform unsupported for {self.shape} x {self.batch}, "
+                              f"products={products}")
+        with torch.cuda.device(self.device):
+            raw = torch.empty(ws + 256, dtype=torch.uint8, device=self.device)
+        addr = raw.data_ptr()
+        ptr = addr + (-addr) % 256
+        self._check(self.lib.qhd_set_transform(self.ctx, int(kind), int(products), ctypes.c_void_p(ptr),
+                                               ctypes.c_size_t(ws)), "qhd_set_transform")
+        self._tc_raw = raw
+
+    def library_call_count(self) -> int:
+        return int(self.lib.qhd_library_call_count(self.ctx))
+
     def set_time(self, t: float) -> None:
         self._check(self.lib.qhd_set_time(self.ctx, float(t)), "qhd_set_time")
 
@@ -295,6 +330,7 @@ class QHD:
         if getattr(self, "ctx", None):
             self.lib.qhd_destroy(self.ctx)
             self.ctx = None
+        self._tc_raw = None
 
     def __del__(self):
         try:
