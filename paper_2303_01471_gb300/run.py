@@ -1,7 +1,7 @@
 """Command-line runner: one seeded instance through the C ABI.
 
   python -m paper_2303_01471_gb300.run --shape 256 256 256 --family wells --K 32 \
-      --T 0.02 --dt 1e-3 [--repeat 2]
+      --T 0.02 --dt 1e-3 [--repeat 2] [--batch B] [--tc PRODUCTS]
 
 Prints the observables and the device time of the evolve call as JSON.  Used
 for profiling single configurations (e.g. under ncu) and as a usage example.
@@ -34,6 +34,8 @@ def main(argv=None):
     ap.add_argument("--dt", type=float, default=0.01)
     ap.add_argument("--batch", type=int, default=1)
     ap.add_argument("--repeat", type=int, default=1)
+    ap.add_argument("--tc", type=int, default=0, choices=[0, 3, 5, 10],
+                    help="tensor-core DFT transform with this many products (0: FFT passes)")
     a = ap.parse_args(argv)
     kw = {"K": a.K} if a.family == "wells" else {}
     insts = [workloads.make(a.family, a.seed + b, a.shape, **kw) for b in range(a.batch)]
@@ -41,6 +43,8 @@ def main(argv=None):
     sim = qhd.QHD(a.shape, batch=a.batch)
     sim.set_potential(f)
     sim.set_schedule(qhd.Schedule())
+    if a.tc:
+        sim.set_transform(qhd.TRANSFORM_TC_DFT, a.tc)
     times = []
     for _ in range(a.repeat):
         sim.reset_state()
