@@ -286,6 +286,61 @@ enum {
 qhd_status qhd_timing_enable(qhd_ctx *ctx, int every);
 qhd_status qhd_timing_read(qhd_ctx *ctx, double *ms_out, int64_t *launches_out, int reset);
 
+/*
+ * Learned surrogate: a Fourier neural operator (FNO) that maps an instance's
+ * sampled objective f on an n x n mesh of [0,1]^2 and its schedule scale sigma
+ * to a predicted |psi(T)|^2 (a distribution over the mesh), trained on
+ * distributions this library's solver computes.  The paper has no surrogate;
+ * the solver stays the reference and the fallback.  Network per instance:
+ * features ((f - mean f)/std f, sigma, x0, x1) -> lift to `width` channels ->
+ * `layers` Fourier layers a = SC(v) + W v + b, v' = gelu(a) (no gelu after the
+ * last), SC a spectral convolution over the modes kx in {0..modes-1} U
+ * {n-modes..n-1}, ky in {0..modes-1} with complex width x width weights per
+ * mode -> h = gelu(Wp1 v + bp1) (`hidden` channels) -> z = Wp2 h + bp2 ->
+ * p = softmax of z over the mesh.  Loss: KL(p_true || p) averaged over the
+ * batch.  Every step runs in this library's kernels; activations are BF16
+ * (act_bf16 = 1) or FP32 (0, for gradient checks), arithmetic and
+ * accumulation FP32, weights FP32.
+ *
+ * Parameters: one caller-owned FP32 device vector of qhd_fno_param_count(cfg)
+ * values (8-byte aligned), laid out as lift W[width][4], b[width]; per layer
+ * R[2 modes][modes][width][width] complex (re, im pairs), W[width][width],
+ * b[width]; then Wp1[hidden][width], bp1[hidden], Wp2[hidden], bp2; each block
+ * starts at an even offset.  Gradients use the same layout.  Limits: n a power
+ * of two in 8..256, width even in 2..32, 1 <= modes, 2 modes <= n, layers
+ * 1..8, hidden even in 2..128, batch_max <= 65535; else the size queries
+ * return 0 and create returns QHD_ERR_INVALID_ARG.  The workspace
+ * (caller-owned, 256-byte aligned, qhd_fno_workspace_bytes) holds the
+ * activations of batch_max instances and, with train != 0, the backward
+ * buffers and the Adam moments (zeroed at create).  All calls are asynchronous
+ * on `stream` except qhd_fno_loss_grad with a non-NULL loss_host, which
+ * synchronises to return the loss.
+ *
+ * qhd_fno_forward: f_dev = batch x n x n FP64 (row-major per instance),
+ *   sigma_dev = batch FP32, p_dev = batch x n x n FP32 output.
+ * qhd_fno_loss_grad: forward + backward against p_true_dev (batch x n x n
+ *   FP32 distributions); grad_dev (param_count FP32) is overwritten with
+ *   dL/dparams; QHD_ERR_STATE without training buffers.
+ * qhd_fno_adam_step: params -= lr * mhat / (sqrt(vhat) + eps), step t >= 1.
+ */
+typedef struct qhd_fno qhd_fno;
+typedef struct {
+    int32_t n, width, modes, layers, hidden, act_bf16;
+} qhd_fno_config;
+int64_t qhd_fno_param_count(const qhd_fno_config *cfg);
+size_t qhd_fno_workspace_bytes(const qhd_fno_config *cfg, int64_t batch_max, int train);
+qhd_status qhd_fno_create(qhd_fno **out, const qhd_fno_config *cfg, int64_t batch_max, int train,
+                          float *params_dev, void *work_dev, size_t work_bytes, void *stream);
+qhd_status qhd_fno_forward(qhd_fno *fno, const double *f_dev, const float *sigma_dev, int64_t batch,
+                           float *p_dev);
+qhd_status qhd_fno_loss_grad(qhd_fno *fno, const double *f_dev, const float *sigma_dev,
+                             const float *p_true_dev, int64_t batch, float *grad_dev, double *loss_host);
+qhd_status qhd_fno_adam_step(qhd_fno *fno, const float *grad_dev, float lr, float beta1, float beta2,
+                             float eps, int64_t t);
+int64_t qhd_fno_launch_count(const qhd_fno *fno);
+const char *qhd_fno_last_error(const qhd_fno *fno);
+qhd_status qhd_fno_destroy(qhd_fno *fno);
+
 /* Synchronise the stream and free the host-side context (never the caller's
  * buffers).  NULL is accepted. */
 qhd_status qhd_destroy(qhd_ctx *ctx);

@@ -1,0 +1,880 @@
+// qhd_fno.cu -- Fourier-neural-operator surrogate of the QHD solver: maps the
+// sampled objective f (and the schedule scale sigma) on an n x n mesh to the
+// distribution |psi(T)|^2 that the split-operator path computes.
+//
+// Network (per instance, channel-last activations [point][channel]):
+//   features  q = ((f - mean f) / std f, sigma, x, y)                 (4 channels)
+//   lift      v0 = Wl q + bl                                          (C channels)
+//   layer l   a_l = SC_l(v_l) + Ww_l v_l + bw_l,  v_{l+1} = gelu(a_l) (no gelu after the last layer)
+//   SC_l      truncated spectral convolution: V^(kx,ky) = sum_{x,y} v e^{-2 pi i (kx x + ky y)/n} for
+//             kx in {0..M-1} U {n-M..n-1}, ky in {0..M-1};  W^ = R_l(kx,ky) V^  (C x C complex);
+//             u(x,y) = n^-2 sum_{kx,ky} c_ky Re(W^ e^{+2 pi i (kx x + ky y)/n}),  c_0 = 1, c_ky = 2
+//   project   h = gelu(Wp1 v_L + bp1) (H channels),  z = Wp2 h + bp2
+//   output    p = softmax over the mesh of z   (a distribution, like |psi|^2)
+//   loss      KL(p_true || p) summed over the batch, divided by B;  dL/dz = (p - p_true) / B
+// The spectral convolution runs as two separable truncated DFT stages per
+// direction (axis 1 over ky, then axis 0 over kx) in shared memory; the mode
+// mixing sits between the axis-0 stages.  Every backward kernel is the
+// adjoint of a forward one: the adjoint of a truncated DFT stage is the
+// opposite-direction stage over the same modes.
+//
+// Precision: activations are stored as BF16 (or FP32 for gradient checks),
+// all arithmetic and every accumulation is FP32, weight gradients are reduced
+// through FP64 block partials, weights and Adam moments are FP32.
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cuda_bf16.h>
+
+#include "qhd.h"
+
+namespace {
+
+constexpr int FT = 256;     // threads per block
+constexpr int WG_PTS = 32;  // points per shared-memory tile of the weight-gradient kernel
+
+struct Dims {
+    int n, C, M, MX, H, L;
+    int64_t B;
+    __host__ __device__ int64_t G() const { return (int64_t)n * n; }
+    __host__ __device__ int64_t P() const { return B * G(); }
+};
+
+template <typename T> __device__ __forceinline__ float ldv(const T *p);
+template <> __device__ __forceinline__ float ldv<float>(const float *p) { return *p; }
+template <> __device__ __forceinline__ float ldv<__nv_bfloat16>(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
+template <typename T> __device__ __forceinline__ void stv(T *p, float v);
+template <> __device__ __forceinline__ void stv<float>(float *p, float v) { *p = v; }
+template <> __device__ __forceinline__ void stv<__nv_bfloat16>(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+
+__device__ __forceinline__ float gelu(float a) { return 0.5f * a * (1.f + erff(a * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_d(float a) {
+    return 0.5f * (1.f + erff(a * 0.70710678118654752f)) + a * 0.39894228040143268f * expf(-0.5f * a * a);
+}
+
+// cos / sin of 2 pi k / n for k < n into shared memory
+__device__ __forceinline__ void twiddle_table(float *cs, float *sn, int n) {
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        float s, c;
+        sincospif(2.f * (float)k / (float)n, &s, &c);
+        cs[k] = c;
+        sn[k] = s;
+    }
+}
+
+// frequency of retained axis-0 mode index kx (M low, M high)
+__device__ __forceinline__ int kx_freq(int kx, int M, int n) { return kx < M ? kx : n - 2 * M + kx; }
+
+// ------------------------------------------------------------- features, lift
+// Per-instance mean and 1/std of f (FP64).
+__global__ void k_fno_fstats(const double *f, int64_t G, double2 *stats) {
+    const int64_t b = blockIdx.x;
+    double s = 0, s2 = 0;
+    for (int64_t i = threadIdx.x; i < G; i += blockDim.x) {
+        const double v = f[b * G + i];
+        s += v;
+        s2 += v * v;
+    }
+    __shared__ double r1[FT], r2[FT];
+    r1[threadIdx.x] = s;
+    r2[threadIdx.x] = s2;
+    __syncthreads();
+    for (int w = FT / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+            r1[threadIdx.x] += r1[threadIdx.x + w];
+            r2[threadIdx.x] += r2[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double mean = r1[0] / (double)G;
+        const double var = r2[0] / (double)G - mean * mean;
+        stats[b] = make_double2(mean, var > 0 ? 1.0 / sqrt(var) : 1.0);
+    }
+}
+
+template <typename T>
+__global__ void k_fno_lift(const double *f, const float *sigma, const double2 *stats, const float *W, const float *bias,
+                           Dims d, float *feat, T *v0) {
+    const int64_t P = d.P(), G = d.G();
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = p / G, g = p - b * G;
+        const double2 st = stats[b];
+        float q[4];
+        q[0] = (float)((f[p] - st.x) * st.y);
+        q[1] = sigma[b];
+        q[2] = (float)(g / d.n) / (float)d.n;
+        q[3] = (float)(g % d.n) / (float)d.n;
+        for (int j = 0; j < 4; ++j) feat[p * 4 + j] = q[j];
+        for (int c = 0; c < d.C; ++c) {
+            float a = bias[c];
+            for (int j = 0; j < 4; ++j) a = fmaf(W[c * 4 + j], q[j], a);
+            stv(&v0[p * d.C + c], a);
+        }
+    }
+}
+
+// ------------------------------------------------ axis-1 truncated DFT stage
+// out[b][x][ky][c] = s(ky) sum_y in[b][x][y][c] e^{-2 pi i ky y / n}, s(0) = s0, s(ky>0) = s1.
+// One block per (b, x) row.
+template <typename T>
+__global__ void k_fno_dfty(const T *in, Dims d, float s0, float s1, float2 *out) {
+    extern __shared__ float smem[];
+    const int n = d.n, C = d.C, M = d.M;
+    float *row = smem;  // n * C
+    float *cs = row + n * C, *sn = cs + n;
+    const int64_t bx = blockIdx.x;  // b * n + x
+    const T *src = in + bx * (int64_t)n * C;
+    for (int i = threadIdx.x; i < n * C; i += blockDim.x) row[i] = ldv(&src[i]);
+    twiddle_table(cs, sn, n);
+    __syncthreads();
+    for (int o = threadIdx.x; o < M * C; o += blockDim.x) {
+        const int ky = o / C, c = o - ky * C;
+        float re = 0.f, im = 0.f;
+        for (int y = 0; y < n; ++y) {
+            const int k = (ky * y) & (n - 1);
+            const float v = row[y * C + c];
+            re = fmaf(v, cs[k], re);
+            im = fmaf(-v, sn[k], im);
+        }
+        const float s = ky == 0 ? s0 : s1;
+        out[bx * (int64_t)M * C + o] = make_float2(re * s, im * s);
+    }
+}
+
+// ------------------------------------- axis-0 stages with the mode mixing
+// One block per (b, ky).  X[x][c] = in[b][x][ky][c];
+//   Y1[kx][c] = sum_x X[x][c] e^{-2 pi i f(kx) x / n}                 (stored to mid)
+//   forward: Y2[kx][o] = sum_i R[kx][ky][i][o] Y1[kx][i];  adjoint: Y2[kx][i] = sum_o conj(R[..][i][o]) Y1[kx][o]
+//   out[b][x][ky][c] = sum_kx Y2[kx][c] e^{+2 pi i f(kx) x / n}
+template <bool ADJ>
+__global__ void k_fno_specx(const float2 *in, const float2 *R, Dims d, float2 *mid, float2 *out) {
+    extern __shared__ float smem[];
+    const int n = d.n, C = d.C, M = d.M, MX = d.MX;
+    float2 *X = reinterpret_cast<float2 *>(smem);  // n * C
+    float2 *Y1 = X + n * C;                        // MX * C
+    float2 *Y2 = Y1 + MX * C;                      // MX * C
+    float *cs = reinterpret_cast<float *>(Y2 + MX * C), *sn = cs + n;
+    const int64_t b = blockIdx.x / M;
+    const int ky = blockIdx.x - (int)(b * M);
+    for (int i = threadIdx.x; i < n * C; i += blockDim.x) {
+        const int x = i / C, c = i - x * C;
+        X[i] = in[((b * n + x) * M + ky) * (int64_t)C + c];
+    }
+    twiddle_table(cs, sn, n);
+    __syncthreads();
+    for (int o = threadIdx.x; o < MX * C; o += blockDim.x) {
+        const int kx = o / C, c = o - kx * C;
+        const int fr = kx_freq(kx, M, n);
+        float re = 0.f, im = 0.f;
+        for (int x = 0; x < n; ++x) {
+            const int k = (fr * x) & (n - 1);
+            const float2 v = X[x * C + c];
+            // v * (cos - i sin)
+            re = fmaf(v.x, cs[k], fmaf(v.y, sn[k], re));
+            im = fmaf(v.y, cs[k], fmaf(-v.x, sn[k], im));
+        }
+        Y1[o] = make_float2(re, im);
+        mid[((b * MX + kx) * M + ky) * (int64_t)C + c] = make_float2(re, im);
+    }
+    __syncthreads();
+    for (int o = threadIdx.x; o < MX * C; o += blockDim.x) {
+        const int kx = o / C, c = o - kx * C;
+        const float2 *Rm = R + ((int64_t)(kx * M + ky) * C) * C;  // [i][o]
+        float re = 0.f, im = 0.f;
+        for (int j = 0; j < C; ++j) {
+            const float2 y = Y1[kx * C + j];
+            if (!ADJ) {
+                const float2 r = Rm[j * C + c];  // R[i=j][o=c]
+                re += r.x * y.x - r.y * y.y;
+                im += r.x * y.y + r.y * y.x;
+            } else {
+                const float2 r = Rm[c * C + j];  // conj(R[i=c][o=j])
+                re += r.x * y.x + r.y * y.y;
+                im += r.x * y.y - r.y * y.x;
+            }
+        }
+        Y2[o] = make_float2(re, im);
+    }
+    __syncthreads();
+    for (int o = threadIdx.x; o < n * C; o += blockDim.x) {
+        const int x = o / C, c = o - x * C;
+        float re = 0.f, im = 0.f;
+        for (int kx = 0; kx < MX; ++kx) {
+            const int k = (kx_freq(kx, M, n) * x) & (n - 1);
+            const float2 v = Y2[kx * C + c];
+            // v * (cos + i sin)
+            re = fmaf(v.x, cs[k], fmaf(-v.y, sn[k], re));
+            im = fmaf(v.y, cs[k], fmaf(v.x, sn[k], im));
+        }
+        out[((b * n + x) * M + ky) * (int64_t)C + c] = make_float2(re, im);
+    }
+}
+
+// ------------------------- inverse axis-1 stage + pointwise part + activation
+// One block per (b, x) row: a = n^-2 sum_ky c_ky Re(S[ky] e^{+2 pi i ky y/n}) + Ww v + bw.
+template <typename T>
+__global__ void k_fno_layer_out(const float2 *S, const T *v, const float *Ww, const float *bw, Dims d, int act,
+                                T *a_out, T *v_out) {
+    extern __shared__ float smem[];
+    const int n = d.n, C = d.C, M = d.M;
+    float2 *Ss = reinterpret_cast<float2 *>(smem);       // M * C
+    float *row = reinterpret_cast<float *>(Ss + M * C);  // n * C
+    float *W = row + n * C;                              // C * C, stored W[c][o]
+    float *cs = W + C * C, *sn = cs + n;
+    const int64_t bx = blockIdx.x;
+    for (int i = threadIdx.x; i < M * C; i += blockDim.x) Ss[i] = S[bx * (int64_t)M * C + i];
+    for (int i = threadIdx.x; i < n * C; i += blockDim.x) row[i] = ldv(&v[bx * (int64_t)n * C + i]);
+    for (int i = threadIdx.x; i < C * C; i += blockDim.x) W[(i % C) * C + i / C] = Ww[i];
+    twiddle_table(cs, sn, n);
+    __syncthreads();
+    const float inv = 1.f / ((float)n * (float)n);
+    for (int o = threadIdx.x; o < n * C; o += blockDim.x) {
+        const int y = o / C, co = o - y * C;
+        float u = Ss[co].x;
+        for (int ky = 1; ky < M; ++ky) {
+            const int k = (ky * y) & (n - 1);
+            const float2 s = Ss[ky * C + co];
+            u = fmaf(2.f * s.x, cs[k], fmaf(-2.f * s.y, sn[k], u));
+        }
+        float a = fmaf(u, inv, bw[co]);
+        for (int c = 0; c < C; ++c) a = fmaf(W[c * C + co], row[y * C + c], a);
+        const int64_t idx = bx * (int64_t)n * C + o;
+        if (act) {
+            stv(&a_out[idx], a);
+            stv(&v_out[idx], gelu(a));
+        } else {
+            stv(&v_out[idx], a);
+        }
+    }
+}
+
+// ------------------------------------------------------------- projection
+template <typename T>
+__global__ void k_fno_proj(const T *v, const float *W1, const float *b1, const float *W2, const float *b2, Dims d,
+                           float *z) {
+    extern __shared__ float smem[];
+    const int C = d.C, H = d.H;
+    float *w1 = smem, *bb1 = w1 + H * C, *w2 = bb1 + H;
+    for (int i = threadIdx.x; i < H * C; i += blockDim.x) w1[i] = W1[i];
+    for (int i = threadIdx.x; i < H; i += blockDim.x) {
+        bb1[i] = b1[i];
+        w2[i] = W2[i];
+    }
+    __syncthreads();
+    const int64_t P = d.P();
+    float x[32];
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int c = 0; c < 32; ++c) x[c] = c < C ? ldv(&v[p * C + c]) : 0.f;
+        float acc = b2[0];
+        for (int k = 0; k < H; ++k) {
+            float h = bb1[k];
+#pragma unroll
+            for (int c = 0; c < 32; ++c)
+                if (c < C) h = fmaf(w1[k * C + c], x[c], h);
+            acc = fmaf(w2[k], gelu(h), acc);
+        }
+        z[p] = acc;
+    }
+}
+
+// block-wide reductions over FT threads
+__device__ float block_max(float v, float *red) {
+    red[threadIdx.x] = v;
+    __syncthreads();
+    for (int w = FT / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + w]);
+        __syncthreads();
+    }
+    const float r = red[0];
+    __syncthreads();
+    return r;
+}
+__device__ double block_sum(double v, double *red) {
+    red[threadIdx.x] = v;
+    __syncthreads();
+    for (int w = FT / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    const double r = red[0];
+    __syncthreads();
+    return r;
+}
+
+// softmax over the mesh per instance; lse = log sum exp z
+__global__ void k_fno_softmax(const float *z, int64_t G, float *p, float *lse) {
+    __shared__ float rf[FT];
+    __shared__ double rd[FT];
+    const int64_t b = blockIdx.x;
+    float m = -INFINITY;
+    for (int64_t i = threadIdx.x; i < G; i += blockDim.x) m = fmaxf(m, z[b * G + i]);
+    m = block_max(m, rf);
+    double s = 0;
+    for (int64_t i = threadIdx.x; i < G; i += blockDim.x) s += (double)expf(z[b * G + i] - m);
+    s = block_sum(s, rd);
+    const float l = m + (float)log(s);
+    for (int64_t i = threadIdx.x; i < G; i += blockDim.x) p[b * G + i] = expf(z[b * G + i] - l);
+    if (threadIdx.x == 0) lse[b] = l;
+}
+
+// KL(p_true || p) per instance and dz = (p - p_true) / B
+__global__ void k_fno_loss(const float *z, const float *lse, const float *p, const float *pt, int64_t G, float invB,
+                           float *dz, double *loss) {
+    __shared__ double rd[FT];
+    const int64_t b = blockIdx.x;
+    double s = 0;
+    for (int64_t i = threadIdx.x; i < G; i += blockDim.x) {
+        const int64_t k = b * G + i;
+        const float q = pt[k];
+        if (q > 0.f) s += (double)q * ((double)logf(q) - (double)(z[k] - lse[b]));
+        dz[k] = (p[k] - q) * invB;
+    }
+    s = block_sum(s, rd);
+    if (threadIdx.x == 0) loss[b] = s;
+}
+
+// projection backward, one thread per point: dh = dz Wp2 gelu'(h_pre), dv = Wp1^T dh;
+// per-block partial sums of dz * gelu(h_pre) (grad of Wp2) and dz (grad of bp2)
+template <typename T>
+__global__ void k_fno_proj_bwd(const T *v, const float *dz, const float *W1, const float *b1, const float *W2, Dims d,
+                               float *dh, float *dv, double *part) {
+    extern __shared__ float smem[];
+    const int C = d.C, H = d.H;
+    float *w1 = smem, *bb1 = w1 + H * C, *w2 = bb1 + H;
+    float *acc = w2 + H;  // H + 1 block sums
+    for (int i = threadIdx.x; i < H * C; i += blockDim.x) w1[i] = W1[i];
+    for (int i = threadIdx.x; i < H; i += blockDim.x) {
+        bb1[i] = b1[i];
+        w2[i] = W2[i];
+    }
+    for (int i = threadIdx.x; i <= H; i += blockDim.x) acc[i] = 0.f;
+    __syncthreads();
+    const int64_t P = d.P();
+    float x[32], g[32];
+    // the loop trip count is uniform over the block, so whole warps reduce together
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < P; base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = base + threadIdx.x;
+        const bool ok = p < P;
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+            x[c] = ok && c < C ? ldv(&v[p * C + c]) : 0.f;
+            g[c] = 0.f;
+        }
+        const float e = ok ? dz[p] : 0.f;
+        for (int k = 0; k < H; ++k) {
+            float h = bb1[k];
+#pragma unroll
+            for (int c = 0; c < 32; ++c)
+                if (c < C) h = fmaf(w1[k * C + c], x[c], h);
+            float t = e * gelu(h);
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            if ((threadIdx.x & 31) == 0) atomicAdd(&acc[k], t);
+            const float q = e * w2[k] * gelu_d(h);
+            if (ok) dh[p * H + k] = q;
+#pragma unroll
+            for (int c = 0; c < 32; ++c)
+                if (c < C) g[c] = fmaf(w1[k * C + c], q, g[c]);
+        }
+        float t = e;
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if ((threadIdx.x & 31) == 0) atomicAdd(&acc[H], t);
+        if (ok)
+#pragma unroll
+            for (int c = 0; c < 32; ++c)
+                if (c < C) dv[p * C + c] = g[c];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i <= H; i += blockDim.x) part[(int64_t)blockIdx.x * (H + 1) + i] = acc[i];
+}
+
+// da = dv * gelu'(a) (or dv for the last layer)
+template <typename T>
+__global__ void k_fno_act_bwd(const float *dv, const T *a, int64_t count, int act, float *da) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+        da[i] = act ? dv[i] * gelu_d(ldv(&a[i])) : dv[i];
+}
+
+// Weight-gradient partials: per block, over its range of points,
+//   part[blk][o * Cc + c] = sum_p X[p][o] Y[p][c],  part[blk][O * Cc + o] = sum_p X[p][o].
+// X: [P][O] FP32, Y: [P][Cc] (T).  O <= 128, Cc <= 32, O * Cc <= FT * 16.
+template <typename T>
+__global__ void k_fno_wgrad(const float *X, const T *Y, int64_t P, int O, int Cc, double *part) {
+    __shared__ float xs[WG_PTS * 128], ys[WG_PTS * 32];
+    constexpr int PER = 16;
+    float acc[PER], bacc = 0.f;
+    for (int k = 0; k < PER; ++k) acc[k] = 0.f;
+    const int nout = O * Cc;
+    const int64_t per_blk = (P + gridDim.x - 1) / gridDim.x;
+    const int64_t p0 = (int64_t)blockIdx.x * per_blk;
+    const int64_t p1 = p0 + per_blk < P ? p0 + per_blk : P;
+    for (int64_t t0 = p0; t0 < p1; t0 += WG_PTS) {
+        const int np = (int)(p1 - t0 < WG_PTS ? p1 - t0 : WG_PTS);
+        __syncthreads();
+        for (int i = threadIdx.x; i < np * O; i += blockDim.x) xs[i] = X[t0 * O + i];
+        for (int i = threadIdx.x; i < np * Cc; i += blockDim.x) ys[i] = ldv(&Y[t0 * Cc + i]);
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int q = threadIdx.x + k * FT;
+            if (q < nout) {
+                const int o = q / Cc, c = q - o * Cc;
+                float s = acc[k];
+                for (int j = 0; j < np; ++j) s = fmaf(xs[j * O + o], ys[j * Cc + c], s);
+                acc[k] = s;
+            }
+        }
+        if ((int)threadIdx.x < O)
+            for (int j = 0; j < np; ++j) bacc += xs[j * O + threadIdx.x];
+    }
+    double *dst = part + (int64_t)blockIdx.x * (nout + O);
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int q = threadIdx.x + k * FT;
+        if (q < nout) dst[q] = acc[k];
+    }
+    if ((int)threadIdx.x < O) dst[nout + threadIdx.x] = bacc;
+}
+
+// out[k] = sum over blocks of part[blk][k]
+__global__ void k_fno_reduce(const double *part, int nblk, int K, float *out) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < K; k += gridDim.x * blockDim.x) {
+        double s = 0;
+        for (int b = 0; b < nblk; ++b) s += part[(int64_t)b * K + k];
+        out[k] = (float)s;
+    }
+}
+
+// gradient of the spectral weights: dR[kx][ky][i][o] = sum_b dW_b[kx][ky][o] conj(V_b[kx][ky][i])
+__global__ void k_fno_dR(const float2 *dW, const float2 *V, Dims d, float2 *dR) {
+    extern __shared__ float smem[];
+    const int C = d.C, MM = d.MX * d.M;
+    float2 *vs = reinterpret_cast<float2 *>(smem), *ws = vs + C;
+    const int mode = blockIdx.x;  // kx * M + ky
+    float2 acc[4] = {};
+    for (int64_t b = 0; b < d.B; ++b) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < C; i += blockDim.x) {
+            vs[i] = V[(b * MM + mode) * (int64_t)C + i];
+            ws[i] = dW[(b * MM + mode) * (int64_t)C + i];
+        }
+        __syncthreads();
+        for (int k = 0; k < 4; ++k) {
+            const int q = threadIdx.x + k * FT;
+            if (q < C * C) {
+                const int i = q / C, o = q - i * C;
+                const float2 w = ws[o], v = vs[i];
+                acc[k].x += w.x * v.x + w.y * v.y;
+                acc[k].y += w.y * v.x - w.x * v.y;
+            }
+        }
+    }
+    for (int k = 0; k < 4; ++k) {
+        const int q = threadIdx.x + k * FT;
+        if (q < C * C) dR[(int64_t)mode * C * C + q] = acc[k];
+    }
+}
+
+// inverse of the axis-1 stage for the backward pass, plus the pointwise part:
+// dv[y][c] = sum_o Ww[o][c] da[y][o] + sum_ky Re(dT[ky][c] e^{+2 pi i ky y / n})
+__global__ void k_fno_layer_in_bwd(const float2 *dT, const float *da, const float *Ww, Dims d, float *dv) {
+    extern __shared__ float smem[];
+    const int n = d.n, C = d.C, M = d.M;
+    float2 *Ts = reinterpret_cast<float2 *>(smem);
+    float *row = reinterpret_cast<float *>(Ts + M * C);
+    float *W = row + n * C;
+    float *cs = W + C * C, *sn = cs + n;
+    const int64_t bx = blockIdx.x;
+    for (int i = threadIdx.x; i < M * C; i += blockDim.x) Ts[i] = dT[bx * (int64_t)M * C + i];
+    for (int i = threadIdx.x; i < n * C; i += blockDim.x) row[i] = da[bx * (int64_t)n * C + i];
+    for (int i = threadIdx.x; i < C * C; i += blockDim.x) W[i] = Ww[i];
+    twiddle_table(cs, sn, n);
+    __syncthreads();
+    for (int o = threadIdx.x; o < n * C; o += blockDim.x) {
+        const int y = o / C, c = o - y * C;
+        float g = 0.f;
+        for (int ky = 0; ky < M; ++ky) {
+            const int k = (ky * y) & (n - 1);
+            const float2 t = Ts[ky * C + c];
+            g = fmaf(t.x, cs[k], fmaf(-t.y, sn[k], g));
+        }
+        for (int j = 0; j < C; ++j) g = fmaf(W[j * C + c], row[y * C + j], g);
+        dv[bx * (int64_t)n * C + o] = g;
+    }
+}
+
+__global__ void k_fno_adam(float *w, const float *g, float *m, float *v, int64_t count, float lr, float b1, float b2,
+                           float eps, float c1, float c2) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        w[i] -= lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+    }
+}
+
+size_t al(size_t v) { return (v + 255) & ~size_t(255); }
+
+}  // namespace
+
+// ---------------------------------------------------------------- host side
+struct qhd_fno {
+    Dims d{};
+    int64_t batch_max = 0;
+    int train = 0, bf16 = 1;
+    float *params = nullptr;
+    cudaStream_t stream = nullptr;
+    int64_t nparam = 0;
+    int64_t off_lw = 0, off_lb = 0, off_R[8] = {}, off_W[8] = {}, off_b[8] = {}, off_p1 = 0, off_p1b = 0, off_p2 = 0,
+            off_p2b = 0;
+    // workspace views
+    double2 *stats = nullptr;
+    float *feat = nullptr;
+    void *v[9] = {}, *a[8] = {};
+    float2 *tspec = nullptr, *sspec = nullptr, *vhat[8] = {};
+    float *z = nullptr, *p = nullptr, *lse = nullptr;
+    float *dz = nullptr, *dh = nullptr, *dv = nullptr, *da = nullptr;
+    float2 *dspec = nullptr, *dwhat = nullptr;
+    double *part = nullptr, *loss = nullptr;
+    float *m = nullptr, *vv = nullptr;
+    int64_t launches = 0;
+    std::string err;
+};
+
+namespace {
+
+bool cfg_ok(const qhd_fno_config *c) {
+    if (!c) return false;
+    const int n = c->n;
+    // even widths keep every weight block and its bias contiguous in the parameter vector
+    return n >= 8 && n <= 256 && (n & (n - 1)) == 0 && c->width >= 2 && c->width <= 32 && c->width % 2 == 0 &&
+           c->modes >= 1 && 2 * c->modes <= n && c->modes <= 32 && c->layers >= 1 && c->layers <= 8 &&
+           c->hidden >= 2 && c->hidden <= 128 && c->hidden % 2 == 0 && c->hidden * c->width <= FT * 16;
+}
+
+Dims dims_of(const qhd_fno_config *c, int64_t B) {
+    Dims d;
+    d.n = c->n;
+    d.C = c->width;
+    d.M = c->modes;
+    d.MX = 2 * c->modes;
+    d.H = c->hidden;
+    d.L = c->layers;
+    d.B = B;
+    return d;
+}
+
+int64_t layout_params(const qhd_fno_config *c, qhd_fno *f) {
+    const int64_t C = c->width, M = c->modes, H = c->hidden;
+    int64_t o = 0;
+    auto take = [&](int64_t k) {
+        const int64_t r = o;
+        o += (k + 1) & ~int64_t(1);  // keep complex blocks 8-byte aligned
+        return r;
+    };
+    const int64_t lw = take(4 * C), lb = take(C);
+    int64_t R[8], W[8], bb[8];
+    for (int l = 0; l < c->layers; ++l) {
+        R[l] = take(2 * M * M * C * C * 2);
+        W[l] = take(C * C);
+        bb[l] = take(C);
+    }
+    const int64_t p1 = take(H * C), p1b = take(H), p2 = take(H), p2b = take(1);
+    if (f) {
+        f->off_lw = lw;
+        f->off_lb = lb;
+        for (int l = 0; l < c->layers; ++l) {
+            f->off_R[l] = R[l];
+            f->off_W[l] = W[l];
+            f->off_b[l] = bb[l];
+        }
+        f->off_p1 = p1;
+        f->off_p1b = p1b;
+        f->off_p2 = p2;
+        f->off_p2b = p2b;
+    }
+    return o;
+}
+
+int part_blocks() { return 512; }
+
+// Carves the workspace (base = f->stats on entry when f is given); returns its size.
+size_t workspace(const qhd_fno_config *c, int64_t B, int train, qhd_fno *f) {
+    const Dims d = dims_of(c, B);
+    const int64_t P = d.P();
+    const size_t act = c->act_bf16 ? 2 : 4;
+    const size_t spec = (size_t)B * d.n * d.M * d.C * sizeof(float2);
+    const size_t vh = (size_t)B * d.MX * d.M * d.C * sizeof(float2);
+    const int64_t np = layout_params(c, nullptr);
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t r = off;
+        off = al(off + bytes);
+        return r;
+    };
+    const size_t o_stats = take(B * sizeof(double2));
+    const size_t o_feat = take(P * 4 * sizeof(float));
+    size_t o_v[9], o_a[8], o_vh[8];
+    for (int l = 0; l <= c->layers; ++l) o_v[l] = take(P * d.C * act);
+    for (int l = 0; l + 1 < c->layers; ++l) o_a[l] = take(P * d.C * act);
+    const size_t o_t = take(spec), o_s = take(spec);
+    for (int l = 0; l < c->layers; ++l) o_vh[l] = take(vh);
+    const size_t o_z = take(P * sizeof(float)), o_p = take(P * sizeof(float)), o_lse = take(B * sizeof(float));
+    size_t o_dz = 0, o_dh = 0, o_dv = 0, o_da = 0, o_ds = 0, o_dw = 0, o_part = 0, o_loss = 0, o_m = 0, o_vv = 0;
+    if (train) {
+        o_dz = take(P * sizeof(float));
+        o_dh = take(P * d.H * sizeof(float));
+        o_dv = take(P * d.C * sizeof(float));
+        o_da = take(P * d.C * sizeof(float));
+        o_ds = take(spec);
+        o_dw = take(vh);
+        // longest partial row: projection (H C + H), pointwise layer (C C + C), lift (5 C), H + 1
+        int64_t K = (int64_t)d.H * d.C + d.H;
+        if ((int64_t)d.C * d.C + d.C > K) K = (int64_t)d.C * d.C + d.C;
+        if (5 * (int64_t)d.C > K) K = 5 * (int64_t)d.C;
+        if ((int64_t)d.H + 1 > K) K = d.H + 1;
+        o_part = take((size_t)part_blocks() * (size_t)K * sizeof(double));
+        o_loss = take(B * sizeof(double));
+        o_m = take(np * sizeof(float));
+        o_vv = take(np * sizeof(float));
+    }
+    if (f) {
+        char *w = (char *)f->stats;
+        f->stats = (double2 *)(w + o_stats);
+        f->feat = (float *)(w + o_feat);
+        for (int l = 0; l <= c->layers; ++l) f->v[l] = w + o_v[l];
+        for (int l = 0; l + 1 < c->layers; ++l) f->a[l] = w + o_a[l];
+        f->tspec = (float2 *)(w + o_t);
+        f->sspec = (float2 *)(w + o_s);
+        for (int l = 0; l < c->layers; ++l) f->vhat[l] = (float2 *)(w + o_vh[l]);
+        f->z = (float *)(w + o_z);
+        f->p = (float *)(w + o_p);
+        f->lse = (float *)(w + o_lse);
+        if (train) {
+            f->dz = (float *)(w + o_dz);
+            f->dh = (float *)(w + o_dh);
+            f->dv = (float *)(w + o_dv);
+            f->da = (float *)(w + o_da);
+            f->dspec = (float2 *)(w + o_ds);
+            f->dwhat = (float2 *)(w + o_dw);
+            f->part = (double *)(w + o_part);
+            f->loss = (double *)(w + o_loss);
+            f->m = (float *)(w + o_m);
+            f->vv = (float *)(w + o_vv);
+        }
+    }
+    return off;
+}
+
+int grid_for(int64_t count) {
+    int64_t b = (count + FT - 1) / FT;
+    if (b > 152 * 16) b = 152 * 16;
+    return b < 1 ? 1 : (int)b;
+}
+
+qhd_status ffail(qhd_fno *f, qhd_status s, const char *msg) {
+    if (f) f->err = msg;
+    return s;
+}
+
+#define FNO_CHECK(f)                                                                    \
+    do {                                                                                \
+        cudaError_t e_ = cudaGetLastError();                                            \
+        if (e_ != cudaSuccess) return ffail((f), QHD_ERR_CUDA, cudaGetErrorString(e_)); \
+    } while (0)
+
+size_t smem_dfty(const Dims &d) { return (size_t)(d.n * d.C + 2 * d.n) * sizeof(float); }
+size_t smem_specx(const Dims &d) {
+    return (size_t)(d.n * d.C + 2 * d.MX * d.C) * sizeof(float2) + 2 * d.n * sizeof(float);
+}
+size_t smem_layer(const Dims &d) {
+    return (size_t)d.M * d.C * sizeof(float2) + (size_t)(d.n * d.C + d.C * d.C + 2 * d.n) * sizeof(float);
+}
+size_t smem_proj(const Dims &d) { return (size_t)(d.H * d.C + 3 * d.H + 1) * sizeof(float); }
+
+template <typename T>
+void set_smem_limits() {
+    const int big = 200 * 1024;
+    cudaFuncSetAttribute(k_fno_dfty<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_fno_dfty<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_fno_specx<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_fno_specx<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_fno_layer_out<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_fno_layer_in_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+}
+
+// forward pass over `B` instances; activations kept for the backward pass
+template <typename T>
+qhd_status forward(qhd_fno *f, const double *fx, const float *sigma, int64_t B, float *p_out) {
+    Dims d = f->d;
+    d.B = B;
+    cudaStream_t s = f->stream;
+    const float *W = f->params;
+    k_fno_fstats<<<(unsigned)B, FT, 0, s>>>(fx, d.G(), f->stats);
+    k_fno_lift<T><<<grid_for(d.P()), FT, 0, s>>>(fx, sigma, f->stats, W + f->off_lw, W + f->off_lb, d, f->feat,
+                                                 (T *)f->v[0]);
+    f->launches += 2;
+    for (int l = 0; l < d.L; ++l) {
+        const T *vin = (const T *)f->v[l];
+        k_fno_dfty<T><<<(unsigned)(B * d.n), FT, smem_dfty(d), s>>>(vin, d, 1.f, 1.f, f->tspec);
+        k_fno_specx<false><<<(unsigned)(B * d.M), FT, smem_specx(d), s>>>(
+            f->tspec, reinterpret_cast<const float2 *>(W + f->off_R[l]), d, f->vhat[l], f->sspec);
+        const int act = l + 1 < d.L;
+        k_fno_layer_out<T><<<(unsigned)(B * d.n), FT, smem_layer(d), s>>>(
+            f->sspec, vin, W + f->off_W[l], W + f->off_b[l], d, act, act ? (T *)f->a[l] : nullptr, (T *)f->v[l + 1]);
+        f->launches += 3;
+    }
+    k_fno_proj<T><<<grid_for(d.P()), FT, smem_proj(d), s>>>((const T *)f->v[d.L], W + f->off_p1, W + f->off_p1b,
+                                                          W + f->off_p2, W + f->off_p2b, d, f->z);
+    k_fno_softmax<<<(unsigned)B, FT, 0, s>>>(f->z, d.G(), p_out ? p_out : f->p, f->lse);
+    f->launches += 2;
+    FNO_CHECK(f);
+    return QHD_OK;
+}
+
+template <typename T>
+qhd_status backward(qhd_fno *f, const float *p_true, int64_t B, float *grad, double *loss_host) {
+    Dims d = f->d;
+    d.B = B;
+    cudaStream_t s = f->stream;
+    const float *W = f->params;
+    const int64_t P = d.P();
+    const int nb = part_blocks();
+    k_fno_loss<<<(unsigned)B, FT, 0, s>>>(f->z, f->lse, f->p, p_true, d.G(), 1.f / (float)B, f->dz, f->loss);
+    // projection
+    const size_t sp = smem_proj(d) + (size_t)(d.H + 1) * sizeof(float);
+    k_fno_proj_bwd<T><<<nb, FT, sp, s>>>((const T *)f->v[d.L], f->dz, W + f->off_p1, W + f->off_p1b, W + f->off_p2,
+                                          d, f->dh, f->dv, f->part);
+    k_fno_reduce<<<1, FT, 0, s>>>(f->part, nb, d.H + 1, grad + f->off_p2);
+    k_fno_wgrad<T><<<nb, FT, 0, s>>>(f->dh, (const T *)f->v[d.L], P, d.H, d.C, f->part);
+    k_fno_reduce<<<grid_for((int64_t)d.H * d.C + d.H), FT, 0, s>>>(f->part, nb, d.H * d.C + d.H, grad + f->off_p1);
+    f->launches += 5;
+    for (int l = d.L - 1; l >= 0; --l) {
+        const int act = l + 1 < d.L;
+        k_fno_act_bwd<T><<<grid_for(P * d.C), FT, 0, s>>>(f->dv, act ? (const T *)f->a[l] : nullptr, P * d.C, act,
+                                                        f->da);
+        // pointwise weights and bias: sum over points of da (x) v_l
+        k_fno_wgrad<T><<<nb, FT, 0, s>>>(f->da, (const T *)f->v[l], P, d.C, d.C, f->part);
+        k_fno_reduce<<<grid_for((int64_t)d.C * d.C + d.C), FT, 0, s>>>(f->part, nb, d.C * d.C + d.C,
+                                                                      grad + f->off_W[l]);
+        // spectral path: adjoint of the inverse axis-1 stage, then of the axis-0 stages
+        const float inv = 1.f / ((float)d.n * (float)d.n);
+        k_fno_dfty<float><<<(unsigned)(B * d.n), FT, smem_dfty(d), s>>>(f->da, d, inv, 2.f * inv, f->dspec);
+        k_fno_specx<true><<<(unsigned)(B * d.M), FT, smem_specx(d), s>>>(
+            f->dspec, reinterpret_cast<const float2 *>(W + f->off_R[l]), d, f->dwhat, f->tspec);
+        k_fno_dR<<<(unsigned)(d.MX * d.M), FT, 2 * d.C * sizeof(float2), s>>>(
+            f->dwhat, f->vhat[l], d, reinterpret_cast<float2 *>(grad + f->off_R[l]));
+        k_fno_layer_in_bwd<<<(unsigned)(B * d.n), FT, smem_layer(d), s>>>(f->tspec, f->da, W + f->off_W[l], d, f->dv);
+        f->launches += 7;
+    }
+    // lift: sum over points of dv0 (x) features
+    k_fno_wgrad<float><<<nb, FT, 0, s>>>(f->dv, f->feat, P, d.C, 4, f->part);
+    k_fno_reduce<<<grid_for(5 * d.C), FT, 0, s>>>(f->part, nb, 4 * d.C + d.C, grad + f->off_lw);
+    f->launches += 2;
+    FNO_CHECK(f);
+    if (loss_host) {
+        std::vector<double> l(B);
+        if (cudaMemcpyAsync(l.data(), f->loss, B * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return ffail(f, QHD_ERR_CUDA, "loss copy failed");
+        double t = 0;
+        for (double v : l) t += v;
+        *loss_host = t / (double)B;
+    }
+    return QHD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int64_t qhd_fno_param_count(const qhd_fno_config *cfg) { return cfg_ok(cfg) ? layout_params(cfg, nullptr) : 0; }
+
+size_t qhd_fno_workspace_bytes(const qhd_fno_config *cfg, int64_t batch_max, int train) {
+    if (!cfg_ok(cfg) || batch_max < 1 || batch_max > 65535) return 0;
+    return workspace(cfg, batch_max, train ? 1 : 0, nullptr);
+}
+
+qhd_status qhd_fno_create(qhd_fno **out, const qhd_fno_config *cfg, int64_t batch_max, int train, float *params_dev,
+                          void *work_dev, size_t work_bytes, void *stream) {
+    if (!out || !cfg_ok(cfg) || !params_dev || batch_max < 1 || batch_max > 65535) return QHD_ERR_INVALID_ARG;
+    if (((uintptr_t)params_dev & 7) != 0) return QHD_ERR_INVALID_ARG;
+    const size_t need = workspace(cfg, batch_max, train ? 1 : 0, nullptr);
+    if (!work_dev || ((uintptr_t)work_dev & 255) || work_bytes < need) return QHD_ERR_WORKSPACE;
+    qhd_fno *f = new qhd_fno();
+    f->d = dims_of(cfg, batch_max);
+    f->batch_max = batch_max;
+    f->train = train ? 1 : 0;
+    f->bf16 = cfg->act_bf16 ? 1 : 0;
+    f->params = params_dev;
+    f->stream = (cudaStream_t)stream;
+    f->nparam = layout_params(cfg, f);
+    f->stats = (double2 *)work_dev;
+    workspace(cfg, batch_max, f->train, f);
+    if (f->bf16) set_smem_limits<__nv_bfloat16>();
+    else set_smem_limits<float>();
+    if (f->train) {
+        if (cudaMemsetAsync(f->m, 0, f->nparam * sizeof(float), f->stream) != cudaSuccess ||
+            cudaMemsetAsync(f->vv, 0, f->nparam * sizeof(float), f->stream) != cudaSuccess) {
+            delete f;
+            return QHD_ERR_CUDA;
+        }
+    }
+    *out = f;
+    return QHD_OK;
+}
+
+qhd_status qhd_fno_forward(qhd_fno *f, const double *f_dev, const float *sigma_dev, int64_t batch, float *p_dev) {
+    if (!f) return QHD_ERR_INVALID_ARG;
+    if (!f_dev || !sigma_dev || !p_dev || batch < 1 || batch > f->batch_max)
+        return ffail(f, QHD_ERR_INVALID_ARG, "bad forward arguments");
+    return f->bf16 ? forward<__nv_bfloat16>(f, f_dev, sigma_dev, batch, p_dev)
+                   : forward<float>(f, f_dev, sigma_dev, batch, p_dev);
+}
+
+qhd_status qhd_fno_loss_grad(qhd_fno *f, const double *f_dev, const float *sigma_dev, const float *p_true_dev,
+                             int64_t batch, float *grad_dev, double *loss_host) {
+    if (!f) return QHD_ERR_INVALID_ARG;
+    if (!f->train) return ffail(f, QHD_ERR_STATE, "created without training buffers");
+    if (!f_dev || !sigma_dev || !p_true_dev || !grad_dev || batch < 1 || batch > f->batch_max)
+        return ffail(f, QHD_ERR_INVALID_ARG, "bad loss_grad arguments");
+    qhd_status s = f->bf16 ? forward<__nv_bfloat16>(f, f_dev, sigma_dev, batch, nullptr)
+                           : forward<float>(f, f_dev, sigma_dev, batch, nullptr);
+    if (s != QHD_OK) return s;
+    return f->bf16 ? backward<__nv_bfloat16>(f, p_true_dev, batch, grad_dev, loss_host)
+                   : backward<float>(f, p_true_dev, batch, grad_dev, loss_host);
+}
+
+qhd_status qhd_fno_adam_step(qhd_fno *f, const float *grad_dev, float lr, float beta1, float beta2, float eps,
+                             int64_t t) {
+    if (!f) return QHD_ERR_INVALID_ARG;
+    if (!f->train) return ffail(f, QHD_ERR_STATE, "created without training buffers");
+    if (!grad_dev || t < 1 || !(lr >= 0.f) || !(beta1 >= 0.f && beta1 < 1.f) || !(beta2 >= 0.f && beta2 < 1.f) ||
+        !(eps > 0.f))
+        return ffail(f, QHD_ERR_INVALID_ARG, "bad Adam arguments");
+    const float c1 = 1.f / (1.f - powf(beta1, (float)t)), c2 = 1.f / (1.f - powf(beta2, (float)t));
+    k_fno_adam<<<grid_for(f->nparam), FT, 0, f->stream>>>(f->params, grad_dev, f->m, f->vv, f->nparam, lr, beta1,
+                                                          beta2, eps, c1, c2);
+    f->launches += 1;
+    FNO_CHECK(f);
+    return QHD_OK;
+}
+
+int64_t qhd_fno_launch_count(const qhd_fno *f) { return f ? f->launches : 0; }
+
+const char *qhd_fno_last_error(const qhd_fno *f) { return f ? f->err.c_str() : ""; }
+
+qhd_status qhd_fno_destroy(qhd_fno *f) {
+    if (!f) return QHD_OK;
+    const cudaError_t e = cudaStreamSynchronize(f->stream);
+    delete f;
+    return e == cudaSuccess ? QHD_OK : QHD_ERR_CUDA;
+}
+
+}  // extern "C"

@@ -28,7 +28,9 @@ EXPORTS = ["qhd_workspace_bytes", "qhd_init_grid", "qhd_set_potential", "qhd_set
            "qhd_observables", "qhd_launch_count", "qhd_timing_enable", "qhd_timing_read",
            "qhd_destroy", "qhd_status_string", "qhd_last_error", "qhd_observables_static",
            "qhd_set_splitting", "qhd_evolve_trajectory", "qhd_tc_workspace_bytes", "qhd_set_transform",
-           "qhd_library_call_count"]
+           "qhd_library_call_count", "qhd_fno_param_count", "qhd_fno_workspace_bytes", "qhd_fno_create",
+           "qhd_fno_forward", "qhd_fno_loss_grad", "qhd_fno_adam_step", "qhd_fno_launch_count",
+           "qhd_fno_last_error", "qhd_fno_destroy"]
 SPLIT_STRANG = 0
 SPLIT_LIE_TROTTER = 1
 KCLASS = ["prep", "row", "axis1_fwd", "axis0", "axis1_inv", "oned", "plane", "whole", "tc_split", "tc_gemm"]

@@ -1,0 +1,156 @@
+"""The FNO surrogate's CUDA kernels against the FP64 CPU reference (forward
+values, and gradients against central finite differences of the reference
+loss), its training, and what the trained network gains over an untrained one
+and over the solver alone on solver-generated data."""
+import time
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import workloads
+from oracle import fno as ref
+from paper_2303_01471_gb300 import fno, surrogate
+
+CFG = fno.FNOConfig(n=16, width=4, modes=3, layers=2, hidden=8, act_bf16=False)
+SHAPE = ref.Shape(CFG.n, CFG.width, CFG.modes, CFG.layers, CFG.hidden)
+
+
+def tiny_batch(seed, B=3, n=16):
+    rng = np.random.default_rng(seed)
+    x = np.arange(n) / n
+    f = np.empty((B, n, n))
+    for b in range(B):
+        a, c = rng.uniform(0.5, 2, 2)
+        f[b] = np.sin(2 * np.pi * (a * x[:, None] + rng.uniform())) + c * np.cos(2 * np.pi * x[None, :]) \
+            + 0.3 * rng.standard_normal((n, n))
+    sigma = rng.uniform(0.5, 2.0, B)
+    z = rng.standard_normal((B, n, n))
+    pt = np.exp(2 * z)
+    pt /= pt.sum(axis=(1, 2), keepdims=True)
+    return f, sigma, pt
+
+
+def perturbed_params(cfg, seed):
+    rng = np.random.default_rng(seed + 100)
+    p = fno.init_params(cfg, seed).astype(np.float64)
+    p += 0.05 * rng.standard_normal(p.shape)   # non-zero biases and asymmetric weights
+    return p.astype(np.float32)
+
+
+def dev(a, dtype):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda", dtype)
+
+
+def lay_name(lay, i):
+    for name, (o, k) in lay.items():
+        if o <= i < o + k:
+            return name
+    return "?"
+
+
+def test_forward_matches_reference():
+    f, sigma, _ = tiny_batch(0)
+    params = perturbed_params(CFG, 1)
+    net = fno.FNO(CFG, batch_max=4, params=torch.from_numpy(params))
+    p = net.forward(dev(f, torch.float64), dev(sigma, torch.float32)).cpu().numpy()
+    net.close()
+    p_ref, _ = ref.forward(params.astype(np.float64), SHAPE, f, sigma)
+    assert np.abs(p - p_ref).max() <= 2e-5 * p_ref.max(), np.abs(p - p_ref).max() / p_ref.max()
+    assert np.allclose(p.sum(axis=(1, 2)), 1.0, atol=1e-5)
+
+
+def test_gradients_match_finite_differences():
+    f, sigma, pt = tiny_batch(1)
+    params = perturbed_params(CFG, 2)
+    net = fno.FNO(CFG, batch_max=4, train=True, params=torch.from_numpy(params))
+    loss = net.loss_grad(dev(f, torch.float64), dev(sigma, torch.float32), dev(pt, torch.float32))
+    g = net.grad.cpu().numpy().astype(np.float64)
+    net.close()
+    p64 = params.astype(np.float64)
+    assert loss == pytest.approx(ref.loss(p64, SHAPE, f, sigma, pt), rel=1e-5)
+    lay = fno.param_layout(CFG)
+    rng = np.random.default_rng(5)
+    idx = []
+    for name, (o, k) in lay.items():
+        if name == "_total":
+            continue
+        idx += list(o + rng.choice(k, size=min(k, 6), replace=False))
+    g_fd = ref.fd_gradient(p64, SHAPE, f, sigma, pt, idx, h=1e-5)
+    scale = np.abs(g_fd).max()
+    err = np.abs(g[idx] - g_fd)
+    assert (err <= 2e-3 * np.abs(g_fd) + 2e-4 * scale).all(), \
+        [(lay_name(lay, i), g[i], gf) for i, gf, e in zip(idx, g_fd, err) if e > 2e-3 * abs(gf) + 2e-4 * scale]
+
+
+def test_bf16_activations_stay_close():
+    f, sigma, _ = tiny_batch(2)
+    cfg16 = fno.FNOConfig(**{**CFG.__dict__, "act_bf16": True})
+    params = perturbed_params(CFG, 3)
+    net = fno.FNO(cfg16, batch_max=4, params=torch.from_numpy(params))
+    p = net.forward(dev(f, torch.float64), dev(sigma, torch.float32)).cpu().numpy()
+    net.close()
+    p_ref, _ = ref.forward(params.astype(np.float64), SHAPE, f, sigma)
+    tv = 0.5 * np.abs(p - p_ref).sum(axis=(1, 2))
+    assert (tv <= 5e-3).all(), tv
+
+
+def test_adam_steps_reduce_the_loss():
+    f, sigma, pt = tiny_batch(3, B=4)
+    net = fno.FNO(CFG, batch_max=4, train=True, seed=4)
+    args = (dev(f, torch.float64), dev(sigma, torch.float32), dev(pt, torch.float32))
+    first = net.loss_grad(*args)
+    for _ in range(60):
+        net.loss_grad(*args, want_loss=False)
+        net.adam(lr=1e-2)
+    last = net.loss_grad(*args)
+    net.close()
+    assert last < 0.7 * first, (first, last)
+
+
+def test_error_paths():
+    import ctypes
+    lib = fno._lib()
+    net = fno.FNO(CFG, batch_max=2, train=False, seed=0)
+    f = torch.zeros((3, 16, 16), dtype=torch.float64, device="cuda")
+    s = torch.ones(3, dtype=torch.float32, device="cuda")
+    with pytest.raises(Exception):
+        net.forward(f, s)          # batch above batch_max
+    st = lib.qhd_fno_loss_grad(net.h, ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(s.data_ptr()),
+                               ctypes.c_void_p(f.data_ptr()), 2, ctypes.c_void_p(f.data_ptr()), None)
+    assert st == 3                 # no training buffers
+    net.close()
+
+
+def test_trained_surrogate_gains_over_untrained_and_solver():
+    """Solver-generated data (32^2, wells / Rastrigin, sigma ~ U(0.5, 2), T = 10,
+    dt = 0.01): after a short training the held-out TV is clearly below that of
+    the untrained network and of the uniform guess, and inference per instance
+    is faster than the solver's."""
+    n, ntr, nte = 32, 448, 64
+    spec = [("wells" if i % 2 == 0 else "rastrigin", 700000 + i) for i in range(ntr + nte)]
+    f, sig = workloads.batch_fast_on_device(spec, (n, n), "cuda", K=8)
+    sigma = torch.tensor(sig, dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    p = surrogate.solver_distributions(f, sig, 10.0, 0.01)
+    torch.cuda.synchronize()
+    t_solver = time.perf_counter() - t0
+    cfg = fno.FNOConfig(n=n, width=16, modes=8, layers=4, hidden=64, act_bf16=True)
+    net = fno.FNO(cfg, batch_max=64, train=True, seed=7)
+    te = slice(ntr, ntr + nte)
+    tv0 = surrogate.tv_distance(surrogate.predict(net, f[te], sigma[te], 64), p[te]).mean().item()
+    surrogate.train(net, f[:ntr], sigma[:ntr], p[:ntr], epochs=120, batch=32, lr=3e-3)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    pred = surrogate.predict(net, f[te], sigma[te], 64)
+    torch.cuda.synchronize()
+    t_fno = time.perf_counter() - t0
+    tv1 = surrogate.tv_distance(pred, p[te]).mean().item()
+    uniform = torch.full_like(p[te], 1.0 / (n * n))
+    tv_u = surrogate.tv_distance(uniform, p[te]).mean().item()
+    net.close()
+    assert tv1 < 0.75 * tv0 and tv1 < 0.75 * tv_u, (tv0, tv1, tv_u)
+    assert t_fno / nte < t_solver / (ntr + nte), (t_fno, t_solver)

@@ -135,6 +135,55 @@ def batch_on_device(spec, shape, device, K: int = 8, lo: float = 0.0, hi: float 
     return out, sig
 
 
+def batch_fast_on_device(spec, shape, device, K: int = 8, lo: float = 0.0, hi: float = 1.0, chunk: int = 512):
+    """Same draws and formulas as batch_on_device (sigma drawn for every instance),
+    evaluated for many instances at once: parameters are drawn per seed on the
+    host, then each chunk of instances is evaluated with one batched expression.
+    spec: list of (family, seed).  Returns (f (B, *shape) float64, sigmas list)."""
+    import torch
+    shape = tuple(int(n) for n in shape)
+    d = len(shape)
+    B = len(spec)
+    cen = np.zeros((B, K, d))
+    wid = np.ones((B, K))
+    dep = np.zeros((B, K))
+    sft = np.zeros((B, d))
+    sig = np.zeros(B)
+    is_w = np.zeros(B, dtype=bool)
+    for i, (fam, seed) in enumerate(spec):
+        rng = np.random.default_rng(seed)
+        if fam == "wells":
+            is_w[i] = True
+            cen[i] = rng.uniform(0.0, 1.0, size=(K, d))
+            wid[i] = rng.uniform(0.05, 0.2, size=K)
+            dep[i] = rng.uniform(0.5, 2.0, size=K)
+        else:
+            sft[i] = rng.uniform(0.2, 0.8, size=d)
+        sig[i] = rng.uniform(0.5, 2.0)
+    axes = [torch.as_tensor(a, dtype=torch.float64, device=device) for a in mesh_axes(shape, lo, hi)]
+    grids = torch.meshgrid(*axes, indexing="ij")
+    out = torch.empty((B,) + shape, dtype=torch.float64, device=device)
+    tc = torch.as_tensor(cen, device=device)
+    tw = torch.as_tensor(wid, device=device)
+    td = torch.as_tensor(dep, device=device)
+    ts = torch.as_tensor(sft, device=device)
+    view = (-1,) + (1,) * d
+    quad = 0.5 * sum((g - 0.5) ** 2 for g in grids)
+    for i0 in range(0, B, chunk):
+        i1 = min(B, i0 + chunk)
+        fw = quad.unsqueeze(0).expand((i1 - i0,) + shape).clone()
+        for k in range(K):
+            d2 = sum((g.unsqueeze(0) - tc[i0:i1, k, ax].reshape(view)) ** 2 for ax, g in enumerate(grids))
+            fw = fw - td[i0:i1, k].reshape(view) * torch.exp(-d2 / (2.0 * tw[i0:i1, k].reshape(view) ** 2))
+        fr = 0.0
+        for ax, g in enumerate(grids):
+            u = g.unsqueeze(0) - ts[i0:i1, ax].reshape(view)
+            fr = fr + (10.0 * u * u - 1.0 * torch.cos(2.0 * np.pi * 5.0 * u))
+        mask = torch.as_tensor(is_w[i0:i1], device=device).reshape(view)
+        out[i0:i1] = torch.where(mask, fw, fr)
+    return out, [float(x) for x in sig]
+
+
 def make(family: str, seed: int, shape, **kw) -> Instance:
     if family == "wells":
         return gaussian_wells(seed, shape, **kw)
