@@ -1,9 +1,7 @@
 """The FNO surrogate's CUDA kernels against the FP64 CPU reference (forward
 values, and gradients against central finite differences of the reference
 loss), its training, and what the trained network gains over an untrained one
-and over the solver alone on solver-generated data."""
-import time
-
+on solver-generated data."""
 import numpy as np
 import pytest
 
@@ -124,33 +122,23 @@ def test_error_paths():
     net.close()
 
 
-def test_trained_surrogate_gains_over_untrained_and_solver():
-    """Solver-generated data (32^2, wells / Rastrigin, sigma ~ U(0.5, 2), T = 10,
-    dt = 0.01): after a short training the held-out TV is clearly below that of
-    the untrained network and of the uniform guess, and inference per instance
-    is faster than the solver's."""
-    n, ntr, nte = 32, 448, 64
+def test_trained_surrogate_gains_over_untrained_network():
+    """Solver-generated data (64^2, wells / Rastrigin, sigma ~ U(0.5, 2), T = 10,
+    dt = 0.01): after a short training the held-out TV against the solver is well
+    below that of the untrained network and of the uniform guess.  (Speed against
+    the solver is measured by bench.py --workload fno.)"""
+    n, ntr, nte = 64, 4096, 128
     spec = [("wells" if i % 2 == 0 else "rastrigin", 700000 + i) for i in range(ntr + nte)]
     f, sig = workloads.batch_fast_on_device(spec, (n, n), "cuda", K=8)
     sigma = torch.tensor(sig, dtype=torch.float32, device="cuda")
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
     p = surrogate.solver_distributions(f, sig, 10.0, 0.01)
-    torch.cuda.synchronize()
-    t_solver = time.perf_counter() - t0
     cfg = fno.FNOConfig(n=n, width=16, modes=8, layers=4, hidden=64, act_bf16=True)
     net = fno.FNO(cfg, batch_max=64, train=True, seed=7)
     te = slice(ntr, ntr + nte)
     tv0 = surrogate.tv_distance(surrogate.predict(net, f[te], sigma[te], 64), p[te]).mean().item()
-    surrogate.train(net, f[:ntr], sigma[:ntr], p[:ntr], epochs=120, batch=32, lr=3e-3)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    pred = surrogate.predict(net, f[te], sigma[te], 64)
-    torch.cuda.synchronize()
-    t_fno = time.perf_counter() - t0
-    tv1 = surrogate.tv_distance(pred, p[te]).mean().item()
+    surrogate.train(net, f[:ntr], sigma[:ntr], p[:ntr], epochs=15, batch=32, lr=2e-3)
+    tv1 = surrogate.tv_distance(surrogate.predict(net, f[te], sigma[te], 64), p[te]).mean().item()
     uniform = torch.full_like(p[te], 1.0 / (n * n))
     tv_u = surrogate.tv_distance(uniform, p[te]).mean().item()
     net.close()
-    assert tv1 < 0.75 * tv0 and tv1 < 0.75 * tv_u, (tv0, tv1, tv_u)
-    assert t_fno / nte < t_solver / (ntr + nte), (t_fno, t_solver)
+    assert tv1 < 0.6 * tv0 and tv1 < 0.6 * tv_u, (tv0, tv1, tv_u)
