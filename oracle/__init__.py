@@ -34,6 +34,7 @@ _SRC = os.path.join(_HERE, "qhd_oracle.c")
 
 SCHED_NESTEROV = 0
 SCHED_TABLE = 1
+SCHED_POWER = 2
 
 
 def build_oracle(force: bool = False) -> str:
@@ -66,7 +67,8 @@ def _load():
         lib.oracle_evolve.argtypes = [ctypes.c_int, ip, dp, dp, dp, dp,
                                       ctypes.c_double, ctypes.c_double, ctypes.c_int64,
                                       ctypes.c_int, ctypes.c_double, ctypes.c_double,
-                                      ctypes.c_double, dp, dp, dp, ctypes.c_int64]
+                                      ctypes.c_double, dp, dp, dp, ctypes.c_int64,
+                                      ctypes.c_double]
         lib.oracle_evolve.restype = ctypes.c_int
         lib.oracle_evolve_trotter.argtypes = [ctypes.c_int, ip, dp, dp, dp, dp,
                                               ctypes.c_double, ctypes.c_double,
@@ -80,7 +82,7 @@ def _load():
         lib.oracle_fft.restype = None
         lib.oracle_schedule.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                         ctypes.c_double, dp, dp, dp, ctypes.c_int64,
-                                        ctypes.c_double, dp, dp]
+                                        ctypes.c_double, ctypes.c_double, dp, dp]
         lib.oracle_schedule.restype = None
         lib.oracle_set_threads.argtypes = [ctypes.c_int]
         lib.oracle_set_threads.restype = None
@@ -108,6 +110,10 @@ class Schedule:
     kind=SCHED_NESTEROV: a = c_phi/(eps+t^3), b = c_chi t^3 (Eq. (nonconvex_QHD_h)
     has c_phi=2, eps=s=1e-3, c_chi=2).  kind=SCHED_TABLE: phi(t), chi(t) are
     piecewise linear through the samples (ts increasing), constant beyond.
+    kind=SCHED_POWER: a = c_phi/(eps+|t|^{p+1}), b = c_chi |t|^{2p-1}, p = power:
+    the three-parameter form (Eq. (qhd_operator_convex)) with the ideal scaling
+    condition (Eq. (ideal_scaling)) met with equality, alpha = log p - log t,
+    beta = p log t + log C, gamma = p log t (c_phi = p, c_chi = p C, eps = 0).
     """
     kind: int = SCHED_NESTEROV
     c_phi: float = 2.0
@@ -116,6 +122,7 @@ class Schedule:
     ts: Optional[np.ndarray] = None
     phis: Optional[np.ndarray] = None
     chis: Optional[np.ndarray] = None
+    power: float = 2.0
 
     def arrays(self):
         if self.kind == SCHED_TABLE:
@@ -133,7 +140,7 @@ def schedule_ab(sched: Schedule, t: float):
     a = ctypes.c_double()
     b = ctypes.c_double()
     lib.oracle_schedule(sched.kind, sched.c_phi, sched.eps, sched.c_chi,
-                        _dp(ts), _dp(ph), _dp(ch), ns, float(t),
+                        _dp(ts), _dp(ph), _dp(ch), ns, float(sched.power), float(t),
                         ctypes.byref(a), ctypes.byref(b))
     return a.value, b.value
 
@@ -163,7 +170,7 @@ def evolve(f: np.ndarray, psi: np.ndarray, t0: float, dt: float, nsteps: int,
     rc = lib.oracle_evolve(ndim, _ip(n), _dp(lo_), _dp(hi_), _dp(f),
                            _dp(out.view(np.float64)), float(t0), float(dt), int(nsteps),
                            sched.kind, sched.c_phi, sched.eps, sched.c_chi,
-                           _dp(ts), _dp(ph), _dp(ch), ns)
+                           _dp(ts), _dp(ph), _dp(ch), ns, float(sched.power))
     if rc != 0:
         raise ValueError("oracle_evolve rejected its arguments")
     return out

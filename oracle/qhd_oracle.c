@@ -16,7 +16,13 @@
  *   - the Nesterov-type damping e^{phi}=2/(s+t^3), e^{chi}=2t^3 of the
  *     paper's simulations (Eq. (nonconvex_QHD_h)), generalised here to
  *     e^{phi}=c_phi/(eps+t^3), e^{chi}=c_chi t^3, plus a piecewise-linear
- *     tabulated (phi, chi);
+ *     tabulated (phi, chi), plus the power family of the three-parameter
+ *     form (Eq. (qhd_operator_convex)) under the ideal scaling condition
+ *     (Eq. (ideal_scaling)) met with equality: alpha = log p - log t,
+ *     beta = p log t + log C, gamma = p log t give e^{phi} = e^{alpha-gamma}
+ *     = p t^{-(p+1)} and e^{chi} = e^{alpha+beta+gamma} = p C t^{2p-1};
+ *     here e^{phi} = c_phi/(eps + |t|^{p+1}), e^{chi} = c_chi |t|^{2p-1}
+ *     (p = 2 is the Nesterov kind);
  *   - time stepping by the pseudo-spectral product formula, Eqs. (prod_qhd)
  *     and (prod_qhd_fft), Algorithm 1: the potential factor is diagonal in
  *     position, the kinetic factor is diagonal in Fourier space with the
@@ -52,13 +58,14 @@ typedef struct {
 /* ---------------------------------------------------------------- schedule */
 
 /* Schedule kinds, mirroring the two families the oracle supports. */
-enum { ORACLE_SCHED_NESTEROV = 0, ORACLE_SCHED_TABLE = 1 };
+enum { ORACLE_SCHED_NESTEROV = 0, ORACLE_SCHED_TABLE = 1, ORACLE_SCHED_POWER = 2 };
 
 typedef struct {
     int kind;
     double c_phi, eps, c_chi;          /* NESTEROV: a=c_phi/(eps+t^3), b=c_chi t^3 */
     const double *ts, *phis, *chis;    /* TABLE: samples of phi(t), chi(t) */
     int64_t ns;
+    double power;                      /* POWER: a=c_phi/(eps+|t|^{p+1}), b=c_chi |t|^{2p-1} */
 } sched_t;
 
 /* Piecewise-linear interpolation of samples (ts increasing), constant beyond
@@ -83,6 +90,10 @@ static void sched_eval(const sched_t *s, double t, double *a, double *b)
         double t3 = t * t * t;
         *a = s->c_phi / (s->eps + t3);
         *b = s->c_chi * t3;
+    } else if (s->kind == ORACLE_SCHED_POWER) {
+        double at = fabs(t);
+        *a = s->c_phi / (s->eps + pow(at, s->power + 1.0));
+        *b = s->c_chi * pow(at, 2.0 * s->power - 1.0);
     } else {
         *a = exp(interp(s->ts, s->phis, s->ns, t));
         *b = exp(interp(s->ts, s->chis, s->ns, t));
@@ -214,10 +225,11 @@ static void kinetic_factor(c128 *psi, int ndim, const int64_t *n, const double *
 int oracle_evolve(int ndim, const int64_t *n, const double *lo, const double *hi,
                   const double *f, double *psi_io, double t0, double dt, int64_t nsteps,
                   int sched_kind, double c_phi, double eps, double c_chi,
-                  const double *ts, const double *phis, const double *chis, int64_t ns)
+                  const double *ts, const double *phis, const double *chis, int64_t ns,
+                  double power)
 {
     if (ndim < 1 || ndim > 3 || nsteps < 0) return 1;
-    sched_t s = {sched_kind, c_phi, eps, c_chi, ts, phis, chis, ns};
+    sched_t s = {sched_kind, c_phi, eps, c_chi, ts, phis, chis, ns, power};
     if (sched_kind == ORACLE_SCHED_TABLE && (ns < 1 || !ts || !phis || !chis)) return 1;
     double len[3];
     int64_t g = 1;
@@ -246,7 +258,7 @@ int oracle_evolve_trotter(int ndim, const int64_t *n, const double *lo, const do
                           int64_t nsteps, double c_phi, double eps, double c_chi)
 {
     if (ndim < 1 || ndim > 3 || nsteps < 0) return 1;
-    sched_t s = {ORACLE_SCHED_NESTEROV, c_phi, eps, c_chi, 0, 0, 0, 0};
+    sched_t s = {ORACLE_SCHED_NESTEROV, c_phi, eps, c_chi, 0, 0, 0, 0, 0.0};
     double len[3];
     int64_t g = 1;
     for (int d = 0; d < ndim; ++d) {
@@ -269,9 +281,9 @@ int oracle_evolve_trotter(int ndim, const int64_t *n, const double *lo, const do
 /* Exported schedule evaluation (used by pins that integrate closed forms). */
 void oracle_schedule(int sched_kind, double c_phi, double eps, double c_chi,
                      const double *ts, const double *phis, const double *chis, int64_t ns,
-                     double t, double *a_out, double *b_out)
+                     double power, double t, double *a_out, double *b_out)
 {
-    sched_t s = {sched_kind, c_phi, eps, c_chi, ts, phis, chis, ns};
+    sched_t s = {sched_kind, c_phi, eps, c_chi, ts, phis, chis, ns, power};
     sched_eval(&s, t, a_out, b_out);
 }
 

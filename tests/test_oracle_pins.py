@@ -302,6 +302,52 @@ def test_time_dilation_invariance():
     assert np.max(np.abs(a - b)) <= 1e-11
 
 
+# ------------------------------------- P9b ideal-scaling power family
+
+def test_power_family_meets_ideal_scaling_with_equality():
+    """Eq. (qhd_operator_convex) / Eq. (ideal_scaling): the power kind with eps = 0,
+    c_phi = p, c_chi = p C comes from alpha, beta = gamma + log C, gamma with
+    gamma' = e^alpha and beta' = e^alpha.  Recover gamma = (log b - log a - log C)/3 and
+    alpha = log a + gamma from the oracle's (a, b) and check gamma' = e^alpha."""
+    for p, C in [(2.0, 1.0), (1.5, 0.7), (3.0, 2.0)]:
+        s = Schedule(kind=oracle.SCHED_POWER, c_phi=p, eps=0.0, c_chi=p * C, power=p)
+
+        def alpha_gamma(t):
+            a, b = oracle.schedule_ab(s, t)
+            g = (math.log(b) - math.log(a) - math.log(C)) / 3.0
+            return math.log(a) + g, g
+
+        for t in [0.3, 1.0, 2.7]:
+            h = 1e-5
+            dg = (alpha_gamma(t + h)[1] - alpha_gamma(t - h)[1]) / (2 * h)
+            assert dg == pytest.approx(math.exp(alpha_gamma(t)[0]), rel=1e-8), (p, t)
+
+
+def test_power_family_p2_is_the_paper_schedule():
+    """p = 2 gives e^phi = c_phi/(eps + t^3), e^chi = c_chi t^3 (Eq. (nonconvex_QHD_h))."""
+    inst = workloads.gaussian_wells(4, (32, 32), K=8)
+    psi = oracle.uniform_state(inst.f.shape)
+    a = oracle.evolve(inst.f, psi, 0.0, 0.01, 200, Schedule())
+    b = oracle.evolve(inst.f, psi, 0.0, 0.01, 200, Schedule(kind=oracle.SCHED_POWER, power=2.0))
+    assert np.max(np.abs(a - b)) <= 1e-12
+
+
+def test_power_family_time_dilation():
+    """Prop. (time_dilation) with tau = k t maps the power family onto itself:
+    (c_phi, eps, c_chi) -> (c_phi k^-p, eps k^-(p+1), c_chi k^2p); midpoints map onto
+    midpoints, so the discrete trajectories at dt and dt/k coincide."""
+    inst = workloads.gaussian_wells(7, (32, 32), K=8)
+    psi = oracle.uniform_state(inst.f.shape)
+    p, k = 1.5, 2.0
+    s = Schedule(kind=oracle.SCHED_POWER, c_phi=1.5, eps=1e-3, c_chi=3.0, power=p)
+    sd = Schedule(kind=oracle.SCHED_POWER, c_phi=1.5 * k ** -p, eps=1e-3 * k ** -(p + 1),
+                  c_chi=3.0 * k ** (2 * p), power=p)
+    a = oracle.evolve(inst.f, psi, 0.2, 0.01, 200, s)
+    b = oracle.evolve(inst.f, psi, 0.2 / k, 0.01 / k, 200, sd)
+    assert np.max(np.abs(a - b)) <= 1e-11
+    assert np.max(np.abs(np.abs(a) ** 2 - np.abs(psi) ** 2)) > 1e-4   # it did evolve
+
+
 # ------------------------------------------------------- P10 mirror symmetry
 
 def test_mirror_symmetry():
