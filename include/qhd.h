@@ -64,19 +64,28 @@ typedef enum {
     QHD_SCHED_NESTEROV = 0,
     /* phi(t), chi(t) piecewise linear through n_samples points (t strictly
      * increasing), constant outside [t[0], t[n-1]]; a = e^phi, b = e^chi. */
-    QHD_SCHED_TABLE = 1
+    QHD_SCHED_TABLE = 1,
+    /* e^{phi_t} = c_phi / (eps + |t|^{p+1}), e^{chi_t} = c_chi |t|^{2p-1},
+     * p = power in [0.5, 8].  The three-parameter Hamiltonian of
+     * Eq. (qhd_operator_convex) with the ideal scaling condition
+     * (Eq. (ideal_scaling)) met with equality, alpha_t = log p - log t,
+     * beta_t = p log t + log C, gamma_t = p log t, has e^{alpha-gamma} =
+     * p t^{-(p+1)} and e^{alpha+beta+gamma} = p C t^{2p-1}: c_phi = p,
+     * c_chi = p C, with eps regularising t -> 0.  p = 2 is QHD_SCHED_NESTEROV. */
+    QHD_SCHED_POWER = 2
 } qhd_sched_kind;
 
 typedef struct {
     int32_t kind;       /* qhd_sched_kind                                        */
-    double c_phi;       /* NESTEROV: > 0                                          */
-    double eps;         /* NESTEROV: >= 0; eps = 0 is allowed only if no step     */
-                        /*           midpoint is t = 0                            */
-    double c_chi;       /* NESTEROV: >= 0                                         */
+    double c_phi;       /* NESTEROV, POWER: > 0                                   */
+    double eps;         /* NESTEROV, POWER: >= 0; eps = 0 is allowed only if no   */
+                        /*           step midpoint is t = 0                       */
+    double c_chi;       /* NESTEROV, POWER: >= 0                                  */
     const double *t;    /* TABLE: host arrays of n_samples values, copied by the  */
     const double *phi;  /*        library during qhd_set_schedule                 */
     const double *chi;
     int64_t n_samples;  /* TABLE: 1 .. 256                                        */
+    double power;       /* POWER: p in [0.5, 8]; ignored by the other kinds       */
 } qhd_schedule;
 
 /* Observables of one instance (Eq. (expect_O); Fig. 2 caption). */

@@ -465,10 +465,16 @@ qhd_status qhd_set_schedule(qhd_ctx *c, const qhd_schedule *s) {
         d.eps = q.eps;
         d.c_chi = q.c_chi;
         d.t = d.phi = d.chi = nullptr;
-        if (q.kind == QHD_SCHED_NESTEROV) {
+        d.power = 0.0;
+        if (q.kind == QHD_SCHED_NESTEROV || q.kind == QHD_SCHED_POWER) {
             if (!std::isfinite(q.c_phi) || !(q.c_phi > 0) || !std::isfinite(q.eps) || q.eps < 0 ||
                 !std::isfinite(q.c_chi) || q.c_chi < 0)
-                return fail(c, QHD_ERR_INVALID_ARG, "instance %lld: bad Nesterov schedule", (long long)b);
+                return fail(c, QHD_ERR_INVALID_ARG, "instance %lld: bad Nesterov / power schedule", (long long)b);
+            if (q.kind == QHD_SCHED_POWER) {
+                if (!std::isfinite(q.power) || !(q.power >= 0.5 && q.power <= 8.0))
+                    return fail(c, QHD_ERR_INVALID_ARG, "instance %lld: power must be in [0.5, 8]", (long long)b);
+                d.power = q.power;
+            }
         } else if (q.kind == QHD_SCHED_TABLE) {
             if (!q.t || !q.phi || !q.chi || q.n_samples < 1 || q.n_samples > MAX_TABLE_SAMPLES)
                 return fail(c, QHD_ERR_INVALID_ARG, "instance %lld: bad table schedule", (long long)b);
@@ -506,6 +512,8 @@ qhd_status qhd_set_schedule(qhd_ctx *c, const qhd_schedule *s) {
         const qhd_schedule &p = s[0], &q = s[b];
         if (p.kind != q.kind) shared = false;
         else if (p.kind == QHD_SCHED_NESTEROV) shared = p.c_phi == q.c_phi && p.eps == q.eps;
+        else if (p.kind == QHD_SCHED_POWER)
+            shared = p.c_phi == q.c_phi && p.eps == q.eps && p.power == q.power;
         else {
             shared = p.n_samples == q.n_samples;
             for (int64_t i = 0; shared && i < p.n_samples; ++i) shared = p.t[i] == q.t[i] && p.phi[i] == q.phi[i];

@@ -277,6 +277,10 @@ __device__ void sched_eval_dev(const SchedDev &s, double t, double *a, double *b
         const double t3 = __dmul_rn(__dmul_rn(t, t), t);
         *a = __ddiv_rn(s.c_phi, __dadd_rn(s.eps, t3));
         *b = __dmul_rn(s.c_chi, t3);
+    } else if (s.kind == 2) {
+        const double at = fabs(t);
+        *a = __ddiv_rn(s.c_phi, __dadd_rn(s.eps, pow(at, s.power + 1.0)));
+        *b = __dmul_rn(s.c_chi, pow(at, 2.0 * s.power - 1.0));
     } else {
         *a = exp(interp_dev(s.t, s.phi, s.ns, t));
         *b = exp(interp_dev(s.t, s.chi, s.ns, t));

@@ -11,10 +11,11 @@ enum : int { MODE_FWD = 1, MODE_INV = 2, MODE_KIN = 4 };
 
 // Damping schedule as the device evaluates it (one per instance).
 struct SchedDev {
-    int32_t kind;  // 0 Nesterov, 1 table
+    int32_t kind;  // 0 Nesterov, 1 table, 2 power family
     int32_t ns;    // table samples
     double c_phi, eps, c_chi;
     const double *t, *phi, *chi;  // workspace copies of the samples
+    double power;  // power family: p
 };
 
 // Per-instance potential data written by set_potential.

@@ -21,6 +21,7 @@ STATUS = {0: "QHD_OK", 1: "QHD_ERR_INVALID_ARG", 2: "QHD_ERR_UNSUPPORTED", 3: "Q
           4: "QHD_ERR_CUDA", 5: "QHD_ERR_TIMEOUT", 6: "QHD_ERR_WORKSPACE"}
 SCHED_NESTEROV = 0
 SCHED_TABLE = 1
+SCHED_POWER = 2
 
 # Every entry point declared in include/qhd.h.
 EXPORTS = ["qhd_workspace_bytes", "qhd_init_grid", "qhd_set_potential", "qhd_set_potential_device",
@@ -48,7 +49,7 @@ class _Schedule(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("c_phi", ctypes.c_double), ("eps", ctypes.c_double),
                 ("c_chi", ctypes.c_double), ("t", ctypes.POINTER(ctypes.c_double)),
                 ("phi", ctypes.POINTER(ctypes.c_double)), ("chi", ctypes.POINTER(ctypes.c_double)),
-                ("n_samples", ctypes.c_int64)]
+                ("n_samples", ctypes.c_int64), ("power", ctypes.c_double)]
 
 
 class _Obs(ctypes.Structure):
@@ -139,6 +140,7 @@ class Schedule:
     ts: Optional[np.ndarray] = None
     phis: Optional[np.ndarray] = None
     chis: Optional[np.ndarray] = None
+    power: float = 2.0   # SCHED_POWER only
 
 
 @dataclass
@@ -238,6 +240,7 @@ class QHD:
             arr[i].c_phi = s.c_phi
             arr[i].eps = s.eps
             arr[i].c_chi = s.c_chi
+            arr[i].power = s.power
             if s.kind == SCHED_TABLE:
                 t = np.ascontiguousarray(s.ts, dtype=np.float64)
                 p = np.ascontiguousarray(s.phis, dtype=np.float64)

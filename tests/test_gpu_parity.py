@@ -35,7 +35,7 @@ NORM_FP32_FLOOR_PER_1K = 1e-6
 
 def to_oracle_sched(s: qhd.Schedule) -> oracle.Schedule:
     return oracle.Schedule(kind=s.kind, c_phi=s.c_phi, eps=s.eps, c_chi=s.c_chi,
-                           ts=s.ts, phis=s.phis, chis=s.chis)
+                           ts=s.ts, phis=s.phis, chis=s.chis, power=s.power)
 
 
 def run_gpu(f, sched, T, dt, lo=0.0, hi=1.0, batch_f=None, t0=None, psi0=None):
@@ -118,6 +118,35 @@ def test_parity_nonunit_box_and_table_schedule():
     psi_o = oracle.evolve(inst.f, oracle.uniform_state(shape), 0.0, dt, n, to_oracle_sched(sched),
                           lo=np.array(lo), hi=np.array(hi))
     compare(psi_g, obs[0], inst.f, psi_o, lo=np.array(lo), hi=np.array(hi), steps=n)
+
+
+@pytest.mark.parametrize("shape,power", [((64, 64), 1.5), ((128, 128), 3.0), ((256, 32), 0.5), ((4, 64, 32), 2.5)],
+                         ids=lambda v: "x".join(map(str, v)) if isinstance(v, tuple) else str(v))
+def test_parity_power_family_schedule(shape, power):
+    """Ideal-scaling power family (Eq. (qhd_operator_convex) with Eq. (ideal_scaling)
+    met with equality): e^phi = c_phi/(eps + t^{p+1}), e^chi = c_chi t^{2p-1}."""
+    inst = workloads.gaussian_wells(13, shape, K=4)
+    sched = qhd.Schedule(kind=qhd.SCHED_POWER, c_phi=power, eps=1e-3, c_chi=power * 1.3, power=power)
+    dt, n = 0.01, 200
+    psi_g, obs = run_gpu(inst.f, sched, n * dt, dt)
+    psi_o = oracle.evolve(inst.f, oracle.uniform_state(shape), 0.0, dt, n, to_oracle_sched(sched))
+    compare(psi_g, obs[0], inst.f, psi_o, steps=n)
+
+
+def test_power_family_batch_shares_kinetic_table_and_rejects_bad_power():
+    shape = (32, 32)
+    insts = [workloads.gaussian_wells(s, shape, K=4) for s in (41, 42)]
+    fb = np.stack([i.f for i in insts])
+    scheds = [qhd.Schedule(kind=qhd.SCHED_POWER, c_phi=2.5, c_chi=c, power=2.5) for c in (1.0, 3.0)]
+    psi_g, obs = run_gpu(None, scheds, 1.0, 0.01, batch_f=fb)
+    for b, inst in enumerate(insts):
+        psi_o = oracle.evolve(inst.f, oracle.uniform_state(shape), 0.0, 0.01, 100, to_oracle_sched(scheds[b]))
+        compare(psi_g[b], obs[b], inst.f, psi_o, steps=100)
+    sim = qhd.QHD(shape)
+    for bad in (0.25, 9.0, float("nan")):
+        with pytest.raises(qhd.QHDError):
+            sim.set_schedule(qhd.Schedule(kind=qhd.SCHED_POWER, power=bad))
+    sim.close()
 
 
 @pytest.mark.parametrize("own_kinetic", [False, True], ids=["shared-kinetic", "own-kinetic"])
