@@ -68,12 +68,12 @@ def _load():
                                       ctypes.c_double, ctypes.c_double, ctypes.c_int64,
                                       ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                       ctypes.c_double, dp, dp, dp, ctypes.c_int64,
-                                      ctypes.c_double]
+                                      ctypes.c_double, ctypes.c_int]
         lib.oracle_evolve.restype = ctypes.c_int
         lib.oracle_evolve_trotter.argtypes = [ctypes.c_int, ip, dp, dp, dp, dp,
                                               ctypes.c_double, ctypes.c_double,
                                               ctypes.c_int64, ctypes.c_double,
-                                              ctypes.c_double, ctypes.c_double]
+                                              ctypes.c_double, ctypes.c_double, ctypes.c_int]
         lib.oracle_evolve_trotter.restype = ctypes.c_int
         lib.oracle_observables.argtypes = [ctypes.c_int, ip, dp, dp, dp, dp,
                                            ctypes.c_double, dp, dp]
@@ -159,9 +159,15 @@ def uniform_state(shape) -> np.ndarray:
     return np.full(shape, 1.0 / np.sqrt(g), dtype=np.complex128)
 
 
+KINETIC_SPECTRAL = 0
+KINETIC_FD2 = 1
+
+
 def evolve(f: np.ndarray, psi: np.ndarray, t0: float, dt: float, nsteps: int,
-           sched: Schedule = Schedule(), lo=0.0, hi=1.0) -> np.ndarray:
-    """Return psi after nsteps Strang steps (complex128, shape of f)."""
+           sched: Schedule = Schedule(), lo=0.0, hi=1.0, kinetic: int = KINETIC_SPECTRAL) -> np.ndarray:
+    """Return psi after nsteps Strang steps (complex128, shape of f).  kinetic:
+    KINETIC_SPECTRAL (-Lap exact on the mesh's Fourier modes) or KINETIC_FD2 (the
+    central second difference of Eq. (discretize-pde) on the periodic mesh)."""
     lib = _load()
     f = np.ascontiguousarray(f, dtype=np.float64)
     out = np.ascontiguousarray(psi, dtype=np.complex128).copy()
@@ -170,14 +176,14 @@ def evolve(f: np.ndarray, psi: np.ndarray, t0: float, dt: float, nsteps: int,
     rc = lib.oracle_evolve(ndim, _ip(n), _dp(lo_), _dp(hi_), _dp(f),
                            _dp(out.view(np.float64)), float(t0), float(dt), int(nsteps),
                            sched.kind, sched.c_phi, sched.eps, sched.c_chi,
-                           _dp(ts), _dp(ph), _dp(ch), ns, float(sched.power))
+                           _dp(ts), _dp(ph), _dp(ch), ns, float(sched.power), int(kinetic))
     if rc != 0:
         raise ValueError("oracle_evolve rejected its arguments")
     return out
 
 
 def evolve_trotter(f, psi, t0, dt, nsteps, c_phi=2.0, eps=1e-3, c_chi=2.0,
-                   lo=0.0, hi=1.0) -> np.ndarray:
+                   lo=0.0, hi=1.0, kinetic: int = KINETIC_SPECTRAL) -> np.ndarray:
     """First-order product formula of Eq. (prod_qhd), left-end-point coefficients."""
     lib = _load()
     f = np.ascontiguousarray(f, dtype=np.float64)
@@ -185,7 +191,7 @@ def evolve_trotter(f, psi, t0, dt, nsteps, c_phi=2.0, eps=1e-3, c_chi=2.0,
     ndim, n, lo_, hi_ = _grid_args(f.shape, lo, hi)
     rc = lib.oracle_evolve_trotter(ndim, _ip(n), _dp(lo_), _dp(hi_), _dp(f),
                                    _dp(out.view(np.float64)), float(t0), float(dt),
-                                   int(nsteps), c_phi, eps, c_chi)
+                                   int(nsteps), c_phi, eps, c_chi, int(kinetic))
     if rc != 0:
         raise ValueError("oracle_evolve_trotter rejected its arguments")
     return out

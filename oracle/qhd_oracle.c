@@ -195,9 +195,12 @@ static void potential_factor(c128 *psi, const double *f, int64_t g, double h, do
 }
 
 /* psi_hat <- exp(-i * dt * a * |k|^2 / 2) psi_hat, k_d = 2 pi m_d / L_d with the
- * signed frequency number m_d in [-N_d/2, N_d/2). */
+ * signed frequency number m_d in [-N_d/2, N_d/2).
+ * kinetic = 1 replaces -Lap by the central second difference of Eq. (discretize-pde),
+ * (2 psi_j - psi_{j+1} - psi_{j-1}) / h_d^2 with h_d = L_d / N_d, on the periodic mesh:
+ * its eigenvalue for the Fourier mode m_d is (4 / h_d^2) sin^2(pi m_d / N_d). */
 static void kinetic_factor(c128 *psi, int ndim, const int64_t *n, const double *len,
-                           double dt, double a)
+                           double dt, double a, int kinetic)
 {
     int64_t g = 1;
     for (int d = 0; d < ndim; ++d) g *= n[d];
@@ -209,8 +212,14 @@ static void kinetic_factor(c128 *psi, int ndim, const int64_t *n, const double *
             int64_t idx = rem % n[d];
             rem /= n[d];
             int64_t m = idx < n[d] / 2 ? idx : idx - n[d];
-            double k = 2.0 * ORACLE_PI * (double)m / len[d];
-            k2 += k * k;
+            if (kinetic == 1) {
+                double h = len[d] / (double)n[d];
+                double sn = sin(ORACLE_PI * (double)m / (double)n[d]);
+                k2 += 4.0 * sn * sn / (h * h);
+            } else {
+                double k = 2.0 * ORACLE_PI * (double)m / len[d];
+                k2 += k * k;
+            }
         }
         apply_phase(&psi[i], dt * a * k2 / 2.0);
     }
@@ -226,7 +235,7 @@ int oracle_evolve(int ndim, const int64_t *n, const double *lo, const double *hi
                   const double *f, double *psi_io, double t0, double dt, int64_t nsteps,
                   int sched_kind, double c_phi, double eps, double c_chi,
                   const double *ts, const double *phis, const double *chis, int64_t ns,
-                  double power)
+                  double power, int kinetic)
 {
     if (ndim < 1 || ndim > 3 || nsteps < 0) return 1;
     sched_t s = {sched_kind, c_phi, eps, c_chi, ts, phis, chis, ns, power};
@@ -244,7 +253,7 @@ int oracle_evolve(int ndim, const int64_t *n, const double *lo, const double *hi
         sched_eval(&s, t, &a, &b);
         potential_factor(psi, f, g, dt / 2.0, b);
         fft_nd(psi, ndim, n, -1);
-        kinetic_factor(psi, ndim, n, len, dt, a);
+        kinetic_factor(psi, ndim, n, len, dt, a, kinetic);
         fft_nd(psi, ndim, n, +1);
         potential_factor(psi, f, g, dt / 2.0, b);
     }
@@ -255,7 +264,7 @@ int oracle_evolve(int ndim, const int64_t *n, const double *lo, const double *hi
  * at the left end point t_j = t0 + j dt, psi <- IFFT K(dt) FFT P(dt) psi. */
 int oracle_evolve_trotter(int ndim, const int64_t *n, const double *lo, const double *hi,
                           const double *f, double *psi_io, double t0, double dt,
-                          int64_t nsteps, double c_phi, double eps, double c_chi)
+                          int64_t nsteps, double c_phi, double eps, double c_chi, int kinetic)
 {
     if (ndim < 1 || ndim > 3 || nsteps < 0) return 1;
     sched_t s = {ORACLE_SCHED_NESTEROV, c_phi, eps, c_chi, 0, 0, 0, 0, 0.0};
@@ -272,7 +281,7 @@ int oracle_evolve_trotter(int ndim, const int64_t *n, const double *lo, const do
         sched_eval(&s, t, &a, &b);
         potential_factor(psi, f, g, dt, b);
         fft_nd(psi, ndim, n, -1);
-        kinetic_factor(psi, ndim, n, len, dt, a);
+        kinetic_factor(psi, ndim, n, len, dt, a, kinetic);
         fft_nd(psi, ndim, n, +1);
     }
     return 0;
