@@ -181,6 +181,22 @@ enum { QHD_SPLIT_STRANG = 0, QHD_SPLIT_LIE_TROTTER = 1 };
 qhd_status qhd_set_splitting(qhd_ctx *ctx, int kind);
 
 /*
+ * Discretisation of the kinetic operator -Lap/2 used by later qhd_evolve
+ * calls (default QHD_KINETIC_SPECTRAL).
+ * QHD_KINETIC_SPECTRAL: exact on the mesh's Fourier modes, eigenvalue
+ *   |k|^2 / 2 with k_d = 2 pi m_d / L_d (Eq. (prod_qhd_fft)).
+ * QHD_KINETIC_FD2: the central second difference of Eq. (discretize-pde),
+ *   (2 psi_j - psi_{j+1} - psi_{j-1}) / (2 h_d^2) per axis with h_d = L_d / N_d,
+ *   on the same periodic mesh (the paper states it with vanishing boundary
+ *   values; the periodic wrap is kept here so that the same transforms
+ *   diagonalise it); eigenvalue (2 / h_d^2) sin^2(pi m_d / N_d) per axis.
+ * Every transform path (FFT passes and the tensor-core form) honours it.
+ * Unknown kinds give QHD_ERR_INVALID_ARG.
+ */
+enum { QHD_KINETIC_SPECTRAL = 0, QHD_KINETIC_FD2 = 1 };
+qhd_status qhd_set_kinetic(qhd_ctx *ctx, int kind);
+
+/*
  * Transform used by qhd_evolve for the per-axis DFTs of the kinetic step
  * (Eq. prod_qhd_fft).  QHD_TRANSFORM_FFT (default): the shared-memory FFT
  * passes.  QHD_TRANSFORM_TC_DFT: each axis transform is a dense product with

@@ -130,6 +130,7 @@ struct qhd_ctx {
     bool have_f = false, have_sched = false;
     bool kt_shared = false;  // every instance has the same kinetic schedule
     int split = QHD_SPLIT_STRANG;
+    int kinetic = QHD_KINETIC_SPECTRAL;
     double t = 0.0;
     int64_t steps_done = 0;
     int64_t launches = 0;
@@ -640,6 +641,7 @@ qhd_status qhd_evolve(qhd_ctx *c, double T, double dt) {
     pa.ksum = c->ksum;
     pa.inv_g = 1.0 / (double)c->g;
     pa.split = c->split == QHD_SPLIT_LIE_TROTTER ? 1 : 0;
+    pa.kinetic = c->kinetic == QHD_KINETIC_FD2 ? 1 : 0;
 
     const int64_t ch = c->kt_shared ? c->L.chunk_shared : c->L.chunk;
     const int64_t ktb = c->kt_shared ? 1 : B;
@@ -933,6 +935,15 @@ qhd_status qhd_set_transform(qhd_ctx *c, int transform, int products, void *tc_w
 }
 
 int64_t qhd_library_call_count(const qhd_ctx *c) { return c ? c->lib_calls : 0; }
+
+qhd_status qhd_set_kinetic(qhd_ctx *c, int kind) {
+    qhd_status s = check_ctx(c);
+    if (s != QHD_OK) return s;
+    if (kind != QHD_KINETIC_SPECTRAL && kind != QHD_KINETIC_FD2)
+        return fail(c, QHD_ERR_INVALID_ARG, "unknown kinetic operator %d", kind);
+    c->kinetic = kind;
+    return QHD_OK;
+}
 
 qhd_status qhd_timing_enable(qhd_ctx *c, int every) {
     qhd_status s = check_ctx(c);

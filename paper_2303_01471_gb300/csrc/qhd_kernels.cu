@@ -306,6 +306,7 @@ __global__ void k_prep(PrepArgs a) {
     const int64_t b = blockIdx.y;
     const int64_t j = a.j0 + jl;    // global step index
     __shared__ uint64_t s_k[3];
+    __shared__ double s_fd[3];
     if (threadIdx.x == 0) {
         const SchedDev &sd = a.sched[b];
         const double PI = 3.141592653589793238462643383279502884;
@@ -336,6 +337,10 @@ __global__ void k_prep(PrepArgs a) {
             // turns per unit m^2: dt * a * |2 pi m / L|^2 / 2 / (2 pi) = dt a pi m^2 / L^2
             const double kap = __ddiv_rn(__dmul_rn(__dmul_rn(a.dt, a_p), PI), __dmul_rn(a.len[d], a.len[d]));
             s_k[d] = frac_to_u64(kap);
+            // finite difference: turns per unit sin^2(pi m/N) =
+            // dt * a * (4 / h^2) / 2 / (2 pi) = dt a N^2 / (pi L^2)
+            const double nn = (double)a.n[d];
+            s_fd[d] = __ddiv_rn(__dmul_rn(__dmul_rn(a.dt, a_p), nn * nn), __dmul_rn(PI, __dmul_rn(a.len[d], a.len[d])));
         }
     }
     __syncthreads();
@@ -347,7 +352,13 @@ __global__ void k_prep(PrepArgs a) {
         const int idx = i - a.koff[d];
         const int nd = a.n[d];
         const int m = idx < nd / 2 ? idx : idx - nd;
-        const uint32_t u = turns_mul(s_k[d], (uint32_t)(m * m));
+        uint32_t u;
+        if (a.kinetic == 1) {
+            const double sp = sinpi((double)m / (double)nd);
+            u = (uint32_t)(frac_to_u64(__dmul_rn(s_fd[d], __dmul_rn(sp, sp))) >> 32);
+        } else {
+            u = turns_mul(s_k[d], (uint32_t)(m * m));
+        }
         double s, c;
         sincospi((double)(int32_t)u * 4.656612873077392578125e-10, &s, &c);
         const double scale = d == 0 ? a.inv_g : 1.0;  // exact power of two

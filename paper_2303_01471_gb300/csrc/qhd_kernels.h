@@ -111,6 +111,7 @@ struct PrepArgs {
     int ksum;
     double inv_g;          // 1/G (exact power of two)
     int split;             // 0 Strang (midpoint, merged halves), 1 first-order Lie-Trotter
+    int kinetic;           // 0 spectral |k|^2, 1 central second difference (4/h^2) sin^2(pi m/N)
 };
 
 struct ObsArgs {

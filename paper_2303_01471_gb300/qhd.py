@@ -29,11 +29,13 @@ EXPORTS = ["qhd_workspace_bytes", "qhd_init_grid", "qhd_set_potential", "qhd_set
            "qhd_observables", "qhd_launch_count", "qhd_timing_enable", "qhd_timing_read",
            "qhd_destroy", "qhd_status_string", "qhd_last_error", "qhd_observables_static",
            "qhd_set_splitting", "qhd_evolve_trajectory", "qhd_tc_workspace_bytes", "qhd_set_transform",
-           "qhd_library_call_count", "qhd_fno_param_count", "qhd_fno_workspace_bytes", "qhd_fno_create",
+           "qhd_library_call_count", "qhd_set_kinetic", "qhd_fno_param_count", "qhd_fno_workspace_bytes", "qhd_fno_create",
            "qhd_fno_forward", "qhd_fno_loss_grad", "qhd_fno_adam_step", "qhd_fno_launch_count",
            "qhd_fno_last_error", "qhd_fno_destroy"]
 SPLIT_STRANG = 0
 SPLIT_LIE_TROTTER = 1
+KINETIC_SPECTRAL = 0
+KINETIC_FD2 = 1
 KCLASS = ["prep", "row", "axis1_fwd", "axis0", "axis1_inv", "oned", "plane", "whole", "tc_split", "tc_gemm"]
 TRANSFORM_FFT = 0
 TRANSFORM_TC_DFT = 1
@@ -114,6 +116,8 @@ def load(build_if_missing: bool = True):
     lib.qhd_evolve_trajectory.restype = st
     lib.qhd_set_splitting.argtypes = [vp, ctypes.c_int]
     lib.qhd_set_splitting.restype = st
+    lib.qhd_set_kinetic.argtypes = [vp, ctypes.c_int]
+    lib.qhd_set_kinetic.restype = st
     lib.qhd_tc_workspace_bytes.argtypes = [ctypes.c_int, i64p, ctypes.c_int64, ctypes.c_int]
     lib.qhd_tc_workspace_bytes.restype = ctypes.c_size_t
     lib.qhd_set_transform.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, ctypes.c_size_t]
@@ -285,6 +289,11 @@ class QHD:
 
     def library_call_count(self) -> int:
         return int(self.lib.qhd_library_call_count(self.ctx))
+
+    def set_kinetic(self, kind: int) -> None:
+        """KINETIC_SPECTRAL (default) or KINETIC_FD2 (central second difference of
+        Eq. (discretize-pde) on the periodic mesh)."""
+        self._check(self.lib.qhd_set_kinetic(self.ctx, int(kind)), "qhd_set_kinetic")
 
     def set_time(self, t: float) -> None:
         self._check(self.lib.qhd_set_time(self.ctx, float(t)), "qhd_set_time")

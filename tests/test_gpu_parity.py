@@ -38,12 +38,14 @@ def to_oracle_sched(s: qhd.Schedule) -> oracle.Schedule:
                            ts=s.ts, phis=s.phis, chis=s.chis, power=s.power)
 
 
-def run_gpu(f, sched, T, dt, lo=0.0, hi=1.0, batch_f=None, t0=None, psi0=None):
+def run_gpu(f, sched, T, dt, lo=0.0, hi=1.0, batch_f=None, t0=None, psi0=None, kinetic=None):
     shape = f.shape if batch_f is None else batch_f.shape[1:]
     batch = 1 if batch_f is None else batch_f.shape[0]
     sim = qhd.QHD(shape, lo=lo, hi=hi, batch=batch)
     sim.set_potential(f if batch_f is None else batch_f)
     sim.set_schedule(sched)
+    if kinetic is not None:
+        sim.set_kinetic(kinetic)
     sim.reset_state()
     if psi0 is not None:
         sim.psi.copy_(torch.from_numpy(psi0.astype(np.complex64)).reshape(sim.psi.shape))
@@ -146,6 +148,31 @@ def test_power_family_batch_shares_kinetic_table_and_rejects_bad_power():
     for bad in (0.25, 9.0, float("nan")):
         with pytest.raises(qhd.QHDError):
             sim.set_schedule(qhd.Schedule(kind=qhd.SCHED_POWER, power=bad))
+    sim.close()
+
+
+@pytest.mark.parametrize("shape", [(256,), (64, 64), (1024, 32), (128, 256), (4, 64, 32), (8, 16, 4)],
+                         ids=lambda s: "x".join(map(str, s)))
+def test_parity_fd_kinetic_operator(shape):
+    """Central-difference kinetic operator of Eq. (discretize-pde) on the periodic
+    mesh, on every launch structure (1-D, cluster-resident 2-D, row + column passes,
+    3-D plane pass, 3-D generic passes), on a non-unit box."""
+    inst = workloads.gaussian_wells(14, shape, K=4)
+    lo, hi = 0.0, 2.0
+    dt, n = 0.01, 100
+    psi_g, obs = run_gpu(inst.f, qhd.Schedule(), n * dt, dt, lo=lo, hi=hi, kinetic=qhd.KINETIC_FD2)
+    psi_o = oracle.evolve(inst.f, oracle.uniform_state(shape), 0.0, dt, n, oracle.Schedule(), lo=lo, hi=hi,
+                          kinetic=oracle.KINETIC_FD2)
+    compare(psi_g, obs[0], inst.f, psi_o, lo=np.full(len(shape), lo), hi=np.full(len(shape), hi), steps=n)
+    # the operator is not the spectral one
+    psi_s = oracle.evolve(inst.f, oracle.uniform_state(shape), 0.0, dt, n, oracle.Schedule(), lo=lo, hi=hi)
+    assert np.abs(np.abs(psi_s) ** 2 - np.abs(psi_o) ** 2).max() > 1e-3 * (np.abs(psi_o) ** 2).max()
+
+
+def test_unknown_kinetic_operator_is_rejected():
+    sim = qhd.QHD((16, 16))
+    with pytest.raises(qhd.QHDError):
+        sim.set_kinetic(7)
     sim.close()
 
 

@@ -239,3 +239,22 @@ def test_tc_error_paths():
     assert lib.qhd_set_transform(sim.ctx, 1, 5, ctypes.c_void_p(base), need) == 0
     assert lib.qhd_set_transform(sim.ctx, 0, 0, None, 0) == 0
     sim.close()
+
+
+def test_tc_fixed_with_fd_kinetic_operator():
+    """The tensor-core form with the central-difference kinetic operator."""
+    n = 128
+    inst = workloads.gaussian_wells(15, (n, n), K=8)
+    sim = qhd.QHD((n, n))
+    sim.set_potential(inst.f)
+    sim.set_schedule(qhd.Schedule())
+    sim.set_kinetic(qhd.KINETIC_FD2)
+    sim.set_transform(qhd.TRANSFORM_TC_DFT, 10)
+    sim.reset_state()
+    sim.evolve(1.0, 0.01)
+    obs = sim.observables(0.1)
+    psi = sim.psi.cpu().numpy().astype(np.complex128)
+    sim.close()
+    psi_o = oracle.evolve(inst.f, oracle.uniform_state((n, n)), 0.0, 0.01, 100, oracle.Schedule(),
+                          kinetic=oracle.KINETIC_FD2)
+    check(psi[0], obs[0], inst.f, psi_o, 100)
