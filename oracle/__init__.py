@@ -84,6 +84,9 @@ def _load():
                                         ctypes.c_double, dp, dp, dp, ctypes.c_int64,
                                         ctypes.c_double, ctypes.c_double, dp, dp]
         lib.oracle_schedule.restype = None
+        lib.oracle_apply_h.argtypes = [ctypes.c_int, ip, dp, dp, dp, dp, dp, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_int]
+        lib.oracle_apply_h.restype = ctypes.c_int
         lib.oracle_set_threads.argtypes = [ctypes.c_int]
         lib.oracle_set_threads.restype = None
         lib.oracle_max_threads.argtypes = []
@@ -238,3 +241,38 @@ def set_threads(n: int) -> None:
 
 def max_threads() -> int:
     return int(_load().oracle_max_threads())
+
+
+def apply_h(f: np.ndarray, psi: np.ndarray, a: float, b: float, lo=0.0, hi=1.0,
+            kinetic: int = KINETIC_SPECTRAL) -> np.ndarray:
+    """H psi with H = a (-Lap/2) + b f (Eq. (qhd_operator)) on the mesh, with the
+    spectral or the finite-difference kinetic operator."""
+    lib = _load()
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    x = np.ascontiguousarray(psi, dtype=np.complex128).reshape(f.shape)
+    out = np.empty_like(x)
+    ndim, n, lo_, hi_ = _grid_args(f.shape, lo, hi)
+    rc = lib.oracle_apply_h(ndim, _ip(n), _dp(lo_), _dp(hi_), _dp(f), _dp(x.view(np.float64)),
+                            _dp(out.view(np.float64)), float(a), float(b), int(kinetic))
+    if rc != 0:
+        raise ValueError("oracle_apply_h rejected its arguments")
+    return out
+
+
+def lowest_eigs(f: np.ndarray, a: float, b: float, k: int, lo=0.0, hi=1.0,
+                kinetic: int = KINETIC_SPECTRAL, return_vectors: bool = False):
+    """The k lowest eigenvalues (ascending) of H = a (-Lap/2) + b f, a real symmetric
+    operator on the mesh: scipy's Lanczos (ARPACK eigsh) on the oracle's apply_h."""
+    import scipy.sparse.linalg as sla
+    shape = f.shape
+    G = int(np.prod(shape))
+
+    def mv(x):
+        return apply_h(f, x.reshape(shape).astype(np.complex128), a, b, lo, hi, kinetic).real.ravel()
+
+    op = sla.LinearOperator((G, G), matvec=mv, dtype=np.float64)
+    vals, vecs = sla.eigsh(op, k=k, which="SA", tol=1e-12, ncv=max(2 * k + 1, 40))
+    order = np.argsort(vals)
+    if return_vectors:
+        return vals[order], vecs[:, order]
+    return vals[order]

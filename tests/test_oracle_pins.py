@@ -516,3 +516,72 @@ def test_observables_argmin_tie_takes_lowest_index():
     f[3, 0] = 0.0
     ob = oracle.observables(f, oracle.uniform_state((4, 4)), lo=0.0, hi=1.0)
     assert tuple(ob.x_star[:2]) == (0.25, 0.5)
+
+
+# ------------------------------------- P13 the Hamiltonian and its spectrum
+
+@pytest.mark.parametrize("kinetic", [0, 1])
+@pytest.mark.parametrize("shape,lengths", [((8,), (1.0,)), ((4, 8), (1.0, 2.0)), ((4, 2, 4), (1.0, 1.0, 0.5))])
+def test_apply_h_equals_dense_matrix(shape, lengths, kinetic):
+    """H = a (-Lap/2) + b f (Eq. (qhd_operator)) against dense matrices written out
+    independently: Trefethen's spectral second derivative, or the central
+    difference of Eq. (discretize-pde)."""
+    rng = np.random.default_rng(9)
+    f = rng.uniform(-1, 1, size=shape)
+    psi = rng.normal(size=shape) + 1j * rng.normal(size=shape)
+    a, b = 0.7, 1.9
+    if kinetic == 0:
+        K = dense_kinetic(shape, lengths)
+    else:
+        G = int(np.prod(shape))
+        D = np.zeros((G, G))
+        for ax in range(len(shape)):
+            term = np.ones((1, 1))
+            for j in range(len(shape)):
+                term = np.kron(term, fd_laplacian(shape[j], lengths[j]) if j == ax else np.eye(shape[j]))
+            D += term
+        K = -0.5 * D
+    H = a * K + b * np.diag(f.ravel())
+    got = oracle.apply_h(f, psi, a, b, lo=0.0, hi=np.asarray(lengths), kinetic=kinetic)
+    assert np.max(np.abs(got.ravel() - H @ psi.ravel())) <= 1e-11 * np.abs(H).max() * np.abs(psi).max() * 10
+
+
+def test_free_particle_spectrum_closed_form():
+    """f = 0: the eigenvalues are a |k|^2 / 2, k = 2 pi m / L, with their multiplicities."""
+    shape, L, a = (16, 8), (1.0, 2.0), 1.3
+    got = oracle.lowest_eigs(np.zeros(shape), a, 1.0, 10, hi=np.asarray(L))
+    ms = [(m0, m1) for m0 in range(-8, 8) for m1 in range(-4, 4)]
+    want = sorted(a / 2 * ((2 * np.pi * m0 / L[0]) ** 2 + (2 * np.pi * m1 / L[1]) ** 2) for m0, m1 in ms)[:10]
+    assert np.allclose(got, want, rtol=1e-9, atol=1e-9)
+
+
+def test_harmonic_oscillator_spectrum():
+    """H = a (-1/2 d^2/dx^2) + b omega^2 x^2 / 2 has E_n = sqrt(a b) omega (n + 1/2)
+    (the oscillator of Lemma (expect_potential)); a wide, fine periodic box resolves
+    the low levels to spectral accuracy."""
+    n, L = 128, 24.0
+    x = -L / 2 + np.arange(n) * L / n
+    a, b, om = 0.8, 1.7, 1.1
+    got = oracle.lowest_eigs(0.5 * om ** 2 * x ** 2, a, b, 5, lo=-L / 2, hi=L / 2)
+    want = np.sqrt(a * b) * om * (np.arange(5) + 0.5)
+    assert np.allclose(got, want, rtol=1e-9)
+
+
+def test_paper_levy_semiclassical_energy_ratio():
+    """The paper's worked example: the Levy function's Hessian at (1, 1) gives
+    omega_1 ~ 1.4979, omega_2 ~ 0.3536 and the semi-classical ratio E1/E0 ~ 1.3819
+    (fixture).  The printed omegas follow from the printed Hessian eigenvalues, and
+    the oracle's lowest levels of H for the quadratic model reproduce the ratio."""
+    import json, os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_levy_energy_ratio.json")))
+    lam1 = (np.pi ** 2 + 1 + 10 * np.sin(1.0) ** 2) / 8
+    om1, om2 = np.sqrt(lam1), np.sqrt(gold["hessian_eigenvalue_2"])
+    tol = 0.5 * 10.0 ** -gold["printed_digits"]
+    assert abs(om1 - gold["omega_1"]) <= tol and abs(om2 - gold["omega_2"]) <= tol
+    n, L = 64, 24.0
+    x = -L / 2 + np.arange(n) * L / n
+    X1, X2 = np.meshgrid(x, x, indexing="ij")
+    f = 0.5 * om1 ** 2 * X1 ** 2 + 0.5 * om2 ** 2 * X2 ** 2
+    E = oracle.lowest_eigs(f, 1.0, 1.0, 2, lo=-L / 2, hi=L / 2)
+    assert abs(E[1] / E[0] - gold["semiclassical_ratio"]) <= tol
+    assert E[1] / E[0] == pytest.approx((om1 + 3 * om2) / (om1 + om2), rel=1e-8)
