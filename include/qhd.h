@@ -312,6 +312,37 @@ qhd_status qhd_timing_enable(qhd_ctx *ctx, int every);
 qhd_status qhd_timing_read(qhd_ctx *ctx, double *ms_out, int64_t *launches_out, int reset);
 
 /*
+ * Spectrum of the QHD Hamiltonian (the probability spectrum and energy ratio
+ * of the paper's section on the three phases of QHD):
+ *   H(t) = e^{phi_t} (-Lap/2) + e^{chi_t} f
+ * on the context's mesh, with its kinetic discretisation (qhd_set_kinetic)
+ * and instance `inst`'s f and schedule.  H is real symmetric on the mesh.
+ *
+ * qhd_apply_hamiltonian: out = H(t) in for one instance; in_dev, out_dev are
+ *   G complex64 values each (distinct buffers).  Asynchronous on the stream.
+ *   Kinetic part by the context's transforms (forward along every axis, the
+ *   real factor e^{phi} |k|^2 / 2 or its finite-difference counterpart, inverse),
+ *   potential part e^{chi} f in as a pointwise product.
+ * qhd_lowest_eigenpairs: m Lanczos steps with full reorthogonalisation from a
+ *   seeded random start vector, then the k lowest Ritz pairs (1 <= k <= m,
+ *   2 <= m <= 512, m <= G).  Outputs (host arrays of k doubles, each optional):
+ *   eigvals (ascending), residuals ||H u - theta u|| with ||u|| = 1 (computed
+ *   with qhd_apply_hamiltonian), overlaps |<u, psi>|^2 / <psi, psi> with the
+ *   instance's current state (the probability spectrum); eigvecs_dev
+ *   (optional, k * G complex64) receives the normalised Ritz vectors.  A
+ *   single start vector resolves each distinct eigenvalue once: degenerate
+ *   levels appear once.  work_dev: caller-owned, 256-byte aligned,
+ *   qhd_spectrum_workspace_bytes(ctx, m) bytes.  Synchronises the stream.
+ * Errors: QHD_ERR_STATE without potential and schedule, QHD_ERR_INVALID_ARG
+ *   for inst, m, k out of range, QHD_ERR_WORKSPACE for a short workspace.
+ */
+size_t qhd_spectrum_workspace_bytes(const qhd_ctx *ctx, int m);
+qhd_status qhd_apply_hamiltonian(qhd_ctx *ctx, int64_t inst, double t, const void *in_dev, void *out_dev);
+qhd_status qhd_lowest_eigenpairs(qhd_ctx *ctx, int64_t inst, double t, int m, int k, uint64_t seed,
+                                 void *work_dev, size_t work_bytes, double *eigvals, double *residuals,
+                                 double *overlaps, void *eigvecs_dev);
+
+/*
  * Learned surrogate: a Fourier neural operator (FNO) that maps an instance's
  * sampled objective f on an n x n mesh of [0,1]^2 and its schedule scale sigma
  * to a predicted |psi(T)|^2 (a distribution over the mesh), trained on

@@ -13,6 +13,7 @@
 #include "qhd.h"
 #include "qhd_device.cuh"
 #include "qhd_kernels.h"
+#include "qhd_spectrum.h"
 #include "qhd_tcdft.h"
 
 using namespace qhd;
@@ -137,6 +138,13 @@ struct qhd_ctx {
     qhd_status sticky = QHD_OK;
     std::string err;
     std::vector<InstDev> inst_host;
+    // host copy of the schedules (spectrum: a(t), b(t) on the host)
+    struct HostSched {
+        int kind = 0;
+        double c_phi = 0, eps = 0, c_chi = 0, power = 0;
+        std::vector<double> t, phi, chi;
+    };
+    std::vector<HostSched> sched_host;
     std::vector<double> coord_host;
     // device-time accounting (qhd_timing_*)
     // tensor-core transform (qhd_set_transform)
@@ -521,6 +529,21 @@ qhd_status qhd_set_schedule(qhd_ctx *c, const qhd_schedule *s) {
         }
     }
     c->kt_shared = shared;
+    c->sched_host.assign((size_t)B, qhd_ctx::HostSched{});
+    for (int64_t b = 0; b < B; ++b) {
+        const qhd_schedule &q = s[b];
+        qhd_ctx::HostSched &h = c->sched_host[(size_t)b];
+        h.kind = q.kind;
+        h.c_phi = q.c_phi;
+        h.eps = q.eps;
+        h.c_chi = q.c_chi;
+        h.power = q.kind == QHD_SCHED_POWER ? q.power : 0.0;
+        if (q.kind == QHD_SCHED_TABLE) {
+            h.t.assign(q.t, q.t + q.n_samples);
+            h.phi.assign(q.phi, q.phi + q.n_samples);
+            h.chi.assign(q.chi, q.chi + q.n_samples);
+        }
+    }
     c->have_sched = true;
     return QHD_OK;
 }
@@ -987,3 +1010,61 @@ qhd_status qhd_destroy(qhd_ctx *c) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------- views for qhd_spectrum.cu
+namespace qhd {
+
+qhd_status ctx_view(qhd_ctx *c, CtxView *v) {
+    qhd_status s = check_ctx(c);
+    if (s != QHD_OK) return s;
+    if (!c->have_f || !c->have_sched) return fail(c, QHD_ERR_STATE, "needs set_potential and set_schedule first");
+    v->ndim = c->ndim;
+    for (int d = 0; d < 3; ++d) {
+        v->n[d] = d < c->ndim ? c->n[d] : 1;
+        v->len[d] = d < c->ndim ? c->hi[d] - c->lo[d] : 1.0;
+        v->tw[d] = d < c->ndim ? c->tw[d] : nullptr;
+    }
+    v->batch = c->batch;
+    v->g = c->g;
+    v->psi = c->psi;
+    v->f64 = c->f64;
+    v->kinetic = c->kinetic;
+    v->stream = c->stream;
+    return QHD_OK;
+}
+
+static double host_interp(const std::vector<double> &ts, const std::vector<double> &vs, double t) {
+    const size_t n = ts.size();
+    if (t <= ts[0]) return vs[0];
+    if (t >= ts[n - 1]) return vs[n - 1];
+    size_t lo = 0, hi = n - 1;
+    while (hi - lo > 1) {
+        const size_t mid = (lo + hi) / 2;
+        if (ts[mid] <= t) lo = mid;
+        else hi = mid;
+    }
+    const double w = (t - ts[lo]) / (ts[hi] - ts[lo]);
+    return vs[lo] + w * (vs[hi] - vs[lo]);
+}
+
+void ctx_sched_ab(const qhd_ctx *c, int64_t inst, double t, double *a, double *b) {
+    const qhd_ctx::HostSched &h = c->sched_host[(size_t)inst];
+    if (h.kind == QHD_SCHED_NESTEROV) {
+        const double t3 = t * t * t;
+        *a = h.c_phi / (h.eps + t3);
+        *b = h.c_chi * t3;
+    } else if (h.kind == QHD_SCHED_POWER) {
+        const double at = std::fabs(t);
+        *a = h.c_phi / (h.eps + std::pow(at, h.power + 1.0));
+        *b = h.c_chi * std::pow(at, 2.0 * h.power - 1.0);
+    } else {
+        *a = std::exp(host_interp(h.t, h.phi, t));
+        *b = std::exp(host_interp(h.t, h.chi, t));
+    }
+}
+
+qhd_status ctx_fail(qhd_ctx *c, qhd_status s, const char *msg) { return fail(c, s, "%s", msg); }
+
+int64_t ctx_grid_points(const qhd_ctx *c) { return c ? c->g : 0; }
+
+}  // namespace qhd

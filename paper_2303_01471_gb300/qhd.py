@@ -29,7 +29,8 @@ EXPORTS = ["qhd_workspace_bytes", "qhd_init_grid", "qhd_set_potential", "qhd_set
            "qhd_observables", "qhd_launch_count", "qhd_timing_enable", "qhd_timing_read",
            "qhd_destroy", "qhd_status_string", "qhd_last_error", "qhd_observables_static",
            "qhd_set_splitting", "qhd_evolve_trajectory", "qhd_tc_workspace_bytes", "qhd_set_transform",
-           "qhd_library_call_count", "qhd_set_kinetic", "qhd_fno_param_count", "qhd_fno_workspace_bytes", "qhd_fno_create",
+           "qhd_library_call_count", "qhd_set_kinetic", "qhd_spectrum_workspace_bytes",
+           "qhd_apply_hamiltonian", "qhd_lowest_eigenpairs", "qhd_fno_param_count", "qhd_fno_workspace_bytes", "qhd_fno_create",
            "qhd_fno_forward", "qhd_fno_loss_grad", "qhd_fno_adam_step", "qhd_fno_launch_count",
            "qhd_fno_last_error", "qhd_fno_destroy"]
 SPLIT_STRANG = 0
@@ -118,6 +119,13 @@ def load(build_if_missing: bool = True):
     lib.qhd_set_splitting.restype = st
     lib.qhd_set_kinetic.argtypes = [vp, ctypes.c_int]
     lib.qhd_set_kinetic.restype = st
+    lib.qhd_spectrum_workspace_bytes.argtypes = [vp, ctypes.c_int]
+    lib.qhd_spectrum_workspace_bytes.restype = ctypes.c_size_t
+    lib.qhd_apply_hamiltonian.argtypes = [vp, ctypes.c_int64, ctypes.c_double, vp, vp]
+    lib.qhd_apply_hamiltonian.restype = st
+    lib.qhd_lowest_eigenpairs.argtypes = [vp, ctypes.c_int64, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_uint64, vp, ctypes.c_size_t, dp, dp, dp, vp]
+    lib.qhd_lowest_eigenpairs.restype = st
     lib.qhd_tc_workspace_bytes.argtypes = [ctypes.c_int, i64p, ctypes.c_int64, ctypes.c_int]
     lib.qhd_tc_workspace_bytes.restype = ctypes.c_size_t
     lib.qhd_set_transform.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, ctypes.c_size_t]
@@ -294,6 +302,36 @@ class QHD:
         """KINETIC_SPECTRAL (default) or KINETIC_FD2 (central second difference of
         Eq. (discretize-pde) on the periodic mesh)."""
         self._check(self.lib.qhd_set_kinetic(self.ctx, int(kind)), "qhd_set_kinetic")
+
+    def apply_hamiltonian(self, x, t: float, inst: int = 0):
+        """H(t) x for instance `inst` (x: complex64 CUDA tensor with the mesh's G values)."""
+        import torch
+        x = x.contiguous()
+        out = torch.empty_like(x)
+        self._check(self.lib.qhd_apply_hamiltonian(self.ctx, int(inst), float(t), ctypes.c_void_p(x.data_ptr()),
+                                                   ctypes.c_void_p(out.data_ptr())), "qhd_apply_hamiltonian")
+        return out
+
+    def lowest_eigenpairs(self, t: float, k: int, m: int = 64, inst: int = 0, seed: int = 1, vectors: bool = False):
+        """The k lowest eigenvalues of H(t) (Lanczos, m steps) with residuals and the
+        probability spectrum |<n|psi>|^2 of the current state; returns numpy arrays
+        (eigvals, residuals, overlaps) and, with vectors=True, a (k, *shape) tensor."""
+        import torch
+        ws = int(self.lib.qhd_spectrum_workspace_bytes(self.ctx, int(m)))
+        if ws == 0:
+            raise QHDError(1, f"bad Lanczos size m={m}")
+        work = torch.empty(ws + 256, dtype=torch.uint8, device=self.device)
+        ptr = work.data_ptr() + (-work.data_ptr()) % 256
+        ev = np.zeros(k)
+        rs = np.zeros(k)
+        ov = np.zeros(k)
+        vecs = torch.empty((k, *self.shape), dtype=torch.complex64, device=self.device) if vectors else None
+        dp = ctypes.POINTER(ctypes.c_double)
+        self._check(self.lib.qhd_lowest_eigenpairs(
+            self.ctx, int(inst), float(t), int(m), int(k), int(seed), ctypes.c_void_p(ptr), ctypes.c_size_t(ws),
+            ev.ctypes.data_as(dp), rs.ctypes.data_as(dp), ov.ctypes.data_as(dp),
+            ctypes.c_void_p(vecs.data_ptr()) if vectors else None), "qhd_lowest_eigenpairs")
+        return (ev, rs, ov, vecs) if vectors else (ev, rs, ov)
 
     def set_time(self, t: float) -> None:
         self._check(self.lib.qhd_set_time(self.ctx, float(t)), "qhd_set_time")
