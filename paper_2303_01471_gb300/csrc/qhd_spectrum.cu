@@ -81,6 +81,7 @@ struct HMult {
 };
 
 __device__ __forceinline__ double kin_eig(int i, int n, double len, int kinetic) {
+    if (n == 1) return 0.0;  // an axis the grid does not have
     const int m = i < n / 2 ? i : i - n;
     if (kinetic == QHD_KINETIC_FD2) {
         const double h = len / (double)n;
