@@ -325,13 +325,15 @@ qhd_status qhd_timing_read(qhd_ctx *ctx, double *ms_out, int64_t *launches_out, 
  *   potential part e^{chi} f in as a pointwise product.
  * qhd_lowest_eigenpairs: m Lanczos steps with full reorthogonalisation from a
  *   seeded random start vector, then the k lowest Ritz pairs (1 <= k <= m,
- *   2 <= m <= 512, m <= G).  Outputs (host arrays of k doubles, each optional):
+ *   2 <= m <= 1024, m <= G).  Convergence of the low levels needs m of order
+ *   sqrt(spread of H / level gap): a few hundred on meshes of 64^2 and up (the
+ *   returned residuals show it).  Outputs (host arrays of k doubles, each optional):
  *   eigvals (ascending), residuals ||H u - theta u|| with ||u|| = 1 (computed
  *   with qhd_apply_hamiltonian), overlaps |<u, psi>|^2 / <psi, psi> with the
  *   instance's current state (the probability spectrum); eigvecs_dev
  *   (optional, k * G complex64) receives the normalised Ritz vectors.  A
- *   single start vector resolves each distinct eigenvalue once: degenerate
- *   levels appear once.  work_dev: caller-owned, 256-byte aligned,
+ *   single start vector resolves each distinct eigenvalue once: a degenerate
+ *   level may appear only once.  work_dev: caller-owned, 256-byte aligned,
  *   qhd_spectrum_workspace_bytes(ctx, m) bytes.  Synchronises the stream.
  * Errors: QHD_ERR_STATE without potential and schedule, QHD_ERR_INVALID_ARG
  *   for inst, m, k out of range, QHD_ERR_WORKSPACE for a short workspace.

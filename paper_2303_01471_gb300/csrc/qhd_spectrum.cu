@@ -341,7 +341,7 @@ extern "C" {
 
 size_t qhd_spectrum_workspace_bytes(const qhd_ctx *ctx, int m) {
     const int64_t g = ctx_grid_points(ctx);
-    if (g <= 0 || m < 2 || m > 512) return 0;
+    if (g <= 0 || m < 2 || m > 1024) return 0;
     size_t t = 0;
     t += al((size_t)(m + 1) * g * sizeof(float2));  // Lanczos basis
     t += 2 * al((size_t)g * sizeof(float2));        // Ritz vector, H times it
@@ -371,7 +371,7 @@ qhd_status qhd_lowest_eigenpairs(qhd_ctx *ctx, int64_t inst, double t, int m, in
     qhd_status st = ctx_view(ctx, &v);
     if (st != QHD_OK) return st;
     const int64_t g = v.g;
-    if (inst < 0 || inst >= v.batch || m < 2 || m > 512 || (int64_t)m > g || k < 1 || k > m || !std::isfinite(t))
+    if (inst < 0 || inst >= v.batch || m < 2 || m > 1024 || (int64_t)m > g || k < 1 || k > m || !std::isfinite(t))
         return ctx_fail(ctx, QHD_ERR_INVALID_ARG, "lowest_eigenpairs: bad instance, time, m or k");
     const size_t need = qhd_spectrum_workspace_bytes(ctx, m);
     if (!work_dev || ((uintptr_t)work_dev & 255) || work_bytes < need)

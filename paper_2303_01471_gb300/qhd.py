@@ -312,7 +312,7 @@ class QHD:
                                                    ctypes.c_void_p(out.data_ptr())), "qhd_apply_hamiltonian")
         return out
 
-    def lowest_eigenpairs(self, t: float, k: int, m: int = 64, inst: int = 0, seed: int = 1, vectors: bool = False):
+    def lowest_eigenpairs(self, t: float, k: int, m: int = 400, inst: int = 0, seed: int = 1, vectors: bool = False):
         """The k lowest eigenvalues of H(t) (Lanczos, m steps) with residuals and the
         probability spectrum |<n|psi>|^2 of the current state; returns numpy arrays
         (eigvals, residuals, overlaps) and, with vectors=True, a (k, *shape) tensor."""

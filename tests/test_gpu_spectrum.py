@@ -45,7 +45,7 @@ def test_lowest_eigenvalues_match_arpack():
     inst = workloads.gaussian_wells(22, (64, 64), K=8)
     t = 2.0
     sim = make_sim(inst.f)
-    ev, rs, ov = sim.lowest_eigenpairs(t, k=4, m=120)
+    ev, rs, ov = sim.lowest_eigenpairs(t, k=4, m=400)
     sim.close()
     a, b = oracle.schedule_ab(oracle.Schedule(), t)
     want = oracle.lowest_eigs(inst.f, a, b, 4)
@@ -62,7 +62,7 @@ def test_harmonic_oscillator_levels():
     a, b = 0.8, 1.7
     sched = qhd.Schedule(kind=qhd.SCHED_TABLE, ts=np.array([-1e9, 1e9]), phis=np.log([a, a]), chis=np.log([b, b]))
     sim = make_sim(f, lo=-L / 2, hi=L / 2, sched=sched)
-    ev, rs, _ = sim.lowest_eigenpairs(0.0, k=4, m=80)
+    ev, rs, _ = sim.lowest_eigenpairs(0.0, k=4, m=200)
     sim.close()
     want = np.sqrt(a * b) * om * (np.arange(4) + 0.5)
     assert np.allclose(ev, want, rtol=2e-5), (ev, want)
@@ -78,7 +78,7 @@ def test_paper_levy_semiclassical_ratio_on_gpu():
     f = 0.5 * om1 ** 2 * X1 ** 2 + 0.5 * om2 ** 2 * X2 ** 2
     sched = qhd.Schedule(kind=qhd.SCHED_TABLE, ts=np.array([-1e9, 1e9]), phis=np.zeros(2), chis=np.zeros(2))
     sim = make_sim(f, lo=-L / 2, hi=L / 2, sched=sched)
-    ev, rs, _ = sim.lowest_eigenpairs(0.0, k=2, m=100)
+    ev, rs, _ = sim.lowest_eigenpairs(0.0, k=2, m=400)
     sim.close()
     assert abs(ev[1] / ev[0] - gold["semiclassical_ratio"]) <= 0.5 * 10.0 ** -gold["printed_digits"] + 1e-5
 
@@ -90,7 +90,7 @@ def test_probability_spectrum_of_an_evolved_state():
     inst = workloads.gaussian_wells(23, (64, 64), K=8)
     sim = make_sim(inst.f)
     sim.evolve(5.0, 0.01)
-    ev, rs, ov, vecs = sim.lowest_eigenpairs(5.0, k=3, m=150, vectors=True)
+    ev, rs, ov, vecs = sim.lowest_eigenpairs(5.0, k=3, m=400, vectors=True)
     sim.close()
     assert 0.0 <= ov.sum() <= 1.0 + 1e-5
     psi_o = oracle.evolve(inst.f, oracle.uniform_state(inst.shape), 0.0, 0.01, 500, oracle.Schedule())
