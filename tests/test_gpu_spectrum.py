@@ -62,7 +62,7 @@ def test_harmonic_oscillator_levels():
     a, b = 0.8, 1.7
     sched = qhd.Schedule(kind=qhd.SCHED_TABLE, ts=np.array([-1e9, 1e9]), phis=np.log([a, a]), chis=np.log([b, b]))
     sim = make_sim(f, lo=-L / 2, hi=L / 2, sched=sched)
-    ev, rs, _ = sim.lowest_eigenpairs(0.0, k=4, m=200)
+    ev, rs, _ = sim.lowest_eigenpairs(0.0, k=4, m=100)
     sim.close()
     want = np.sqrt(a * b) * om * (np.arange(4) + 0.5)
     assert np.allclose(ev, want, rtol=2e-5), (ev, want)
