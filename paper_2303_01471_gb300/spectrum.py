@@ -1,0 +1,95 @@
+"""Energy ratio E1/E0(t) and probability spectrum along a QHD evolution (the
+quantities of the paper's section on the three phases of QHD), on one seeded
+Gaussian-well instance, with the semi-classical prediction
+(omega_1 + 3 omega_2) / (omega_1 + omega_2) of Eq. (semiclassical_ratio)
+from the Hessian of f at its minimiser.
+
+  python -m paper_2303_01471_gb300.spectrum --shape 128 128 --seed 0 \
+      --times 0.1 0.5 1 2 5 10 [--K 8] [--dt 0.01] [--m 400] [--k 4]
+
+Evolution, the Hamiltonian and Lanczos all run in libqhd.so's kernels; this
+module only orders the calls.  Prints one JSON object.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def wells_hessian_at_minimum(inst):
+    """Continuous minimiser of a Gaussian-well f (Newton from the mesh argmin) and
+    the eigenvalues of its Hessian there (closed-form derivatives)."""
+    c, w, D = inst.params["centres"], inst.params["widths"], inst.params["depths"]
+    d = len(inst.shape)
+
+    def grad_hess(x):
+        g = x - 0.5
+        H = np.eye(d)
+        for k in range(len(D)):
+            r = x - c[k]
+            e = D[k] * np.exp(-r @ r / (2 * w[k] ** 2))
+            g = g + e * r / w[k] ** 2
+            H = H + e * (np.eye(d) / w[k] ** 2 - np.outer(r, r) / w[k] ** 4)
+        return g, H
+
+    idx = np.unravel_index(int(np.argmin(inst.f)), inst.shape)
+    x = np.array([i / n for i, n in zip(idx, inst.shape)], dtype=np.float64)
+    for _ in range(50):
+        g, H = grad_hess(x)
+        step = np.linalg.solve(H, g)
+        x = x - step
+        if np.abs(step).max() < 1e-14:
+            break
+    return x, np.linalg.eigvalsh(grad_hess(x)[1])
+
+
+def energy_ratio_trajectory(shape, seed, times, K=8, dt=0.01, m=400, k=4):
+    import torch
+    import workloads
+    from paper_2303_01471_gb300 import qhd
+
+    inst = workloads.gaussian_wells(seed, shape, K=K)
+    sim = qhd.QHD(shape)
+    sim.set_potential(torch.from_numpy(inst.f).cuda())
+    sim.set_schedule(qhd.Schedule())
+    sim.reset_state()
+    rows, t = [], 0.0
+    for tt in sorted(times):
+        if tt > t:
+            sim.evolve(tt - t, dt)
+            t = tt
+        ev, rs, ov = sim.lowest_eigenpairs(t, k=k, m=m)
+        obs = sim.observables(0.1)[0]
+        rows.append({"t": t, "E": ev.tolist(), "E1_over_E0": float(ev[1] / ev[0]), "residuals": rs.tolist(),
+                     "prob_spectrum": ov.tolist(), "p_succ": obs.p_succ})
+    sim.close()
+    xs, lam = wells_hessian_at_minimum(inst)
+    om = np.sqrt(np.sort(lam)[::-1])   # omega_1 >= omega_2
+    pred = float((om[0] + 3 * om[1]) / (om[0] + om[1])) if len(om) > 1 else 3.0
+    return {"shape": list(shape), "seed": seed, "K": K, "dt": dt, "lanczos_steps": m, "minimiser": xs.tolist(),
+            "hessian_eigenvalues": lam.tolist(), "semiclassical_ratio": pred, "trajectory": rows}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--shape", type=int, nargs="+", default=[128, 128])
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--K", type=int, default=8)
+    ap.add_argument("--times", type=float, nargs="+", default=[0.1, 0.5, 1.0, 2.0, 5.0, 10.0])
+    ap.add_argument("--dt", type=float, default=0.01)
+    ap.add_argument("--m", type=int, default=400)
+    ap.add_argument("--k", type=int, default=4)
+    a = ap.parse_args(argv)
+    print(json.dumps(energy_ratio_trajectory(tuple(a.shape), a.seed, a.times, a.K, a.dt, a.m, a.k)))
+
+
+if __name__ == "__main__":
+    main()
