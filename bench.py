@@ -44,6 +44,9 @@ WORKLOAD = ("QHD at scale, complex64, T=10, dt=1e-3 (10^4 Strang steps each): "
 # algorithmic bytes per grid point per launch of each pass (psi read+write,
 # plus the 32-bit fixed-point potential in the pass that applies it)
 BYTES_PER_POINT = {"row": 20, "axis1_fwd": 16, "axis0": 16, "axis1_inv": 16, "plane": 20}
+# DRAM bytes (read + write) of one launch, from one ncu capture of the current
+# kernel (profiles/k_plane_pass_256cube_full.md); drop an entry when its kernel changes
+TRAFFIC_PER_LAUNCH = {("plane", "256x256x256"): 201498112 + 77571072}
 
 
 def peaks():
@@ -277,7 +280,8 @@ def run_ours(args, rank, world, local_rank, dist):
     roofline = {"bound": "hbm", "kernel": f"{dom['kernel']} pass, {dom['instance']}",
                 "achieved": dom["gbs"], "peak": peak, "unit": "GB/s",
                 "frac": round(dom["gbs"] / peak, 4), "peak_source": peak_src,
-                "traffic": None,
+                "traffic": TRAFFIC_PER_LAUNCH.get((dom["kernel"], dom["instance"])),
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch",
                 "algorithmic_bytes_per_launch": dom["bytes_per_launch"]}
 
     result = {
