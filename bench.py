@@ -315,6 +315,158 @@ def run_ours(args, rank, world, local_rank, dist):
     return result
 
 
+# ------------------------------------------------------------ Sim-QHD (box mesh)
+SIMQHD_WORKLOAD = ("Sim-QHD on 5-d box QPs: 256 seeded instances of 1/2 x^T Q x + b^T x on [0,1]^5 "
+                   "(Q symmetric, entries U[-1,1]; b U[-1,1]), finite-difference mesh r=8 (9^5 points), relaxed "
+                   "kinetic operator A' of the Hamming encoding, binomial (discrete Gaussian) psi0, "
+                   "e^phi=2/(1e-3+t^3), e^chi=2 sigma t^3 with sigma ~ U(0.5,2), T=10, dt=0.01 (1000 Strang steps), "
+                   "complex64")
+FP32_LANES_PER_SM, SM_COUNT = 128, 152
+
+
+def run_simqhd(args, rank, world, local_rank, dist):
+    """One bench step: set F from (Q, b) on the device, binomial psi0, 1000
+    Strang steps and the observables of every instance, all in one batched
+    context.  Roofline: the dominant pass against the FP32 FMA rate."""
+    import torch
+    from paper_2303_01471_gb300 import lattice, qhd
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    d, r, B = 5, 8, args.simqhd_count
+    T = args.profile_T if args.profile_T is not None else 10.0
+    dt = 0.01
+    nsteps = int(round(T / dt))
+    qps = [workloads.box_qp(100000 * rank + i, d) for i in range(B)]
+    Q = np.stack([q for q, _ in qps])
+    bvec = np.stack([b for _, b in qps])
+    sig = np.random.default_rng(7 + rank).uniform(0.5, 2.0, B)
+    lat = lattice.Lattice(d, r, lattice.RELAXED, batch=B, device=dev)
+    lat.set_schedule([qhd.Schedule(c_chi=2.0 * s) for s in sig])
+    G = lat.grid_points
+    pts_per_step = G * B * nsteps
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+
+    def one_step():
+        lat.set_qp(Q, bvec)
+        lat.reset_state(lattice.INIT_GROUND)
+        lat.evolve(T, dt)
+        return lat.observables(0.1, 0.01)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    lat.timing_read(reset=True)
+    lat.timing_enable(8)
+    launches0 = lat.launch_count()
+    step_ms = []
+    barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    with Clocks(local_rank) as clk:
+        for _ in range(args.steps):
+            flush.random_(0, 255)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            obs = one_step()
+            e1.record()
+            torch.cuda.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+    barrier()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    launches = lat.launch_count() - launches0
+    tm = lat.timing_read(reset=True)
+    lat.timing_enable(0)
+    ms_per_step = max_over_ranks(float(sum(step_ms)), dist, dev) / args.steps
+    value = whole_job_rate(pts_per_step, world, ms_per_step / 1e3)
+
+    # end to end through the public API: Q, b from the host, observables back
+    e2e_ms = []
+    for _ in range(args.steps):
+        flush.random_(0, 255)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        one_step()
+        torch.cuda.synchronize()
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_step = max_over_ranks(statistics.mean(e2e_ms), dist, dev)
+
+    # roofline: algorithmic FP32 flops of the dominant pass (a dense n-point complex
+    # matrix-vector product per line and axis: 8 n flops per point per axis)
+    n = r + 1
+    axes = {"pass0": 3, "pass1": 2}
+    kernels, best = [], None
+    for cls in ("pass0", "pass1"):
+        ms, cnt = tm[cls]
+        if cnt == 0:
+            continue
+        avg_s = ms / cnt / 1e3
+        flops = 8 * n * axes[cls] * G * B
+        row = {"kernel": cls, "axes": axes[cls], "timed_launches": cnt, "avg_us": round(avg_s * 1e6, 3),
+               "tflops": round(flops / avg_s / 1e12, 3), "gbs": round((20 if cls == "pass0" else 16) * G * B / avg_s / 1e9, 1),
+               "share_est": round(avg_s * nsteps / (ms_per_step / 1e3), 4)}
+        kernels.append(row)
+        if best is None or row["share_est"] > best["share_est"]:
+            best = row
+    clk_sum = clk.summary()
+    sm_mhz = clk_sum.get("sm_max_mhz") or 2070.0
+    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    roofline = {"bound": "alu", "kernel": f"{best['kernel']} (U along {best['axes']} axes)",
+                "achieved": best["tflops"], "peak": round(peak, 2), "unit": "TFLOP/s",
+                "frac": round(best["tflops"] / peak, 4),
+                "peak_source": f"derived: {SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flops x {sm_mhz:.0f} MHz",
+                "traffic": None, "algorithmic_flops_per_point_per_axis": 8 * n}
+    result = {
+        "metric": METRIC, "value": value, "unit": "grid-point Strang steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded box QPs)",
+        "instances_per_s": B * world / (ms_per_step / 1e3),
+        "config": {"workload": SIMQHD_WORKLOAD, "instances_per_rank": B, "parallelism": f"replicas x{world}",
+                   "l2": "psi + fixed-point F of 256 instances (181 MB) exceed L2; a 512 MiB write flushes L2 between timed steps"},
+        "e2e": {"value": whole_job_rate(pts_per_step, world, e2e_step / 1e3), "unit": "grid-point Strang steps/s",
+                "h2d_bytes_per_step": int(Q.nbytes + bvec.nbytes), "d2h_bytes_per_step": 64 * B,
+                "ms_per_step": e2e_step},
+        "gpu_launches": launches, "roofline": roofline, "kernels": kernels, "clocks": clk_sum,
+        "wall_s_timed_region": wall,
+        "observables_first": {"norm": obs[0].norm, "e_f": obs[0].e_f, "p_succ": obs[0].p_succ,
+                              "p_gap": obs[0].p_gap},
+    }
+    if args.profile_T is not None:
+        result["profiling_run"] = f"evolutions shortened to T={T}: not a bench value"
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        from oracle import lattice as OL
+        F = OL.qp_potential(Q[0], bvec[0], r)
+        psi = OL.initial_state(d, r, OL.LATTICE_RELAXED, OL.INIT_KINETIC_GROUND)
+        steps_done, t_used = 0, 0.0
+        while steps_done < nsteps and t_used < args.cpu_budget:
+            k = min(50, nsteps - steps_done)
+            t0 = time.perf_counter()
+            psi = OL.evolve(F, psi, r, OL.LATTICE_RELAXED, steps_done * dt, dt, k,
+                            oracle.Schedule(c_chi=2.0 * sig[0]))
+            t_used += time.perf_counter() - t0
+            steps_done += k
+        result["cpu_baseline"] = {"value": G * steps_done / t_used, "unit": "grid-point Strang steps/s",
+                                  "cores": 1, "kind": "oracle",
+                                  "sample": f"instance 0, {steps_done} of {nsteps} steps in {t_used:.1f}s (numpy FP64)"}
+        if steps_done == nsteps:
+            o = OL.observables(F, psi, r)
+            prob = torch.empty((B, *lat.shape), dtype=torch.float32, device=dev)
+            lat.observables(prob=prob)
+            result["parity_instance0"] = {"tv": float(0.5 * np.abs(prob[0].double().cpu().numpy() - o.prob).sum()),
+                                          "ef_rel": abs(obs[0].e_f - o.e_f) / max(abs(o.e_f), 1e-3 * np.ptp(F)),
+                                          "norm_drift": obs[0].norm - 1.0}
+    lat.close()
+    return result
+
+
 # ------------------------------------------------------------- ragged batch
 RAGGED_WORKLOAD = ("Batched QHD: 4096 instances, 2048 x 128^2 + 2048 x 256^2 on [0,1]^2, families alternating "
                    "Gaussian wells (K=8) / Rastrigin type, per-instance sigma ~ U(0.5,2) (e^chi = 2 sigma t^3), "
@@ -749,7 +901,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["scale", "ragged", "tcdft", "fno"], default="scale")
+    ap.add_argument("--workload", choices=["scale", "ragged", "tcdft", "fno", "simqhd"], default="scale")
+    ap.add_argument("--simqhd-count", type=int, default=256)
     ap.add_argument("--fno-train", type=int, default=50000)
     ap.add_argument("--fno-test", type=int, default=10000)
     ap.add_argument("--fno-epochs", type=int, default=10)
@@ -788,6 +941,8 @@ def main():
         res = run_tcdft(args, rank, world, local_rank, dist)
     elif args.workload == "fno":
         res = run_fno(args, rank, world, local_rank, dist)
+    elif args.workload == "simqhd":
+        res = run_simqhd(args, rank, world, local_rank, dist)
     else:
         res = run_ours(args, rank, world, local_rank, dist)
     if rank == 0 and res is not None:

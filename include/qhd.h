@@ -399,6 +399,92 @@ int64_t qhd_fno_launch_count(const qhd_fno *fno);
 const char *qhd_fno_last_error(const qhd_fno *fno);
 qhd_status qhd_fno_destroy(qhd_fno *fno);
 
+/*
+ * QHD on the finite-difference box mesh (the paper's section on implementing
+ * QHD on quantum Ising machines: Eq. (discretize-pde), Eq. (finite-qhd-discrete)
+ * and the relaxed form Eq. (relaxed-qhd-discrete) with Eq. (relaxed_adjacency);
+ * its classical simulation is the Sim-QHD solver of the QP benchmark).  The
+ * mesh has r cells per edge of [0,1]^d: points x_j = j / r, j = 0..r, so
+ * n = r + 1 per axis and G = n^d; arrays are row-major, last axis fastest.
+ *
+ *     H(t) = e^{phi_t} sum_k K_k + e^{chi_t} F,     K = -(r^2 / 2) A  (per axis)
+ *
+ * A is the chain adjacency (QHD_LATTICE_CHAIN: the central second difference
+ * with vanishing values beyond the mesh, its -2 diagonal dropped as a global
+ * phase as the paper does) or the relaxed A' with the entries
+ * sqrt((j+1)(r-j)/r), j = 0..r-1 (QHD_LATTICE_RELAXED: S_x / sqrt(r) on the
+ * Hamming-weight states of r qubits, the operator the Hamming encoding
+ * realises).  Time stepping: the Strang product formula with a = e^{phi},
+ * b = e^{chi} at the step midpoints.  The axis terms commute, so the kinetic
+ * factor exp(-i dt a sum_k K_k) is applied as the dense n x n matrix
+ * exp(-i dt a K) along every axis; the potential phase exp(-i theta F) uses the
+ * exact fixed-point turns of the Fourier-mesh path.  psi is complex64.
+ *
+ * Limits: ndim 1..6, r 1..16, batch >= 1, batch * G <= 2^31.  Device memory
+ * and the stream belong to the caller; ownership, asynchrony, error statuses
+ * and sticky CUDA failures follow the qhd_ctx conventions above.
+ *
+ * qhd_lattice_workspace_bytes: bytes of 256-byte aligned device workspace;
+ *   0 for sizes out of the limits.
+ * qhd_lattice_init: psi_dev caller-owned batch*G complex64 (8-byte aligned);
+ *   kind a qhd_lattice_kind; work_dev / work_bytes as sized above; stream a
+ *   cudaStream_t (0 = legacy default stream).
+ * qhd_lattice_set_potential: f_dev = batch*G FP64 on the device (copied);
+ *   non-finite values or a range >= 2^31 give QHD_ERR_INVALID_ARG.
+ *   Synchronises the stream.
+ * qhd_lattice_set_qp: F(x) = 1/2 x^T Q x + b^T x on the mesh
+ *   (Eq. (finite-quadratic-obj)), formed on the device in FP64 from host arrays
+ *   Q_host (batch*d*d, row-major per instance; only its symmetric part enters)
+ *   and b_host (batch*d).  Synchronises the stream.
+ * qhd_lattice_set_schedule: as qhd_set_schedule (batch schedules).
+ * qhd_lattice_reset_state: init = QHD_LATTICE_INIT_UNIFORM (G^{-1/2}) or
+ *   QHD_LATTICE_INIT_GROUND (the product over the axes of the ground state of
+ *   -A: the amplitudes sqrt(binom(r,j) / 2^r) for A', the Hamming encoding's
+ *   initial state; sqrt(2/(r+2)) sin(pi (j+1)/(r+2)) for the chain); t = 0.
+ * qhd_lattice_evolve: round(T/dt) Strang steps from the current time, same
+ *   rules as qhd_evolve (dt != 0, T/dt an integer within 1e-9, T and dt of
+ *   one sign); needs potential and schedule (else QHD_ERR_STATE).  Async.
+ * qhd_lattice_observables: out (host, batch): norm, E[f], p_succ (mass within
+ *   `radius`, Euclidean, of the mesh argmin x*, lowest flat index on ties),
+ *   p_gap (mass on points with f - min f <= gap); prob_dev (optional,
+ *   batch*G FP32) receives |psi|^2; marginals_host (optional, batch*d*n
+ *   doubles, [b][k][j]) the probabilities of the measurement elements
+ *   E^{(k)}_j of Eq. (Ekj).  FP64 accumulation in a fixed order.
+ *   Synchronises the stream.
+ * qhd_lattice_timing_enable / _read: as qhd_timing_* with the kernel classes
+ *   QHD_LKCLASS_* (every = 0 switches sampling off).
+ */
+typedef struct qhd_lattice qhd_lattice;
+typedef enum { QHD_LATTICE_CHAIN = 0, QHD_LATTICE_RELAXED = 1 } qhd_lattice_kind;
+typedef enum { QHD_LATTICE_INIT_UNIFORM = 0, QHD_LATTICE_INIT_GROUND = 1 } qhd_lattice_init_kind;
+enum {
+    QHD_LKCLASS_PREP = 0,  /* schedule, potential coefficients, axis propagators */
+    QHD_LKCLASS_PASS0 = 1, /* the pass with the potential phase (last axes)      */
+    QHD_LKCLASS_PASS1 = 2, /* the other passes                                   */
+    QHD_LKCLASS_COUNT = 3
+};
+typedef struct {
+    double t, norm, e_f, p_succ, p_gap;
+    double f_min;        /* min of F over the mesh                       */
+    int64_t argmin;      /* its flat index (lowest on ties)              */
+    int64_t steps_done;  /* steps since the last qhd_lattice_reset_state */
+} qhd_lattice_obs;
+size_t qhd_lattice_workspace_bytes(int ndim, int r, int64_t batch);
+qhd_status qhd_lattice_init(qhd_lattice **out, int ndim, int r, int kind, int64_t batch, void *psi_dev,
+                            void *work_dev, size_t work_bytes, void *stream);
+qhd_status qhd_lattice_set_potential(qhd_lattice *lat, const double *f_dev);
+qhd_status qhd_lattice_set_qp(qhd_lattice *lat, const double *Q_host, const double *b_host);
+qhd_status qhd_lattice_set_schedule(qhd_lattice *lat, const qhd_schedule *s);
+qhd_status qhd_lattice_reset_state(qhd_lattice *lat, int init);
+qhd_status qhd_lattice_evolve(qhd_lattice *lat, double T, double dt);
+qhd_status qhd_lattice_observables(qhd_lattice *lat, qhd_lattice_obs *out, float *prob_dev, double *marginals_host,
+                                   double radius, double gap);
+qhd_status qhd_lattice_timing_enable(qhd_lattice *lat, int every);
+qhd_status qhd_lattice_timing_read(qhd_lattice *lat, double *ms_out, int64_t *launches_out, int reset);
+int64_t qhd_lattice_launch_count(const qhd_lattice *lat);
+const char *qhd_lattice_last_error(const qhd_lattice *lat);
+qhd_status qhd_lattice_destroy(qhd_lattice *lat);
+
 /* Synchronise the stream and free the host-side context (never the caller's
  * buffers).  NULL is accepted. */
 qhd_status qhd_destroy(qhd_ctx *ctx);

@@ -13,6 +13,7 @@
 #include "qhd.h"
 #include "qhd_device.cuh"
 #include "qhd_kernels.h"
+#include "qhd_sched.cuh"
 #include "qhd_spectrum.h"
 #include "qhd_tcdft.h"
 
@@ -20,7 +21,7 @@ using namespace qhd;
 
 namespace {
 
-constexpr int MAX_TABLE_SAMPLES = 256;
+constexpr int MAX_TABLE_SAMPLES = SCHED_MAX_SAMPLES;
 constexpr size_t KT_BUDGET = size_t(64) << 20;  // bytes of kinetic tables per chunk
 constexpr int64_t MAX_CHUNK = 1024;
 constexpr int OBS_BLOCKS_MAX = 1024;
@@ -463,71 +464,17 @@ qhd_status qhd_set_schedule(qhd_ctx *c, const qhd_schedule *s) {
     if (st != QHD_OK) return st;
     if (!s) return fail(c, QHD_ERR_INVALID_ARG, "schedule is NULL");
     const int64_t B = c->batch;
-    std::vector<SchedDev> dev((size_t)B);
-    std::vector<double> samples((size_t)(3 * MAX_TABLE_SAMPLES * B), 0.0);
-    for (int64_t b = 0; b < B; ++b) {
-        const qhd_schedule &q = s[b];
-        SchedDev &d = dev[(size_t)b];
-        d.kind = q.kind;
-        d.ns = 0;
-        d.c_phi = q.c_phi;
-        d.eps = q.eps;
-        d.c_chi = q.c_chi;
-        d.t = d.phi = d.chi = nullptr;
-        d.power = 0.0;
-        if (q.kind == QHD_SCHED_NESTEROV || q.kind == QHD_SCHED_POWER) {
-            if (!std::isfinite(q.c_phi) || !(q.c_phi > 0) || !std::isfinite(q.eps) || q.eps < 0 ||
-                !std::isfinite(q.c_chi) || q.c_chi < 0)
-                return fail(c, QHD_ERR_INVALID_ARG, "instance %lld: bad Nesterov / power schedule", (long long)b);
-            if (q.kind == QHD_SCHED_POWER) {
-                if (!std::isfinite(q.power) || !(q.power >= 0.5 && q.power <= 8.0))
-                    return fail(c, QHD_ERR_INVALID_ARG, "instance %lld: power must be in [0.5, 8]", (long long)b);
-                d.power = q.power;
-            }
-        } else if (q.kind == QHD_SCHED_TABLE) {
-            if (!q.t || !q.phi || !q.chi || q.n_samples < 1 || q.n_samples > MAX_TABLE_SAMPLES)
-                return fail(c, QHD_ERR_INVALID_ARG, "instance %lld: bad table schedule", (long long)b);
-            for (int64_t i = 0; i < q.n_samples; ++i) {
-                if (!std::isfinite(q.t[i]) || !std::isfinite(q.phi[i]) || !std::isfinite(q.chi[i]))
-                    return fail(c, QHD_ERR_INVALID_ARG, "instance %lld: non-finite table sample", (long long)b);
-                if (i > 0 && !(q.t[i] > q.t[i - 1]))
-                    return fail(c, QHD_ERR_INVALID_ARG, "instance %lld: table times not increasing", (long long)b);
-            }
-            double *base = c->samples + (size_t)(3 * MAX_TABLE_SAMPLES * b);
-            d.ns = (int32_t)q.n_samples;
-            d.t = base;
-            d.phi = base + MAX_TABLE_SAMPLES;
-            d.chi = base + 2 * MAX_TABLE_SAMPLES;
-            double *hb = samples.data() + (size_t)(3 * MAX_TABLE_SAMPLES * b);
-            for (int64_t i = 0; i < q.n_samples; ++i) {
-                hb[i] = q.t[i];
-                hb[MAX_TABLE_SAMPLES + i] = q.phi[i];
-                hb[2 * MAX_TABLE_SAMPLES + i] = q.chi[i];
-            }
-        } else {
-            return fail(c, QHD_ERR_INVALID_ARG, "instance %lld: unknown schedule kind %d", (long long)b, q.kind);
-        }
-    }
+    std::vector<SchedDev> dev;
+    std::vector<double> samples;
+    bool shared = false;
+    const std::string why = convert_schedules(s, B, c->samples, dev, samples, &shared);
+    if (!why.empty()) return fail(c, QHD_ERR_INVALID_ARG, "%s", why.c_str());
     QHD_CUDA(c, cudaMemcpyAsync(c->samples, samples.data(), samples.size() * sizeof(double), cudaMemcpyHostToDevice,
                                 c->stream));
     QHD_CUDA(c, cudaMemcpyAsync(c->sched, dev.data(), dev.size() * sizeof(SchedDev), cudaMemcpyHostToDevice,
                                 c->stream));
     // the host vectors die on return: wait for the copies
     QHD_CUDA(c, cudaStreamSynchronize(c->stream));
-    // One kinetic table serves every instance when the kinetic weights e^{phi}
-    // agree (e.g. instances that differ only in the potential scale).
-    bool shared = true;
-    for (int64_t b = 1; b < B && shared; ++b) {
-        const qhd_schedule &p = s[0], &q = s[b];
-        if (p.kind != q.kind) shared = false;
-        else if (p.kind == QHD_SCHED_NESTEROV) shared = p.c_phi == q.c_phi && p.eps == q.eps;
-        else if (p.kind == QHD_SCHED_POWER)
-            shared = p.c_phi == q.c_phi && p.eps == q.eps && p.power == q.power;
-        else {
-            shared = p.n_samples == q.n_samples;
-            for (int64_t i = 0; shared && i < p.n_samples; ++i) shared = p.t[i] == q.t[i] && p.phi[i] == q.phi[i];
-        }
-    }
     c->kt_shared = shared;
     c->sched_host.assign((size_t)B, qhd_ctx::HostSched{});
     for (int64_t b = 0; b < B; ++b) {

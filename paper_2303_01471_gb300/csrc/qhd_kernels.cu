@@ -22,6 +22,7 @@
 // so the FP32 sine/cosine only ever sees a reduced argument.
 #include "qhd_device.cuh"
 #include "qhd_kernels.h"
+#include "qhd_sched.cuh"
 
 namespace qhd {
 
@@ -257,49 +258,6 @@ __global__ void __launch_bounds__(ROW_THREADS) k_oned(OneDArgs a) {
 // ------------------------------------------------------------- prep kernel
 // Schedule evaluation at the step midpoints, the merged potential coefficients
 // and the per-axis kinetic phase tables of one chunk of steps.
-
-__device__ double interp_dev(const double *ts, const double *vs, int ns, double t) {
-    if (t <= ts[0]) return vs[0];
-    if (t >= ts[ns - 1]) return vs[ns - 1];
-    int lo = 0, hi = ns - 1;
-    while (hi - lo > 1) {
-        int mid = (lo + hi) / 2;
-        if (ts[mid] <= t) lo = mid;
-        else hi = mid;
-    }
-    const double w = __ddiv_rn(__dsub_rn(t, ts[lo]), __dsub_rn(ts[hi], ts[lo]));
-    return __dadd_rn(vs[lo], __dmul_rn(w, __dsub_rn(vs[hi], vs[lo])));
-}
-
-// a = e^{phi}, b = e^{chi} at time t.
-__device__ void sched_eval_dev(const SchedDev &s, double t, double *a, double *b) {
-    if (s.kind == 0) {
-        const double t3 = __dmul_rn(__dmul_rn(t, t), t);
-        *a = __ddiv_rn(s.c_phi, __dadd_rn(s.eps, t3));
-        *b = __dmul_rn(s.c_chi, t3);
-    } else if (s.kind == 2) {
-        const double at = fabs(t);
-        *a = __ddiv_rn(s.c_phi, __dadd_rn(s.eps, pow(at, s.power + 1.0)));
-        *b = __dmul_rn(s.c_chi, pow(at, 2.0 * s.power - 1.0));
-    } else {
-        *a = exp(interp_dev(s.t, s.phi, s.ns, t));
-        *b = exp(interp_dev(s.t, s.chi, s.ns, t));
-    }
-}
-
-// frac(y) as a 64-bit fraction of one turn, rounded to 2^-64.
-__device__ uint64_t frac_to_u64(double y) {
-    const double f = y - floor(y);                  // exact
-    const double h = f * 4294967296.0;              // exact
-    double hf = floor(h);
-    double lf = rint((h - hf) * 4294967296.0);      // exact except the final rounding
-    if (lf >= 4294967296.0) {
-        lf = 0.0;
-        hf += 1.0;
-    }
-    uint32_t hi = hf >= 4294967296.0 ? 0u : (uint32_t)hf;
-    return ((uint64_t)hi << 32) | (uint64_t)(uint32_t)lf;
-}
 
 __global__ void k_prep(PrepArgs a) {
     const int64_t jl = blockIdx.x;  // local step 0..cnt (cnt is the extra potential entry)

@@ -32,7 +32,11 @@ EXPORTS = ["qhd_workspace_bytes", "qhd_init_grid", "qhd_set_potential", "qhd_set
            "qhd_library_call_count", "qhd_set_kinetic", "qhd_spectrum_workspace_bytes",
            "qhd_apply_hamiltonian", "qhd_lowest_eigenpairs", "qhd_fno_param_count", "qhd_fno_workspace_bytes", "qhd_fno_create",
            "qhd_fno_forward", "qhd_fno_loss_grad", "qhd_fno_adam_step", "qhd_fno_launch_count",
-           "qhd_fno_last_error", "qhd_fno_destroy"]
+           "qhd_fno_last_error", "qhd_fno_destroy", "qhd_lattice_workspace_bytes", "qhd_lattice_init",
+           "qhd_lattice_set_potential", "qhd_lattice_set_qp", "qhd_lattice_set_schedule",
+           "qhd_lattice_reset_state", "qhd_lattice_evolve", "qhd_lattice_observables",
+           "qhd_lattice_timing_enable", "qhd_lattice_timing_read", "qhd_lattice_launch_count",
+           "qhd_lattice_last_error", "qhd_lattice_destroy"]
 SPLIT_STRANG = 0
 SPLIT_LIE_TROTTER = 1
 KINETIC_SPECTRAL = 0
@@ -165,6 +169,34 @@ class Observables:
     steps_done: int
 
 
+def schedule_array(sched, batch: int):
+    """A ctypes array of `batch` qhd_schedule records from one Schedule (shared)
+    or a list of them, plus the numpy arrays its table pointers refer to (keep
+    them alive for the call)."""
+    scheds: List[Schedule] = list(sched) if isinstance(sched, (list, tuple)) else [sched] * batch
+    if len(scheds) != batch:
+        raise ValueError("one schedule per instance")
+    arr = (_Schedule * batch)()
+    keep = []
+    for i, s in enumerate(scheds):
+        arr[i].kind = s.kind
+        arr[i].c_phi = s.c_phi
+        arr[i].eps = s.eps
+        arr[i].c_chi = s.c_chi
+        arr[i].power = s.power
+        if s.kind == SCHED_TABLE:
+            t = np.ascontiguousarray(s.ts, dtype=np.float64)
+            p = np.ascontiguousarray(s.phis, dtype=np.float64)
+            c = np.ascontiguousarray(s.chis, dtype=np.float64)
+            keep += [t, p, c]
+            dp = ctypes.POINTER(ctypes.c_double)
+            arr[i].t = t.ctypes.data_as(dp)
+            arr[i].phi = p.ctypes.data_as(dp)
+            arr[i].chi = c.ctypes.data_as(dp)
+            arr[i].n_samples = len(t)
+    return arr, keep
+
+
 def workspace_bytes(shape: Sequence[int], batch: int = 1) -> int:
     lib = load()
     n = (ctypes.c_int64 * len(shape))(*shape)
@@ -242,27 +274,7 @@ class QHD:
                     "qhd_set_potential")
 
     def set_schedule(self, sched) -> None:
-        scheds: List[Schedule] = list(sched) if isinstance(sched, (list, tuple)) else [sched] * self.batch
-        if len(scheds) != self.batch:
-            raise ValueError("one schedule per instance")
-        arr = (_Schedule * self.batch)()
-        keep = []
-        for i, s in enumerate(scheds):
-            arr[i].kind = s.kind
-            arr[i].c_phi = s.c_phi
-            arr[i].eps = s.eps
-            arr[i].c_chi = s.c_chi
-            arr[i].power = s.power
-            if s.kind == SCHED_TABLE:
-                t = np.ascontiguousarray(s.ts, dtype=np.float64)
-                p = np.ascontiguousarray(s.phis, dtype=np.float64)
-                c = np.ascontiguousarray(s.chis, dtype=np.float64)
-                keep += [t, p, c]
-                dp = ctypes.POINTER(ctypes.c_double)
-                arr[i].t = t.ctypes.data_as(dp)
-                arr[i].phi = p.ctypes.data_as(dp)
-                arr[i].chi = c.ctypes.data_as(dp)
-                arr[i].n_samples = len(t)
+        arr, keep = schedule_array(sched, self.batch)
         self._check(self.lib.qhd_set_schedule(self.ctx, arr), "qhd_set_schedule")
 
     def reset_state(self) -> None:

@@ -73,3 +73,28 @@ def test_null_context_and_status_strings(lib):
     assert lib.qhd_launch_count(None) == 0
     for s in range(7):
         assert lib.qhd_status_string(s)
+
+
+def test_lattice_sizes_and_argument_checks_without_a_device(lib):
+    from paper_2303_01471_gb300 import lattice
+    lib = lattice._lib()
+    ws = lib.qhd_lattice_workspace_bytes(5, 8, 4)
+    assert ws > 4 * 9 ** 5 * 12
+    for bad in [(0, 8, 1), (7, 8, 1), (2, 0, 1), (2, 17, 1), (2, 8, 0), (6, 16, 1 << 10)]:
+        assert lib.qhd_lattice_workspace_bytes(*bad) == 0, bad
+    h = ctypes.c_void_p()
+    fake = ctypes.c_void_p(0x10000000)  # never dereferenced: checks fail first
+    assert lib.qhd_lattice_init(None, 2, 8, 1, 1, fake, fake, ws, None) == 1
+    assert lib.qhd_lattice_init(ctypes.byref(h), 2, 8, 2, 1, fake, fake, ws, None) == 1       # kind
+    assert lib.qhd_lattice_init(ctypes.byref(h), 2, 8, 1, 1, None, fake, ws, None) == 1
+    assert lib.qhd_lattice_init(ctypes.byref(h), 2, 8, 1, 1, ctypes.c_void_p(0x10000004), fake, ws, None) == 1
+    small = lib.qhd_lattice_workspace_bytes(2, 8, 1)
+    assert lib.qhd_lattice_init(ctypes.byref(h), 2, 8, 1, 1, fake, None, small, None) == 6
+    assert lib.qhd_lattice_init(ctypes.byref(h), 2, 8, 1, 1, fake, fake, small - 1, None) == 6
+    assert lib.qhd_lattice_init(ctypes.byref(h), 2, 8, 1, 1, fake, ctypes.c_void_p(0x10000010), small, None) == 6
+    assert not h.value
+    assert lib.qhd_lattice_evolve(None, 1.0, 0.1) == 1
+    assert lib.qhd_lattice_reset_state(None, 0) == 1
+    assert lib.qhd_lattice_destroy(None) == 0
+    assert lib.qhd_lattice_last_error(None) == b""
+    assert lib.qhd_lattice_launch_count(None) == 0

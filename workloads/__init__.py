@@ -190,3 +190,18 @@ def make(family: str, seed: int, shape, **kw) -> Instance:
     if family == "rastrigin":
         return rastrigin(seed, shape, **kw)
     raise ValueError(f"unknown family {family!r}")
+
+
+def box_qp(seed: int, d: int = 5):
+    """A seeded synthetic box-constrained QP, minimise 1/2 x^T Q x + b^T x over
+    [0,1]^d, standing in for the paper's QP benchmark instances (which are not
+    in this repository): Q symmetric with upper-triangle entries ~ U[-1, 1]
+    (indefinite in general, so the problem is non-convex), b ~ U[-1, 1]^d.
+    Draw order: the upper triangle of Q row by row, then b.  Returns (Q, b)."""
+    rng = np.random.default_rng(seed)
+    Q = np.zeros((d, d))
+    iu = np.triu_indices(d)
+    Q[iu] = rng.uniform(-1.0, 1.0, len(iu[0]))
+    Q = Q + np.triu(Q, 1).T
+    b = rng.uniform(-1.0, 1.0, d)
+    return Q, b
