@@ -20,9 +20,9 @@
 // inner indices, read as W-wide row segments).  The first pass applies the
 // merged potential phase on load; the last pass of an evolve call applies the
 // final half phase on store.  U is computed per step in FP64 from the host's
-// eigendecomposition of A (U = V diag(exp(i dt a r^2/2 lambda)) V^T) and
-// carried as FP32 hi + lo: the same rounded matrix would otherwise perturb the
-// norm coherently in step after step.
+// eigendecomposition of A (U = V diag(exp(i dt a r^2/2 lambda)) V^T).  The
+// state is fixed point (see below), which keeps the norm to ~1e-8 over 10^3
+// steps where FP32 storage drifts by several 1e-6 on concentrated states.
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -51,18 +51,66 @@ constexpr int OBS_BLOCKS_MAX = 1024;
 constexpr int MINMAX_BLOCKS_MAX = 512;
 
 // ------------------------------------------------------------------ kernels
+// The working state is fixed point: each amplitude component is an int32 in
+// units of 2^-30 (|psi| <= 1 by unitarity, so |component| < 2^31 with room to
+// spare).  A line transform forms every output as an exact int64 sum of
+// int32 x int32 products and rounds it once; the potential phase is an exact
+// int64 complex product rounded once.  Every stored value therefore carries one
+// rounding of at most 2^-31 absolute, independent of how concentrated the state
+// is, where FP32 storage carries 2^-24 relative on the few dominant amplitudes
+// of a concentrated state.
+constexpr int FX_SHIFT = 30;
+constexpr double FX_ONE = 1073741824.0;  // 2^30
+
+__device__ __forceinline__ int fx_round(long long v) {
+    return (int)((v + (1ll << (FX_SHIFT - 1))) >> FX_SHIFT);
+}
+
+// Potential phase table: T[k] = exp(-2 pi i k / PHASE_TAB) as Q1.30 (rounded
+// from FP64) and as FP32 (for the small correction term).
+struct LatPhase {
+    int2 fx;
+    float2 f;
+};
+
+// z * exp(-2 pi i u / 2^32) in fixed point.  u = 2^24 k + r as in the FP32
+// path: exp(-2 pi i u / 2^32) = T[k] (1 + eps), eps = exp(-i delta) - 1 with
+// delta = 2 pi r / 2^32, |delta| <= pi / 256, from its Taylor series.  T[k] eps
+// is below 0.0123 in modulus, so its FP32 value times 2^30 is below 2^24 and
+// converts with an error of about one unit; the factor is accurate to ~2^-30.
+__device__ __forceinline__ int2 fx_phase(int2 z, uint32_t u, const LatPhase *tab) {
+    const uint32_t k = ((u + (1u << 23)) >> 24) & (PHASE_TAB - 1);
+    const int32_t r = (int32_t)(u - (k << 24));
+    const float d = (float)r * 1.4629180792671596e-09f;  // 2 pi / 2^32
+    const float d2 = d * d;
+    const float cm1 = d2 * fmaf(d2, 1.0f / 24.0f, -0.5f);  // cos d - 1
+    const float sn = d * fmaf(d2, -1.0f / 6.0f, 1.0f);     // sin d
+    const LatPhase t = tab[k];
+    const float er = fmaf(t.f.x, cm1, t.f.y * sn), ei = fmaf(t.f.y, cm1, -t.f.x * sn);
+    const long long wr = t.fx.x + __float2int_rn(er * (float)FX_ONE);
+    const long long wi = t.fx.y + __float2int_rn(ei * (float)FX_ONE);
+    return make_int2(fx_round(z.x * wr - z.y * wi), fx_round(z.x * wi + z.y * wr));
+}
+
 struct LatPass {
-    float2 *psi;
+    int2 *psi;                 // Q1.30 state
     const uint32_t *fq;
     const uint64_t *pot_pre;   // [batch] phase coefficient applied on load, or null
     const uint64_t *pot_post;  // [batch] applied on store, or null
     uint32_t dither_pre, dither_post;
-    const float4 *U;           // this step's propagator [u_batch][n*n], U[i][m], (hi.re, hi.im, lo.re, lo.im)
+    const int2 *U;             // this step's propagator blocks [u_batch][M*M + H*H], Q1.30
     int64_t u_batch;
-    const float4 *ptab;
+    const LatPhase *ptab;
     int P, q, W, pitch, lines_per_col;
     int64_t col_count, col_stride, g_stride, row_stride, rows_per_inst, tiles_per_row;
+    uint64_t mg_P, mg_W, mg_lpc;   // reciprocals for division by P, W, lines_per_col
+    uint64_t mg_s[12];             // ... and by the group strides N^ax
 };
+
+// floor(l / d) for l < 2^16 and 1 <= d <= 2^13 from mg = floor(2^32 / d) + 1
+// (exact in that range: l * (mg - 2^32/d) / 2^32 < 2^-16 < 1/d).
+__host__ __device__ __forceinline__ uint64_t lat_magic(uint32_t d) { return (uint64_t(1) << 32) / d + 1; }
+__device__ __forceinline__ int lat_div(int l, uint64_t mg) { return (int)(((uint64_t)(uint32_t)l * mg) >> 32); }
 
 // Shared-memory index of group point g: even line lengths get one pad slot per
 // line so that threads walking lines of stride 1 hit distinct banks.
@@ -71,18 +119,30 @@ __device__ __forceinline__ int lat_idx(int g) {
     return (N & 1) ? g : g + g / N;
 }
 
+// Both per-axis operators commute with the reversal j -> n-1-j, and so does U.
+// With s_m = x_m + x_{n-1-m}, a_m = x_m - x_{n-1-m} (m < H = n/2; s_H = x_H for
+// odd n), y = U x is
+//     y_i = S_i + A_i,  y_{n-1-i} = S_i - A_i  (i < H),   y_H = S_H  (odd n),
+//     S = Ps s,  A = Pa a,   Ps_{im} = (U_{im} + U_{i,n-1-m}) / 2  (Ps_{iH} = U_{iH}),
+//     Pa_{im} = (U_{im} - U_{i,n-1-m}) / 2,
+// an M x M and an H x H block (M = n - H) instead of n x n: 41 products for
+// n = 9 rather than 81.  s and a are exact integer sums; each output is one
+// exact int64 sum rounded once.
 template <int N>
 __global__ void __launch_bounds__(PASS_THREADS_MAX) k_lat_pass(LatPass a) {
-    extern __shared__ __align__(16) float4 lsm[];
-    float4 *ptab = lsm;
-    float4 *U = lsm + PHASE_TAB;
-    float2 *tile = reinterpret_cast<float2 *>(U + N * N);
+    constexpr int H = N / 2, M = N - H;
+    extern __shared__ __align__(16) LatPhase lsm[];
+    LatPhase *ptab = lsm;
+    int2 *Ps = reinterpret_cast<int2 *>(lsm + PHASE_TAB);
+    int2 *Pa = Ps + M * M;
+    int2 *tile = Pa + H * H;
     const int64_t row = blockIdx.x / a.tiles_per_row;
     const int64_t c0 = (blockIdx.x - row * a.tiles_per_row) * a.W;
     const int64_t inst = row / a.rows_per_inst;
-    if (a.pot_pre || a.pot_post) load_phase_tab(ptab, a.ptab);
-    const float4 *Ug = a.U + (a.u_batch == 1 ? 0 : inst) * (N * N);
-    for (int i = threadIdx.x; i < N * N; i += blockDim.x) U[i] = __ldg(&Ug[i]);
+    if (a.pot_pre || a.pot_post)
+        for (int i = threadIdx.x; i < PHASE_TAB; i += blockDim.x) ptab[i] = a.ptab[i];
+    const int2 *Ug = a.U + (a.u_batch == 1 ? 0 : inst) * (M * M + H * H);
+    for (int i = threadIdx.x; i < M * M + H * H; i += blockDim.x) Ps[i] = __ldg(&Ug[i]);
     __syncthreads();
     const int P = a.P, W = a.W, pitch = a.pitch;
     const int64_t left = a.col_count - c0;
@@ -95,16 +155,16 @@ __global__ void __launch_bounds__(PASS_THREADS_MAX) k_lat_pass(LatPass a) {
         for (int l = threadIdx.x; l < tot; l += blockDim.x) {
             int g, col;
             if (contig) {
-                col = l / P;
+                col = lat_div(l, a.mg_P);
                 g = l - col * P;
             } else {
-                g = l / W;
+                g = lat_div(l, a.mg_W);
                 col = l - g * W;
             }
             if (col >= ncol) continue;
             const int64_t off = base + col * a.col_stride + (int64_t)g * a.g_stride;
-            float2 v = a.psi[off];
-            if (a.pot_pre) v = apply_phase_tab(v, turns_mul(c, __ldg(&a.fq[off])) + a.dither_pre, ptab);
+            int2 v = a.psi[off];
+            if (a.pot_pre) v = fx_phase(v, turns_mul(c, __ldg(&a.fq[off])) + a.dither_pre, ptab);
             tile[col * pitch + lat_idx<N>(g)] = v;
         }
     }
@@ -113,33 +173,51 @@ __global__ void __launch_bounds__(PASS_THREADS_MAX) k_lat_pass(LatPass a) {
     const int lines = lpc * W;
     int s = 1;  // stride of the current axis inside the group (last axis first)
     for (int ax = 0; ax < a.q; ++ax, s *= N) {
+        const uint64_t mg_s = a.mg_s[ax];
         for (int l = threadIdx.x; l < lines; l += blockDim.x) {
-            const int col = l / lpc;
+            const int col = lat_div(l, a.mg_lpc);
             const int h = l - col * lpc;
             if (col >= ncol) continue;
-            const int hs = h / s;
+            const int hs = lat_div(h, mg_s);
             const int g0 = hs * (s * N) + (h - hs * s);
-            float2 *cb = tile + col * pitch;
-            float2 x[N];
+            int2 *cb = tile + col * pitch;
+            int2 x[N];
 #pragma unroll
             for (int m = 0; m < N; ++m) x[m] = cb[lat_idx<N>(g0 + m * s)];
-            float2 y[N];
+            int2 sv[M], av[H];
 #pragma unroll
-            for (int i = 0; i < N; ++i) {
-                float hr = 0.f, hi = 0.f, lr = 0.f, li = 0.f;
+            for (int m = 0; m < H; ++m) {
+                sv[m] = make_int2(x[m].x + x[N - 1 - m].x, x[m].y + x[N - 1 - m].y);
+                av[m] = make_int2(x[m].x - x[N - 1 - m].x, x[m].y - x[N - 1 - m].y);
+            }
+            if (N & 1) sv[M - 1] = x[H];
+            int2 y[N];
 #pragma unroll
-                for (int m = 0; m < N; ++m) {
-                    const float4 u = U[i * N + m];
-                    hr = fmaf(u.x, x[m].x, hr);
-                    hr = fmaf(-u.y, x[m].y, hr);
-                    hi = fmaf(u.x, x[m].y, hi);
-                    hi = fmaf(u.y, x[m].x, hi);
-                    lr = fmaf(u.z, x[m].x, lr);
-                    lr = fmaf(-u.w, x[m].y, lr);
-                    li = fmaf(u.z, x[m].y, li);
-                    li = fmaf(u.w, x[m].x, li);
+            for (int i = 0; i < M; ++i) {
+                long long sr = 0, si = 0;
+#pragma unroll
+                for (int m = 0; m < M; ++m) {
+                    const int2 u = Ps[i * M + m];
+                    sr += (long long)u.x * sv[m].x;
+                    sr -= (long long)u.y * sv[m].y;
+                    si += (long long)u.x * sv[m].y;
+                    si += (long long)u.y * sv[m].x;
                 }
-                y[i] = make_float2(hr + lr, hi + li);
+                if (i < H) {
+                    long long ar = 0, ai = 0;
+#pragma unroll
+                    for (int m = 0; m < H; ++m) {
+                        const int2 u = Pa[i * H + m];
+                        ar += (long long)u.x * av[m].x;
+                        ar -= (long long)u.y * av[m].y;
+                        ai += (long long)u.x * av[m].y;
+                        ai += (long long)u.y * av[m].x;
+                    }
+                    y[i] = make_int2(fx_round(sr + ar), fx_round(si + ai));
+                    y[N - 1 - i] = make_int2(fx_round(sr - ar), fx_round(si - ai));
+                } else {
+                    y[i] = make_int2(fx_round(sr), fx_round(si));
+                }
             }
 #pragma unroll
             for (int m = 0; m < N; ++m) cb[lat_idx<N>(g0 + m * s)] = y[m];
@@ -151,16 +229,16 @@ __global__ void __launch_bounds__(PASS_THREADS_MAX) k_lat_pass(LatPass a) {
         for (int l = threadIdx.x; l < tot; l += blockDim.x) {
             int g, col;
             if (contig) {
-                col = l / P;
+                col = lat_div(l, a.mg_P);
                 g = l - col * P;
             } else {
-                g = l / W;
+                g = lat_div(l, a.mg_W);
                 col = l - g * W;
             }
             if (col >= ncol) continue;
             const int64_t off = base + col * a.col_stride + (int64_t)g * a.g_stride;
-            float2 v = tile[col * pitch + lat_idx<N>(g)];
-            if (a.pot_post) v = apply_phase_tab(v, turns_mul(c, __ldg(&a.fq[off])) + a.dither_post, ptab);
+            int2 v = tile[col * pitch + lat_idx<N>(g)];
+            if (a.pot_post) v = fx_phase(v, turns_mul(c, __ldg(&a.fq[off])) + a.dither_post, ptab);
             a.psi[off] = v;
         }
     }
@@ -170,14 +248,23 @@ struct LatPrep {
     const SchedDev *sched;
     const InstDev *inst;
     uint64_t *pot;       // [cnt+1][batch]
-    float4 *U;           // [cnt][u_batch][n*n]
+    int2 *U;             // [cnt][u_batch][n*n]
     const double *V;     // eigenvectors of A, V[i*n + k] = component i of vector k
     const double *lam;   // eigenvalues of A
     double kin_scale;    // r^2 / 2
     double t_start, dt;
     int64_t j0, cnt, nsteps, batch, u_batch;
+    uint64_t step_base;  // global index of the chunk's first step (rounding dither)
     int n;
 };
+
+// Unbiased rounding of U to Q1.30: floor(U 2^30 + v) with v uniform in [0,1)
+// from a counter hash of (step, entry), so that the rounding error of a matrix
+// that changes little from step to step does not repeat coherently.
+__device__ __forceinline__ int fx_dither_round(double v, uint64_t key) {
+    const uint32_t h = step_dither(key);
+    return (int)floor(v * FX_ONE + (double)h * 2.3283064365386963e-10);
+}
 
 __global__ void k_lat_prep(LatPrep a) {
     const int64_t jl = blockIdx.x;  // local step 0..cnt (cnt: the final half phase)
@@ -211,7 +298,7 @@ __global__ void k_lat_prep(LatPrep a) {
         sincos(ph, &s_s[threadIdx.x], &s_c[threadIdx.x]);
     }
     __syncthreads();
-    float4 *out = a.U + (jl * a.u_batch + b) * (int64_t)(n * n);
+    __shared__ double s_ur[LAT_MAX_N * LAT_MAX_N], s_ui[LAT_MAX_N * LAT_MAX_N];
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
         const int i = e / n, m = e - (e / n) * n;
         double re = 0.0, im = 0.0;
@@ -220,9 +307,38 @@ __global__ void k_lat_prep(LatPrep a) {
             re = __dadd_rn(re, __dmul_rn(w, s_c[k]));
             im = __dadd_rn(im, __dmul_rn(w, s_s[k]));
         }
-        const float hr = (float)re, hi = (float)im;
-        out[e] = make_float4(hr, hi, (float)(re - (double)hr), (float)(im - (double)hi));
+        s_ur[e] = re;
+        s_ui[e] = im;
     }
+    __syncthreads();
+    // reversal-symmetric blocks Ps (M x M) and Pa (H x H) of U, see k_lat_pass
+    const int H = n / 2, M = n - H;
+    int2 *out = a.U + (jl * a.u_batch + b) * (int64_t)(M * M + H * H);
+    const uint64_t key0 = ((a.step_base + (uint64_t)jl) * 0x100000001B3ull) ^ ((uint64_t)b * 0x9E3779B97F4A7C15ull);
+    for (int e = threadIdx.x; e < M * M + H * H; e += blockDim.x) {
+        double re, im;
+        if (e < M * M) {
+            const int i = e / M, m = e - (e / M) * M;
+            if (m == H) {  // odd n: the middle column
+                re = s_ur[i * n + H];
+                im = s_ui[i * n + H];
+            } else {
+                re = 0.5 * (s_ur[i * n + m] + s_ur[i * n + n - 1 - m]);
+                im = 0.5 * (s_ui[i * n + m] + s_ui[i * n + n - 1 - m]);
+            }
+        } else {
+            const int e2 = e - M * M, i = e2 / H, m = e2 - (e2 / H) * H;
+            re = 0.5 * (s_ur[i * n + m] - s_ur[i * n + n - 1 - m]);
+            im = 0.5 * (s_ui[i * n + m] - s_ui[i * n + n - 1 - m]);
+        }
+        out[e] = make_int2(fx_dither_round(re, key0 + 2 * e), fx_dither_round(im, key0 + 2 * e + 1));
+    }
+}
+
+// |psi|^2 of a Q1.30 amplitude in FP64.
+__device__ __forceinline__ double fx_prob(int2 z) {
+    const double x = (double)z.x / FX_ONE, y = (double)z.y / FX_ONE;
+    return __dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y));
 }
 
 // Multi-index digit k (axis k, row-major, n per axis) of flat index i.
@@ -231,7 +347,7 @@ __device__ __forceinline__ int lat_digit(int64_t i, int k, int d, int n) {
     return (int)(i % n);
 }
 
-__global__ void k_lat_ground(float2 *psi, const double *v, int n, int d, int64_t g, int64_t total) {
+__global__ void k_lat_ground(int2 *psi, const double *v, int n, int d, int64_t g, int64_t total) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += (int64_t)gridDim.x * blockDim.x) {
         int64_t rem = i % g;
@@ -240,7 +356,34 @@ __global__ void k_lat_ground(float2 *psi, const double *v, int n, int d, int64_t
             amp *= v[rem % n];
             rem /= n;
         }
-        psi[i] = make_float2((float)amp, 0.0f);
+        psi[i] = make_int2(__double2int_rn(amp * FX_ONE), 0);
+    }
+}
+
+__global__ void k_lat_fill(int2 *psi, int value, int64_t total) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x)
+        psi[i] = make_int2(value, 0);
+}
+
+// complex64 <-> Q1.30.  Loading flags components of modulus >= 2 (or not
+// finite), which the format cannot hold, and leaves them zero.
+__global__ void k_lat_from_c64(int2 *psi, const float2 *in, int64_t total, int *bad) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 z = in[i];
+        const bool ok = fabsf(z.x) < 2.0f && fabsf(z.y) < 2.0f;  // false for NaN too
+        if (!ok) atomicOr(bad, 1);
+        psi[i] = ok ? make_int2(__double2int_rn((double)z.x * FX_ONE), __double2int_rn((double)z.y * FX_ONE))
+                    : make_int2(0, 0);
+    }
+}
+
+__global__ void k_lat_to_c64(float2 *out, const int2 *psi, int64_t total) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int2 z = psi[i];
+        out[i] = make_float2((float)((double)z.x / FX_ONE), (float)((double)z.y / FX_ONE));
     }
 }
 
@@ -269,7 +412,7 @@ __global__ void k_lat_qp(double *f, const double *Q, const double *bv, int n, in
 }
 
 struct LatObs {
-    const float2 *psi;
+    const int2 *psi;
     const double *f64;
     const double *fmin;   // [batch]
     const double *xs;     // [batch][LAT_MAX_D] mesh minimiser
@@ -295,15 +438,15 @@ __device__ double lat_block_sum(double v, double *sh) {
 
 __global__ void k_lat_obs_partial(LatObs a) {
     const int64_t b = blockIdx.y;
-    const float2 *psi = a.psi + b * a.g;
+    const int2 *psi = a.psi + b * a.g;
     const double *f = a.f64 + b * a.g;
     const double fmin = a.fmin[b];
     const double *xs = a.xs + b * LAT_MAX_D;
     double sn = 0.0, sf = 0.0, sp = 0.0, sg = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.g;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const float2 z = psi[i];
-        const double p = __dadd_rn(__dmul_rn((double)z.x, (double)z.x), __dmul_rn((double)z.y, (double)z.y));
+        const int2 z = psi[i];
+        const double p = fx_prob(z);
         if (a.prob) a.prob[b * a.g + i] = (float)p;
         sn += p;
         sf += p * f[i];
@@ -350,18 +493,17 @@ __global__ void k_lat_obs_final(const double *partial, double *result, int nblk)
 
 // Marginal of axis k at mesh index j: the sum of |psi|^2 over the points whose
 // k-th index is j (one block per (k, j) and instance, fixed summation order).
-__global__ void k_lat_marginal(const float2 *psi, double *out, int64_t g, int d, int n) {
+__global__ void k_lat_marginal(const int2 *psi, double *out, int64_t g, int d, int n) {
     const int kj = blockIdx.x, k = kj / n, j = kj - (kj / n) * n;
     const int64_t b = blockIdx.y;
     int64_t inner = 1;
     for (int a = d - 1; a > k; --a) inner *= n;
     const int64_t cnt = g / n;
-    const float2 *pb = psi + b * g;
+    const int2 *pb = psi + b * g;
     double s = 0.0;
     for (int64_t idx = threadIdx.x; idx < cnt; idx += blockDim.x) {
         const int64_t hi = idx / inner, lo = idx - hi * inner;
-        const float2 z = pb[(hi * n + j) * inner + lo];
-        s += __dadd_rn(__dmul_rn((double)z.x, (double)z.x), __dmul_rn((double)z.y, (double)z.y));
+        s += fx_prob(pb[(hi * n + j) * inner + lo]);
     }
     __shared__ double sh[32];
     s = lat_block_sum(s, sh);
@@ -472,7 +614,8 @@ std::vector<PassPlan> plan_passes(int d, int n, int64_t batch) {
         p.threads = (int)th;
         p.tiles_per_row = (p.col_count + W - 1) / W;
         p.blocks = p.rows * p.tiles_per_row;
-        p.smem = sizeof(float4) * (size_t)(PHASE_TAB + n * n) + sizeof(float2) * (size_t)(p.W * p.pitch);
+        const int hh = n / 2, mm = n - hh;
+        p.smem = sizeof(LatPhase) * PHASE_TAB + sizeof(int2) * (size_t)(mm * mm + hh * hh + p.W * p.pitch);
         out.push_back(p);
         a1 = a0;
     }
@@ -525,8 +668,8 @@ void jacobi_eig(int n, std::vector<double> A, std::vector<double> &V, std::vecto
 }
 
 struct LatLayout {
-    size_t f64, fq, sched, samples, inst, xs, fmin, mm, ptab, V, lam, ground, Q, bq, U, pot, obs_part, obs_res, marg,
-        total;
+    size_t f64, fq, sched, samples, inst, xs, fmin, mm, ptab, flag, V, lam, ground, Q, bq, U, pot, obs_part, obs_res,
+        marg, total;
     int64_t chunk, chunk_shared;
     int obs_blocks, mm_blocks;
 };
@@ -550,7 +693,7 @@ LatLayout lat_layout(int d, int r, int64_t batch) {
     };
     L.obs_blocks = blocks_for(G, OBS_BLOCKS_MAX);
     L.mm_blocks = blocks_for(G, MINMAX_BLOCKS_MAX);
-    const size_t ubytes = sizeof(float4) * (size_t)(n * n);
+    const size_t ubytes = sizeof(int2) * (size_t)((n - n / 2) * (n - n / 2) + (n / 2) * (n / 2));
     int64_t ch = (int64_t)(U_BUDGET / (ubytes * (size_t)batch));
     L.chunk = ch < 1 ? 1 : ch > LAT_MAX_CHUNK ? LAT_MAX_CHUNK : ch;
     ch = (int64_t)(U_BUDGET / ubytes);
@@ -563,7 +706,8 @@ LatLayout lat_layout(int d, int r, int64_t batch) {
     L.xs = take(sizeof(double) * LAT_MAX_D * (size_t)batch);
     L.fmin = take(sizeof(double) * (size_t)batch);
     L.mm = take(sizeof(MinMaxPart) * (size_t)(L.mm_blocks * batch));
-    L.ptab = take(sizeof(float4) * PHASE_TAB);
+    L.ptab = take(sizeof(LatPhase) * PHASE_TAB);
+    L.flag = take(sizeof(int));
     L.V = take(sizeof(double) * (size_t)(n * n));
     L.lam = take(sizeof(double) * (size_t)n);
     L.ground = take(sizeof(double) * (size_t)n);
@@ -585,7 +729,7 @@ LatLayout lat_layout(int d, int r, int64_t batch) {
 struct qhd_lattice {
     int d = 0, r = 0, n = 0, kind = 0;
     int64_t batch = 1, g = 1;
-    float2 *psi = nullptr;
+    int2 *psi = nullptr;  // Q1.30 state (the caller's buffer)
     char *work = nullptr;
     size_t work_bytes = 0;
     cudaStream_t stream = nullptr;
@@ -599,7 +743,9 @@ struct qhd_lattice {
     double *samples = nullptr;
     InstDev *inst = nullptr;
     MinMaxPart *mm = nullptr;
-    float4 *ptab = nullptr, *U = nullptr;
+    LatPhase *ptab = nullptr;
+    int2 *U = nullptr;
+    int *flag = nullptr;
     uint64_t *pot = nullptr;
     // host state
     bool have_f = false, have_sched = false, u_shared = false;
@@ -783,7 +929,7 @@ qhd_status qhd_lattice_init(qhd_lattice **out, int ndim, int r, int kind, int64_
     c->kind = kind;
     c->batch = batch;
     c->g = ipow(c->n, ndim);
-    c->psi = (float2 *)psi_dev;
+    c->psi = (int2 *)psi_dev;
     c->work = (char *)work_dev;
     c->work_bytes = work_bytes;
     c->stream = (cudaStream_t)stream;
@@ -797,13 +943,14 @@ qhd_status qhd_lattice_init(qhd_lattice **out, int ndim, int r, int kind, int64_
     c->xs = (double *)(c->work + L.xs);
     c->fmin = (double *)(c->work + L.fmin);
     c->mm = (MinMaxPart *)(c->work + L.mm);
-    c->ptab = (float4 *)(c->work + L.ptab);
+    c->ptab = (LatPhase *)(c->work + L.ptab);
+    c->flag = (int *)(c->work + L.flag);
     c->V = (double *)(c->work + L.V);
     c->lam = (double *)(c->work + L.lam);
     c->ground = (double *)(c->work + L.ground);
     c->Q = (double *)(c->work + L.Q);
     c->bq = (double *)(c->work + L.bq);
-    c->U = (float4 *)(c->work + L.U);
+    c->U = (int2 *)(c->work + L.U);
     c->pot = (uint64_t *)(c->work + L.pot);
     c->obs_part = (double *)(c->work + L.obs_part);
     c->obs_res = (double *)(c->work + L.obs_res);
@@ -825,12 +972,12 @@ qhd_status qhd_lattice_init(qhd_lattice **out, int ndim, int r, int kind, int64_
     double sum = 0.0;
     for (int i = 0; i < n; ++i) sum += V[(size_t)(i * n + top)];
     for (int i = 0; i < n; ++i) ground[(size_t)i] = (sum < 0 ? -1.0 : 1.0) * V[(size_t)(i * n + top)];
-    std::vector<float4> ptab((size_t)PHASE_TAB);
+    std::vector<LatPhase> ptab((size_t)PHASE_TAB);
     for (int k = 0; k < PHASE_TAB; ++k) {
         const double ang = -2.0 * 3.141592653589793238462643383279502884 * (double)k / PHASE_TAB;
         const double cr = std::cos(ang), ci = std::sin(ang);
-        const float hr = (float)cr, hi = (float)ci;
-        ptab[(size_t)k] = make_float4(hr, hi, (float)(cr - (double)hr), (float)(ci - (double)hi));
+        ptab[(size_t)k].fx = make_int2((int)std::nearbyint(cr * FX_ONE), (int)std::nearbyint(ci * FX_ONE));
+        ptab[(size_t)k].f = make_float2((float)cr, (float)ci);
     }
     cudaError_t e = cudaMemcpyAsync(c->V, V.data(), V.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess)
@@ -839,7 +986,7 @@ qhd_status qhd_lattice_init(qhd_lattice **out, int ndim, int r, int kind, int64_
         e = cudaMemcpyAsync(c->ground, ground.data(), ground.size() * sizeof(double), cudaMemcpyHostToDevice,
                             c->stream);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(c->ptab, ptab.data(), ptab.size() * sizeof(float4), cudaMemcpyHostToDevice, c->stream);
+        e = cudaMemcpyAsync(c->ptab, ptab.data(), ptab.size() * sizeof(LatPhase), cudaMemcpyHostToDevice, c->stream);
     size_t smax = 0;
     for (auto &p : c->passes) smax = p.smem > smax ? p.smem : smax;
     if (e == cudaSuccess && smax > 48 * 1024) e = pass_smem_attr(n, smax);
@@ -903,7 +1050,8 @@ qhd_status qhd_lattice_reset_state(qhd_lattice *c, int init) {
     if (s != QHD_OK) return s;
     const int64_t total = c->g * c->batch;
     if (init == QHD_LATTICE_INIT_UNIFORM) {
-        LAT_LAUNCH(c, launch_uniform(c->psi, total, (float)(1.0 / std::sqrt((double)c->g)), c->stream));
+        const int v = (int)std::nearbyint(FX_ONE / std::sqrt((double)c->g));
+        LAT_LAUNCH(c, (k_lat_fill<<<grid_blocks(total), 256, 0, c->stream>>>(c->psi, v, total), cudaGetLastError()));
     } else if (init == QHD_LATTICE_INIT_GROUND) {
         LAT_LAUNCH(c, (k_lat_ground<<<grid_blocks(total), 256, 0, c->stream>>>(c->psi, c->ground, c->n, c->d, c->g,
                                                                                 total),
@@ -951,6 +1099,7 @@ qhd_status qhd_lattice_evolve(qhd_lattice *c, double T, double dt) {
         const bool last_chunk = j0 + cnt == nsteps;
         pa.j0 = j0;
         pa.cnt = cnt;
+        pa.step_base = (uint64_t)(c->steps_done + j0);
         {
             LatTimed tm(c, QHD_LKCLASS_PREP, true);
             LAT_LAUNCH(c, (k_lat_prep<<<dim3((unsigned)(cnt + 1), (unsigned)B), 64, 0, c->stream>>>(pa),
@@ -968,7 +1117,7 @@ qhd_status qhd_lattice_evolve(qhd_lattice *c, double T, double dt) {
                 a.pot_post = (p == np - 1 && last_chunk && jl == cnt - 1) ? c->pot + cnt * B : nullptr;
                 a.dither_pre = step_dither((uint64_t)jg);
                 a.dither_post = step_dither((uint64_t)jg + 1);
-                a.U = c->U + jl * ub * (int64_t)(n * n);
+                a.U = c->U + jl * ub * (int64_t)((n - n / 2) * (n - n / 2) + (n / 2) * (n / 2));
                 a.u_batch = ub;
                 a.ptab = c->ptab;
                 a.P = pl.P;
@@ -982,6 +1131,10 @@ qhd_status qhd_lattice_evolve(qhd_lattice *c, double T, double dt) {
                 a.row_stride = pl.row_stride;
                 a.rows_per_inst = pl.rows_per_inst;
                 a.tiles_per_row = pl.tiles_per_row;
+                a.mg_P = lat_magic((uint32_t)pl.P);
+                a.mg_W = lat_magic((uint32_t)pl.W);
+                a.mg_lpc = lat_magic((uint32_t)(pl.P / n));
+                for (int k = 0, sk = 1; k < pl.q; ++k, sk *= n) a.mg_s[k] = lat_magic((uint32_t)sk);
                 LatTimed tm(c, p == 0 ? QHD_LKCLASS_PASS0 : QHD_LKCLASS_PASS1, sample);
                 LAT_LAUNCH(c, launch_pass(n, a, pl.blocks, pl.threads, pl.smem, c->stream));
             }
@@ -1041,6 +1194,32 @@ qhd_status qhd_lattice_observables(qhd_lattice *c, qhd_lattice_obs *out, float *
         o.argmin = c->argmin_host[(size_t)b];
         o.steps_done = c->steps_done;
     }
+    return QHD_OK;
+}
+
+qhd_status qhd_lattice_get_state(qhd_lattice *c, void *out_dev) {
+    qhd_status s = lcheck(c);
+    if (s != QHD_OK) return s;
+    if (!out_dev || ((uintptr_t)out_dev & 7)) return lfail(c, QHD_ERR_INVALID_ARG, "out_dev NULL or misaligned");
+    const int64_t total = c->g * c->batch;
+    LAT_LAUNCH(c, (k_lat_to_c64<<<grid_blocks(total), 256, 0, c->stream>>>((float2 *)out_dev, c->psi, total),
+                   cudaGetLastError()));
+    return QHD_OK;
+}
+
+qhd_status qhd_lattice_set_state(qhd_lattice *c, const void *in_dev) {
+    qhd_status s = lcheck(c);
+    if (s != QHD_OK) return s;
+    if (!in_dev || ((uintptr_t)in_dev & 7)) return lfail(c, QHD_ERR_INVALID_ARG, "in_dev NULL or misaligned");
+    const int64_t total = c->g * c->batch;
+    LAT_CUDA(c, cudaMemsetAsync(c->flag, 0, sizeof(int), c->stream));
+    LAT_LAUNCH(c, (k_lat_from_c64<<<grid_blocks(total), 256, 0, c->stream>>>(c->psi, (const float2 *)in_dev, total,
+                                                                            c->flag),
+                   cudaGetLastError()));
+    int bad = 0;
+    LAT_CUDA(c, cudaMemcpyAsync(&bad, c->flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    LAT_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (bad) return lfail(c, QHD_ERR_INVALID_ARG, "state component not finite or of modulus >= 2 (set to 0)");
     return QHD_OK;
 }
 

@@ -64,6 +64,10 @@ def _lib():
     lib.qhd_lattice_set_schedule.restype = st
     lib.qhd_lattice_reset_state.argtypes = [vp, ctypes.c_int]
     lib.qhd_lattice_reset_state.restype = st
+    lib.qhd_lattice_get_state.argtypes = [vp, vp]
+    lib.qhd_lattice_get_state.restype = st
+    lib.qhd_lattice_set_state.argtypes = [vp, vp]
+    lib.qhd_lattice_set_state.restype = st
     lib.qhd_lattice_evolve.argtypes = [vp, ctypes.c_double, ctypes.c_double]
     lib.qhd_lattice_evolve.restype = st
     lib.qhd_lattice_observables.argtypes = [vp, ctypes.POINTER(_LatObs), vp, dp, ctypes.c_double, ctypes.c_double]
@@ -88,8 +92,9 @@ def workspace_bytes(ndim: int, r: int, batch: int = 1) -> int:
 
 class Lattice:
     """`batch` instances of QHD on the mesh {0, 1/r, ..., 1}^ndim with the chain
-    (CHAIN) or relaxed (RELAXED) kinetic operator.  psi: torch complex64 of
-    shape (batch, r+1, ..., r+1), owned here and borrowed by the library."""
+    (CHAIN) or relaxed (RELAXED) kinetic operator.  The working state `psi_fx`
+    (torch int32, shape (batch, r+1, ..., r+1, 2): re, im in units of 2^-30) is
+    owned here and borrowed by the library; state() / set_state() convert."""
 
     def __init__(self, ndim: int, r: int, kind: int = RELAXED, batch: int = 1, device=None, stream=None):
         import torch
@@ -105,13 +110,13 @@ class Lattice:
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         with torch.cuda.device(self.device):
             self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
-            self.psi = torch.zeros((self.batch, *self.shape), dtype=torch.complex64, device=self.device)
+            self.psi_fx = torch.zeros((self.batch, *self.shape, 2), dtype=torch.int32, device=self.device)
             self._work_raw = torch.empty(ws + 256, dtype=torch.uint8, device=self.device)
         addr = self._work_raw.data_ptr()
         self.work_ptr = addr + (-addr) % 256
         h = ctypes.c_void_p()
         st = self.lib.qhd_lattice_init(ctypes.byref(h), self.ndim, self.r, self.kind, self.batch,
-                                       ctypes.c_void_p(self.psi.data_ptr()), ctypes.c_void_p(self.work_ptr),
+                                       ctypes.c_void_p(self.psi_fx.data_ptr()), ctypes.c_void_p(self.work_ptr),
                                        ctypes.c_size_t(ws), ctypes.c_void_p(self.stream.cuda_stream))
         if st != qhd.QHD_OK:
             raise qhd.QHDError(st, "qhd_lattice_init failed")
@@ -148,6 +153,21 @@ class Lattice:
 
     def reset_state(self, init: int = INIT_GROUND) -> None:
         self._check(self.lib.qhd_lattice_reset_state(self.h, int(init)), "qhd_lattice_reset_state")
+
+    def state(self):
+        """The state as a new complex64 tensor (batch, r+1, ..., r+1)."""
+        import torch
+        out = torch.empty((self.batch, *self.shape), dtype=torch.complex64, device=self.device)
+        self._check(self.lib.qhd_lattice_get_state(self.h, ctypes.c_void_p(out.data_ptr())), "qhd_lattice_get_state")
+        return out
+
+    def set_state(self, psi) -> None:
+        """Load a complex64 CUDA tensor with batch * (r+1)^ndim values."""
+        import torch
+        z = psi.to(torch.complex64).contiguous()
+        if not z.is_cuda or z.numel() != self.batch * self.grid_points:
+            raise ValueError("psi must be a CUDA tensor with batch*G values")
+        self._check(self.lib.qhd_lattice_set_state(self.h, ctypes.c_void_p(z.data_ptr())), "qhd_lattice_set_state")
 
     def evolve(self, T: float, dt: float) -> None:
         self._check(self.lib.qhd_lattice_evolve(self.h, float(T), float(dt)), "qhd_lattice_evolve")

@@ -23,7 +23,7 @@ def oracle_run(F, r, kind, init, T, dt, sched):
     return OL.evolve(F, psi0, r, kind, 0.0, dt, int(round(T / dt)), sched)
 
 
-def compare(lat, Fs, psis_ref, r, radius=0.1, gap=0.01):
+def compare(lat, Fs, psis_ref, r, radius=0.1, gap=0.01, steps=1000):
     prob = torch.empty((lat.batch, *lat.shape), dtype=torch.float32, device="cuda")
     obs = lat.observables(radius, gap, prob=prob, marginals=True)
     p_gpu = prob.double().cpu().numpy()
@@ -79,7 +79,7 @@ def test_chain_3d_r16_uniform_per_instance_kinetic():
     lat.evolve(T, dt)
     Fs = [OL.qp_potential(Q, b, r) for Q, b in qps]
     refs = [oracle_run(F, r, OL.LATTICE_CHAIN, OL.INIT_UNIFORM, T, dt, s) for F, s in zip(Fs, oscheds)]
-    compare(lat, Fs, refs, r, radius=0.15)
+    compare(lat, Fs, refs, r, radius=0.15, steps=500)
     lat.close()
 
 
@@ -100,7 +100,7 @@ def test_shapes_against_oracle(d, r, kind):
     lat.evolve(T, dt)
     okind = OL.LATTICE_CHAIN if kind == lattice.CHAIN else OL.LATTICE_RELAXED
     refs = [oracle_run(F, r, okind, OL.INIT_KINETIC_GROUND, T, dt, oracle.Schedule()) for F in Fs]
-    compare(lat, Fs, refs, r, radius=0.3, gap=0.5)
+    compare(lat, Fs, refs, r, radius=0.3, gap=0.5, steps=300)
     lat.close()
 
 
@@ -116,34 +116,49 @@ def test_several_chunks_and_split_evolve_calls():
     lat.reset_state(lattice.INIT_GROUND)
     lat.evolve(25.0, 0.01)
     ref = oracle_run(F, r, OL.LATTICE_RELAXED, OL.INIT_KINETIC_GROUND, 25.0, 0.01, oracle.Schedule())
-    compare(lat, [F], [ref], r)
+    compare(lat, [F], [ref], r, steps=2500)
     lat.reset_state(lattice.INIT_GROUND)
     lat.evolve(12.5, 0.01)
     lat.evolve(12.5, 0.01)
     mid = oracle_run(F, r, OL.LATTICE_RELAXED, OL.INIT_KINETIC_GROUND, 12.5, 0.01, oracle.Schedule())
     ref2 = OL.evolve(F, mid, r, OL.LATTICE_RELAXED, 12.5, 0.01, 1250, oracle.Schedule())
-    compare(lat, [F], [ref2], r)
+    compare(lat, [F], [ref2], r, steps=2500)
     lat.close()
 
 
-def test_initial_states_and_time_reversal():
+def test_initial_states_state_io_and_time_reversal():
     d, r = 3, 8
     for kind, okind in ((lattice.RELAXED, OL.LATTICE_RELAXED), (lattice.CHAIN, OL.LATTICE_CHAIN)):
         lat = lattice.Lattice(d, r, kind)
         lat.reset_state(lattice.INIT_GROUND)
         want = OL.initial_state(d, r, okind, OL.INIT_KINETIC_GROUND)
-        got = lat.psi[0].cpu().numpy()
-        assert np.abs(got - want).max() <= 1e-7
+        assert np.abs(lat.psi_fx[0].double().cpu().numpy()[..., 0] / 2 ** 30 - want.real).max() <= 2 ** -31
+        assert int(lat.psi_fx[..., 1].abs().max()) == 0
+        assert np.abs(lat.state()[0].cpu().numpy() - want).max() <= 1e-7
         lat.reset_state(lattice.INIT_UNIFORM)
-        assert np.abs(lat.psi[0].cpu().numpy() - 9 ** -1.5).max() <= 1e-8
+        assert np.abs(lat.state()[0].cpu().numpy() - 9 ** -1.5).max() <= 1e-8
         Q, b = workloads.box_qp(41, d)
         lat.set_qp(Q[None], b[None])
         lat.set_schedule(qhd.Schedule())
-        lat.reset_state(lattice.INIT_GROUND)
-        psi0 = lat.psi.clone()
+        # a state of the caller's own, loaded through set_state, evolved, and back
+        rng = np.random.default_rng(3)
+        z = rng.standard_normal((1,) + (r + 1,) * d) + 1j * rng.standard_normal((1,) + (r + 1,) * d)
+        z /= np.linalg.norm(z)
+        lat.set_state(torch.from_numpy(z.astype(np.complex64)).cuda())
+        psi0 = lat.state()[0].cpu().numpy().astype(np.complex128)
         lat.evolve(5.0, 0.01)
+        ref = OL.evolve(OL.qp_potential(Q, b, r), z[0], r, okind, 0.0, 0.01, 500, oracle.Schedule())
+        got = lat.state()[0].cpu().numpy()
+        assert 0.5 * np.abs(np.abs(got) ** 2 - np.abs(ref) ** 2).sum() <= TV_MAX
         lat.evolve(-5.0, -0.01)
-        assert (lat.psi - psi0).abs().max().item() <= 2e-5
+        # back to psi0 up to a global phase (each step adds a pseudo-random one)
+        back = lat.state()[0].cpu().numpy().astype(np.complex128)
+        assert abs(abs(np.vdot(psi0, back)) - 1.0) <= 1e-6
+        assert np.abs(np.abs(back) ** 2 - np.abs(psi0) ** 2).max() <= 1e-7
+        bad = torch.zeros((1,) + (r + 1,) * d, dtype=torch.complex64, device="cuda")
+        bad[0, 1, 2, 3] = 3.0
+        with pytest.raises(qhd.QHDError):
+            lat.set_state(bad)
         lat.close()
 
 
