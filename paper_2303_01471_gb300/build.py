@@ -18,7 +18,7 @@ CSRC = os.path.join(PKG, "csrc")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libqhd.so")
 SOURCES = ["qhd_kernels.cu", "qhd_plane.cu", "qhd_host.cu", "qhd_static.cu", "qhd_tcdft.cu", "qhd_fno.cu", "qhd_spectrum.cu",
-           "qhd_lattice.cu"]
+           "qhd_lattice.cu", "qhd_probe.cu"]
 HEADERS = ["qhd_device.cuh", "qhd_kernels.h", "qhd_plane.cuh", "qhd_tcdft.h", "qhd_spectrum.h", "qhd_sched.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -341,20 +341,15 @@ __device__ __forceinline__ double fx_prob(int2 z) {
     return __dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y));
 }
 
-// Multi-index digit k (axis k, row-major, n per axis) of flat index i.
-__device__ __forceinline__ int lat_digit(int64_t i, int k, int d, int n) {
-    for (int a = d - 1; a > k; --a) i /= n;
-    return (int)(i % n);
-}
-
 __global__ void k_lat_ground(int2 *psi, const double *v, int n, int d, int64_t g, int64_t total) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += (int64_t)gridDim.x * blockDim.x) {
-        int64_t rem = i % g;
+        uint32_t rem = (uint32_t)(i % g);  // G < 2^31
         double amp = 1.0;
         for (int k = d - 1; k >= 0; --k) {
-            amp *= v[rem % n];
-            rem /= n;
+            const uint32_t q = rem / (uint32_t)n;
+            amp *= v[rem - q * n];
+            rem = q;
         }
         psi[i] = make_int2(__double2int_rn(amp * FX_ONE), 0);
     }
@@ -392,11 +387,12 @@ __global__ void k_lat_qp(double *f, const double *Q, const double *bv, int n, in
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t inst = i / g;
-        int64_t rem = i - inst * g;
+        uint32_t rem = (uint32_t)(i - inst * g);
         double x[LAT_MAX_D];
         for (int k = d - 1; k >= 0; --k) {
-            x[k] = (double)(rem % n) / r;
-            rem /= n;
+            const uint32_t q = rem / (uint32_t)n;
+            x[k] = (double)(rem - q * n) / r;
+            rem = q;
         }
         const double *Qi = Q + inst * d * d;
         const double *bi = bv + inst * d;
@@ -451,9 +447,16 @@ __global__ void k_lat_obs_partial(LatObs a) {
         sn += p;
         sf += p * f[i];
         // squared Euclidean distance to x*, summed over the axes in ascending order
+        int dig[LAT_MAX_D];
+        uint32_t rem = (uint32_t)i;
+        for (int k = a.d - 1; k >= 0; --k) {
+            const uint32_t q = rem / (uint32_t)a.n;
+            dig[k] = (int)(rem - q * a.n);
+            rem = q;
+        }
         double r2 = 0.0;
         for (int k = 0; k < a.d; ++k) {
-            const double dx = __dsub_rn(__ddiv_rn((double)lat_digit(i, k, a.d, a.n), a.r), xs[k]);
+            const double dx = __dsub_rn(__ddiv_rn((double)dig[k], a.r), xs[k]);
             r2 = __dadd_rn(r2, __dmul_rn(dx, dx));
         }
         if (r2 < a.radius2) sp += p;

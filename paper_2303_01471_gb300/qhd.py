@@ -36,7 +36,7 @@ EXPORTS = ["qhd_workspace_bytes", "qhd_init_grid", "qhd_set_potential", "qhd_set
            "qhd_lattice_set_potential", "qhd_lattice_set_qp", "qhd_lattice_set_schedule",
            "qhd_lattice_reset_state", "qhd_lattice_get_state", "qhd_lattice_set_state", "qhd_lattice_evolve", "qhd_lattice_observables",
            "qhd_lattice_timing_enable", "qhd_lattice_timing_read", "qhd_lattice_launch_count",
-           "qhd_lattice_last_error", "qhd_lattice_destroy"]
+           "qhd_lattice_last_error", "qhd_lattice_destroy", "qhd_probe_alu_rates"]
 SPLIT_STRANG = 0
 SPLIT_LIE_TROTTER = 1
 KINETIC_SPECTRAL = 0
@@ -136,6 +136,8 @@ def load(build_if_missing: bool = True):
     lib.qhd_set_transform.restype = st
     lib.qhd_library_call_count.argtypes = [vp]
     lib.qhd_library_call_count.restype = ctypes.c_int64
+    lib.qhd_probe_alu_rates.argtypes = [dp]
+    lib.qhd_probe_alu_rates.restype = st
     lib.qhd_destroy.argtypes = [vp]
     lib.qhd_destroy.restype = st
     lib.qhd_status_string.argtypes = [st]
@@ -195,6 +197,16 @@ def schedule_array(sched, batch: int):
             arr[i].chi = c.ctypes.data_as(dp)
             arr[i].n_samples = len(t)
     return arr, keep
+
+
+def probe_alu_rates():
+    """(FP32 FMAs/s, 32x32->64-bit integer multiply-adds/s) measured on the current device."""
+    lib = load()
+    out = (ctypes.c_double * 2)()
+    st = lib.qhd_probe_alu_rates(out)
+    if st != QHD_OK:
+        raise QHDError(st, "qhd_probe_alu_rates failed")
+    return out[0], out[1]
 
 
 def workspace_bytes(shape: Sequence[int], batch: int = 1) -> int:
