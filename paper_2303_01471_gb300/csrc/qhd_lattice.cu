@@ -43,7 +43,7 @@ constexpr int LAT_MAX_D = 6;
 constexpr int LAT_MAX_R = 16;
 constexpr int LAT_MAX_N = LAT_MAX_R + 1;
 constexpr int GROUP_MAX = 1024;          // points of one column (the group's axes)
-constexpr int TILE_MAX = 6144;           // points of one tile (48 KB of complex64)
+constexpr int TILE_MAX = 4608;           // points of one tile (36 KB): with 64 registers, 4 CTAs per SM
 constexpr int PASS_THREADS_MAX = 256;
 constexpr int64_t LAT_MAX_CHUNK = 1024;
 constexpr size_t U_BUDGET = size_t(64) << 20;  // bytes of propagators per chunk
@@ -129,7 +129,7 @@ __device__ __forceinline__ int lat_idx(int g) {
 // n = 9 rather than 81.  s and a are exact integer sums; each output is one
 // exact int64 sum rounded once.
 template <int N>
-__global__ void __launch_bounds__(PASS_THREADS_MAX) k_lat_pass(LatPass a) {
+__global__ void __launch_bounds__(PASS_THREADS_MAX, 4) k_lat_pass(LatPass a) {
     constexpr int H = N / 2, M = N - H;
     extern __shared__ __align__(16) LatPhase lsm[];
     LatPhase *ptab = lsm;
