@@ -382,8 +382,8 @@ __global__ void k_lat_to_c64(float2 *out, const int2 *psi, int64_t total) {
     }
 }
 
-__global__ void k_lat_qp(double *f, const double *Q, const double *bv, int n, int d, double r, int64_t g,
-                         int64_t total) {
+__global__ void k_lat_qp(double *f, const double *Q, const double *bv, const double *coord, int n, int d,
+                         int64_t g, int64_t total) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t inst = i / g;
@@ -391,7 +391,7 @@ __global__ void k_lat_qp(double *f, const double *Q, const double *bv, int n, in
         double x[LAT_MAX_D];
         for (int k = d - 1; k >= 0; --k) {
             const uint32_t q = rem / (uint32_t)n;
-            x[k] = (double)(rem - q * n) / r;
+            x[k] = coord[rem - q * n];
             rem = q;
         }
         const double *Qi = Q + inst * d * d;
@@ -412,6 +412,7 @@ struct LatObs {
     const double *f64;
     const double *fmin;   // [batch]
     const double *xs;     // [batch][LAT_MAX_D] mesh minimiser
+    const double *coord;  // mesh coordinates j / r, j = 0..r
     float *prob;
     double *partial;      // [batch][nblk][4]
     int64_t g;
@@ -456,7 +457,7 @@ __global__ void k_lat_obs_partial(LatObs a) {
         }
         double r2 = 0.0;
         for (int k = 0; k < a.d; ++k) {
-            const double dx = __dsub_rn(__ddiv_rn((double)dig[k], a.r), xs[k]);
+            const double dx = __dsub_rn(a.coord[dig[k]], xs[k]);
             r2 = __dadd_rn(r2, __dmul_rn(dx, dx));
         }
         if (r2 < a.radius2) sp += p;
@@ -671,8 +672,8 @@ void jacobi_eig(int n, std::vector<double> A, std::vector<double> &V, std::vecto
 }
 
 struct LatLayout {
-    size_t f64, fq, sched, samples, inst, xs, fmin, mm, ptab, flag, V, lam, ground, Q, bq, U, pot, obs_part, obs_res,
-        marg, total;
+    size_t f64, fq, sched, samples, inst, xs, fmin, mm, ptab, flag, V, lam, ground, coord, Q, bq, U, pot, obs_part,
+        obs_res, marg, total;
     int64_t chunk, chunk_shared;
     int obs_blocks, mm_blocks;
 };
@@ -714,6 +715,7 @@ LatLayout lat_layout(int d, int r, int64_t batch) {
     L.V = take(sizeof(double) * (size_t)(n * n));
     L.lam = take(sizeof(double) * (size_t)n);
     L.ground = take(sizeof(double) * (size_t)n);
+    L.coord = take(sizeof(double) * (size_t)n);
     L.Q = take(sizeof(double) * (size_t)(d * d * batch));
     L.bq = take(sizeof(double) * (size_t)(d * batch));
     const int64_t umax = L.chunk * batch > L.chunk_shared ? L.chunk * batch : L.chunk_shared;
@@ -739,7 +741,8 @@ struct qhd_lattice {
     LatLayout L{};
     std::vector<PassPlan> passes;
     // workspace views
-    double *f64 = nullptr, *xs = nullptr, *fmin = nullptr, *V = nullptr, *lam = nullptr, *ground = nullptr;
+    double *f64 = nullptr, *xs = nullptr, *fmin = nullptr, *V = nullptr, *lam = nullptr, *ground = nullptr,
+           *coord = nullptr;
     double *Q = nullptr, *bq = nullptr, *obs_part = nullptr, *obs_res = nullptr, *marg = nullptr;
     uint32_t *fq = nullptr;
     SchedDev *sched = nullptr;
@@ -951,6 +954,7 @@ qhd_status qhd_lattice_init(qhd_lattice **out, int ndim, int r, int kind, int64_
     c->V = (double *)(c->work + L.V);
     c->lam = (double *)(c->work + L.lam);
     c->ground = (double *)(c->work + L.ground);
+    c->coord = (double *)(c->work + L.coord);
     c->Q = (double *)(c->work + L.Q);
     c->bq = (double *)(c->work + L.bq);
     c->U = (int2 *)(c->work + L.U);
@@ -982,7 +986,11 @@ qhd_status qhd_lattice_init(qhd_lattice **out, int ndim, int r, int kind, int64_
         ptab[(size_t)k].fx = make_int2((int)std::nearbyint(cr * FX_ONE), (int)std::nearbyint(ci * FX_ONE));
         ptab[(size_t)k].f = make_float2((float)cr, (float)ci);
     }
+    std::vector<double> coord((size_t)n);
+    for (int j = 0; j < n; ++j) coord[(size_t)j] = (double)j / (double)r;
     cudaError_t e = cudaMemcpyAsync(c->V, V.data(), V.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->coord, coord.data(), coord.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(c->lam, lam.data(), lam.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess)
@@ -1023,8 +1031,8 @@ qhd_status qhd_lattice_set_qp(qhd_lattice *c, const double *Q_host, const double
     LAT_CUDA(c, cudaMemcpyAsync(c->Q, Q_host, sizeof(double) * (size_t)nq, cudaMemcpyHostToDevice, c->stream));
     LAT_CUDA(c, cudaMemcpyAsync(c->bq, b_host, sizeof(double) * (size_t)nb, cudaMemcpyHostToDevice, c->stream));
     const int64_t total = c->g * c->batch;
-    LAT_LAUNCH(c, (k_lat_qp<<<grid_blocks(total), 256, 0, c->stream>>>(c->f64, c->Q, c->bq, c->n, c->d,
-                                                                        (double)c->r, c->g, total),
+    LAT_LAUNCH(c, (k_lat_qp<<<grid_blocks(total), 256, 0, c->stream>>>(c->f64, c->Q, c->bq, c->coord, c->n,
+                                                                        c->d, c->g, total),
                    cudaGetLastError()));
     return lat_potential_common(c);
 }
@@ -1162,6 +1170,7 @@ qhd_status qhd_lattice_observables(qhd_lattice *c, qhd_lattice_obs *out, float *
     a.f64 = c->f64;
     a.fmin = c->fmin;
     a.xs = c->xs;
+    a.coord = c->coord;
     a.prob = prob_dev;
     a.partial = c->obs_part;
     a.g = c->g;
