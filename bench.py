@@ -400,10 +400,11 @@ def run_simqhd(args, rank, world, local_rank, dist):
 
     # roofline: the passes are bound by 32x32->64-bit integer multiply-adds.
     # Algorithmic work per point and axis: the reversal-symmetric blocks of the
-    # n x n propagator, 4 (M^2 + H^2) / n integer MADs (M = n - n//2, H = n//2).
+    # n x n propagator, M^2 + H^2 complex terms per line (M = n - n//2, H = n//2)
+    # of three integer MADs each (Gauss's three-product complex multiply).
     n = r + 1
     hh, mm = n // 2, n - n // 2
-    mads_pp_axis = 4.0 * (mm * mm + hh * hh) / n
+    mads_pp_axis = 3.0 * (mm * mm + hh * hh) / n
     ffma_rate, imad_rate = qhd.probe_alu_rates()
     axes = {"pass0": 3, "pass1": 2}
     kernels, best = [], None

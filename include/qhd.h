@@ -419,9 +419,9 @@ qhd_status qhd_fno_destroy(qhd_fno *fno);
  * factor exp(-i dt a sum_k K_k) is applied as the dense n x n matrix
  * exp(-i dt a K) along every axis; the potential phase exp(-i theta F) uses the
  * exact fixed-point turns of the Fourier-mesh path.  The state is held in
- * fixed point: every amplitude component is an int32 in units of 2^-30
- * (Q1.30), each line product is an exact int64 sum rounded once, so the norm
- * is kept to ~1e-8 per 10^3 steps however concentrated the state is.
+ * fixed point: every amplitude component is an int32 in units of 2^-29, each
+ * line product is an exact int64 sum rounded once, so the norm is kept to
+ * ~1e-8 per 10^3 steps however concentrated the state is.
  *
  * Limits: ndim 1..6, r 1..16, batch >= 1, batch * G <= 2^31.  Device memory
  * and the stream belong to the caller; ownership, asynchrony, error statuses
@@ -430,15 +430,17 @@ qhd_status qhd_fno_destroy(qhd_fno *fno);
  * qhd_lattice_workspace_bytes: bytes of 256-byte aligned device workspace;
  *   0 for sizes out of the limits.
  * qhd_lattice_init: psi_dev caller-owned, 8-byte aligned, batch*G pairs of
- *   int32 (re, im) in units of 2^-30: the working state, read and written by
+ *   int32 (re, im) in units of 2^-29: the working state, read and written by
  *   the library (use qhd_lattice_get_state / _set_state for complex64); kind a
  *   qhd_lattice_kind; work_dev / work_bytes as sized above; stream a
  *   cudaStream_t (0 = legacy default stream).
  * qhd_lattice_get_state: out_dev (batch*G complex64, 8-byte aligned) receives
  *   the state.  Async.
  * qhd_lattice_set_state: the state from in_dev (batch*G complex64), rounded to
- *   the nearest 2^-30; a component that is not finite or has modulus >= 2 is
- *   set to 0 and the call returns QHD_ERR_INVALID_ARG.  Synchronises the stream.
+ *   the nearest 2^-29.  Every instance must have norm^2 <= 1 + 1e-3 (the
+ *   integer line products are sized for it) and finite components; otherwise
+ *   the state is set to 0 and the call returns QHD_ERR_INVALID_ARG.
+ *   Synchronises the stream.
  * qhd_lattice_set_potential: f_dev = batch*G FP64 on the device (copied);
  *   non-finite values or a range >= 2^31 give QHD_ERR_INVALID_ARG.
  *   Synchronises the stream.

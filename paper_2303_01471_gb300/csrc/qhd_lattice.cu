@@ -52,15 +52,17 @@ constexpr int MINMAX_BLOCKS_MAX = 512;
 
 // ------------------------------------------------------------------ kernels
 // The working state is fixed point: each amplitude component is an int32 in
-// units of 2^-30 (|psi| <= 1 by unitarity, so |component| < 2^31 with room to
-// spare).  A line transform forms every output as an exact int64 sum of
+// units of 2^-29 (|psi| <= 1 by unitarity, so |component| <= 2^29, and the
+// sums re + im of the three-product complex multiply stay below 2^31).  A line transform forms every output as an exact int64 sum of
 // int32 x int32 products and rounds it once; the potential phase is an exact
 // int64 complex product rounded once.  Every stored value therefore carries one
-// rounding of at most 2^-31 absolute, independent of how concentrated the state
+// rounding of at most 2^-30 absolute, independent of how concentrated the state
 // is, where FP32 storage carries 2^-24 relative on the few dominant amplitudes
 // of a concentrated state.
-constexpr int FX_SHIFT = 30;
-constexpr double FX_ONE = 1073741824.0;  // 2^30
+constexpr int FX_SHIFT = 30;                 // scale of U and of the phase factors: Q1.30
+constexpr double FX_ONE = 1073741824.0;      // 2^30
+constexpr double FX_STATE = 536870912.0;     // 2^29: the state is Q2.29 (one bit of headroom for
+                                             // the sums of the three-product complex multiply)
 
 __device__ __forceinline__ int fx_round(long long v) {
     return (int)((v + (1ll << (FX_SHIFT - 1))) >> FX_SHIFT);
@@ -98,7 +100,7 @@ struct LatPass {
     const uint64_t *pot_pre;   // [batch] phase coefficient applied on load, or null
     const uint64_t *pot_post;  // [batch] applied on store, or null
     uint32_t dither_pre, dither_post;
-    const int2 *U;             // this step's propagator blocks [u_batch][M*M + H*H], Q1.30
+    const int4 *U;             // this step's propagator blocks [u_batch][M*M + H*H]: (re, im, re + im, 0), Q1.30
     int64_t u_batch;
     const LatPhase *ptab;
     int P, q, W, pitch, lines_per_col;
@@ -129,19 +131,19 @@ __device__ __forceinline__ int lat_idx(int g) {
 // n = 9 rather than 81.  s and a are exact integer sums; each output is one
 // exact int64 sum rounded once.
 template <int N>
-__global__ void __launch_bounds__(PASS_THREADS_MAX, 4) k_lat_pass(LatPass a) {
+__global__ void __launch_bounds__(PASS_THREADS_MAX, N <= 9 ? 4 : 2) k_lat_pass(LatPass a) {
     constexpr int H = N / 2, M = N - H;
     extern __shared__ __align__(16) LatPhase lsm[];
     LatPhase *ptab = lsm;
-    int2 *Ps = reinterpret_cast<int2 *>(lsm + PHASE_TAB);
-    int2 *Pa = Ps + M * M;
-    int2 *tile = Pa + H * H;
+    int4 *Ps = reinterpret_cast<int4 *>(lsm + PHASE_TAB);
+    int4 *Pa = Ps + M * M;
+    int2 *tile = reinterpret_cast<int2 *>(Pa + H * H);
     const int64_t row = blockIdx.x / a.tiles_per_row;
     const int64_t c0 = (blockIdx.x - row * a.tiles_per_row) * a.W;
     const int64_t inst = row / a.rows_per_inst;
     if (a.pot_pre || a.pot_post)
         for (int i = threadIdx.x; i < PHASE_TAB; i += blockDim.x) ptab[i] = a.ptab[i];
-    const int2 *Ug = a.U + (a.u_batch == 1 ? 0 : inst) * (M * M + H * H);
+    const int4 *Ug = a.U + (a.u_batch == 1 ? 0 : inst) * (M * M + H * H);
     for (int i = threadIdx.x; i < M * M + H * H; i += blockDim.x) Ps[i] = __ldg(&Ug[i]);
     __syncthreads();
     const int P = a.P, W = a.W, pitch = a.pitch;
@@ -184,35 +186,41 @@ __global__ void __launch_bounds__(PASS_THREADS_MAX, 4) k_lat_pass(LatPass a) {
             int2 x[N];
 #pragma unroll
             for (int m = 0; m < N; ++m) x[m] = cb[lat_idx<N>(g0 + m * s)];
-            int2 sv[M], av[H];
+            // (s, a) and their re + im sums; |s|^2 + |a|^2 <= 4 |x|^2 keeps every sum
+            // below 2^31 at the 2^-29 scale
+            int3 sv[M], av[H];
 #pragma unroll
             for (int m = 0; m < H; ++m) {
-                sv[m] = make_int2(x[m].x + x[N - 1 - m].x, x[m].y + x[N - 1 - m].y);
-                av[m] = make_int2(x[m].x - x[N - 1 - m].x, x[m].y - x[N - 1 - m].y);
+                const int sx = x[m].x + x[N - 1 - m].x, sy = x[m].y + x[N - 1 - m].y;
+                const int ax = x[m].x - x[N - 1 - m].x, ay = x[m].y - x[N - 1 - m].y;
+                sv[m] = make_int3(sx, sy, sx + sy);
+                av[m] = make_int3(ax, ay, ax + ay);
             }
-            if (N & 1) sv[M - 1] = x[H];
+            if (N & 1) sv[M - 1] = make_int3(x[H].x, x[H].y, x[H].x + x[H].y);
             int2 y[N];
 #pragma unroll
             for (int i = 0; i < M; ++i) {
-                long long sr = 0, si = 0;
+                // three products per complex term (Gauss): with k1 = ur vr, k2 = ui vi,
+                // k3 = (ur + ui)(vr + vi):  re = k1 - k2,  im = k3 - k1 - k2
+                long long s1 = 0, s2 = 0, s3 = 0;
 #pragma unroll
                 for (int m = 0; m < M; ++m) {
-                    const int2 u = Ps[i * M + m];
-                    sr += (long long)u.x * sv[m].x;
-                    sr -= (long long)u.y * sv[m].y;
-                    si += (long long)u.x * sv[m].y;
-                    si += (long long)u.y * sv[m].x;
+                    const int4 u = Ps[i * M + m];
+                    s1 += (long long)u.x * sv[m].x;
+                    s2 += (long long)u.y * sv[m].y;
+                    s3 += (long long)u.z * sv[m].z;
                 }
+                const long long sr = s1 - s2, si = s3 - s1 - s2;
                 if (i < H) {
-                    long long ar = 0, ai = 0;
+                    long long a1 = 0, a2 = 0, a3 = 0;
 #pragma unroll
                     for (int m = 0; m < H; ++m) {
-                        const int2 u = Pa[i * H + m];
-                        ar += (long long)u.x * av[m].x;
-                        ar -= (long long)u.y * av[m].y;
-                        ai += (long long)u.x * av[m].y;
-                        ai += (long long)u.y * av[m].x;
+                        const int4 u = Pa[i * H + m];
+                        a1 += (long long)u.x * av[m].x;
+                        a2 += (long long)u.y * av[m].y;
+                        a3 += (long long)u.z * av[m].z;
                     }
+                    const long long ar = a1 - a2, ai = a3 - a1 - a2;
                     y[i] = make_int2(fx_round(sr + ar), fx_round(si + ai));
                     y[N - 1 - i] = make_int2(fx_round(sr - ar), fx_round(si - ai));
                 } else {
@@ -248,7 +256,7 @@ struct LatPrep {
     const SchedDev *sched;
     const InstDev *inst;
     uint64_t *pot;       // [cnt+1][batch]
-    int2 *U;             // [cnt][u_batch][n*n]
+    int4 *U;             // [cnt][u_batch][M*M + H*H]
     const double *V;     // eigenvectors of A, V[i*n + k] = component i of vector k
     const double *lam;   // eigenvalues of A
     double kin_scale;    // r^2 / 2
@@ -313,7 +321,7 @@ __global__ void k_lat_prep(LatPrep a) {
     __syncthreads();
     // reversal-symmetric blocks Ps (M x M) and Pa (H x H) of U, see k_lat_pass
     const int H = n / 2, M = n - H;
-    int2 *out = a.U + (jl * a.u_batch + b) * (int64_t)(M * M + H * H);
+    int4 *out = a.U + (jl * a.u_batch + b) * (int64_t)(M * M + H * H);
     const uint64_t key0 = ((a.step_base + (uint64_t)jl) * 0x100000001B3ull) ^ ((uint64_t)b * 0x9E3779B97F4A7C15ull);
     for (int e = threadIdx.x; e < M * M + H * H; e += blockDim.x) {
         double re, im;
@@ -331,13 +339,14 @@ __global__ void k_lat_prep(LatPrep a) {
             re = 0.5 * (s_ur[i * n + m] - s_ur[i * n + n - 1 - m]);
             im = 0.5 * (s_ui[i * n + m] - s_ui[i * n + n - 1 - m]);
         }
-        out[e] = make_int2(fx_dither_round(re, key0 + 2 * e), fx_dither_round(im, key0 + 2 * e + 1));
+        const int ur = fx_dither_round(re, key0 + 2 * e), ui = fx_dither_round(im, key0 + 2 * e + 1);
+        out[e] = make_int4(ur, ui, ur + ui, 0);
     }
 }
 
 // |psi|^2 of a Q1.30 amplitude in FP64.
 __device__ __forceinline__ double fx_prob(int2 z) {
-    const double x = (double)z.x / FX_ONE, y = (double)z.y / FX_ONE;
+    const double x = (double)z.x / FX_STATE, y = (double)z.y / FX_STATE;
     return __dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y));
 }
 
@@ -351,7 +360,7 @@ __global__ void k_lat_ground(int2 *psi, const double *v, int n, int d, int64_t g
             amp *= v[rem - q * n];
             rem = q;
         }
-        psi[i] = make_int2(__double2int_rn(amp * FX_ONE), 0);
+        psi[i] = make_int2(__double2int_rn(amp * FX_STATE), 0);
     }
 }
 
@@ -361,15 +370,16 @@ __global__ void k_lat_fill(int2 *psi, int value, int64_t total) {
         psi[i] = make_int2(value, 0);
 }
 
-// complex64 <-> Q1.30.  Loading flags components of modulus >= 2 (or not
-// finite), which the format cannot hold, and leaves them zero.
+// complex64 <-> the 2^-29 fixed-point state.  Loading flags components of
+// modulus >= 2 (or not finite) and leaves them zero; qhd_lattice_set_state
+// then checks every instance's norm.
 __global__ void k_lat_from_c64(int2 *psi, const float2 *in, int64_t total, int *bad) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += (int64_t)gridDim.x * blockDim.x) {
         const float2 z = in[i];
         const bool ok = fabsf(z.x) < 2.0f && fabsf(z.y) < 2.0f;  // false for NaN too
         if (!ok) atomicOr(bad, 1);
-        psi[i] = ok ? make_int2(__double2int_rn((double)z.x * FX_ONE), __double2int_rn((double)z.y * FX_ONE))
+        psi[i] = ok ? make_int2(__double2int_rn((double)z.x * FX_STATE), __double2int_rn((double)z.y * FX_STATE))
                     : make_int2(0, 0);
     }
 }
@@ -378,7 +388,7 @@ __global__ void k_lat_to_c64(float2 *out, const int2 *psi, int64_t total) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int2 z = psi[i];
-        out[i] = make_float2((float)((double)z.x / FX_ONE), (float)((double)z.y / FX_ONE));
+        out[i] = make_float2((float)((double)z.x / FX_STATE), (float)((double)z.y / FX_STATE));
     }
 }
 
@@ -619,7 +629,8 @@ std::vector<PassPlan> plan_passes(int d, int n, int64_t batch) {
         p.tiles_per_row = (p.col_count + W - 1) / W;
         p.blocks = p.rows * p.tiles_per_row;
         const int hh = n / 2, mm = n - hh;
-        p.smem = sizeof(LatPhase) * PHASE_TAB + sizeof(int2) * (size_t)(mm * mm + hh * hh + p.W * p.pitch);
+        p.smem = sizeof(LatPhase) * PHASE_TAB + sizeof(int4) * (size_t)(mm * mm + hh * hh) +
+                 sizeof(int2) * (size_t)(p.W * p.pitch);
         out.push_back(p);
         a1 = a0;
     }
@@ -697,7 +708,7 @@ LatLayout lat_layout(int d, int r, int64_t batch) {
     };
     L.obs_blocks = blocks_for(G, OBS_BLOCKS_MAX);
     L.mm_blocks = blocks_for(G, MINMAX_BLOCKS_MAX);
-    const size_t ubytes = sizeof(int2) * (size_t)((n - n / 2) * (n - n / 2) + (n / 2) * (n / 2));
+    const size_t ubytes = sizeof(int4) * (size_t)((n - n / 2) * (n - n / 2) + (n / 2) * (n / 2));
     int64_t ch = (int64_t)(U_BUDGET / (ubytes * (size_t)batch));
     L.chunk = ch < 1 ? 1 : ch > LAT_MAX_CHUNK ? LAT_MAX_CHUNK : ch;
     ch = (int64_t)(U_BUDGET / ubytes);
@@ -750,7 +761,7 @@ struct qhd_lattice {
     InstDev *inst = nullptr;
     MinMaxPart *mm = nullptr;
     LatPhase *ptab = nullptr;
-    int2 *U = nullptr;
+    int4 *U = nullptr;
     int *flag = nullptr;
     uint64_t *pot = nullptr;
     // host state
@@ -957,7 +968,7 @@ qhd_status qhd_lattice_init(qhd_lattice **out, int ndim, int r, int kind, int64_
     c->coord = (double *)(c->work + L.coord);
     c->Q = (double *)(c->work + L.Q);
     c->bq = (double *)(c->work + L.bq);
-    c->U = (int2 *)(c->work + L.U);
+    c->U = (int4 *)(c->work + L.U);
     c->pot = (uint64_t *)(c->work + L.pot);
     c->obs_part = (double *)(c->work + L.obs_part);
     c->obs_res = (double *)(c->work + L.obs_res);
@@ -1061,7 +1072,7 @@ qhd_status qhd_lattice_reset_state(qhd_lattice *c, int init) {
     if (s != QHD_OK) return s;
     const int64_t total = c->g * c->batch;
     if (init == QHD_LATTICE_INIT_UNIFORM) {
-        const int v = (int)std::nearbyint(FX_ONE / std::sqrt((double)c->g));
+        const int v = (int)std::nearbyint(FX_STATE / std::sqrt((double)c->g));
         LAT_LAUNCH(c, (k_lat_fill<<<grid_blocks(total), 256, 0, c->stream>>>(c->psi, v, total), cudaGetLastError()));
     } else if (init == QHD_LATTICE_INIT_GROUND) {
         LAT_LAUNCH(c, (k_lat_ground<<<grid_blocks(total), 256, 0, c->stream>>>(c->psi, c->ground, c->n, c->d, c->g,
@@ -1228,10 +1239,42 @@ qhd_status qhd_lattice_set_state(qhd_lattice *c, const void *in_dev) {
     LAT_LAUNCH(c, (k_lat_from_c64<<<grid_blocks(total), 256, 0, c->stream>>>(c->psi, (const float2 *)in_dev, total,
                                                                             c->flag),
                    cudaGetLastError()));
+    // Per-instance norms (the observables reduction; its other sums are not used
+    // here).  The integer line products are sized for states of norm <= 1.
+    LatObs o{};
+    o.psi = c->psi;
+    o.f64 = c->f64;
+    o.fmin = c->fmin;
+    o.xs = c->xs;
+    o.coord = c->coord;
+    o.prob = nullptr;
+    o.partial = c->obs_part;
+    o.g = c->g;
+    o.d = c->d;
+    o.n = c->n;
+    o.r = (double)c->r;
+    o.radius2 = 0.0;
+    o.gap = -1.0;
+    o.nblk = c->L.obs_blocks;
+    LAT_LAUNCH(c, (k_lat_obs_partial<<<dim3((unsigned)o.nblk, (unsigned)c->batch), 256, 0, c->stream>>>(o),
+                   cudaGetLastError()));
+    LAT_LAUNCH(c, (k_lat_obs_final<<<(unsigned)c->batch, 256, 0, c->stream>>>(c->obs_part, c->obs_res, o.nblk),
+                   cudaGetLastError()));
+    std::vector<double> res((size_t)(4 * c->batch));
     int bad = 0;
     LAT_CUDA(c, cudaMemcpyAsync(&bad, c->flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    LAT_CUDA(c, cudaMemcpyAsync(res.data(), c->obs_res, res.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                                c->stream));
     LAT_CUDA(c, cudaStreamSynchronize(c->stream));
-    if (bad) return lfail(c, QHD_ERR_INVALID_ARG, "state component not finite or of modulus >= 2 (set to 0)");
+    int64_t worst = -1;
+    for (int64_t b = 0; b < c->batch; ++b)
+        if (!(res[(size_t)(4 * b)] <= 1.0 + 1e-3)) worst = b;
+    if (bad || worst >= 0) {
+        LAT_LAUNCH(c, (k_lat_fill<<<grid_blocks(total), 256, 0, c->stream>>>(c->psi, 0, total), cudaGetLastError()));
+        if (bad) return lfail(c, QHD_ERR_INVALID_ARG, "state component not finite or of modulus >= 2 (state set to 0)");
+        return lfail(c, QHD_ERR_INVALID_ARG, "instance %lld: state norm^2 %g > 1 + 1e-3 (state set to 0)",
+                     (long long)worst, res[(size_t)(4 * worst)]);
+    }
     return QHD_OK;
 }
 

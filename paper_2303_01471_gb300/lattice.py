@@ -93,7 +93,7 @@ def workspace_bytes(ndim: int, r: int, batch: int = 1) -> int:
 class Lattice:
     """`batch` instances of QHD on the mesh {0, 1/r, ..., 1}^ndim with the chain
     (CHAIN) or relaxed (RELAXED) kinetic operator.  The working state `psi_fx`
-    (torch int32, shape (batch, r+1, ..., r+1, 2): re, im in units of 2^-30) is
+    (torch int32, shape (batch, r+1, ..., r+1, 2): re, im in units of 2^-29) is
     owned here and borrowed by the library; state() / set_state() convert."""
 
     def __init__(self, ndim: int, r: int, kind: int = RELAXED, batch: int = 1, device=None, stream=None):

@@ -132,7 +132,7 @@ def test_initial_states_state_io_and_time_reversal():
         lat = lattice.Lattice(d, r, kind)
         lat.reset_state(lattice.INIT_GROUND)
         want = OL.initial_state(d, r, okind, OL.INIT_KINETIC_GROUND)
-        assert np.abs(lat.psi_fx[0].double().cpu().numpy()[..., 0] / 2 ** 30 - want.real).max() <= 2 ** -31
+        assert np.abs(lat.psi_fx[0].double().cpu().numpy()[..., 0] / 2 ** 29 - want.real).max() <= 2 ** -30
         assert int(lat.psi_fx[..., 1].abs().max()) == 0
         assert np.abs(lat.state()[0].cpu().numpy() - want).max() <= 1e-7
         lat.reset_state(lattice.INIT_UNIFORM)
@@ -156,9 +156,13 @@ def test_initial_states_state_io_and_time_reversal():
         assert abs(abs(np.vdot(psi0, back)) - 1.0) <= 1e-6
         assert np.abs(np.abs(back) ** 2 - np.abs(psi0) ** 2).max() <= 1e-7
         bad = torch.zeros((1,) + (r + 1,) * d, dtype=torch.complex64, device="cuda")
-        bad[0, 1, 2, 3] = 3.0
+        bad[0, 1, 2, 3] = 3.0                   # not representable
         with pytest.raises(qhd.QHDError):
             lat.set_state(bad)
+        big = torch.full((1,) + (r + 1,) * d, 0.5, dtype=torch.complex64, device="cuda")   # norm^2 = 182
+        with pytest.raises(qhd.QHDError):
+            lat.set_state(big)
+        assert int(lat.psi_fx.abs().max()) == 0
         lat.close()
 
 
