@@ -122,6 +122,18 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def device_record(dev):
+    """SM count, L2 size and the measured arithmetic rates of the device the bench ran on."""
+    import torch
+    from paper_2303_01471_gb300 import qhd
+    p = torch.cuda.get_device_properties(dev)
+    rates = qhd.probe_alu_rates()
+    return {"name": p.name, "sms": p.multi_processor_count,
+            "l2_bytes": getattr(p, "L2_cache_size", None),
+            "measured": {"fp32_fma_per_s": rates[0], "int64_mad_per_s": rates[1],
+                         "fp64_fma_per_s": rates[2], "sfu_sin_per_s": rates[3]}}
+
+
 # ------------------------------------------------------------ multi-rank logic
 def max_over_ranks(value: float, dist, device=None) -> float:
     """Maximum of a per-rank timing over all ranks (every rank gets the result)."""
@@ -300,6 +312,7 @@ def run_ours(args, rank, world, local_rank, dist):
         "roofline": roofline,
         "kernels": kernels,
         "clocks": clk.summary(),
+        "device": device_record(dev),
         "wall_s_timed_region": wall,
         "observables": [{"instance": "x".join(map(str, i.shape)), "norm": o.norm, "e_f": o.e_f,
                          "p_succ": o.p_succ} for i, o in zip(insts, obs)],
@@ -405,7 +418,7 @@ def run_simqhd(args, rank, world, local_rank, dist):
     n = r + 1
     hh, mm = n // 2, n - n // 2
     mads_pp_axis = 3.0 * (mm * mm + hh * hh) / n
-    ffma_rate, imad_rate = qhd.probe_alu_rates()
+    ffma_rate, imad_rate, _, _ = qhd.probe_alu_rates()
     axes = {"pass0": 3, "pass1": 2}
     kernels, best = [], None
     for cls in ("pass0", "pass1"):
@@ -439,6 +452,7 @@ def run_simqhd(args, rank, world, local_rank, dist):
                 "h2d_bytes_per_step": int(Q.nbytes + bvec.nbytes), "d2h_bytes_per_step": 64 * B,
                 "ms_per_step": e2e_step},
         "gpu_launches": launches, "roofline": roofline, "kernels": kernels, "clocks": clk_sum,
+        "device": device_record(dev),
         "wall_s_timed_region": wall,
         "observables_first": {"norm": obs[0].norm, "e_f": obs[0].e_f, "p_succ": obs[0].p_succ,
                               "p_gap": obs[0].p_gap},

@@ -500,11 +500,12 @@ const char *qhd_lattice_last_error(const qhd_lattice *lat);
 qhd_status qhd_lattice_destroy(qhd_lattice *lat);
 
 /* Arithmetic throughput of the current device (no paper counterpart; used to
- * state roofline peaks): timed loops of independent FP32 FMAs and of
- * 32 x 32 -> 64-bit integer multiply-adds on every SM.  out[0] = FP32 FMAs/s,
- * out[1] = integer multiply-adds/s.  Allocates nothing; runs on the legacy
- * default stream and synchronises it.  Errors: QHD_ERR_INVALID_ARG for a NULL
- * out, QHD_ERR_CUDA for a failed launch or event. */
+ * state roofline peaks): timed loops of independent operations on every SM.
+ * out (4 doubles): [0] FP32 FMAs/s, [1] 32 x 32 -> 64-bit integer
+ * multiply-adds/s, [2] FP64 FMAs/s, [3] hardware sine approximations/s.
+ * Allocates nothing; runs on the legacy default stream and synchronises it.
+ * Errors: QHD_ERR_INVALID_ARG for a NULL out, QHD_ERR_CUDA for a failed launch
+ * or event. */
 qhd_status qhd_probe_alu_rates(double *out);
 
 /* Synchronise the stream and free the host-side context (never the caller's

@@ -200,13 +200,14 @@ def schedule_array(sched, batch: int):
 
 
 def probe_alu_rates():
-    """(FP32 FMAs/s, 32x32->64-bit integer multiply-adds/s) measured on the current device."""
+    """Measured on the current device: (FP32 FMAs/s, 32x32->64-bit integer
+    multiply-adds/s, FP64 FMAs/s, hardware sine approximations/s)."""
     lib = load()
-    out = (ctypes.c_double * 2)()
+    out = (ctypes.c_double * 4)()
     st = lib.qhd_probe_alu_rates(out)
     if st != QHD_OK:
         raise QHDError(st, "qhd_probe_alu_rates failed")
-    return out[0], out[1]
+    return tuple(out)
 
 
 def workspace_bytes(shape: Sequence[int], batch: int = 1) -> int:
