@@ -95,7 +95,7 @@ __device__ __forceinline__ int2 fx_phase(int2 z, uint32_t u, const LatPhase *tab
 }
 
 struct LatPass {
-    int2 *psi;                 // Q1.30 state
+    int2 *psi;                 // state, units of 2^-29
     const uint32_t *fq;
     const uint64_t *pot_pre;   // [batch] phase coefficient applied on load, or null
     const uint64_t *pot_post;  // [batch] applied on store, or null
@@ -344,7 +344,7 @@ __global__ void k_lat_prep(LatPrep a) {
     }
 }
 
-// |psi|^2 of a Q1.30 amplitude in FP64.
+// |psi|^2 of a fixed-point amplitude (units of 2^-29) in FP64.
 __device__ __forceinline__ double fx_prob(int2 z) {
     const double x = (double)z.x / FX_STATE, y = (double)z.y / FX_STATE;
     return __dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y));
@@ -745,7 +745,7 @@ LatLayout lat_layout(int d, int r, int64_t batch) {
 struct qhd_lattice {
     int d = 0, r = 0, n = 0, kind = 0;
     int64_t batch = 1, g = 1;
-    int2 *psi = nullptr;  // Q1.30 state (the caller's buffer)
+    int2 *psi = nullptr;  // state in units of 2^-29 (the caller's buffer)
     char *work = nullptr;
     size_t work_bytes = 0;
     cudaStream_t stream = nullptr;

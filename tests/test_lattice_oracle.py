@@ -220,3 +220,29 @@ def test_observables_definitions():
     assert o.e_f == pytest.approx(-0.4 - 0.1 - 0.3 * 0.995)
     assert np.allclose(o.marginals[0], [0.2, 0.7, 0, 0.1, 0]) and np.allclose(o.marginals[1], [0.3, 0, 0.4, 0.3, 0])
     assert o.norm == pytest.approx(1.0)
+
+
+def test_chain_drops_only_a_global_phase_of_the_printed_laplacian():
+    """Eq. (discretize-pde) prints L = r^2 tridiag(1, -2, 1); the chain operator
+    drops the -2 diagonal.  A Strang run with the printed operator (dense
+    exponentials of the Kronecker sum) equals the oracle's run times the global
+    phase exp(-i r^2 d sum_j dt a_j)."""
+    d, r = 2, 3
+    n = r + 1
+    rng = np.random.default_rng(8)
+    Q, b = random_qp(rng, d)
+    F = L.qp_potential(Q, b, r)
+    Lp = r * r * (np.diag(-2.0 * np.ones(n)) + np.diag(np.ones(n - 1), 1) + np.diag(np.ones(n - 1), -1))
+    Kp = np.kron(-0.5 * Lp, np.eye(n)) + np.kron(np.eye(n), -0.5 * Lp)
+    sch = oracle.Schedule()
+    t0, dt, steps = 0.5, 0.01, 60
+    psi0 = L.initial_state(d, r, L.LATTICE_CHAIN, L.INIT_UNIFORM)
+    psi = psi0.ravel().astype(complex)
+    acc = 0.0
+    for j in range(steps):
+        a, bb = oracle.schedule_ab(sch, t0 + (j + 0.5) * dt)
+        P = np.exp(-0.5j * dt * bb * F.ravel())
+        psi = P * (scipy.linalg.expm(-1j * dt * a * Kp) @ (P * psi))
+        acc += dt * a
+    got = L.evolve(F, psi0, r, L.LATTICE_CHAIN, t0, dt, steps, sch).ravel()
+    assert np.abs(psi - np.exp(-1j * r * r * d * acc) * got).max() < 1e-10
