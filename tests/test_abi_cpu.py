@@ -98,3 +98,7 @@ def test_lattice_sizes_and_argument_checks_without_a_device(lib):
     assert lib.qhd_lattice_destroy(None) == 0
     assert lib.qhd_lattice_last_error(None) == b""
     assert lib.qhd_lattice_launch_count(None) == 0
+
+
+def test_probe_rejects_null_output_without_a_device(lib):
+    assert lib.qhd_probe_alu_rates(None) == 1
