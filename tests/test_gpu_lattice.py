@@ -167,10 +167,11 @@ def test_initial_states_state_io_and_time_reversal():
 
 
 def test_full_size_sampled_instances():
-    """The benchmark's launch configuration (64 instances of the 5-d, r = 8
-    Sim-QHD problem, sigma ~ U(0.5, 2)): two sampled instances against the oracle."""
-    d, r, B, T, dt = 5, 8, 64, 10.0, 0.01
-    qps = [workloads.box_qp(1000 + i, d) for i in range(B)]
+    """The benchmark's launch configuration and instances (bench.py --workload
+    simqhd, rank 0: 256 instances of the 5-d, r = 8 Sim-QHD problem, seeds
+    0..255, sigma ~ U(0.5, 2) from seed 7): two sampled instances against the oracle."""
+    d, r, B, T, dt = 5, 8, 256, 10.0, 0.01
+    qps = [workloads.box_qp(i, d) for i in range(B)]
     sig = np.random.default_rng(7).uniform(0.5, 2.0, B)
     lat = lattice.Lattice(d, r, lattice.RELAXED, batch=B)
     lat.set_qp(np.stack([q for q, _ in qps]), np.stack([b for _, b in qps]))
