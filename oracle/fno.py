@@ -3,7 +3,7 @@
 Only ``tests/`` and the CPU legs of ``bench.py`` may import this module.  It
 shares no code with the CUDA kernels: the network is written here from its
 definition with explicit DFT matrices and numpy contractions, slow and
-obviously correct, and serves as the judge of the GPU forward pass and (by
+obviously correct, and serves as the reference for the GPU forward pass and (by
 central finite differences) of the GPU gradients.
 
 Network (per instance; the paper has no surrogate, this is the definition the

@@ -1,7 +1,7 @@
 /*
  * qhd_oracle.c -- plain FP64 CPU oracle for the QHD split-operator simulation.
  *
- * TEST INFRASTRUCTURE ONLY.  This file is the slow, obviously-correct judge of
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, obviously-correct reference for
  * the CUDA path.  Only the test suite, the smoke check and the CPU-baseline leg
  * of the benchmark may load it.  It shares no code, header, table or helper
  * with the product library, and the product library never calls it.

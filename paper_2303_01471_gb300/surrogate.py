@@ -5,7 +5,7 @@ libqhd.so's kernels).
 The solver produces the training targets: |psi(T)|^2 of each instance under
 the paper's schedule with its own potential weight sigma (e^chi = 2 sigma t^3),
 computed by batched contexts of the split-operator path.  The surrogate then
-predicts that distribution directly from f and sigma; the solver is the judge
+predicts that distribution directly from f and sigma; the solver is the measure
 of its error (TV against the solver's |psi(T)|^2) and the fallback for
 instances above the accepted TV.
 """
