@@ -105,8 +105,9 @@ size_t qhd_workspace_bytes(int ndim, const int64_t *n, int64_t batch);
 
 /*
  * Create a context.  ndim in 1..3; every n[k] a power of two in 2..1024;
- * lo[k] < hi[k], both finite; batch >= 1 independent instances sharing the
- * mesh (each with its own f and schedule).  psi_dev: caller-owned device
+ * lo[k] < hi[k], both finite; 1 <= batch <= 65535 independent instances
+ * sharing the mesh (each with its own f and schedule); G <= 2^30 and
+ * batch * G <= 2^34.  psi_dev: caller-owned device
  * buffer of batch*G complex64, 8-byte aligned.  work_dev: caller-owned device
  * buffer of work_bytes >= qhd_workspace_bytes(...), 256-byte aligned.
  * stream: a cudaStream_t (NULL = legacy default stream).  Both buffers must
@@ -423,7 +424,7 @@ qhd_status qhd_fno_destroy(qhd_fno *fno);
  * line product is an exact int64 sum rounded once, so the norm is kept to
  * ~1e-8 per 10^3 steps however concentrated the state is.
  *
- * Limits: ndim 1..6, r 1..16, batch >= 1, batch * G <= 2^31.  Device memory
+ * Limits: ndim 1..6, r 1..16, 1 <= batch <= 65535, batch * G <= 2^31.  Device memory
  * and the stream belong to the caller; ownership, asynchrony, error statuses
  * and sticky CUDA failures follow the qhd_ctx conventions above.
  *

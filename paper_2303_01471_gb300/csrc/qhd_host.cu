@@ -48,7 +48,8 @@ bool shape_ok(int ndim, const int64_t *n, int64_t batch) {
         if (!supported_n(n[d])) return false;
     const int64_t g = grid_points(ndim, n);
     if (g > (int64_t(1) << 30)) return false;
-    if (batch > (int64_t(1) << 20) || g * batch > (int64_t(1) << 34)) return false;
+    // batch indexes the second grid dimension of the per-instance kernels (<= 65535)
+    if (batch > 65535 || g * batch > (int64_t(1) << 34)) return false;
     return true;
 }
 

@@ -569,7 +569,8 @@ int64_t ipow(int64_t b, int e) {
 }
 
 bool sizes_ok(int ndim, int r, int64_t batch) {
-    if (ndim < 1 || ndim > LAT_MAX_D || r < 1 || r > LAT_MAX_R || batch < 1) return false;
+    // batch indexes the second grid dimension of the per-instance kernels (<= 65535)
+    if (ndim < 1 || ndim > LAT_MAX_D || r < 1 || r > LAT_MAX_R || batch < 1 || batch > 65535) return false;
     const int64_t g = ipow(r + 1, ndim);
     return batch <= (int64_t(1) << 31) / g;
 }

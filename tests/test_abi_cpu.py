@@ -45,6 +45,7 @@ def test_workspace_bytes_valid_and_invalid(lib):
         assert lib.qhd_workspace_bytes(len(bad), n, 1) == 0, bad
     n = (ctypes.c_int64 * 2)(8, 8)
     assert lib.qhd_workspace_bytes(2, n, 0) == 0
+    assert lib.qhd_workspace_bytes(2, n, 65535) > 0 and lib.qhd_workspace_bytes(2, n, 65536) == 0
 
 
 def test_init_rejects_bad_arguments_without_a_device(lib):
@@ -80,7 +81,7 @@ def test_lattice_sizes_and_argument_checks_without_a_device(lib):
     lib = lattice._lib()
     ws = lib.qhd_lattice_workspace_bytes(5, 8, 4)
     assert ws > 4 * 9 ** 5 * 12
-    for bad in [(0, 8, 1), (7, 8, 1), (2, 0, 1), (2, 17, 1), (2, 8, 0), (6, 16, 1 << 10)]:
+    for bad in [(0, 8, 1), (7, 8, 1), (2, 0, 1), (2, 17, 1), (2, 8, 0), (6, 16, 1 << 10), (1, 1, 65536)]:
         assert lib.qhd_lattice_workspace_bytes(*bad) == 0, bad
     h = ctypes.c_void_p()
     fake = ctypes.c_void_p(0x10000000)  # never dereferenced: checks fail first
