@@ -153,21 +153,40 @@ __global__ void __launch_bounds__(PASS_THREADS_MAX, N <= 9 ? 4 : 2) k_lat_pass(L
     const bool contig = a.g_stride == 1;
     const int tot = P * W;
     {
+        // four loads in flight per thread before their results are used
+        constexpr int UNR = 4;
         const uint64_t c = a.pot_pre ? a.pot_pre[inst] : 0;
-        for (int l = threadIdx.x; l < tot; l += blockDim.x) {
-            int g, col;
-            if (contig) {
-                col = lat_div(l, a.mg_P);
-                g = l - col * P;
-            } else {
-                g = lat_div(l, a.mg_W);
-                col = l - g * W;
+        for (int l0 = threadIdx.x; l0 < tot; l0 += UNR * blockDim.x) {
+            int2 v[UNR];
+            uint32_t q[UNR];
+            int si[UNR];
+#pragma unroll
+            for (int u = 0; u < UNR; ++u) {
+                const int l = l0 + u * blockDim.x;
+                int g, col;
+                if (contig) {
+                    col = lat_div(l, a.mg_P);
+                    g = l - col * P;
+                } else {
+                    g = lat_div(l, a.mg_W);
+                    col = l - g * W;
+                }
+                si[u] = -1;
+                q[u] = 0;
+                if (l < tot && col < ncol) {
+                    const int64_t off = base + col * a.col_stride + (int64_t)g * a.g_stride;
+                    v[u] = a.psi[off];
+                    if (a.pot_pre) q[u] = __ldg(&a.fq[off]);
+                    si[u] = col * pitch + lat_idx<N>(g);
+                }
             }
-            if (col >= ncol) continue;
-            const int64_t off = base + col * a.col_stride + (int64_t)g * a.g_stride;
-            int2 v = a.psi[off];
-            if (a.pot_pre) v = fx_phase(v, turns_mul(c, __ldg(&a.fq[off])) + a.dither_pre, ptab);
-            tile[col * pitch + lat_idx<N>(g)] = v;
+#pragma unroll
+            for (int u = 0; u < UNR; ++u) {
+                if (si[u] < 0) continue;
+                int2 w = v[u];
+                if (a.pot_pre) w = fx_phase(w, turns_mul(c, q[u]) + a.dither_pre, ptab);
+                tile[si[u]] = w;
+            }
         }
     }
     __syncthreads();
