@@ -246,3 +246,39 @@ def test_chain_drops_only_a_global_phase_of_the_printed_laplacian():
         acc += dt * a
     got = L.evolve(F, psi0, r, L.LATTICE_CHAIN, t0, dt, steps, sch).ravel()
     assert np.abs(psi - np.exp(-1j * r * r * d * acc) * got).max() < 1e-10
+
+
+def test_ising_machine_evolution_reproduces_relaxed_qhd():
+    """The relaxed QHD dynamics through the Hamming encoding, end to end: Strang
+    steps of -A(t)/2 S_x + B(t)/2 H_P on d r qubits from |+>^{dr}, with the
+    dictionary's A = r^{3/2} e^{phi}, B = 2 e^{chi} (lambda = 1), give
+    Hamming-weight probabilities equal to the oracle's box-mesh p from the
+    binomial state, step for step (each factor preserves the encoding span and
+    restricts to the box-mesh factor)."""
+    d, r = 2, 3
+    rng = np.random.default_rng(9)
+    Q, b = random_qp(rng, d)
+    F = L.qp_potential(Q, b, r)
+    nq = d * r
+    blk = np.repeat(np.arange(d), r)
+    HP = np.zeros((2 ** nq, 2 ** nq))
+    for j in range(nq):
+        HP += -(Q[blk[j]].sum() + 2 * b[blk[j]]) / (4 * r) * site_op(SZ, j, nq)
+        for k in range(j):
+            HP += Q[blk[j], blk[k]] / (4 * r * r) * site_op(SZ, j, nq) @ site_op(SZ, k, nq)
+    HP += ((1 + 1 / r) * np.trace(Q) / 8 + Q[1, 0] / 4 + b.sum() / 2) * np.eye(2 ** nq)
+    SXn = s_x(nq)
+    sch = oracle.Schedule()
+    t0, dt, steps = 0.2, 0.02, 40
+    q = np.full(2 ** nq, 2.0 ** (-nq / 2), dtype=complex)
+    lat = L.initial_state(d, r, L.LATTICE_RELAXED, L.INIT_KINETIC_GROUND)
+    weights = np.array([[bin(s >> r).count("1"), bin(s & (2 ** r - 1)).count("1")] for s in range(2 ** nq)])
+    for j in range(steps):
+        a, bb = oracle.schedule_ab(sch, t0 + (j + 0.5) * dt)
+        A, B = r ** 1.5 * a, 2 * bb
+        half = scipy.linalg.expm(-0.5j * dt * (B / 2) * HP)
+        q = half @ (scipy.linalg.expm(-1j * dt * (-(A / 2) * SXn)) @ (half @ q))
+        lat = L.evolve(F, lat, r, L.LATTICE_RELAXED, t0 + j * dt, dt, 1, sch)
+        pw = np.zeros((r + 1, r + 1))
+        np.add.at(pw, (weights[:, 0], weights[:, 1]), np.abs(q) ** 2)
+        assert np.abs(pw - np.abs(lat) ** 2).max() < 1e-12, j
