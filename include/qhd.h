@@ -464,6 +464,12 @@ qhd_status qhd_fno_destroy(qhd_fno *fno);
  *   doubles, [b][k][j]) the probabilities of the measurement elements
  *   E^{(k)}_j of Eq. (Ekj).  FP64 accumulation in a fixed order.
  *   Synchronises the stream.
+ * qhd_lattice_evolve_trajectory: advances like qhd_lattice_evolve and, after
+ *   every `every` steps (every >= 1 dividing round(T/dt)), writes (norm, E[F],
+ *   p_succ, p_gap) of every instance into traj_dev, a caller-owned device array
+ *   of (n/every) * batch * 4 doubles: point k, instance b at
+ *   traj_dev[(k*batch + b)*4 + 0..3].  Asynchronous (no host synchronisation
+ *   between points).
  * qhd_lattice_timing_enable / _read: as qhd_timing_* with the kernel classes
  *   QHD_LKCLASS_* (every = 0 switches sampling off).
  */
@@ -492,6 +498,8 @@ qhd_status qhd_lattice_reset_state(qhd_lattice *lat, int init);
 qhd_status qhd_lattice_get_state(qhd_lattice *lat, void *out_dev);
 qhd_status qhd_lattice_set_state(qhd_lattice *lat, const void *in_dev);
 qhd_status qhd_lattice_evolve(qhd_lattice *lat, double T, double dt);
+qhd_status qhd_lattice_evolve_trajectory(qhd_lattice *lat, double T, double dt, int64_t every, double radius,
+                                         double gap, double *traj_dev);
 qhd_status qhd_lattice_observables(qhd_lattice *lat, qhd_lattice_obs *out, float *prob_dev, double *marginals_host,
                                    double radius, double gap);
 qhd_status qhd_lattice_timing_enable(qhd_lattice *lat, int every);

@@ -1240,6 +1240,55 @@ qhd_status qhd_lattice_observables(qhd_lattice *c, qhd_lattice_obs *out, float *
     return QHD_OK;
 }
 
+qhd_status qhd_lattice_evolve_trajectory(qhd_lattice *c, double T, double dt, int64_t every, double radius,
+                                         double gap, double *traj_dev) {
+    qhd_status s = lcheck(c);
+    if (s != QHD_OK) return s;
+    if (!traj_dev) return lfail(c, QHD_ERR_INVALID_ARG, "traj_dev is NULL");
+    if (!std::isfinite(radius) || radius < 0 || !std::isfinite(gap))
+        return lfail(c, QHD_ERR_INVALID_ARG, "bad radius or gap");
+    if (!std::isfinite(T) || !std::isfinite(dt) || dt == 0.0)
+        return lfail(c, QHD_ERR_INVALID_ARG, "T and dt must be finite and dt nonzero");
+    const double ratio = T / dt;
+    const double nr = std::nearbyint(ratio);
+    if (!(nr >= 1.0) || std::fabs(ratio - nr) > 1e-9 * nr || nr > 1e12)
+        return lfail(c, QHD_ERR_INVALID_ARG, "T/dt = %.17g is not a positive integer", ratio);
+    const int64_t nsteps = (int64_t)nr;
+    if (every < 1 || nsteps % every != 0)
+        return lfail(c, QHD_ERR_INVALID_ARG, "every = %lld must divide the %lld steps", (long long)every,
+                     (long long)nsteps);
+    if (!c->have_f || !c->have_sched)
+        return lfail(c, QHD_ERR_STATE, "evolve needs a potential and a schedule first");
+    LatObs a{};
+    a.psi = c->psi;
+    a.f64 = c->f64;
+    a.fmin = c->fmin;
+    a.xs = c->xs;
+    a.coord = c->coord;
+    a.prob = nullptr;
+    a.partial = c->obs_part;
+    a.g = c->g;
+    a.d = c->d;
+    a.n = c->n;
+    a.r = (double)c->r;
+    a.radius2 = radius * radius;
+    a.gap = gap;
+    a.nblk = c->L.obs_blocks;
+    // Consecutive segments are one Strang run: the closing half phase of a
+    // segment and the opening one of the next make the merged phase.
+    for (int64_t k = 0; k < nsteps / every; ++k) {
+        s = qhd_lattice_evolve(c, (double)every * dt, dt);
+        if (s != QHD_OK) return s;
+        LAT_LAUNCH(c, (k_lat_obs_partial<<<dim3((unsigned)a.nblk, (unsigned)c->batch), 256, 0, c->stream>>>(a),
+                       cudaGetLastError()));
+        LAT_LAUNCH(c, (k_lat_obs_final<<<(unsigned)c->batch, 256, 0, c->stream>>>(c->obs_part,
+                                                                                  traj_dev + k * c->batch * 4,
+                                                                                  a.nblk),
+                       cudaGetLastError()));
+    }
+    return QHD_OK;
+}
+
 qhd_status qhd_lattice_get_state(qhd_lattice *c, void *out_dev) {
     qhd_status s = lcheck(c);
     if (s != QHD_OK) return s;

@@ -70,6 +70,9 @@ def _lib():
     lib.qhd_lattice_set_state.restype = st
     lib.qhd_lattice_evolve.argtypes = [vp, ctypes.c_double, ctypes.c_double]
     lib.qhd_lattice_evolve.restype = st
+    lib.qhd_lattice_evolve_trajectory.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_int64,
+                                                  ctypes.c_double, ctypes.c_double, vp]
+    lib.qhd_lattice_evolve_trajectory.restype = st
     lib.qhd_lattice_observables.argtypes = [vp, ctypes.POINTER(_LatObs), vp, dp, ctypes.c_double, ctypes.c_double]
     lib.qhd_lattice_observables.restype = st
     lib.qhd_lattice_timing_enable.argtypes = [vp, ctypes.c_int]
@@ -171,6 +174,17 @@ class Lattice:
 
     def evolve(self, T: float, dt: float) -> None:
         self._check(self.lib.qhd_lattice_evolve(self.h, float(T), float(dt)), "qhd_lattice_evolve")
+
+    def evolve_trajectory(self, T: float, dt: float, every: int, radius: float = 0.1, gap: float = 0.01):
+        """Evolve like evolve() and return a (T/dt/every, batch, 4) float64 CUDA tensor of
+        (norm, E[F], p_succ, p_gap) after every `every` steps."""
+        import torch
+        n = int(round(T / dt))
+        out = torch.empty((max(1, n // max(1, int(every))), self.batch, 4), dtype=torch.float64, device=self.device)
+        self._check(self.lib.qhd_lattice_evolve_trajectory(self.h, float(T), float(dt), int(every), float(radius),
+                                                           float(gap), ctypes.c_void_p(out.data_ptr())),
+                    "qhd_lattice_evolve_trajectory")
+        return out
 
     def observables(self, radius: float = 0.1, gap: float = 0.01, prob=None, marginals: bool = False):
         out = (_LatObs * self.batch)()

@@ -34,7 +34,8 @@ EXPORTS = ["qhd_workspace_bytes", "qhd_init_grid", "qhd_set_potential", "qhd_set
            "qhd_fno_forward", "qhd_fno_loss_grad", "qhd_fno_adam_step", "qhd_fno_launch_count",
            "qhd_fno_last_error", "qhd_fno_destroy", "qhd_lattice_workspace_bytes", "qhd_lattice_init",
            "qhd_lattice_set_potential", "qhd_lattice_set_qp", "qhd_lattice_set_schedule",
-           "qhd_lattice_reset_state", "qhd_lattice_get_state", "qhd_lattice_set_state", "qhd_lattice_evolve", "qhd_lattice_observables",
+           "qhd_lattice_reset_state", "qhd_lattice_get_state", "qhd_lattice_set_state", "qhd_lattice_evolve",
+           "qhd_lattice_evolve_trajectory", "qhd_lattice_observables",
            "qhd_lattice_timing_enable", "qhd_lattice_timing_read", "qhd_lattice_launch_count",
            "qhd_lattice_last_error", "qhd_lattice_destroy", "qhd_probe_alu_rates"]
 SPLIT_STRANG = 0

@@ -208,3 +208,35 @@ def test_error_paths():
     with pytest.raises(qhd.QHDError):
         lat.set_potential(bad)
     lat.close()
+
+
+def test_trajectory_records_equal_separate_runs_and_the_oracle():
+    """E[F](t), P_succ(t), p_gap(t) and the norm every 50 steps in one call: the
+    points equal the oracle's observables at those times, and the state at the
+    end equals a plain evolve of the same length."""
+    d, r = 3, 8
+    Q, b = workloads.box_qp(51, d)
+    F = OL.qp_potential(Q, b, r)
+    lat = lattice.Lattice(d, r, lattice.RELAXED)
+    lat.set_qp(Q[None], b[None])
+    lat.set_schedule(qhd.Schedule())
+    lat.reset_state(lattice.INIT_GROUND)
+    traj = lat.evolve_trajectory(3.0, 0.01, 50, radius=0.2, gap=0.05).cpu().numpy()
+    end = lat.state()[0].cpu().numpy()
+    assert traj.shape == (6, 1, 4)
+    psi = OL.initial_state(d, r, OL.LATTICE_RELAXED, OL.INIT_KINETIC_GROUND)
+    for k in range(6):
+        psi = OL.evolve(F, psi, r, OL.LATTICE_RELAXED, 0.5 * k, 0.01, 50, oracle.Schedule())
+        o = OL.observables(F, psi, r, 0.2, 0.05)
+        assert abs(traj[k, 0, 0] - 1.0) <= NORM_MAX
+        assert abs(traj[k, 0, 1] - o.e_f) <= EF_MAX * max(abs(o.e_f), 1e-3 * np.ptp(F)), k
+        assert abs(traj[k, 0, 2] - o.p_succ) <= TV_MAX and abs(traj[k, 0, 3] - o.p_gap) <= TV_MAX, k
+    lat.reset_state(lattice.INIT_GROUND)
+    lat.evolve(3.0, 0.01)
+    plain = lat.state()[0].cpu().numpy().astype(np.complex128)
+    # equal up to the pseudo-random global phase of the segment boundaries
+    assert abs(abs(np.vdot(plain, end.astype(np.complex128))) - 1.0) <= 1e-6
+    assert np.abs(np.abs(plain) ** 2 - np.abs(end) ** 2).max() <= 1e-7
+    with pytest.raises(qhd.QHDError):
+        lat.evolve_trajectory(1.0, 0.01, 30)          # 30 does not divide 100
+    lat.close()
