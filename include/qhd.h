@@ -421,8 +421,8 @@ qhd_status qhd_fno_destroy(qhd_fno *fno);
  * exp(-i dt a K) along every axis; the potential phase exp(-i theta F) uses the
  * exact fixed-point turns of the Fourier-mesh path.  The state is held in
  * fixed point: every amplitude component is an int32 in units of 2^-29, each
- * line product is an exact int64 sum rounded once, so the norm is kept to
- * ~1e-8 per 10^3 steps however concentrated the state is.
+ * line product is an exact int64 sum rounded once, so the norm stays within a
+ * few 1e-7 over 10^3 steps however concentrated the state is.
  *
  * Limits: ndim 1..6, r 1..16, 1 <= batch <= 65535, batch * G <= 2^31.  Device memory
  * and the stream belong to the caller; ownership, asynchrony, error statuses

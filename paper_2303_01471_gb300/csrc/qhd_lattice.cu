@@ -21,8 +21,9 @@
 // merged potential phase on load; the last pass of an evolve call applies the
 // final half phase on store.  U is computed per step in FP64 from the host's
 // eigendecomposition of A (U = V diag(exp(i dt a r^2/2 lambda)) V^T).  The
-// state is fixed point (see below), which keeps the norm to ~1e-8 over 10^3
-// steps where FP32 storage drifts by several 1e-6 on concentrated states.
+// state is fixed point (see below), which keeps the norm to a few 1e-7 at most
+// over 10^3 steps where FP32 storage drifts by several 1e-6 on concentrated
+// states.
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -53,9 +54,10 @@ constexpr int MINMAX_BLOCKS_MAX = 512;
 // ------------------------------------------------------------------ kernels
 // The working state is fixed point: each amplitude component is an int32 in
 // units of 2^-29 (|psi| <= 1 by unitarity, so |component| <= 2^29, and the
-// sums re + im of the three-product complex multiply stay below 2^31).  A line transform forms every output as an exact int64 sum of
-// int32 x int32 products and rounds it once; the potential phase is an exact
-// int64 complex product rounded once.  Every stored value therefore carries one
+// sums re + im of the three-product complex multiply stay below 2^31).  A line
+// transform forms every output as an exact int64 sum of int32 x int32 products
+// and rounds it once; the potential phase is an exact int64 complex product
+// rounded once.  Every stored value therefore carries one
 // rounding of at most 2^-30 absolute, independent of how concentrated the state
 // is, where FP32 storage carries 2^-24 relative on the few dominant amplitudes
 // of a concentrated state.
