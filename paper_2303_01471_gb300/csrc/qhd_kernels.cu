@@ -124,86 +124,6 @@ __global__ void __launch_bounds__(W * LineCfg<N>::T, N <= 256 ? 4 : 1) k_axis(Ax
     for (int e = 0; e < E; ++e) g[(int64_t)(t + T * e) * a.inner] = x[e];
 }
 
-// ------------------------------------- strided axis pass, persistent + prefetch
-// Same transform as k_axis, but each block walks over tiles and prefetches the
-// next tile (N rows x W columns) into shared memory with 16-byte asynchronous
-// copies while it transforms the current one, so global-memory latency
-// overlaps the FFT work even at a few blocks per SM.  Needs W >= 2 and a
-// 16-byte aligned psi.
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int K> __device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(K) : "memory");
-}
-
-template <int N, int W>
-__device__ __forceinline__ void axis_tile_issue(const AxisArgs &a, int64_t tile, int64_t tiles, float2 *buf) {
-    constexpr int NT = W * LineCfg<N>::T;
-    const int64_t o = tile / tiles;
-    const int64_t ci0 = (tile - o * tiles) * W;
-    const float2 *base = a.psi + o * (int64_t)N * a.inner + ci0;
-    for (int i = threadIdx.x; i < N * W / 2; i += NT) {
-        const int row = i / (W / 2), col = (i % (W / 2)) * 2;
-        cp_async16(buf + row * W + col, base + (int64_t)row * a.inner + col);
-    }
-}
-
-template <int N, int W>
-__global__ void __launch_bounds__(W * LineCfg<N>::T, N <= 256 ? 4 : 1) k_axis_pipe(AxisArgs a) {
-    using C = LineCfg<N>;
-    constexpr int E = C::E, T = C::T;
-    constexpr int S = line_stride<N>(false, W);
-    extern __shared__ __align__(16) float2 smp[];
-    float2 *bufs[2] = {smp, smp + N * W};
-    float2 *xch = smp + 2 * N * W;
-    const int c = threadIdx.x % W, t = threadIdx.x / W;
-    const int64_t tiles = a.inner / W;
-    const int64_t ntiles = a.planes * tiles;
-    float2 *sm = xch + (C::TWO_STAGE ? c * S : 0);
-    int64_t tile = blockIdx.x;
-    if (tile < ntiles) axis_tile_issue<N, W>(a, tile, tiles, bufs[0]);
-    cp_async_commit();
-    for (int it = 0; tile < ntiles; ++it, tile += gridDim.x) {
-        const int64_t next = tile + gridDim.x;
-        if (next < ntiles) axis_tile_issue<N, W>(a, next, tiles, bufs[(it + 1) & 1]);
-        cp_async_commit();
-        cp_async_wait<1>();
-        __syncthreads();
-        const float2 *cur = bufs[it & 1];
-        float2 x[E];
-#pragma unroll
-        for (int e = 0; e < E; ++e) x[e] = cur[(t + T * e) * W + c];
-        __syncthreads();  // every thread has read this buffer before it is refilled
-        const int64_t o = tile / tiles;
-        const int64_t ci = (tile - o * tiles) * W + c;
-        if (a.mode & MODE_FWD) line_fft<N, false>(x, sm, t, a.tw2, BlockSync{});
-        if (a.mode & MODE_KIN) {
-            const float4 *kb = a.kt + (a.kt_batch == 1 ? 0 : o) * a.ksum;
-            int64_t i1 = a.ndim == 2 ? ci : (ci >> a.log_n2);
-            if (a.perm1_r) i1 = i1 / a.perm1_r + (int64_t)a.perm1_c * (i1 % a.perm1_r);
-            const float4 k1 = __ldg(&kb[a.koff1 + i1]);
-            float4 k2 = make_float4(1.f, 0.f, 0.f, 0.f);
-            if (a.ndim == 3) k2 = __ldg(&kb[a.koff2 + (ci & ((1 << a.log_n2) - 1))]);
-#pragma unroll
-            for (int e = 0; e < E; ++e) {
-                const float4 k0 = __ldg(&kb[t + T * e]);
-                float2 y = cmul_comp(x[e], make_float2(k0.x, k0.y), make_float2(k0.z, k0.w));
-                y = cmul_comp(y, make_float2(k1.x, k1.y), make_float2(k1.z, k1.w));
-                if (a.ndim == 3) y = cmul_comp(y, make_float2(k2.x, k2.y), make_float2(k2.z, k2.w));
-                x[e] = y;
-            }
-        }
-        if (a.mode & MODE_INV) line_fft<N, true>(x, sm, t, a.tw2, BlockSync{});
-        float2 *g = a.psi + o * (int64_t)N * a.inner + ci;
-#pragma unroll
-        for (int e = 0; e < E; ++e) g[(int64_t)(t + T * e) * a.inner] = x[e];
-    }
-    cp_async_wait<0>();
-}
-
 // --------------------------------------------- 1-D: a whole chunk per launch
 template <int N>
 __global__ void __launch_bounds__(ROW_THREADS) k_oned(OneDArgs a) {
@@ -476,30 +396,6 @@ static cudaError_t axis_w_impl(const AxisArgs &a, cudaStream_t s) {
     constexpr int S = line_stride<N>(false, W);
     const int64_t blocks = a.planes * (a.inner / W);
     const size_t xch = C::TWO_STAGE ? (size_t)W * S * sizeof(float2) : 0;
-#ifdef QHD_AXIS_PIPE
-    if constexpr (W >= 2) {
-        if (((uintptr_t)a.psi & 15) == 0) {
-            // persistent grid: resident blocks per SM x SMs, never more than tiles
-            static int resident = 0;
-            const size_t sm = 2 * (size_t)N * W * sizeof(float2) + xch;
-            if (resident == 0) {
-                cudaError_t e = cudaFuncSetAttribute(k_axis_pipe<N, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                     (int)sm);
-                if (e != cudaSuccess) return e;
-                int per_sm = 0, dev = 0, sms = 0;
-                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_axis_pipe<N, W>, W * C::T, sm);
-                if (e != cudaSuccess) return e;
-                e = cudaGetDevice(&dev);
-                if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-                if (e != cudaSuccess) return e;
-                resident = (per_sm > 0 ? per_sm : 1) * sms;
-            }
-            const int64_t grid = blocks < resident ? blocks : resident;
-            k_axis_pipe<N, W><<<(unsigned)grid, W * C::T, sm, s>>>(a);
-            return cudaGetLastError();
-        }
-    }
-#endif
     k_axis<N, W><<<(unsigned)blocks, W * C::T, xch, s>>>(a);
     return cudaGetLastError();
 }
