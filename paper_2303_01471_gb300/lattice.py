@@ -136,8 +136,9 @@ class Lattice:
 
     def set_potential(self, f) -> None:
         """f: torch float64 CUDA tensor with batch * (r+1)^ndim values."""
+        import torch
         ff = f.contiguous()
-        if not ff.is_cuda or ff.dtype.itemsize != 8 or ff.numel() != self.batch * self.grid_points:
+        if not ff.is_cuda or ff.dtype != torch.float64 or ff.numel() != self.batch * self.grid_points:
             raise ValueError("f must be a float64 CUDA tensor with batch*G values")
         self._check(self.lib.qhd_lattice_set_potential(self.h, ctypes.c_void_p(ff.data_ptr())),
                     "qhd_lattice_set_potential")
