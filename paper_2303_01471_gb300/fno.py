@@ -159,18 +159,35 @@ class FNO:
             msg = self.lib.qhd_fno_last_error(self.h)
             raise _qhd.QHDError(st, f"{what}: {msg.decode() if msg else ''}")
 
+    @staticmethod
+    def _need(t, dtype, shape, what):
+        """The kernels read raw device pointers: insist on the exact dtype, shape and layout."""
+        if not (t.is_cuda and t.dtype == dtype and tuple(t.shape) == tuple(shape) and t.is_contiguous()):
+            raise ValueError(f"{what}: need a contiguous CUDA {dtype} tensor of shape {tuple(shape)}, "
+                             f"got {t.dtype} {tuple(t.shape)} on {t.device}")
+
     def forward(self, f, sigma, out=None):
         """f: torch float64 CUDA (B, n, n); sigma: torch float32 CUDA (B,).  Returns p (B, n, n)."""
         import torch
-        B = f.shape[0]
+        B, n = f.shape[0], self.cfg.n
+        self._need(f, torch.float64, (B, n, n), "f")
+        self._need(sigma, torch.float32, (B,), "sigma")
         if out is None:
-            out = torch.empty((B, self.cfg.n, self.cfg.n), dtype=torch.float32, device=self.device)
+            out = torch.empty((B, n, n), dtype=torch.float32, device=self.device)
+        self._need(out, torch.float32, (B, n, n), "out")
         self._check(self.lib.qhd_fno_forward(self.h, ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(sigma.data_ptr()),
                                              B, ctypes.c_void_p(out.data_ptr())), "qhd_fno_forward")
         return out
 
     def loss_grad(self, f, sigma, p_true, want_loss=True):
         """Overwrites self.grad with dL/dparams; returns the mean KL loss (synchronises) or None."""
+        import torch
+        B, n = f.shape[0], self.cfg.n
+        self._need(f, torch.float64, (B, n, n), "f")
+        self._need(sigma, torch.float32, (B,), "sigma")
+        self._need(p_true, torch.float32, (B, n, n), "p_true")
+        if self.grad is None:
+            raise _qhd.QHDError(3, "qhd_fno_loss_grad: created without training buffers")
         loss = ctypes.c_double()
         self._check(self.lib.qhd_fno_loss_grad(self.h, ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(sigma.data_ptr()),
                                                ctypes.c_void_p(p_true.data_ptr()), f.shape[0],
