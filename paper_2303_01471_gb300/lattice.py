@@ -188,7 +188,10 @@ class Lattice:
         return out
 
     def observables(self, radius: float = 0.1, gap: float = 0.01, prob=None, marginals: bool = False):
+        import torch
         out = (_LatObs * self.batch)()
+        if prob is not None:
+            qhd.need_tensor(prob, torch.float32, self.batch * self.grid_points, "prob")
         marg = np.zeros((self.batch, self.ndim, self.n)) if marginals else None
         mp = marg.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if marginals else None
         pp = ctypes.c_void_p(prob.data_ptr()) if prob is not None else None

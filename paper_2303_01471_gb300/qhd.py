@@ -200,6 +200,14 @@ def schedule_array(sched, batch: int):
     return arr, keep
 
 
+def need_tensor(t, dtype, numel: int, what: str) -> None:
+    """The library reads raw device pointers: insist on a contiguous CUDA tensor of
+    the exact dtype and number of values."""
+    if not (t.is_cuda and t.dtype == dtype and t.numel() == numel and t.is_contiguous()):
+        raise ValueError(f"{what}: need a contiguous CUDA {dtype} tensor with {numel} values, "
+                         f"got {t.dtype} with {t.numel()} on {t.device}")
+
+
 def probe_alu_rates():
     """Measured on the current device: (FP32 FMAs/s, 32x32->64-bit integer
     multiply-adds/s, FP64 FMAs/s, hardware sine approximations/s)."""
@@ -333,6 +341,7 @@ class QHD:
         """H(t) x for instance `inst` (x: complex64 CUDA tensor with the mesh's G values)."""
         import torch
         x = x.contiguous()
+        need_tensor(x, torch.complex64, self.grid_points, "x")
         out = torch.empty_like(x)
         self._check(self.lib.qhd_apply_hamiltonian(self.ctx, int(inst), float(t), ctypes.c_void_p(x.data_ptr()),
                                                    ctypes.c_void_p(out.data_ptr())), "qhd_apply_hamiltonian")
@@ -385,7 +394,10 @@ class QHD:
 
     def observables(self, radius: float = 0.1, prob=None) -> List[Observables]:
         """prob: optional torch float32 CUDA tensor with batch*G values receiving |psi|^2."""
+        import torch
         out = (_Obs * self.batch)()
+        if prob is not None:
+            need_tensor(prob, torch.float32, self.batch * self.grid_points, "prob")
         pp = ctypes.c_void_p(prob.data_ptr()) if prob is not None else ctypes.c_void_p()
         self._check(self.lib.qhd_observables(self.ctx, out, pp, float(radius)), "qhd_observables")
         return [Observables(o.t, o.norm, o.e_f, o.p_succ, tuple(o.x_star), o.steps_done) for o in out]
