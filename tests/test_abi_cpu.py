@@ -103,3 +103,12 @@ def test_lattice_sizes_and_argument_checks_without_a_device(lib):
 
 def test_probe_rejects_null_output_without_a_device(lib):
     assert lib.qhd_probe_alu_rates(None) == 1
+
+
+def test_bindings_reject_tensors_they_cannot_pass_as_raw_pointers():
+    import torch
+    from paper_2303_01471_gb300 import fno
+    with pytest.raises(ValueError):
+        qhd.need_tensor(torch.zeros(4, dtype=torch.float32), torch.float32, 4, "prob")      # host tensor
+    with pytest.raises(ValueError):
+        fno.FNO._need(torch.zeros((2, 8, 8), dtype=torch.float32), torch.float64, (2, 8, 8), "f")
