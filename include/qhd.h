@@ -16,7 +16,14 @@
  * coefficients taken at the step midpoint.  Observables follow Eq. (expect_O)
  * and the success criterion of the Fig. 2 caption.
  *
- * Conventions shared by every entry point
+ * Further families in this header: the spectrum of H(t) (qhd_apply_hamiltonian,
+ * qhd_lowest_eigenpairs), the tensor-core DFT form (qhd_set_transform), the
+ * learned surrogate (qhd_fno_*), QHD on the finite-difference box mesh of the
+ * analog implementation (qhd_lattice_*, its own context and fixed-point state)
+ * and an arithmetic throughput probe (qhd_probe_alu_rates).
+ *
+ * Conventions shared by every entry point (the box mesh states its own state
+ * format)
  * ---------------------------------------
  * - Arrays are row-major with the LAST axis fastest.  The grid point with
  *   multi-index (j_0, ..., j_{d-1}) sits at x_k = lo[k] + j_k (hi[k]-lo[k]) / n[k].
