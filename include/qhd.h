@@ -36,7 +36,8 @@
  *   qhd_observables and qhd_destroy synchronise that stream; the other calls
  *   only enqueue.
  * - Every call returns a qhd_status; no exception crosses the ABI.  A failed
- *   argument check leaves the context unchanged.  A CUDA error or a device
+ *   argument check leaves the context unchanged (except a rejected potential,
+ *   which discards the previous one).  A CUDA error or a device
  *   time-out makes the context sticky-failed: later calls return the same
  *   status until qhd_destroy.  qhd_last_error() gives the message.
  * - One context must not be used from two host threads at once.
@@ -131,7 +132,9 @@ qhd_status qhd_init_grid(qhd_ctx **out, int ndim, const int64_t *n, const double
  * workspace (FP64 for E[f], plus a 32-bit fixed-point copy with a per-instance
  * power-of-two scale used for the potential phase), finds the grid minimiser x*.
  * Every value must be finite and max f - min f < 2^31 per instance, else
- * QHD_ERR_INVALID_ARG.  Synchronises the stream.
+ * QHD_ERR_INVALID_ARG and the previous potential is discarded (evolve and
+ * observables return QHD_ERR_STATE until a valid one is loaded).
+ * Synchronises the stream.
  */
 qhd_status qhd_set_potential(qhd_ctx *ctx, const double *f_host);
 
@@ -450,8 +453,8 @@ qhd_status qhd_fno_destroy(qhd_fno *fno);
  *   the state is set to 0 and the call returns QHD_ERR_INVALID_ARG.
  *   Synchronises the stream.
  * qhd_lattice_set_potential: f_dev = batch*G FP64 on the device (copied);
- *   non-finite values or a range >= 2^31 give QHD_ERR_INVALID_ARG.
- *   Synchronises the stream.
+ *   non-finite values or a range >= 2^31 give QHD_ERR_INVALID_ARG and discard
+ *   the previous potential.  Synchronises the stream.
  * qhd_lattice_set_qp: F(x) = 1/2 x^T Q x + b^T x on the mesh
  *   (Eq. (finite-quadratic-obj)), formed on the device in FP64 from host arrays
  *   Q_host (batch*d*d, row-major per instance; only its symmetric part enters)

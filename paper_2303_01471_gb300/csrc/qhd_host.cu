@@ -409,11 +409,17 @@ static qhd_status set_potential_common(qhd_ctx *c) {
             }
             if (p.fmax > mx) mx = p.fmax;
         }
-        if (nf > 0) return fail(c, QHD_ERR_INVALID_ARG, "instance %lld: %lld non-finite f values", (long long)b,
-                                (long long)nf);
+        // the FP64 copy is already overwritten: a rejected f discards the previous one
+        if (nf > 0) {
+            c->have_f = false;
+            return fail(c, QHD_ERR_INVALID_ARG, "instance %lld: %lld non-finite f values", (long long)b,
+                        (long long)nf);
+        }
         const double range = mx - mn;
-        if (!(range < 2147483648.0))
+        if (!(range < 2147483648.0)) {
+            c->have_f = false;
             return fail(c, QHD_ERR_INVALID_ARG, "instance %lld: f range %g >= 2^31", (long long)b, range);
+        }
         // largest power-of-two scale keeping (f - fmin) * 2^shift below 2^32 - 4096
         int shift = 52;
         if (range > 0.0) {

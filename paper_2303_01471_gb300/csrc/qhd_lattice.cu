@@ -900,12 +900,17 @@ qhd_status lat_potential_common(qhd_lattice *c) {
             }
             if (p.fmax > mx) mx = p.fmax;
         }
-        if (nf > 0)
+        // the FP64 copy is already overwritten: a rejected F discards the previous one
+        if (nf > 0) {
+            c->have_f = false;
             return lfail(c, QHD_ERR_INVALID_ARG, "instance %lld: %lld non-finite f values", (long long)b,
                          (long long)nf);
+        }
         const double range = mx - mn;
-        if (!(range < 2147483648.0))
+        if (!(range < 2147483648.0)) {
+            c->have_f = false;
             return lfail(c, QHD_ERR_INVALID_ARG, "instance %lld: f range %g >= 2^31", (long long)b, range);
+        }
         int shift = 52;
         if (range > 0.0) {
             shift = (int)std::floor(std::log2((4294967296.0 - 4096.0) / range));

@@ -207,6 +207,9 @@ def test_error_paths():
     bad[3] = float("nan")
     with pytest.raises(qhd.QHDError):
         lat.set_potential(bad)
+    with pytest.raises(qhd.QHDError) as e:     # the rejected potential discarded the loaded one
+        lat.evolve(1.0, 0.1)
+    assert e.value.status == 3
     lat.close()
 
 

@@ -367,6 +367,12 @@ def test_error_paths():
     assert e.value.status == 1
     sim.set_potential(np.zeros((16, 16)))
     sim.set_schedule(qhd.Schedule())
+    with pytest.raises(qhd.QHDError):
+        sim.set_potential(f)                 # a rejected potential discards the loaded one
+    with pytest.raises(qhd.QHDError) as e:
+        sim.evolve(1.0, 0.1)
+    assert e.value.status == 3
+    sim.set_potential(np.zeros((16, 16)))
     sim.reset_state()
     for T, dt in [(1.0, 0.3), (1.0, 0.0), (-1.0, 0.1), (float("nan"), 0.1)]:
         with pytest.raises(qhd.QHDError) as e:
