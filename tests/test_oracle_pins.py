@@ -273,6 +273,52 @@ def test_lie_trotter_is_first_order():
     assert 1.9 < errs[0] / errs[1] < 2.1 and 1.9 < errs[1] / errs[2] < 2.1, errs
 
 
+def commuting_closed_form(psi0, c, A, B, lo, hi):
+    """Exact map of i dpsi/dt = [a(t)(-Lap/2) + b(t) c] psi for a constant objective
+    f = c, whose two terms commute: psi(T) = e^{-i c B} F^-1[e^{-i A |k|^2/2} F psi0]
+    with A = int a, B = int b (numpy's FFT, k = 2 pi m / L)."""
+    psi_k = np.fft.fftn(psi0)
+    k2 = 0.0
+    for ax, n in enumerate(psi0.shape):
+        k = 2.0 * np.pi * np.fft.fftfreq(n, d=(hi - lo) / n)
+        sh = [1] * psi0.ndim
+        sh[ax] = n
+        k2 = k2 + (k ** 2).reshape(sh)
+    return np.exp(-1j * c * B) * np.fft.ifftn(np.exp(-1j * A * k2 / 2.0) * psi_k)
+
+
+@pytest.mark.parametrize("shape", [(64,), (32, 16)])
+def test_lie_trotter_samples_the_left_end_point(shape):
+    """Eq. (prod_qhd) takes a_j = e^{phi(js)}, b_j = e^{chi(js)} at the left end of
+    each step.  With a constant objective the potential and kinetic factors commute,
+    so the product formula is exact for whatever times it samples: the result must
+    be the closed form with A = sum_j dt a(t0 + j dt), B = sum_j dt b(t0 + j dt).
+    The midpoint or right-end sums give states far from it, so a misread sampling
+    time fails here (the order test alone cannot tell them apart)."""
+    rng = np.random.default_rng(3)
+    lo, hi = -4.0, 4.0
+    psi0 = rng.normal(size=shape) + 1j * rng.normal(size=shape)
+    psi0 /= np.linalg.norm(psi0)
+    c = 0.7
+    f = np.full(shape, c)
+    t0, dt, n = 0.6, 0.05, 24
+    sched = Schedule()
+    def sums(offset):
+        ab = [oracle.schedule_ab(sched, t0 + (j + offset) * dt) for j in range(n)]
+        return dt * sum(a for a, _ in ab), dt * sum(b for _, b in ab)
+    got = oracle.evolve_trotter(f, psi0, t0, dt, n, lo=lo, hi=hi)
+    left = commuting_closed_form(psi0, c, *sums(0.0), lo, hi)
+    assert np.max(np.abs(got - left)) <= 1e-10
+    for offset in (0.5, 1.0):
+        other = commuting_closed_form(psi0, c, *sums(offset), lo, hi)
+        assert np.max(np.abs(got - other)) > 1e-2
+    # Strang (Eq. (prod_qhd) in symmetric form, midpoint coefficients) is exact
+    # here too, with the midpoint sums
+    strang = oracle.evolve(f, psi0, t0, dt, n, sched, lo=lo, hi=hi)
+    mid = commuting_closed_form(psi0, c, *sums(0.5), lo, hi)
+    assert np.max(np.abs(strang - mid)) <= 1e-10
+
+
 # ----------------------------------------------- P8 reversal, P9 dilation
 
 def test_time_reversal_returns_initial_state():
