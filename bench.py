@@ -125,9 +125,9 @@ class Clocks:
 def device_record(dev):
     """SM count, L2 size and the measured arithmetic rates of the device the bench ran on."""
     import torch
-    from paper_2303_01471_gb300 import qhd
+    from paper_2303_01471_gb300 import probe
     p = torch.cuda.get_device_properties(dev)
-    rates = qhd.probe_alu_rates()
+    rates = probe.alu_rates()
     return {"name": p.name, "sms": p.multi_processor_count,
             "l2_bytes": getattr(p, "L2_cache_size", None),
             "measured": {"fp32_fma_per_s": rates[0], "int64_mad_per_s": rates[1],
@@ -418,7 +418,8 @@ def run_simqhd(args, rank, world, local_rank, dist):
     n = r + 1
     hh, mm = n // 2, n - n // 2
     mads_pp_axis = 3.0 * (mm * mm + hh * hh) / n
-    ffma_rate, imad_rate, _, _ = qhd.probe_alu_rates()
+    from paper_2303_01471_gb300 import probe
+    ffma_rate, imad_rate, _, _ = probe.alu_rates()
     axes = {"pass0": 3, "pass1": 2}
     kernels, best = [], None
     for cls in ("pass0", "pass1"):

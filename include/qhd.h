@@ -19,8 +19,7 @@
  * Further families in this header: the spectrum of H(t) (qhd_apply_hamiltonian,
  * qhd_lowest_eigenpairs), the tensor-core DFT form (qhd_set_transform), the
  * learned surrogate (qhd_fno_*), QHD on the finite-difference box mesh of the
- * analog implementation (qhd_lattice_*, its own context and fixed-point state)
- * and an arithmetic throughput probe (qhd_probe_alu_rates).
+ * analog implementation (qhd_lattice_*, its own context and fixed-point state).
  *
  * Conventions shared by every entry point (the box mesh states its own state
  * format)
@@ -518,14 +517,19 @@ int64_t qhd_lattice_launch_count(const qhd_lattice *lat);
 const char *qhd_lattice_last_error(const qhd_lattice *lat);
 qhd_status qhd_lattice_destroy(qhd_lattice *lat);
 
-/* Arithmetic throughput of the current device (no paper counterpart; used to
- * state roofline peaks): timed loops of independent operations on every SM.
- * out (4 doubles): [0] FP32 FMAs/s, [1] 32 x 32 -> 64-bit integer
- * multiply-adds/s, [2] FP64 FMAs/s, [3] hardware sine approximations/s.
- * Allocates nothing; runs on the legacy default stream and synchronises it.
- * Errors: QHD_ERR_INVALID_ARG for a NULL out, QHD_ERR_CUDA for a failed launch
- * or event. */
-qhd_status qhd_probe_alu_rates(double *out);
+
+/* Failure injection for tests of the error contract above (no counterpart in
+ * the paper).  With kind = QHD_ERR_CUDA or QHD_ERR_TIMEOUT, the after-th
+ * checked CUDA call of this context from now on (a kernel launch, a copy or a
+ * stream synchronisation, counted across entry points, after >= 1) is not
+ * issued: the entry point that reaches it fails with `kind` exactly as if the
+ * runtime had reported an error or a bounded device wait had given up, so the
+ * context becomes sticky-failed and every later call except qhd_destroy
+ * returns `kind`.  Work enqueued before that call stays enqueued; nothing
+ * reaches the GPU in a failed state.  kind = QHD_OK cancels a pending
+ * injection.  Errors: QHD_ERR_INVALID_ARG for another kind or after < 1; a
+ * context that is already sticky-failed returns its status. */
+qhd_status qhd_inject_failure(qhd_ctx *ctx, int kind, int64_t after);
 
 /* Synchronise the stream and free the host-side context (never the caller's
  * buffers).  NULL is accepted. */

@@ -3,7 +3,10 @@
 The translation units compile in parallel; the result is
 paper_2303_01471_gb300/_lib/libqhd.so, a plain C ABI (include/qhd.h) with
 the CUDA runtime linked statically and cuBLAS (the tensor-core transform's
-GEMMs) linked dynamically from the toolkit.
+GEMMs) linked dynamically from the toolkit.  The arithmetic throughput probe
+that the benchmark uses to state roofline peaks is built beside it as its own
+library, _lib/libqhd_probe.so (include/qhd_probe.h), outside the simulator's
+ABI.
 """
 from __future__ import annotations
 
@@ -18,7 +21,9 @@ CSRC = os.path.join(PKG, "csrc")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libqhd.so")
 SOURCES = ["qhd_kernels.cu", "qhd_plane.cu", "qhd_host.cu", "qhd_static.cu", "qhd_tcdft.cu", "qhd_fno.cu", "qhd_spectrum.cu",
-           "qhd_lattice.cu", "qhd_probe.cu"]
+           "qhd_lattice.cu"]
+PROBE_SOURCE = "qhd_probe.cu"
+PROBE_LIB = os.path.join(LIBDIR, "libqhd_probe.so")
 HEADERS = ["qhd_device.cuh", "qhd_kernels.h", "qhd_plane.cuh", "qhd_tcdft.h", "qhd_spectrum.h", "qhd_sched.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -33,11 +38,12 @@ def _nvcc() -> str:
 
 
 def _stale() -> bool:
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or not os.path.exists(PROBE_LIB):
         return True
     t = os.path.getmtime(LIB)
-    deps = [os.path.join(CSRC, s) for s in SOURCES + HEADERS]
+    deps = [os.path.join(CSRC, s) for s in SOURCES + HEADERS + [PROBE_SOURCE]]
     deps.append(os.path.join(ROOT, "include", "qhd.h"))
+    deps.append(os.path.join(ROOT, "include", "qhd_probe.h"))
     deps.append(os.path.abspath(__file__))
     return any(os.path.getmtime(d) > t for d in deps)
 
@@ -69,16 +75,20 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None, out: str
             sys.stderr.write(r.stderr)
         return obj
 
-    with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(compile_one, SOURCES))
-    tmp = target + ".tmp"
+    with ThreadPoolExecutor(max_workers=len(SOURCES) + 1) as ex:
+        objs = list(ex.map(compile_one, SOURCES + [PROBE_SOURCE]))
     cudalib = os.path.join(_cuda_home(), "lib64")
-    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static", "-L" + cudalib, "-lcublas",
-           "-Xlinker", "-rpath," + cudalib]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, target)
+
+    def link(out_path, objects, extra):
+        tmp = out_path + ".tmp"
+        cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objects, "-cudart", "static", *extra]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+        os.replace(tmp, out_path)
+
+    link(target, objs[:-1], ["-L" + cudalib, "-lcublas", "-Xlinker", "-rpath," + cudalib])
+    link(os.path.join(libdir, "libqhd_probe.so"), objs[-1:], [])
     return target
 
 

@@ -87,12 +87,8 @@ __device__ __forceinline__ float2 twiddle_const(float2 v, int k) {
     const double cd = cos64(k * (64 / R));
     const double sd = INV ? sin64(k * (64 / R)) : -sin64(k * (64 / R));
     const float ch = (float)cd, sh = (float)sd;
-#ifdef QHD_PLAIN_CONST_TWIDDLES
-    return make_float2(v.x * ch - v.y * sh, v.x * sh + v.y * ch);
-#else
     const float cl = (float)(cd - (double)ch), sl = (float)(sd - (double)sh);
     return cmul_comp(v, make_float2(ch, sh), make_float2(cl, sl));
-#endif
 }
 
 // -------------------------------------------------------- in-register DFT
@@ -264,11 +260,7 @@ __device__ __forceinline__ void line_fft(float2 *x, float2 *sm, int t, const flo
             for (int m = 1; m < R2; ++m) {
                 const float4 w = __ldg(&tw2[m * R1 + j]);
                 const float2 hi = make_float2(w.x, w.y), lo = make_float2(w.z, w.w);
-#ifdef QHD_PLAIN_TABLE_TWIDDLES
-                v[m] = INV ? cmulc(v[m], hi) : cmul(v[m], hi);
-#else
                 v[m] = INV ? cmulc_comp(v[m], hi, lo) : cmul_comp(v[m], hi, lo);
-#endif
             }
             dft<R2, INV>(v);
 #pragma unroll

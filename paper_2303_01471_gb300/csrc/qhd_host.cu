@@ -139,6 +139,10 @@ struct qhd_ctx {
     int64_t launches = 0;
     qhd_status sticky = QHD_OK;
     std::string err;
+    // failure injection (qhd_inject_failure): the inject_after-th checked CUDA
+    // call from now on is not issued and reports inject_kind instead
+    qhd_status inject_kind = QHD_OK;
+    int64_t inject_after = 0;
     std::vector<InstDev> inst_host;
     // host copy of the schedules (spectrum: a(t), b(t) on the host)
     struct HostSched {
@@ -188,14 +192,26 @@ qhd_status cuda_fail(qhd_ctx *c, cudaError_t e, const char *where) {
     return fail(c, QHD_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
 }
 
+// True when an injected failure is due at this checked call; the call is then
+// skipped and the context fails as the injection asked.
+bool injected(qhd_ctx *c) {
+    if (c->inject_kind == QHD_OK || --c->inject_after > 0) return false;
+    const qhd_status k = c->inject_kind;
+    c->inject_kind = QHD_OK;
+    fail(c, k, "injected failure (%s)", k == QHD_ERR_TIMEOUT ? "device time-out" : "CUDA call");
+    return true;
+}
+
 #define QHD_CUDA(c, call)                                        \
     do {                                                         \
+        if (injected(c)) return (c)->sticky;                     \
         cudaError_t e_ = (call);                                 \
         if (e_ != cudaSuccess) return cuda_fail((c), e_, #call); \
     } while (0)
 
 #define QHD_LAUNCH(c, call)                                      \
     do {                                                         \
+        if (injected(c)) return (c)->sticky;                     \
         cudaError_t e_ = (call);                                 \
         if (e_ != cudaSuccess) return cuda_fail((c), e_, #call); \
         (c)->launches++;                                         \
@@ -336,12 +352,10 @@ qhd_status qhd_init_grid(qhd_ctx **out, int ndim, const int64_t *n, const double
         c->plane_mode = 2;
         dist_axis = 0;
     }
-#ifndef QHD_NO_PLANE3D
     else if (ndim == 3 && plane_supported((int)n[1], (int)n[2])) {
         c->plane_mode = 3;
         dist_axis = 1;
     }
-#endif
     std::vector<float4> twx((size_t)c->ksum, make_float4(0.f, 0.f, 0.f, 0.f));
     if (dist_axis >= 0) {
         const int n1 = (int)n[dist_axis], cc = plane_cluster(n1), rr = n1 / cc;
@@ -953,6 +967,17 @@ qhd_status qhd_timing_read(qhd_ctx *c, double *ms_out, int64_t *launches_out, in
         }
         c->timed.clear();
     }
+    return QHD_OK;
+}
+
+qhd_status qhd_inject_failure(qhd_ctx *c, int kind, int64_t after) {
+    qhd_status s = check_ctx(c);
+    if (s != QHD_OK) return s;
+    if (kind != QHD_ERR_CUDA && kind != QHD_ERR_TIMEOUT && kind != QHD_OK)
+        return fail(c, QHD_ERR_INVALID_ARG, "injected status must be QHD_ERR_CUDA, QHD_ERR_TIMEOUT or QHD_OK");
+    if (kind != QHD_OK && after < 1) return fail(c, QHD_ERR_INVALID_ARG, "after must be >= 1");
+    c->inject_kind = (qhd_status)kind;
+    c->inject_after = after;
     return QHD_OK;
 }
 

@@ -8,7 +8,7 @@
 // SM, timed with CUDA events.
 #include <cuda_runtime.h>
 
-#include "qhd.h"
+#include "qhd_probe.h"
 
 namespace {
 
@@ -76,19 +76,20 @@ __global__ void __launch_bounds__(PROBE_THREADS) k_probe_sfu(float *out, float a
 
 }  // namespace
 
-extern "C" qhd_status qhd_probe_alu_rates(double *out) {
-    if (!out) return QHD_ERR_INVALID_ARG;
+extern "C" int qhd_probe_alu_rates(double *out) {
+    constexpr int OK = 0, ERR_INVALID_ARG = 1, ERR_CUDA = 4;
+    if (!out) return ERR_INVALID_ARG;
     int dev = 0, sms = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return QHD_ERR_CUDA;
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return QHD_ERR_CUDA;
+    if (cudaGetDevice(&dev) != cudaSuccess) return ERR_CUDA;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return ERR_CUDA;
     const int blocks = sms * 16;
     const size_t n = (size_t)blocks * PROBE_THREADS;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    qhd_status st = QHD_OK;
+    int st = OK;
     float ms[4] = {0.f, 0.f, 0.f, 0.f};
-    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) st = QHD_ERR_CUDA;
-    for (int kind = 0; kind < 4 && st == QHD_OK; ++kind) {
-        for (int rep = 0; rep < 2 && st == QHD_OK; ++rep) {  // the first run warms up
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) st = ERR_CUDA;
+    for (int kind = 0; kind < 4 && st == OK; ++kind) {
+        for (int rep = 0; rep < 2 && st == OK; ++rep) {  // the first run warms up
             cudaEventRecord(e0);
             if (kind == 0) k_probe_ffma<<<blocks, PROBE_THREADS>>>(nullptr, 0.999f, 1e-4f, 0);
             else if (kind == 1) k_probe_imad_wide<<<blocks, PROBE_THREADS>>>(nullptr, 3, 0);
@@ -97,16 +98,16 @@ extern "C" qhd_status qhd_probe_alu_rates(double *out) {
             cudaEventRecord(e1);
             if (cudaGetLastError() != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
                 cudaEventElapsedTime(&ms[kind], e0, e1) != cudaSuccess)
-                st = QHD_ERR_CUDA;
+                st = ERR_CUDA;
         }
     }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
-    if (st != QHD_OK) return st;
+    if (st != OK) return st;
     const double ops = (double)n * PROBE_ITERS * 8;
     out[0] = ops / (ms[0] * 1e-3);        // FP32 FMAs per second
     out[1] = ops / (ms[1] * 1e-3);        // 32x32->64 integer multiply-adds per second
     out[2] = ops / 8 / (ms[2] * 1e-3);    // FP64 FMAs per second
     out[3] = ops / (ms[3] * 1e-3);        // hardware sine approximations per second
-    return QHD_OK;
+    return OK;
 }

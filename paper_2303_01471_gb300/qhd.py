@@ -37,7 +37,7 @@ EXPORTS = ["qhd_workspace_bytes", "qhd_init_grid", "qhd_set_potential", "qhd_set
            "qhd_lattice_reset_state", "qhd_lattice_get_state", "qhd_lattice_set_state", "qhd_lattice_evolve",
            "qhd_lattice_evolve_trajectory", "qhd_lattice_observables",
            "qhd_lattice_timing_enable", "qhd_lattice_timing_read", "qhd_lattice_launch_count",
-           "qhd_lattice_last_error", "qhd_lattice_destroy", "qhd_probe_alu_rates"]
+           "qhd_lattice_last_error", "qhd_lattice_destroy", "qhd_inject_failure"]
 SPLIT_STRANG = 0
 SPLIT_LIE_TROTTER = 1
 KINETIC_SPECTRAL = 0
@@ -137,8 +137,8 @@ def load(build_if_missing: bool = True):
     lib.qhd_set_transform.restype = st
     lib.qhd_library_call_count.argtypes = [vp]
     lib.qhd_library_call_count.restype = ctypes.c_int64
-    lib.qhd_probe_alu_rates.argtypes = [dp]
-    lib.qhd_probe_alu_rates.restype = st
+    lib.qhd_inject_failure.argtypes = [vp, ctypes.c_int, ctypes.c_int64]
+    lib.qhd_inject_failure.restype = st
     lib.qhd_destroy.argtypes = [vp]
     lib.qhd_destroy.restype = st
     lib.qhd_status_string.argtypes = [st]
@@ -206,17 +206,6 @@ def need_tensor(t, dtype, numel: int, what: str) -> None:
     if not (t.is_cuda and t.dtype == dtype and t.numel() == numel and t.is_contiguous()):
         raise ValueError(f"{what}: need a contiguous CUDA {dtype} tensor with {numel} values, "
                          f"got {t.dtype} with {t.numel()} on {t.device}")
-
-
-def probe_alu_rates():
-    """Measured on the current device: (FP32 FMAs/s, 32x32->64-bit integer
-    multiply-adds/s, FP64 FMAs/s, hardware sine approximations/s)."""
-    lib = load()
-    out = (ctypes.c_double * 4)()
-    st = lib.qhd_probe_alu_rates(out)
-    if st != QHD_OK:
-        raise QHDError(st, "qhd_probe_alu_rates failed")
-    return tuple(out)
 
 
 def workspace_bytes(shape: Sequence[int], batch: int = 1) -> int:

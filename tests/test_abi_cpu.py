@@ -12,10 +12,10 @@ from paper_2303_01471_gb300 import qhd
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def declared_entry_points():
+def declared_entry_points(header=None):
     names = set()
     for fn in os.listdir(os.path.join(ROOT, "include")):
-        if fn.endswith(".h"):
+        if fn.endswith(".h") and (header is None and fn != "qhd_probe.h" or fn == header):
             src = open(os.path.join(ROOT, "include", fn)).read()
             src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
             names |= set(re.findall(r"\b(qhd_[a-z_0-9]+)\s*\(", src))
@@ -101,8 +101,13 @@ def test_lattice_sizes_and_argument_checks_without_a_device(lib):
     assert lib.qhd_lattice_launch_count(None) == 0
 
 
-def test_probe_rejects_null_output_without_a_device(lib):
-    assert lib.qhd_probe_alu_rates(None) == 1
+def test_probe_library_is_separate_and_rejects_null_output_without_a_device(lib):
+    from paper_2303_01471_gb300 import probe
+    plib = probe.load()
+    for n in declared_entry_points("qhd_probe.h"):
+        assert hasattr(plib, n), n
+        assert not hasattr(lib, n), n      # not part of the simulator's ABI
+    assert plib.qhd_probe_alu_rates(None) == 1
 
 
 def test_bindings_reject_tensors_they_cannot_pass_as_raw_pointers():
