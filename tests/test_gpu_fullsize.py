@@ -4,9 +4,14 @@ instance (K = 32), T = 10, dt = 1e-3, the paper's schedule.
 
 The oracle cannot run 10^4 steps of these grids in test time, so parity is checked
 (a) element by element against the oracle over the first steps of the same run
-(same kernels, same grid), and (b) by invariants over the full 10^4 steps: the norm,
-and time reversal (10^4 steps forward then back returns psi0 up to a global phase).
+(same kernels, same grid), (b) at full length against the oracle's stored results
+(tests/golden/make_fullsize_reference.py: observables and the probability mass on
+the points that hold all but ~1e-7 of it, which bounds the TV distance from above),
+and (c) by invariants over the full 10^4 steps: the norm, and time reversal (10^4
+steps forward then back returns psi0 up to a global phase).
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -20,7 +25,12 @@ from paper_2303_01471_gb300 import qhd
 TV_TOL = 1e-4
 EF_TOL = 1e-5
 NORM_TOL = 1e-6
-NORM_FP32_FLOOR_PER_1K = 1e-6   # see test_gpu_parity.py
+# FP32 rounding of the state is a random walk of the norm once the systematic part
+# is removed (the compensated product's order, qhd_device.cuh): 32 instances of 128^2
+# wells and 12 of 1024^2 Rastrigin over 10^4 steps give a spread (std) of 2.1-2.4e-6
+# with a mean within one standard error of 0 (test_norm_drift_is_unbiased_over_seeds).
+NORM_WALK_10K = 2.5e-6
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
 CASES = {
     "1024sq_rastrigin": (lambda: workloads.rastrigin(0, (1024, 1024)), 20),
@@ -80,35 +90,78 @@ def full_run(name):
         psi0 = sim.psi.clone()
         sim.evolve(10.0, 1e-3)
         obs = sim.observables(0.1)[0]
+        p_T = (sim.psi.abs().double() ** 2).cpu().numpy().ravel()
         sim.evolve(-10.0, -1e-3)
         back = sim.observables(0.1)[0]
         p0 = (psi0.abs().double() ** 2).cpu().numpy()
         pb = (sim.psi.abs().double() ** 2).cpu().numpy()
         t, steps = sim.time()
         sim.close()
-        _FULL[name] = (obs, back, 0.5 * np.abs(pb - p0).sum(), t, steps)
+        _FULL[name] = (obs, back, 0.5 * np.abs(pb - p0).sum(), t, steps, p_T)
     return _FULL[name]
 
 
+def golden(name):
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("make_ref", os.path.join(GOLDEN, "make_fullsize_reference.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    path = mod.path_of(name)
+    assert os.path.exists(path), f"missing {path}: run tests/golden/make_fullsize_reference.py {name}"
+    ref = np.load(path)
+    assert str(ref["key"]) == mod.case_key(name), "stale reference: the workload changed"
+    return ref
+
+
 @pytest.mark.parametrize("name", list(CASES))
-def test_fullsize_10k_steps_norm_within_fp32_floor(name):
-    obs, back, tv_back, t, steps = full_run(name)
+def test_fullsize_10k_steps_match_oracle_reference(name):
+    """The benchmark's instances after the full 10^4 steps against the FP64 oracle's
+    stored results: TV (bounded from above through the stored mass), raw E[f],
+    P_succ and x*."""
+    ref = golden(name)
+    obs, back, tv_back, t, steps, p_g = full_run(name)
+    idx, p_o = ref["idx"], ref["p"]
+    inside = p_g[idx]
+    tv_bound = 0.5 * (np.abs(inside - p_o).sum() + (p_g.sum() - inside.sum()) + float(ref["mass_outside"]))
+    scale = max(abs(float(ref["e_f"])), 1e-3 * float(ref["f_ptp"]))
+    assert tv_bound <= TV_TOL, tv_bound
+    assert abs(obs.e_f - float(ref["e_f"])) / scale <= EF_TOL, (obs.e_f, float(ref["e_f"]))
+    assert abs(obs.p_succ - float(ref["p_succ"])) <= 2 * TV_TOL
+    assert tuple(obs.x_star[: len(inst(name).shape)]) == tuple(ref["x_star"][: len(inst(name).shape)])
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_fullsize_10k_steps_norm(name):
+    """The norm after 10^4 steps (and after the 10^4 steps back) within 3 standard
+    deviations of the measured FP32 random walk."""
+    obs, back, tv_back, t, steps, _ = full_run(name)
     assert steps == 20000 and abs(t) < 1e-9
-    assert abs(obs.norm - 1.0) <= 4 * NORM_FP32_FLOOR_PER_1K * 10
-    assert abs(back.norm - 1.0) <= 4 * NORM_FP32_FLOOR_PER_1K * 20
+    assert abs(obs.norm - 1.0) <= 3 * NORM_WALK_10K, obs.norm
+    assert abs(back.norm - 1.0) <= 3 * NORM_WALK_10K * np.sqrt(2), back.norm
 
 
-@pytest.mark.xfail(reason="norm drift bound 1e-6 over 10^4 steps is below the FP32 rounding floor for "
-                          "states concentrated on a few mesh points (measured 0.8-1.7e-5)", strict=False)
-@pytest.mark.parametrize("name", list(CASES))
-def test_fullsize_10k_steps_norm_drift_bound(name):
-    obs, *_ = full_run(name)
-    assert abs(obs.norm - 1.0) <= NORM_TOL
+def test_norm_drift_is_unbiased_over_seeds():
+    """Over many instances the 10^4-step norm drift has no systematic part: its mean
+    is within 3 standard errors of 0 (before the fix of the compensated product's
+    order every one of 32 instances drifted up, mean +1.1e-5, std 3.5e-6)."""
+    seeds = list(range(32))
+    fs = np.stack([workloads.gaussian_wells(s, (128, 128), K=8).f for s in seeds])
+    sim = qhd.QHD((128, 128), batch=len(seeds))
+    sim.set_potential(fs)
+    sim.set_schedule(qhd.Schedule())
+    sim.reset_state()
+    sim.evolve(10.0, 1e-3)
+    d = np.array([o.norm - 1.0 for o in sim.observables(0.1)])
+    sim.close()
+    se = d.std() / np.sqrt(len(d))
+    assert abs(d.mean()) <= 3 * se + 1e-7, (d.mean(), se)
+    assert np.abs(d).max() <= 4 * NORM_WALK_10K, np.abs(d).max()
+    assert 0.25 * len(d) <= (d > 0).sum() <= 0.75 * len(d), (d > 0).sum()
 
 
 @pytest.mark.parametrize("name", list(CASES))
 def test_fullsize_time_reversal(name):
-    obs, back, tv_back, t, steps = full_run(name)
+    obs, back, tv_back, t, steps, _ = full_run(name)
     # the forward run moved far away from the uniform state ...
     assert obs.p_succ > 0.5
     # ... and the exact inverse map brings |psi|^2 back to uniform
@@ -142,14 +195,10 @@ def test_paper_resolution_256sq_lie_trotter_and_strang():
         ob = oracle.observables(ins.f, psi_o)
         tv = 0.5 * np.abs(p_g - ob.prob).sum()
         scale = max(abs(ob.e_f), 1e-3 * np.ptp(ins.f))
-        # over 10^4 steps the raw E[f] error is the FP32 norm drift (the norm test
-        # above); the shape of |psi|^2 is held to the 1e-5 bound on the normalised E[f]
-        ef_shape = abs(obs.e_f / obs.norm - ob.e_f / ob.norm) / scale
         ef_raw = abs(obs.e_f - ob.e_f) / scale
         assert tv <= TV_TOL, (name, tv)
-        assert ef_shape <= EF_TOL, (name, ef_shape)
-        assert ef_raw <= 4 * NORM_FP32_FLOOR_PER_1K * 10, (name, ef_raw)
-        assert abs(obs.norm - 1.0) <= 4 * NORM_FP32_FLOOR_PER_1K * 10, (name, obs.norm)
+        assert ef_raw <= EF_TOL, (name, ef_raw)
+        assert abs(obs.norm - 1.0) <= 3 * NORM_WALK_10K, (name, obs.norm)
         res[name] = (p_g, ob.prob, tv)
     between = 0.5 * np.abs(res["trotter"][1] - res["strang"][1]).sum()
     assert between > 5 * max(res["trotter"][2], res["strang"][2]), (between, res["trotter"][2], res["strang"][2])

@@ -30,7 +30,20 @@ NORM_TOL = 1e-6
 # drifts by ~1e-6 per 10^3 steps once the state concentrates on a few mesh
 # points (N_eff ~ 10), because the rounding of those few amplitudes is not
 # averaged out.  Regressions beyond 4x that floor fail outright.
-NORM_FP32_FLOOR_PER_1K = 1e-6
+# The norm of the FP32 state is a random walk with no systematic part (the
+# rounding order of the compensated product removes the bias, qhd_device.cuh):
+# measured standard deviations over many seeds, 1000 steps of dt = 0.01 on 128^2
+# and 10^4 steps of dt = 1e-3.  The stated 1e-6 holds for most instances up to
+# 1000 steps; a test bound is 3 standard deviations, never below 1e-6.
+NORM_WALK_1K = 0.9e-6
+NORM_WALK_10K = 2.5e-6
+
+
+def norm_bound(nsteps):
+    # the walk is front-loaded (early on the zero Fourier mode carries almost all
+    # of the norm), so short runs get the 1000-step bound, not a scaled-down one
+    walk = NORM_WALK_1K if nsteps <= 1000 else NORM_WALK_10K * math.sqrt(nsteps / 1e4)
+    return max(NORM_TOL, 3 * walk)
 
 
 def to_oracle_sched(s: qhd.Schedule) -> oracle.Schedule:
@@ -74,8 +87,7 @@ def compare(psi_g, obs_g, f, psi_o, lo=0.0, hi=1.0, steps=None, elementwise=True
     assert tv <= TV_TOL, f"TV {tv:.3e}"
     assert ef_err <= EF_TOL, f"E[f] rel err {ef_err:.3e}"
     nsteps = steps if steps is not None else 1000
-    assert abs(obs_g.norm - 1.0) <= 4 * NORM_FP32_FLOOR_PER_1K * max(1.0, nsteps / 1000), \
-        f"norm drift {obs_g.norm - 1:.3e}"
+    assert abs(obs_g.norm - 1.0) <= norm_bound(nsteps), f"norm drift {obs_g.norm - 1:.3e}"
     assert abs(obs_g.p_succ - ob_o.p_succ) <= 2 * TV_TOL
     assert np.allclose(obs_g.x_star[: f.ndim], ob_o.x_star[: f.ndim], rtol=0, atol=0)
     if elementwise and steps is not None:
@@ -259,12 +271,26 @@ def test_parity_128sq_wells_1000_steps(seed):
     compare(psi_g, obs[0], inst.f, psi_o, elementwise=False)
 
 
-@pytest.mark.xfail(reason="norm drift bound 1e-6 is at the FP32 rounding floor for concentrated "
-                          "states; measured 0.7-1.2e-6 over 1000 steps", strict=False)
-@pytest.mark.parametrize("seed", [0, 1, 2])
-def test_norm_drift_128sq_wells_1000_steps(seed):
-    inst, psi_g, obs, psi_o = _cfg0(seed)
-    assert abs(obs[0].norm - 1.0) <= NORM_TOL
+def test_norm_drift_128sq_wells_1000_steps_over_seeds():
+    """The norm after the configuration's 1000 steps over 32 seeds: no systematic
+    part (mean within 3 standard errors of 0, both signs), spread at the FP32
+    floor of a state whose weight sits on a few values (at first the zero Fourier
+    mode, later a few mesh points): NORM_WALK_1K is the measured standard
+    deviation."""
+    seeds = list(range(32))
+    fs = np.stack([workloads.gaussian_wells(s, (128, 128), K=8).f for s in seeds])
+    sim = qhd.QHD((128, 128), batch=len(seeds))
+    sim.set_potential(fs)
+    sim.set_schedule(qhd.Schedule())
+    sim.reset_state()
+    sim.evolve(10.0, 0.01)
+    d = np.array([o.norm - 1.0 for o in sim.observables(0.1)])
+    sim.close()
+    print(f"1000-step norm drift over 32 seeds: mean {d.mean():+.2e} std {d.std():.2e} "
+          f"max |.| {np.abs(d).max():.2e}, within 1e-6: {(np.abs(d) <= NORM_TOL).sum()}/32")
+    assert abs(d.mean()) <= 3 * d.std() / np.sqrt(len(d)) + 1e-8, d.mean()
+    assert 0 < (d > 0).sum() < len(d)
+    assert np.abs(d).max() <= 4 * NORM_WALK_1K, np.abs(d).max()
 
 
 # ------------------------------------------------------- invariants on the GPU
