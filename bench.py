@@ -44,9 +44,33 @@ WORKLOAD = ("QHD at scale, complex64, T=10, dt=1e-3 (10^4 Strang steps each): "
 # algorithmic bytes per grid point per launch of each pass (psi read+write,
 # plus the 32-bit fixed-point potential in the pass that applies it)
 BYTES_PER_POINT = {"row": 20, "axis1_fwd": 16, "axis0": 16, "axis1_inv": 16, "plane": 20}
-# DRAM bytes (read + write) of one launch, from one ncu capture of the current
-# kernel (profiles/k_plane_pass_256cube_full.md); drop an entry when its kernel changes
-TRAFFIC_PER_LAUNCH = {("plane", "256x256x256"): 201498112 + 77571072}
+# DRAM bytes (read + write) of one launch from an ncu capture (not measured by
+# this run), with the SHA-256 (first 16 hex digits) of the kernel sources it was
+# taken on; bench lines carry the figure only while those sources are unchanged.
+TRAFFIC_PER_LAUNCH = {("plane", "256x256x256"): {"bytes": 201498112 + 77571072, "sources_sha16": None,
+                                                  "captured": "ncu --set full, 2 launches, 256^3 wells"}}
+TRAFFIC_SOURCES = ["paper_2303_01471_gb300/csrc/qhd_plane.cu", "paper_2303_01471_gb300/csrc/qhd_plane.cuh",
+                   "paper_2303_01471_gb300/csrc/qhd_device.cuh"]
+
+
+def sources_sha16(paths=TRAFFIC_SOURCES) -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_entry(kernel: str, instance: str):
+    """(bytes, note) of the recorded capture, or (None, why) when there is none or
+    the kernel sources changed since it was taken."""
+    e = TRAFFIC_PER_LAUNCH.get((kernel, instance))
+    if e is None:
+        return None, "no ncu capture recorded for this kernel"
+    if e["sources_sha16"] != sources_sha16():
+        return None, "kernel sources changed since the recorded ncu capture"
+    return e["bytes"], f"from an earlier ncu capture ({e['captured']}), not measured in this run"
 
 
 def peaks():
@@ -218,10 +242,7 @@ def run_ours(args, rank, world, local_rank, dist):
         one_step()
     torch.cuda.synchronize()
 
-    # ---------------- timed region: device-resident inputs
-    for sim in sims:
-        sim.timing_read(reset=True)
-        sim.timing_enable(16)
+    # ---------------- timed region: device-resident inputs, no per-launch events
     launches0 = sum(s.launch_count() for s in sims)
     step_ms = []
     barrier()
@@ -242,10 +263,18 @@ def run_ours(args, rank, world, local_rank, dist):
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     launches = sum(s.launch_count() for s in sims) - launches0
+    total_ms = max_over_ranks(float(sum(step_ms)), dist, dev)
+    # ---------------- one instrumented step after the timed region: CUDA events
+    # around every 16th launch of each kernel class give the per-kernel durations
+    for sim in sims:
+        sim.timing_read(reset=True)
+        sim.timing_enable(16)
+    flush.random_(0, 255)
+    one_step()
+    torch.cuda.synchronize()
     timing = [s.timing_read(reset=True) for s in sims]
     for sim in sims:
         sim.timing_enable(0)
-    total_ms = max_over_ranks(float(sum(step_ms)), dist, dev)
     ms_per_step = total_ms / args.steps
     value = whole_job_rate(pts_per_step, world, ms_per_step / 1e3)
 
@@ -283,18 +312,20 @@ def run_ours(args, rank, world, local_rank, dist):
     for row in kernels:
         n_launch = nsteps + (1 if row["kernel"] in ("row", "plane") else 0) if row["kernel"] != "prep" else None
         if n_launch is None:
-            n_launch = row["timed_launches"] / args.steps
+            n_launch = row["timed_launches"]
         est.append(row["avg_us"] * 1e-3 * n_launch)
     tot = sum(est)
     for row, e in zip(kernels, est):
         row["share_est"] = round(e / tot, 4) if tot > 0 else None
     dom = max((r for r in kernels if "gbs" in r), key=lambda r: r["share_est"] or 0)
+    traffic, traffic_note = traffic_entry(dom["kernel"], dom["instance"])
     roofline = {"bound": "hbm", "kernel": f"{dom['kernel']} pass, {dom['instance']}",
                 "achieved": dom["gbs"], "peak": peak, "unit": "GB/s",
                 "frac": round(dom["gbs"] / peak, 4), "peak_source": peak_src,
-                "traffic": TRAFFIC_PER_LAUNCH.get((dom["kernel"], dom["instance"])),
-                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch",
-                "algorithmic_bytes_per_launch": dom["bytes_per_launch"]}
+                "traffic": traffic,
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch; " + traffic_note,
+                "algorithmic_bytes_per_launch": dom["bytes_per_launch"],
+                "timing": "CUDA events around every 16th launch of each class, in one step run after the timed region"}
 
     result = {
         "metric": METRIC, "value": value, "unit": "grid-point Strang steps/s",
@@ -319,12 +350,15 @@ def run_ours(args, rank, world, local_rank, dist):
     }
     if args.profile_T is not None:
         result["profiling_run"] = f"evolutions shortened to T={t_end}: not a bench value"
+    for sim in sims:
+        sim.close()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, cores, sample = oracle_sample(insts, budget_s=args.cpu_budget)
         result["cpu_baseline"] = {"value": v, "unit": "grid-point Strang steps/s", "cores": cores,
                                   "kind": "oracle", "sample": sample}
-    for sim in sims:
-        sim.close()
+    if world == 1 and not args.no_configs and args.profile_T is None:
+        # the other configurations, each device-timed with its own parity and roofline
+        result["configs"] = {"c1": c1_plain(args, dev, rank), "c3": c3_ragged(args, dev, rank)}
     return result
 
 
@@ -373,8 +407,6 @@ def run_simqhd(args, rank, world, local_rank, dist):
     for _ in range(args.warmup):
         one_step()
     torch.cuda.synchronize()
-    lat.timing_read(reset=True)
-    lat.timing_enable(8)
     launches0 = lat.launch_count()
     step_ms = []
     barrier()
@@ -395,6 +427,12 @@ def run_simqhd(args, rank, world, local_rank, dist):
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     launches = lat.launch_count() - launches0
+    # per-pass durations from one instrumented step after the timed region
+    lat.timing_read(reset=True)
+    lat.timing_enable(8)
+    flush.random_(0, 255)
+    one_step()
+    torch.cuda.synchronize()
     tm = lat.timing_read(reset=True)
     lat.timing_enable(0)
     ms_per_step = max_over_ranks(float(sum(step_ms)), dist, dev) / args.steps
@@ -488,23 +526,100 @@ def run_simqhd(args, rank, world, local_rank, dist):
 
 
 # ------------------------------------------------------------- ragged batch
-RAGGED_WORKLOAD = ("Batched QHD: 4096 instances, 2048 x 128^2 + 2048 x 256^2 on [0,1]^2, families alternating "
-                   "Gaussian wells (K=8) / Rastrigin type, per-instance sigma ~ U(0.5,2) (e^chi = 2 sigma t^3), "
-                   "T=10, dt=0.01 (1000 Strang steps), complex64")
+FLOP_PER_POINT_STEP_2D = {n: 2 * 2 * 5 * int(np.log2(n)) + 12 for n in (64, 128, 256)}  # FFTs + phases
 
 
-def run_ragged(args, rank, world, local_rank, dist):
-    """Every instance of a size class runs in one batched context whose instances stay
-    resident in thread-block clusters for all 1000 steps; the two size classes run
-    concurrently on two streams.  Compared with one context (one launch sequence)
-    per instance on a sample of instances."""
+def timed_ms(fn, stream, reps):
+    """Device time (ms) of fn() on `stream`, CUDA events, one value per repetition."""
+    import torch
+    out = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        out.append(e0.elapsed_time(e1))
+    return out
+
+
+def fp32_peak_flops():
+    """Measured FP32 FMA rate of this GPU (the probe library), as flop/s."""
+    from paper_2303_01471_gb300 import probe
+    return 2.0 * probe.alu_rates()[0]
+
+
+def c1_plain(args, dev, rank):
+    """C1: one 128^2 Gaussian-well instance (K=8) at a time, T=10, dt=0.01 (1000
+    Strang steps), seeds 0..9: the whole run is one launch of one cluster (4 CTAs).
+    Device-timed per seed (set f on the device, reset, evolve, observables),
+    median reported, parity of each seed against the FP64 oracle."""
     import torch
     import oracle
     from paper_2303_01471_gb300 import qhd
+    seeds = list(range(10))
+    n, T, dt = 128, 10.0, 0.01
+    nsteps = int(round(T / dt))
+    insts = [workloads.gaussian_wells(1000 * rank + s, (n, n), K=8) for s in seeds]
+    sim = qhd.QHD((n, n), device=dev)
+    sim.set_schedule(qhd.Schedule())
+    fdev = [torch.from_numpy(i.f).to(dev) for i in insts]
+    prob = torch.empty(n * n, dtype=torch.float32, device=dev)
+    ms, parity = [], []
+    with Clocks(dev.index or 0) as clk:
+        for k, inst in enumerate(insts):
+            def run():
+                sim.set_potential(fdev[k])
+                sim.reset_state()
+                sim.evolve(T, dt)
+            run()  # warm-up
+            ms.append(statistics.median(timed_ms(run, sim.stream, 5)))
+            obs = sim.observables(0.1, prob=prob)[0]
+            po = oracle.evolve(inst.f, oracle.uniform_state((n, n)), 0.0, dt, nsteps, oracle.Schedule())
+            ob = oracle.observables(inst.f, po)
+            p = prob.double().cpu().numpy().reshape(n, n)
+            parity.append({"seed": 1000 * rank + seeds[k], "tv": float(0.5 * np.abs(p - ob.prob).sum()),
+                           "ef_rel": abs(obs.e_f - ob.e_f) / max(abs(ob.e_f), 1e-3 * np.ptp(inst.f)),
+                           "norm_drift": obs.norm - 1.0})
+    sim.close()
+    med = statistics.median(ms)
+    pts = n * n * nsteps
+    flops = pts * FLOP_PER_POINT_STEP_2D[n]
+    sms_used = qhd_plane_cluster(n)
+    peak_sms = fp32_peak_flops() * sms_used / torch.cuda.get_device_properties(dev).multi_processor_count
+    return {"workload": "128^2 Gaussian wells (K=8), T=10, dt=0.01 (1000 Strang steps), one instance per run, "
+                        "seeds 0..9 (median)",
+            "metric": "grid-point Strang steps/s", "value": pts / (med / 1e3), "ms_per_run_median": med,
+            "ms_per_run": ms, "parity": parity,
+            "parity_max": {"tv": max(r["tv"] for r in parity), "ef_rel": max(r["ef_rel"] for r in parity),
+                           "norm_drift": max(abs(r["norm_drift"]) for r in parity)},
+            "roofline": {"bound": "fp32", "achieved": flops / (med / 1e3) / 1e12,
+                         "peak": peak_sms / 1e12, "unit": "TFLOP/s", "frac": flops / (med / 1e3) / peak_sms,
+                         "peak_source": f"measured FP32 FMA rate x 2, scaled to the {sms_used} SMs one cluster occupies",
+                         "algorithmic_flop_per_point_step": FLOP_PER_POINT_STEP_2D[n]},
+            "timing": "CUDA events on the context's stream, median of 5 runs per seed after a warm-up",
+            "clocks": clk.summary()}
 
-    torch.cuda.set_device(local_rank)
-    dev = torch.device("cuda", local_rank)
-    qhd.load()
+
+def qhd_plane_cluster(n):
+    return {32: 2, 64: 2, 128: 4, 256: 8}[n]
+
+
+RAGGED_WORKLOAD = ("Batched QHD: 4096 instances, 2048 x 128^2 + 2048 x 256^2 on [0,1]^2, families alternating "
+                   "Gaussian wells (K=8) / Rastrigin type, per-instance sigma ~ U(0.5,2) (e^chi = 2 sigma t^3), "
+                   "T=10, dt=0.01 (1000 Strang steps), complex64; one persistent launch (CUDA graph) over both "
+                   "size classes, launch configuration from the autotuner")
+
+
+def c3_ragged(args, dev, rank):
+    """C3: every instance of both size classes in one persistent launch per chunk
+    (qhd_group_*, replayed as a CUDA graph), configuration picked by the autotuner.
+    Baseline: one context per instance, each run a launch sequence of its own,
+    device-timed on a sample of each size."""
+    import torch
+    import oracle
+    from paper_2303_01471_gb300 import autotune, qhd
     count = args.ragged_count
     spec = workloads.ragged_batch_spec(count, seed0=100000 * rank)
     classes = {}
@@ -512,92 +627,109 @@ def run_ragged(args, rank, world, local_rank, dist):
         classes.setdefault(shape, []).append((fam, seed))
     T, dt = 10.0, 0.01
     nsteps = int(round(T / dt))
-    streams = [torch.cuda.Stream(dev) for _ in classes]
     sims, fdev, sigmas = [], [], []
-    for (shape, sp), st in zip(classes.items(), streams):
+    for shape, sp in classes.items():
         f, sig = workloads.batch_on_device(sp, shape, dev)
-        with torch.cuda.stream(st):
-            sim = qhd.QHD(shape, batch=len(sp), device=dev, stream=st)
-            sim.set_schedule([qhd.Schedule(c_chi=2.0 * sg) for sg in sig])
+        sim = qhd.QHD(shape, batch=len(sp), device=dev)
+        sim.set_schedule([qhd.Schedule(c_chi=2.0 * g) for g in sig])
+        sim.set_potential(f)
         sims.append(sim)
         fdev.append(f)
         sigmas.append(sig)
-    torch.cuda.synchronize()
+    tune = autotune.tune_group(sims, T=0.2, dt=dt)
+    grp = qhd.Group(sims, tune["config"])
+    stream = sims[0].stream
 
     def one_step():
-        for sim, f in zip(sims, fdev):
-            sim.set_potential(f)
-            sim.reset_state()
         for sim in sims:
-            sim.evolve(T, dt)
-        return [sim.observables(0.1) for sim in sims]
+            sim.reset_state()
+        grp.evolve(T, dt)
 
-    for _ in range(args.warmup):
-        one_step()
+    one_step()
     torch.cuda.synchronize()
-    launches0 = sum(s.launch_count() for s in sims)
-    times = []
-    with Clocks(local_rank) as clk:
-        for _ in range(args.steps):
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            obs = one_step()
-            torch.cuda.synchronize()
-            times.append(time.perf_counter() - t0)
-    launches = sum(s.launch_count() for s in sims) - launches0
-    step_s = max_over_ranks(statistics.mean(times), dist, dev)
-    inst_per_s = whole_job_rate(count, world, step_s)
-    pts = sum(int(np.prod(sh)) * len(sp) for sh, sp in classes.items()) * nsteps
-
-    # one context per instance (a launch sequence per instance), on a sample
+    launches0 = grp.info()["launches"]
+    with Clocks(dev.index or 0) as clk:
+        ms = timed_ms(one_step, stream, max(2, args.steps))
+    status = grp.status()
+    info = grp.info()
+    step_s = statistics.mean(ms) / 1e3
+    obs = [sim.observables(0.1) for sim in sims]
+    # baseline: one context per instance (prep + whole-run launch per instance)
     per_inst = {}
     for (shape, sp), sig in zip(classes.items(), sigmas):
         nsamp = min(args.ragged_sample, len(sp))
         f1, _ = workloads.batch_on_device(sp[:nsamp], shape, dev)
-        sim = qhd.QHD(shape, device=dev)
+        one = qhd.QHD(shape, device=dev)
         ts = []
         for i in range(nsamp):
-            sim.set_schedule(qhd.Schedule(c_chi=2.0 * sig[i]))
-            sim.set_potential(f1[i])
-            sim.reset_state()
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            sim.evolve(T, dt)
-            sim.observables(0.1)
-            ts.append(time.perf_counter() - t0)
-        sim.close()
-        per_inst["x".join(map(str, shape))] = statistics.mean(ts[1:] if len(ts) > 1 else ts)
-    single_s = sum(per_inst[k] * len(classes[tuple(int(v) for v in k.split("x"))]) for k in per_inst)
+            one.set_schedule(qhd.Schedule(c_chi=2.0 * sig[i]))
+            one.set_potential(f1[i])
 
+            def run():
+                one.reset_state()
+                one.evolve(T, dt)
+            run()
+            ts.append(statistics.median(timed_ms(run, one.stream, 3)))
+        one.close()
+        per_inst[shape] = statistics.mean(ts) / 1e3
+    single_s = sum(per_inst[sh] * len(sp) for sh, sp in classes.items())
     # parity on two instances of each size against the FP64 oracle
     parity = []
     for ci, ((shape, sp), sig) in enumerate(zip(classes.items(), sigmas)):
-        for i in (0, 1):
+        prob = torch.empty(len(sp) * shape[0] * shape[1], dtype=torch.float32, device=dev)
+        sims[ci].observables(0.1, prob=prob)
+        for i in (0, len(sp) - 1):
             fam, seed = sp[i]
             inst = workloads.make(fam, seed, shape)
             po = oracle.evolve(inst.f, oracle.uniform_state(shape), 0.0, dt, nsteps,
                                oracle.Schedule(c_chi=2.0 * sig[i]))
             ob = oracle.observables(inst.f, po)
-            psi = sims[ci].psi[i].abs().double().pow(2).cpu().numpy()
+            p = prob[i * shape[0] * shape[1]:(i + 1) * shape[0] * shape[1]].double().cpu().numpy().reshape(shape)
             o = obs[ci][i]
             parity.append({"shape": "x".join(map(str, shape)), "seed": seed,
-                           "tv": float(0.5 * np.abs(psi - ob.prob).sum()),
+                           "tv": float(0.5 * np.abs(p - ob.prob).sum()),
                            "ef_rel": abs(o.e_f - ob.e_f) / max(abs(ob.e_f), 1e-3 * np.ptp(inst.f)),
                            "norm_drift": o.norm - 1.0})
+    grp.close()
     for sim in sims:
         sim.close()
-    return {
-        "metric": "instances/s", "value": inst_per_s, "unit": "instances/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic (seeded Rastrigin / Gaussian wells)",
-        "config": {"workload": RAGGED_WORKLOAD, "instances_per_rank": count},
-        "grid_point_steps_per_s": pts * world / step_s,
-        "one_context_per_instance": {"instances_per_s": count / single_s, "sample_per_size": args.ragged_sample,
-                                     "s_per_instance": per_inst},
-        "speedup_vs_one_launch_sequence_per_instance": single_s / step_s,
-        "gpu_launches": launches, "clocks": clk.summary(), "parity": parity,
-    }
+    pts = sum(sh[0] * sh[1] * len(sp) for sh, sp in classes.items()) * nsteps
+    flops = sum(sh[0] * sh[1] * len(sp) * FLOP_PER_POINT_STEP_2D[sh[0]] for sh, sp in classes.items()) * nsteps
+    peak = fp32_peak_flops()
+    cfg = tune["config"].as_dict()
+    return {"workload": RAGGED_WORKLOAD, "metric": "instances/s", "value": count / step_s,
+            "ms_per_step": step_s * 1e3, "ms_per_step_runs": ms,
+            "grid_point_steps_per_s": pts / step_s,
+            "one_context_per_instance": {"instances_per_s": count / single_s, "sample_per_size": args.ragged_sample,
+                                         "ms_per_instance": {"x".join(map(str, k)): v * 1e3
+                                                             for k, v in per_inst.items()}},
+            "speedup_vs_one_launch_sequence_per_instance": single_s / step_s,
+            "launch": {"kernel_launches_per_step": info["launches"] - launches0, "graph_captures": info["captures"],
+                       "persistent_clusters": info["clusters"], "ctas_per_cluster": 8,
+                       "config": cfg, "autotuner": {"cached": tune["cached"], "candidates_ms": tune["ms"]},
+                       "status": qhd.STATUS.get(status, status)},
+            "roofline": {"bound": "fp32", "achieved": flops / step_s / 1e12, "peak": peak / 1e12,
+                         "unit": "TFLOP/s", "frac": flops / step_s / peak,
+                         "peak_source": "measured FP32 FMA rate x 2 (whole GPU)",
+                         "algorithmic_flop_per_point_step": {str(k): v for k, v in FLOP_PER_POINT_STEP_2D.items()}},
+            "timing": "CUDA events on the group's stream around reset + group evolve (device time)",
+            "parity": parity, "clocks": clk.summary()}
+
+
+def run_ragged(args, rank, world, local_rank, dist):
+    """--workload ragged: C3 as its own bench line."""
+    import torch
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    r = c3_ragged(args, dev, rank)
+    step_s = max_over_ranks(r["ms_per_step"] / 1e3, dist, dev)
+    return {"metric": "instances/s", "value": whole_job_rate(args.ragged_count, world, step_s),
+            "unit": "instances/s", "n_gpus": world, "steps": max(2, args.steps), "warmup": 1,
+            "ms_per_step": step_s * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic (seeded Rastrigin / Gaussian wells)",
+            "config": {"workload": RAGGED_WORKLOAD, "instances_per_rank": args.ragged_count},
+            "gpu_launches": r["launch"]["kernel_launches_per_step"], "roofline": r["roofline"],
+            "clocks": r["clocks"], "details": r}
 
 
 # ------------------------------------------------------ tensor-core DFT form
@@ -649,9 +781,6 @@ def run_tcdft(args, rank, world, local_rank, dist):
         for _ in range(args.warmup):
             one_step(sim)
         torch.cuda.synchronize()
-        if timing:
-            sim.timing_read(reset=True)
-            sim.timing_enable(25)
         l0, g0 = sim.launch_count(), sim.library_call_count()
         ms = []
         if dist is not None:
@@ -667,10 +796,17 @@ def run_tcdft(args, rank, world, local_rank, dist):
             ms.append(e0.elapsed_time(e1))
         if dist is not None:
             dist.barrier()
-        tm = sim.timing_read(reset=True) if timing else None
-        sim.timing_enable(0)
-        return (max_over_ranks(sum(ms), dist, dev) / k, sim.launch_count() - l0,
-                sim.library_call_count() - g0, tm, obs)
+        launches, calls = sim.launch_count() - l0, sim.library_call_count() - g0
+        tm = None
+        if timing:
+            # per-kernel durations from one instrumented step after the timed region
+            sim.timing_read(reset=True)
+            sim.timing_enable(25)
+            one_step(sim)
+            torch.cuda.synchronize()
+            tm = sim.timing_read(reset=True)
+            sim.timing_enable(0)
+        return max_over_ranks(sum(ms), dist, dev) / k, launches, calls, tm, obs
 
     results = {}
     # ---------------- tensor-core transform
@@ -703,14 +839,14 @@ def run_tcdft(args, rank, world, local_rank, dist):
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
             pk = json.load(fh)
         tpeak, tsrc = float(pk.get("bf16_tflops_sustained", pk["bf16_tflops"])), \
-            "measured (cuBLAS bf16 sustained; fp16 dense rate equals bf16)"
+            "measured (cuBLAS bf16 GEMM, sustained; the fp16 dense rate equals bf16)"
     except Exception:
         tpeak, tsrc = 1700.0, "fallback"
     # per point: read the FP32 product (8 B), write the FP16 operand segments
     # (2 x 2 B each); the fixed-point form also reads the product once for its max
     segs = 4 if args.tc_products == 10 else args.tc_products
     split_bytes = count * n * n * (8 + 4 * segs + (8 if args.tc_products == 10 else 0))
-    roofline = {"bound": "tensor", "kernel": "cuBLAS FP16 GEMM of one axis transform",
+    roofline = {"bound": "tensor", "kernel": "tcgen05 FP16 GEMM of one axis transform (qhd_umma_gemm.cu)",
                 "achieved": round(achieved, 1), "peak": tpeak, "unit": "TFLOP/s",
                 "frac": round(achieved / tpeak, 4), "peak_source": tsrc, "traffic": None,
                 "algorithmic_flop_per_launch": flop_per_gemm,
@@ -921,6 +1057,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="default workload only: skip the 128^2 and ragged-batch configurations")
     ap.add_argument("--workload", choices=["scale", "ragged", "tcdft", "fno", "simqhd"], default="scale")
     ap.add_argument("--simqhd-count", type=int, default=256)
     ap.add_argument("--fno-train", type=int, default=50000)
@@ -932,7 +1070,7 @@ def main():
     ap.add_argument("--fno-seed", type=int, default=0)
     ap.add_argument("--fno-train-budget", type=float, default=600.0)
     ap.add_argument("--tc-count", type=int, default=256)
-    ap.add_argument("--tc-products", type=int, choices=[3, 5, 10], default=10)
+    ap.add_argument("--tc-products", type=int, choices=[3, 5, 10], default=3)
     ap.add_argument("--tc-accuracy-sample", type=int, default=2)
     ap.add_argument("--ragged-count", type=int, default=4096)
     ap.add_argument("--ragged-sample", type=int, default=8)

@@ -518,6 +518,82 @@ const char *qhd_lattice_last_error(const qhd_lattice *lat);
 qhd_status qhd_lattice_destroy(qhd_lattice *lat);
 
 
+/*
+ * Batched persistent launch over several contexts (no counterpart in the
+ * paper; it runs many independent instances of Algorithm 1 at once).
+ *
+ * A group binds 1..8 contexts that are 2-D with a square mesh of edge 64, 128
+ * or 256, use the FFT transform and share one stream, and have a potential and
+ * a schedule loaded.  qhd_group_evolve(g, T, dt) evolves every instance of
+ * every context by T (the same as qhd_evolve on each context, including its
+ * splitting, kinetic operator and clock) in ONE launch per chunk of <= 1024
+ * steps: a grid of clusters of 8 CTAs pulls work items from a device queue,
+ * first the step tables of each context, then groups of instances, each
+ * instance held in the shared memory of `sub` CTAs of a cluster (8 / sub
+ * instances per cluster item).  The launch sequence is captured once into a
+ * CUDA graph and replayed while T, dt and the contexts' clocks at the call
+ * repeat (e.g. reset_state, group_evolve, observables, ...); a change
+ * re-captures.  Waits for the tables are bounded: qhd_group_status
+ * synchronises the stream and returns QHD_ERR_TIMEOUT if one gave up, which
+ * also makes the group and its contexts sticky-failed.
+ *
+ * cfg (may be NULL for the defaults, every field 0): sub_cluster[k] = CTAs per
+ * instance for edge 64 (k = 0: 2, 4 or 8), 128 (k = 1: 4 or 8), 256 (k = 2: 8);
+ * min_blocks = resident CTAs per SM the kernel is compiled for (1 or 2);
+ * clusters = persistent clusters launched (0: as many as fit at once).  These
+ * are the choices the benchmark's autotuner searches.
+ *
+ * Workspace: caller-owned device memory of qhd_group_workspace_bytes(n_ctx)
+ * bytes, 256-byte aligned, kept until qhd_group_destroy.  The contexts must
+ * outlive the group.  Errors: QHD_ERR_INVALID_ARG (NULL, duplicate context,
+ * contexts on different streams, bad cfg), QHD_ERR_STATE (a context without
+ * potential or schedule, or in a failed state), QHD_ERR_UNSUPPORTED (mesh not
+ * square 64/128/256, not 2-D, or the tensor-core transform; more than 16 table
+ * chunks in one call), QHD_ERR_WORKSPACE, QHD_ERR_CUDA.  evolve only enqueues.
+ */
+typedef struct qhd_group qhd_group;
+typedef struct {
+    int32_t sub_cluster[3];
+    int32_t min_blocks;
+    int32_t clusters;
+} qhd_group_config;
+size_t qhd_group_workspace_bytes(int n_ctx);
+qhd_status qhd_group_create(qhd_group **out, qhd_ctx *const *ctxs, int n_ctx, const qhd_group_config *cfg,
+                            void *work_dev, size_t work_bytes);
+qhd_status qhd_group_evolve(qhd_group *g, double T, double dt);
+qhd_status qhd_group_status(qhd_group *g);
+/* Test hook: with on != 0 every later launch waits for one table arrival more
+ * than any producer makes, so its waits run out and qhd_group_status reports
+ * QHD_ERR_TIMEOUT (a bounded wait giving up; nothing faults). */
+qhd_status qhd_group_inject_wait_timeout(qhd_group *g, int on);
+/* out (8 values): clusters launched, min_blocks, shared memory per CTA (bytes),
+ * kernel launches so far, graph captures so far, CTAs per instance for edge 64,
+ * 128, 256 (0 when no context has that edge). */
+qhd_status qhd_group_info(const qhd_group *g, int64_t *out);
+const char *qhd_group_last_error(const qhd_group *g); /* "" if none; g may be NULL */
+qhd_status qhd_group_destroy(qhd_group *g);
+
+/* Dense FP16 product on the 5th-generation tensor cores: the GEMM of the
+ * tensor-core transform (qhd_set_transform), exposed for testing and reuse; no
+ * counterpart in the paper.  C = alpha * A . B^T + beta * C with A row-major
+ * [rows][k] and B row-major [n_cols][k] (FP16, K contiguous, device memory) and
+ * C row-major FP32 [rows][ldc] (device).  group_every_mma = 1: every K = 16
+ * step accumulates into a fresh tensor-memory partial that is added to the FP32
+ * result with a round-to-nearest FMA (when the operands are integers whose
+ * 16-term sums stay below 2^24, every partial is exact and the result is the
+ * exact sum rounded to nearest at each addition); 0: one accumulation over all
+ * of K in tensor memory (the hardware's accumulation).  Requirements: rows >= 1,
+ * n_cols a multiple of 128, k of 64, k <= 2^20, ldc >= n_cols and a
+ * multiple of 4, 16-byte aligned pointers.  err_dev: 2 device words, zero on
+ * entry; word 0 becomes 1 if a bounded wait gave up (~2 s).  Enqueued on
+ * stream (a cudaStream_t, NULL = legacy default); nothing is allocated.
+ * Errors: QHD_ERR_INVALID_ARG, QHD_ERR_CUDA (launch failure). */
+qhd_status qhd_tc_gemm_f16(const void *A_dev, const void *B_dev, float *C_dev, int64_t ldc, int64_t rows,
+                           int64_t n_cols, int64_t k, int group_every_mma, float alpha, float beta,
+                           unsigned *err_dev, void *stream);
+/* Message of the CUDA runtime for the calling thread's last qhd_tc_gemm_f16 ("" after success). */
+const char *qhd_tc_gemm_last_error(void);
+
 /* Failure injection for tests of the error contract above (no counterpart in
  * the paper).  With kind = QHD_ERR_CUDA or QHD_ERR_TIMEOUT, the after-th
  * checked CUDA call of this context from now on (a kernel launch, a copy or a

@@ -2,8 +2,7 @@
 
 The translation units compile in parallel; the result is
 paper_2303_01471_gb300/_lib/libqhd.so, a plain C ABI (include/qhd.h) with
-the CUDA runtime linked statically and cuBLAS (the tensor-core transform's
-GEMMs) linked dynamically from the toolkit.  The arithmetic throughput probe
+the CUDA runtime linked statically and no other library.  The arithmetic throughput probe
 that the benchmark uses to state roofline peaks is built beside it as its own
 library, _lib/libqhd_probe.so (include/qhd_probe.h), outside the simulator's
 ABI.
@@ -21,10 +20,11 @@ CSRC = os.path.join(PKG, "csrc")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libqhd.so")
 SOURCES = ["qhd_kernels.cu", "qhd_plane.cu", "qhd_host.cu", "qhd_static.cu", "qhd_tcdft.cu", "qhd_fno.cu", "qhd_spectrum.cu",
-           "qhd_lattice.cu"]
+           "qhd_lattice.cu", "qhd_group.cu", "qhd_umma_gemm.cu"]
 PROBE_SOURCE = "qhd_probe.cu"
 PROBE_LIB = os.path.join(LIBDIR, "libqhd_probe.so")
-HEADERS = ["qhd_device.cuh", "qhd_kernels.h", "qhd_plane.cuh", "qhd_tcdft.h", "qhd_spectrum.h", "qhd_sched.cuh"]
+HEADERS = ["qhd_device.cuh", "qhd_kernels.h", "qhd_plane.cuh", "qhd_tcdft.h", "qhd_spectrum.h", "qhd_sched.cuh",
+           "qhd_prep.cuh", "qhd_group.h", "qhd_umma.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -87,7 +87,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None, out: str
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
         os.replace(tmp, out_path)
 
-    link(target, objs[:-1], ["-L" + cudalib, "-lcublas", "-Xlinker", "-rpath," + cudalib])
+    link(target, objs[:-1], [])
     link(os.path.join(libdir, "libqhd_probe.so"), objs[-1:], [])
     return target
 

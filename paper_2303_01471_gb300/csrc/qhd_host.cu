@@ -12,6 +12,7 @@
 
 #include "qhd.h"
 #include "qhd_device.cuh"
+#include "qhd_group.h"
 #include "qhd_kernels.h"
 #include "qhd_sched.cuh"
 #include "qhd_spectrum.h"
@@ -124,7 +125,7 @@ struct qhd_ctx {
     InstDev *inst = nullptr;
     float4 *tw[3] = {nullptr, nullptr, nullptr};
     float4 *twx = nullptr;  // exchange twiddles of the cluster-distributed axis
-    float4 *ptab = nullptr; // potential phase table exp(-2 pi i k / PHASE_TAB), hi/lo
+    float4 *ptab = nullptr; // potential phase table exp(-2 pi i (k + 1/2) / PHASE_TAB), hi/lo
     int plane_mode = 0;     // 0 generic passes, 2 whole-run 2-D clusters, 3 3-D plane pass
     double *coord = nullptr;
     double *obs_part = nullptr, *obs_res = nullptr;
@@ -372,7 +373,7 @@ qhd_status qhd_init_grid(qhd_ctx **out, int ndim, const int64_t *n, const double
     c->ptab = (float4 *)(c->work + L.ptab);
     std::vector<float4> ptab((size_t)PHASE_TAB);
     for (int k = 0; k < PHASE_TAB; ++k) {
-        const double ang = 2.0 * 3.141592653589793238462643383279502884 * (double)k / (double)PHASE_TAB;
+        const double ang = 2.0 * 3.141592653589793238462643383279502884 * ((double)k + 0.5) / (double)PHASE_TAB;
         const double cr = cos(ang), ci = -sin(ang);
         const float hr = (float)cr, hi = (float)ci;
         ptab[(size_t)k] = make_float4(hr, hi, (float)(cr - (double)hr), (float)(ci - (double)hi));
@@ -557,7 +558,8 @@ qhd_status evolve_tc_chunk(qhd_ctx *c, int64_t j0, int64_t cnt, bool last_chunk,
     ta.kt_batch = ktb;
     auto gemm = [&](bool inv, bool sample) -> qhd_status {
         TimedScope ts(c, QHD_KCLASS_TC_GEMM, sample);
-        cudaError_t e = tc_gemm(c->tc, inv, &c->lib_calls);
+        if (injected(c)) return c->sticky;
+        cudaError_t e = tc_gemm(c->tc, inv, c->stream, &c->launches);
         if (e != cudaSuccess) return fail(c, QHD_ERR_CUDA, "tensor-core GEMM failed: %s", cudaGetErrorString(e));
         return QHD_OK;
     };
@@ -797,6 +799,12 @@ qhd_status qhd_observables(qhd_ctx *c, qhd_obs *out, float *prob_dev, double rad
     if (!out) return fail(c, QHD_ERR_INVALID_ARG, "out is NULL");
     if (!std::isfinite(radius) || !(radius > 0)) return fail(c, QHD_ERR_INVALID_ARG, "radius must be > 0");
     if (!c->have_f) return fail(c, QHD_ERR_STATE, "observables need set_potential first");
+    if (c->tc) {
+        // a tensor-core GEMM whose bounded wait gave up leaves the state invalid
+        const int to = tc_timed_out(c->tc, c->stream);
+        if (to < 0) return fail(c, QHD_ERR_CUDA, "reading the tensor-core GEMM status failed");
+        if (to > 0) return fail(c, QHD_ERR_TIMEOUT, "a tensor-core GEMM gave up waiting for its operands");
+    }
     ObsArgs a{};
     a.psi = c->psi;
     a.f64 = c->f64;
@@ -1010,6 +1018,43 @@ qhd_status ctx_view(qhd_ctx *c, CtxView *v) {
     v->kinetic = c->kinetic;
     v->stream = c->stream;
     return QHD_OK;
+}
+
+qhd_status ctx_group_view(qhd_ctx *c, GroupCtxView *v) {
+    qhd_status s = check_ctx(c);
+    if (s != QHD_OK) return s;
+    if (!c->have_f || !c->have_sched) return fail(c, QHD_ERR_STATE, "needs set_potential and set_schedule first");
+    v->ndim = c->ndim;
+    for (int d = 0; d < 3; ++d) {
+        v->n[d] = d < c->ndim ? c->n[d] : 1;
+        v->len[d] = d < c->ndim ? c->hi[d] - c->lo[d] : 1.0;
+        v->koff[d] = d < c->ndim ? c->koff[d] : c->ksum;
+    }
+    v->batch = c->batch;
+    v->g = c->g;
+    v->ksum = c->ksum;
+    v->psi = c->psi;
+    v->fq = c->fq;
+    v->pot = c->pot;
+    v->kt = c->kt;
+    v->tw_row = c->ndim >= 2 ? c->tw[1] : nullptr;
+    v->ptab = c->ptab;
+    v->sched = c->sched;
+    v->inst = c->inst;
+    v->chunk = c->kt_shared ? c->L.chunk_shared : c->L.chunk;
+    v->kt_batch = c->kt_shared ? 1 : c->batch;
+    v->split = c->split == QHD_SPLIT_LIE_TROTTER ? 1 : 0;
+    v->kinetic = c->kinetic == QHD_KINETIC_FD2 ? 1 : 0;
+    v->t = c->t;
+    v->steps_done = c->steps_done;
+    v->stream = c->stream;
+    v->whole_run = c->plane_mode == 2 && c->tc == nullptr;
+    return QHD_OK;
+}
+
+void ctx_advance(qhd_ctx *c, int64_t nsteps, double dt) {
+    c->t = c->t + (double)nsteps * dt;
+    c->steps_done += nsteps;
 }
 
 static double host_interp(const std::vector<double> &ts, const std::vector<double> &vs, double t) {

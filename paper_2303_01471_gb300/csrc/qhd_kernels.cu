@@ -23,6 +23,7 @@
 #include "qhd_device.cuh"
 #include "qhd_kernels.h"
 #include "qhd_sched.cuh"
+#include "qhd_prep.cuh"
 
 namespace qhd {
 
@@ -177,73 +178,17 @@ __global__ void __launch_bounds__(ROW_THREADS) k_oned(OneDArgs a) {
 
 // ------------------------------------------------------------- prep kernel
 // Schedule evaluation at the step midpoints, the merged potential coefficients
-// and the per-axis kinetic phase tables of one chunk of steps.
+// and the per-axis kinetic phase tables of one chunk of steps (qhd_prep.cuh).
 
 __global__ void k_prep(PrepArgs a) {
     const int64_t jl = blockIdx.x;  // local step 0..cnt (cnt is the extra potential entry)
     const int64_t b = blockIdx.y;
-    const int64_t j = a.j0 + jl;    // global step index
     __shared__ uint64_t s_k[3];
     __shared__ double s_fd[3];
-    if (threadIdx.x == 0) {
-        const SchedDev &sd = a.sched[b];
-        const double PI = 3.141592653589793238462643383279502884;
-        double a_m = 0, b_m = 0, a_p = 0, b_p = 0, theta = 0;
-        if (a.split == 0) {
-            // Strang: midpoints t_{j-1/2} and t_{j+1/2}; merged half steps
-            if (j >= 1) {
-                const double tm = __dadd_rn(a.t_start, __dmul_rn((double)(j - 1) + 0.5, a.dt));
-                sched_eval_dev(sd, tm, &a_m, &b_m);
-            }
-            if (j < a.nsteps) {
-                const double tp = __dadd_rn(a.t_start, __dmul_rn((double)j + 0.5, a.dt));
-                sched_eval_dev(sd, tp, &a_p, &b_p);
-            }
-            theta = __dmul_rn(a.dt, __dadd_rn(j >= 1 ? b_m : 0.0, j < a.nsteps ? b_p : 0.0)) * 0.5;
-        } else if (j < a.nsteps) {
-            // first-order product formula of Eq. (prod_qhd): a_j, b_j at t_j = t + j dt,
-            // one potential phase dt b_j per step and none after the last
-            const double tj = __dadd_rn(a.t_start, __dmul_rn((double)j, a.dt));
-            sched_eval_dev(sd, tj, &a_p, &b_p);
-            theta = __dmul_rn(a.dt, b_p);
-        }
-        const int shift = a.inst[b].shift;
-        // turns per unit of the fixed-point potential: theta / (2 pi) * 2^-shift
-        const double y = ldexp(theta / (2.0 * PI), -shift);
-        a.pot[jl * a.batch + b] = frac_to_u64(y);
-        for (int d = 0; d < a.ndim; ++d) {
-            // turns per unit m^2: dt * a * |2 pi m / L|^2 / 2 / (2 pi) = dt a pi m^2 / L^2
-            const double kap = __ddiv_rn(__dmul_rn(__dmul_rn(a.dt, a_p), PI), __dmul_rn(a.len[d], a.len[d]));
-            s_k[d] = frac_to_u64(kap);
-            // finite difference: turns per unit sin^2(pi m/N) =
-            // dt * a * (4 / h^2) / 2 / (2 pi) = dt a N^2 / (pi L^2)
-            const double nn = (double)a.n[d];
-            s_fd[d] = __ddiv_rn(__dmul_rn(__dmul_rn(a.dt, a_p), nn * nn), __dmul_rn(PI, __dmul_rn(a.len[d], a.len[d])));
-        }
-    }
+    if (threadIdx.x == 0) prep_coefficients(a, jl, b, s_k, s_fd);
     __syncthreads();
     if (jl >= a.cnt || b >= a.kt_batch) return;
-    float4 *out = a.kt + (jl * a.kt_batch + b) * a.ksum;
-    for (int i = threadIdx.x; i < a.ksum; i += blockDim.x) {
-        int d = 0;
-        while (d + 1 < a.ndim && i >= a.koff[d + 1]) ++d;
-        const int idx = i - a.koff[d];
-        const int nd = a.n[d];
-        const int m = idx < nd / 2 ? idx : idx - nd;
-        uint32_t u;
-        if (a.kinetic == 1) {
-            const double sp = sinpi((double)m / (double)nd);
-            u = (uint32_t)(frac_to_u64(__dmul_rn(s_fd[d], __dmul_rn(sp, sp))) >> 32);
-        } else {
-            u = turns_mul(s_k[d], (uint32_t)(m * m));
-        }
-        double s, c;
-        sincospi((double)(int32_t)u * 4.656612873077392578125e-10, &s, &c);
-        const double scale = d == 0 ? a.inv_g : 1.0;  // exact power of two
-        const double cr = c * scale, ci = -s * scale;
-        const float hr = (float)cr, hi = (float)ci;
-        out[i] = make_float4(hr, hi, (float)(cr - (double)hr), (float)(ci - (double)hi));
-    }
+    for (int i = threadIdx.x; i < a.ksum; i += blockDim.x) prep_kinetic_entry(a, jl, b, i, s_k, s_fd);
 }
 
 // ------------------------------------------------------------ small kernels

@@ -61,40 +61,15 @@ __global__ void __launch_bounds__(PLANE_THREADS, plane_min_blocks<N1, N2, C>()) 
 
 template <int N1, int N2, int C>
 __global__ void __launch_bounds__(PLANE_THREADS, 2) k_plane_whole(PlaneArgs a) {
-    using P = PlaneCfg<N1, N2, C>;
     extern __shared__ __align__(16) float4 smem4[];
     float4 *ptab = smem4;
     float2 *tile = reinterpret_cast<float2 *>(smem4 + PHASE_TAB);
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
-    const int64_t b = blockIdx.x / C;  // instance
     uint32_t tiles[C];
 #pragma unroll
     for (int q = 0; q < C; ++q) tiles[q] = cluster_addr(tile, (uint32_t)q);
-    float2 *g = a.psi + b * (int64_t)N1 * N2 + (int64_t)rank * P::R * N2;
-    const uint32_t *fqr = a.fq + b * (int64_t)N1 * N2;
-    plane_copy<N1, N2, C, true>(tile, g);
-    load_phase_tab(ptab, a.ptab);
-    plane_copy_wait();
-    cluster.sync();
-#pragma unroll 1
-    for (int j = 0; j < a.cnt; ++j) {
-        const uint64_t coef = a.pot[(int64_t)j * a.batch + b];
-        plane_exchange<N1, N2, C, 1>(tiles, rank, j > 0, true, true, a.twx, fqr, coef,
-                                  step_dither(a.dither_base + (uint64_t)j), ptab);
-        cluster.sync();
-        plane_columns<N1, N2, C, false>(tile);
-        __syncthreads();
-        const float4 *kb = a.kt + ((int64_t)j * a.kt_batch + (a.kt_batch == 1 ? 0 : b)) * a.ksum;
-        plane_rows<N1, N2, C, 2>(tile, a.tw_row, kb, kb + N1, rank);
-        __syncthreads();
-        plane_columns<N1, N2, C, true>(tile);
-        cluster.sync();
-    }
-    const uint64_t coef = a.pot[(int64_t)a.cnt * a.batch + b];
-    plane_exchange<N1, N2, C, 1>(tiles, rank, a.cnt > 0, a.final_phase != 0, false, a.twx, fqr, coef, 0u, ptab);
-    cluster.sync();
-    plane_copy<N1, N2, C, false>(tile, g);
+    plane_whole_run<N1, N2, C, 1>(a, blockIdx.x / C, rank, tiles, ptab, tile, true, cluster);
 }
 
 // ---------------------------------------------------------------- launchers

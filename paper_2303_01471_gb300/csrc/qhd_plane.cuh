@@ -114,10 +114,12 @@ __device__ __forceinline__ void plane_rows(float2 *tile, const float4 *__restric
                 line_fft<N2, false>(x, rp, t, tw_row, WarpSyncP{});
                 if (DIR == 2) {
                     // this local row holds frequency rank + C * row along the distributed axis
-                    const float4 k0 = __ldg(&kt0[rank + C * row]);
+                    // plain (coherent) loads: the batched persistent kernel writes
+                    // these tables earlier in the same launch
+                    const float4 k0 = kt0[rank + C * row];
 #pragma unroll
                     for (int e = 0; e < E2; ++e) {
-                        const float4 k1 = __ldg(&kt1[t + T2 * e]);
+                        const float4 k1 = kt1[t + T2 * e];
                         float2 y = cmul_comp(x[e], make_float2(k0.x, k0.y), make_float2(k0.z, k0.w));
                         x[e] = cmul_comp(y, make_float2(k1.x, k1.y), make_float2(k1.z, k1.w));
                     }
@@ -225,6 +227,44 @@ __device__ __forceinline__ void plane_exchange(const uint32_t *base, int rank, b
             for (int q = 0; q < C; ++q) st_cluster(base[q] + off, v[h][q]);
         }
     }
+}
+
+// Every step of a chunk for one 2-D instance b held by the C CTAs whose
+// cluster addresses are tiles[0..C) (rank = this CTA's index among them): per
+// step the cross-cluster exchange with the potential phase, then the local
+// transforms with the kinetic phase in between.  psi touches global memory only
+// at the chunk's start and end.  live = false runs the same steps (and cluster
+// barriers) on whatever the tile holds and touches no global memory but the
+// tables and the potential of instance b (which must be a valid index), so
+// idle CTAs of a shared cluster keep the barrier count of their partners.
+template <int N1, int N2, int C, int INF>
+__device__ __forceinline__ void plane_whole_run(const PlaneArgs &a, int64_t b, int rank, const uint32_t *tiles,
+                                                float4 *ptab, float2 *tile, bool live, cg::cluster_group &cluster) {
+    using P = PlaneCfg<N1, N2, C>;
+    float2 *g = a.psi + b * (int64_t)N1 * N2 + (int64_t)rank * P::R * N2;
+    const uint32_t *fqr = a.fq + b * (int64_t)N1 * N2;
+    if (live) plane_copy<N1, N2, C, true>(tile, g);
+    load_phase_tab(ptab, a.ptab);
+    plane_copy_wait();
+    cluster.sync();
+#pragma unroll 1
+    for (int j = 0; j < a.cnt; ++j) {
+        const uint64_t coef = a.pot[(int64_t)j * a.batch + b];
+        plane_exchange<N1, N2, C, INF>(tiles, rank, j > 0, true, true, a.twx, fqr, coef,
+                                       step_dither(a.dither_base + (uint64_t)j), ptab);
+        cluster.sync();
+        plane_columns<N1, N2, C, false>(tile);
+        __syncthreads();
+        const float4 *kb = a.kt + ((int64_t)j * a.kt_batch + (a.kt_batch == 1 ? 0 : b)) * a.ksum;
+        plane_rows<N1, N2, C, 2>(tile, a.tw_row, kb, kb + N1, rank);
+        __syncthreads();
+        plane_columns<N1, N2, C, true>(tile);
+        cluster.sync();
+    }
+    const uint64_t coef = a.pot[(int64_t)a.cnt * a.batch + b];
+    plane_exchange<N1, N2, C, INF>(tiles, rank, a.cnt > 0, a.final_phase != 0, false, a.twx, fqr, coef, 0u, ptab);
+    cluster.sync();
+    if (live) plane_copy<N1, N2, C, false>(tile, g);
 }
 
 }  // namespace qhd

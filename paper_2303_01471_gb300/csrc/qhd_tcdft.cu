@@ -13,8 +13,9 @@
 // and ends in natural layout, ready for the next step's potential phase.  The
 // state stays in the FP32 product buffer between steps; psi is read at the
 // start of an evolve call and written at its end.  The kernels here apply the
-// phases, transpose and split the operands; the GEMMs are cuBLAS FP16 GEMMs
-// with FP32 accumulation.
+// phases, transpose and split the operands; the GEMMs are the project's
+// tcgen05 kernel (qhd_umma_gemm.cu): FP16 operands, FP32 accumulation in
+// tensor memory, partials added in FP32 with round-to-nearest.
 //
 // Two operand forms.
 //
@@ -29,8 +30,10 @@
 // (2^h >= sqrt n), and the kinetic split takes out the 1/n^2 its table
 // carries.  The tensor cores' FP32 accumulation is not round-to-nearest: the
 // result of a long K loop is biased towards zero (about -1e-9 K relative per
-// GEMM, measured), and over hundreds of steps that bias, not the operand
-// precision, decides the error of this form.
+// GEMM, measured with a library GEMM), and over hundreds of steps that bias,
+// not the operand precision, decides the error of this form.  So every K = 16
+// MMA here is a group of its own: its tensor-memory partial is added to the
+// FP32 result with a round-to-nearest FMA.
 //
 // Fixed-point slices (10 products, an error-free splitting in the manner of
 // Ozaki et al.).  Each instance is scaled by a power of two 2^(7-e) with
@@ -42,8 +45,8 @@
 // rounding (below 2^24 for levels 0 and 1; levels 2 and 3 are ~2^-14 and
 // ~2^-21 corrections), so no bias enters:
 //   level L: [a0 | .. | aL] . [wL; ..; w0]        (K = 2n (L + 1))
-// and the levels are combined smallest first through the GEMM epilogue
-// (C = alpha acc + beta C in FP32, alpha = 2^-7L).  A per-instance
+// and each level is one accumulation group of the GEMM whose exact partial is
+// added to the FP32 result times 2^-7L.  A per-instance
 // power-of-two exponent E (true value = buffer * 2^E) follows the scales and
 // is read back at the end.
 #include <cmath>
@@ -51,7 +54,6 @@
 #include <cstring>
 #include <vector>
 
-#include <cublas_v2.h>
 #include <cuda_fp16.h>
 
 #include "qhd_device.cuh"
@@ -65,7 +67,8 @@ constexpr int TC_S = 14;               // log2 of the operand scale, floating fo
 constexpr int TC_THREADS = 256;
 constexpr int TC_TR = 64, TC_TC = 32;  // transpose tile: input rows x input columns
 constexpr int TC_FIXED = 10;           // products of the fixed-point form
-constexpr size_t TC_CUBLAS_WS = size_t(32) << 20;
+// GEMM tile width (columns of C per CTA)
+int tc_bn(int) { return 128; }
 
 struct SplitOut {
     __half *a;     // B*n rows of segments of 2n FP16
@@ -295,7 +298,7 @@ int log2i(int n) {
 
 // K extent (in units of 2n) of the DFT-matrix buffers of one direction, and
 // the row length (in units of 2n) of the split operands.
-int w_segments(int products) { return products == TC_FIXED ? 1 + 2 + 3 + 4 : products; }
+int w_segments(int products) { return products == TC_FIXED ? 4 : products; }
 int a_segments(int products) { return products == TC_FIXED ? 4 : products; }
 
 }  // namespace
@@ -303,8 +306,8 @@ int a_segments(int products) { return products == TC_FIXED ? 4 : products; }
 struct TcState {
     int n = 0, products = 5, h = 0, l = 0;
     int64_t batch = 0;
-    cublasHandle_t handle = nullptr;
-    __half *w[2] = {nullptr, nullptr};  // forward, inverse; fixed form: levels 0 | 1 | 2 | 3 back to back
+    unsigned *err = nullptr;            // GEMM wait time-out word (2 words)
+    __half *w[2] = {nullptr, nullptr};  // forward, inverse DFT matrix, stored transposed [2n][K]: K-major
     __half *a = nullptr;                // B*n rows of split operands
     float *c = nullptr;                 // B*n x 2n products
     unsigned *maxbits = nullptr;        // fixed form: 2 x B max |z|^2 buffers
@@ -331,7 +334,7 @@ size_t tc_workspace_bytes(int n, int64_t batch, int products) {
     t += tc_align(rows * m * sizeof(float));
     t += tc_align(2 * (size_t)batch * sizeof(unsigned));
     t += tc_align((size_t)batch * sizeof(int));
-    t += TC_CUBLAS_WS;
+    t += tc_align(2 * sizeof(unsigned));  // GEMM wait time-out word
     return t;
 }
 
@@ -377,11 +380,16 @@ TcState *tc_create(int n, int64_t batch, int products, void *ws, size_t ws_bytes
     p += tc_align(2 * (size_t)batch * sizeof(unsigned));
     t->e = (int *)p;
     p += tc_align((size_t)batch * sizeof(int));
-    void *cublas_ws = p;
+    t->err = (unsigned *)p;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     t->grid = (sms > 0 ? sms : 152) * 8;
+    if (cudaMemsetAsync(t->err, 0, 2 * sizeof(unsigned), s) != cudaSuccess) {
+        *why = "clearing the GEMM time-out word failed";
+        delete t;
+        return nullptr;
+    }
 
     // W and conj W from FP64, split on the host
     std::vector<__half> host(wseg * m * m);
@@ -399,7 +407,8 @@ TcState *tc_create(int n, int64_t batch, int products, void *ws, size_t ws_bytes
                     const __half part[3] = {hi, mid, lo};
                     const int seg3[3] = {0, 0, 1}, seg5[5] = {0, 0, 1, 2, 1};
                     const int *seg = products == 3 ? seg3 : seg5;
-                    for (int sidx = 0; sidx < products; ++sidx) host[(sidx * m + row) * m + col] = part[seg[sidx]];
+                    for (int sidx = 0; sidx < products; ++sidx)
+                        host[col * wseg * m + sidx * m + row] = part[seg[sidx]];
                 } else {
                     // integer slices of 2^7 v: w0 + 2^-7 w1 + 2^-14 w2 + 2^-21 w3
                     double r = v * 128.0, w[4];
@@ -407,10 +416,8 @@ TcState *tc_create(int n, int64_t batch, int products, void *ws, size_t ws_bytes
                         w[k] = std::nearbyint(r);
                         r = (r - w[k]) * 128.0;
                     }
-                    // level L pairs [a0 | .. | aL] with [wL; ..; w0]
-                    int sidx = 0;
-                    for (int lev = 0; lev < 4; ++lev)
-                        for (int i = 0; i <= lev; ++i) host[(sidx++ * m + row) * m + col] = __double2half(w[lev - i]);
+                    // segments w0 | w1 | w2 | w3 along K; level L pairs a_i with w_(L-i)
+                    for (int k = 0; k < 4; ++k) host[col * wseg * m + k * m + row] = __double2half(w[k]);
                 }
             }
         if (cudaMemcpyAsync(t->w[d], host.data(), host.size() * sizeof(__half), cudaMemcpyHostToDevice, s) !=
@@ -421,28 +428,10 @@ TcState *tc_create(int n, int64_t batch, int products, void *ws, size_t ws_bytes
             return nullptr;
         }
     }
-    if (cublasCreate(&t->handle) != CUBLAS_STATUS_SUCCESS) {
-        *why = "cublasCreate failed";
-        t->handle = nullptr;
-        delete t;
-        return nullptr;
-    }
-    if (cublasSetStream(t->handle, s) != CUBLAS_STATUS_SUCCESS ||
-        cublasSetWorkspace(t->handle, cublas_ws, TC_CUBLAS_WS) != CUBLAS_STATUS_SUCCESS ||
-        cublasSetMathMode(t->handle, CUBLAS_DEFAULT_MATH) != CUBLAS_STATUS_SUCCESS) {
-        *why = "cuBLAS stream / workspace set-up failed";
-        cublasDestroy(t->handle);
-        delete t;
-        return nullptr;
-    }
     return t;
 }
 
-void tc_destroy(TcState *t) {
-    if (!t) return;
-    if (t->handle) cublasDestroy(t->handle);
-    delete t;
-}
+void tc_destroy(TcState *t) { delete t; }
 
 static SplitOut split_out(TcState *t) {
     SplitOut o;
@@ -542,35 +531,41 @@ cudaError_t tc_split_transpose(TcState *t, cudaStream_t s, int64_t *launches) {
     return cudaGetLastError();
 }
 
-// One cuBLAS GEMM: row-major C[rows][m] = alpha A[rows][:k] . W[k][m] + beta C,
-// A with row length lda; in cuBLAS's column-major terms C^T = W^T A^T.
-static cublasStatus_t gemm_call(TcState *t, const __half *w, int k, int lda, float alpha, float beta) {
+// One axis transform: C[rows][2n] = products of the split rows with the block
+// DFT matrix.  Floating forms: every K = 16 MMA its own accumulation group,
+// alpha = 2^-h.  Fixed form: level L = segments (a_i, w_(L-i)), i = 0..L, one
+// exact group scaled by 2^-7L.
+cudaError_t tc_gemm(TcState *t, bool inverse, cudaStream_t s, int64_t *launches) {
     const int m = 2 * t->n;
-    const int rows = (int)(t->batch * t->n);
-    return cublasGemmEx(t->handle, CUBLAS_OP_N, CUBLAS_OP_N, m, rows, k, &alpha, w, CUDA_R_16F, m, t->a, CUDA_R_16F,
-                        lda, &beta, t->c, CUDA_R_32F, m, CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT);
+    const int kb = m / 64;
+    const __half *w = t->w[inverse ? 1 : 0];
+    const int64_t rows = t->batch * t->n;
+    UgSeg seg[UG_MAX_SEG];
+    int nseg = 0;
+    float alpha = 1.f;
+    int64_t lda, ldb;
+    if (t->products == TC_FIXED) {
+        lda = 4 * (int64_t)m;
+        ldb = 4 * (int64_t)m;
+        for (int lev = 0; lev < 4; ++lev)
+            for (int i = 0; i <= lev; ++i)
+                seg[nseg++] = UgSeg{i * m, (lev - i) * m, kb, ldexpf(1.f, -7 * lev), i == 0 ? (int)UG_OPEN : (int)UG_CONTINUE};
+    } else {
+        lda = ldb = (int64_t)t->products * m;
+        for (int sidx = 0; sidx < t->products; ++sidx) seg[nseg++] = UgSeg{sidx * m, sidx * m, kb, 1.f, (int)UG_EACH_MMA};
+        alpha = ldexpf(1.f, -t->h);
+    }
+    cudaError_t e = umma_gemm(t->a, lda, w, ldb, t->c, m, rows, m, seg, nseg, alpha, 0.f, tc_bn(t->n), t->err, s);
+    ++*launches;
+    return e;
 }
 
-cudaError_t tc_gemm(TcState *t, bool inverse, int64_t *calls) {
-    const int m = 2 * t->n;
-    const __half *w = t->w[inverse ? 1 : 0];
-    cublasStatus_t st;
-    if (t->products == TC_FIXED) {
-        const int lda = 4 * m;
-        const size_t mm = (size_t)m * m;
-        // levels smallest first, combined in the epilogue: C = 2^-7L level_L + C
-        const size_t off[4] = {0, 1, 3, 6};
-        st = CUBLAS_STATUS_SUCCESS;
-        for (int lev = 3; lev >= 0 && st == CUBLAS_STATUS_SUCCESS; --lev)
-            st = gemm_call(t, w + off[lev] * mm, (lev + 1) * m, lda, ldexpf(1.f, -7 * lev), lev == 3 ? 0.f : 1.f);
-        *calls += 4;
-    } else {
-        const int kp = t->products * m;
-        st = gemm_call(t, w, kp, kp, ldexpf(1.f, -t->h), 0.f);
-        *calls += 1;
-    }
-    if (st != CUBLAS_STATUS_SUCCESS) return cudaErrorLaunchFailure;
-    return cudaGetLastError();
+int tc_timed_out(TcState *t, cudaStream_t s) {
+    unsigned v = 0;
+    if (cudaMemcpyAsync(&v, t->err, sizeof v, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return -1;
+    return v ? 1 : 0;
 }
 
 cudaError_t tc_finish(TcState *t, const TcPhaseArgs &a, bool phase, cudaStream_t s, int64_t *launches) {

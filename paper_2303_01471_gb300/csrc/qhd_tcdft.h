@@ -3,11 +3,45 @@
 #include <cstddef>
 #include <cstdint>
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 namespace qhd {
 
 struct TcState;
+
+// ----------------------------------------------- tcgen05 GEMM (qhd_umma_gemm.cu)
+// K segments of C = alpha * sum_g scale_g (A_g . B_g^T) + beta * C: a_k0 / b_k0
+// are the K offsets (elements, multiples of 64) of the segment in A's and B's
+// rows, kblocks its length in blocks of 64.  mode: UG_EACH_MMA makes every
+// K = 16 MMA a group of its own (its partial added in FP32 with round to
+// nearest); UG_OPEN starts a group that accumulates in tensor memory and
+// following UG_CONTINUE segments extend (one FP32 rounding per group).
+enum { UG_EACH_MMA = 0, UG_OPEN = 1, UG_CONTINUE = 2 };
+constexpr int UG_MAX_SEG = 16;
+struct UgSeg {
+    int a_k0, b_k0, kblocks;
+    float scale;
+    int mode;
+};
+struct UgArgs {
+    float *C;
+    int64_t ldc;
+    int64_t rows;        // rows of A and C (the last tile may be partial)
+    int m_tiles, n_tiles;
+    int nseg;
+    UgSeg seg[UG_MAX_SEG];
+    float alpha, beta;
+    unsigned *err;       // 2 words: [0] a bounded wait gave up, [1] scratch of the wind-down waits
+    uint64_t limit_ns;   // global-time limit of each wait
+};
+// n_cols % 128 == 0, lda and ldb multiples of 64; bn = 128; any rows >= 1 (the
+// loads of a partial last row tile read zeros past the end, its stores stop there).
+bool umma_gemm_shape_ok(int64_t rows, int64_t n_cols, int64_t lda, int64_t ldb, int bn);
+// A: FP16 [rows][lda], B: FP16 [n_cols][ldb] (B^T, K contiguous), C: FP32 [rows][ldc].
+cudaError_t umma_gemm(const __half *A, int64_t lda, const __half *B, int64_t ldb, float *C, int64_t ldc, int64_t rows,
+                      int64_t n_cols, const UgSeg *segs, int nseg, float alpha, float beta, int bn, unsigned *err,
+                      cudaStream_t s);
 
 // Arguments of one split kernel: the state lives in the FP32 product buffer
 // of the state object between transforms; psi only at the start and end.
@@ -26,8 +60,7 @@ bool tc_supported(int n0, int n1, int64_t batch);
 // products: 3 or 5 (floating FP16 hi/lo operands), 10 (fixed-point slices, n <= 512)
 bool tc_products_ok(int n, int products);
 size_t tc_workspace_bytes(int n, int64_t batch, int products);
-// Returns nullptr with *why set when the workspace is short, a CUDA call or
-// cuBLAS set-up fails.
+// Returns nullptr with *why set when the workspace is short or a CUDA call fails.
 TcState *tc_create(int n, int64_t batch, int products, void *ws, size_t ws_bytes, cudaStream_t s,
                    const char **why);
 void tc_destroy(TcState *t);
@@ -35,11 +68,14 @@ int tc_products(const TcState *t);
 
 // The four transforms of one Strang step, each a split and the GEMM(s) of one
 // axis transform.  from_psi: the first potential split of an evolve call
-// reads psi.  *launches / *calls count the kernels / cuBLAS calls issued.
+// reads psi.  *launches counts the kernels issued.
 cudaError_t tc_split_potential(TcState *t, const TcPhaseArgs &a, bool from_psi, cudaStream_t s, int64_t *launches);
 cudaError_t tc_split_transpose(TcState *t, cudaStream_t s, int64_t *launches);
 cudaError_t tc_split_kinetic(TcState *t, const TcPhaseArgs &a, cudaStream_t s, int64_t *launches);
-cudaError_t tc_gemm(TcState *t, bool inverse, int64_t *calls);
+cudaError_t tc_gemm(TcState *t, bool inverse, cudaStream_t s, int64_t *launches);
+// 1 when a bounded wait of a tensor-core GEMM gave up (reads a device word;
+// synchronises the stream); -1 when the read itself failed.
+int tc_timed_out(TcState *t, cudaStream_t s);
 // The product buffer (position space, natural layout) -> psi, with the final
 // potential phase a.pot when phase is set.
 cudaError_t tc_finish(TcState *t, const TcPhaseArgs &a, bool phase, cudaStream_t s, int64_t *launches);

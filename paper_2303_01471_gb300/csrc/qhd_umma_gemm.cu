@@ -1,0 +1,395 @@
+// qhd_umma_gemm.cu -- the dense DFT products of the tensor-core transform on the
+// 5th-generation tensor cores (tcgen05.mma, accumulators in tensor memory, TMA
+// operand loads).
+//
+// C[rows][N] = alpha * sum_g scale_g * (A_g . B_g^T) + beta * C, with A FP16
+// row-major (K contiguous) and B FP16 stored as B^T, row-major [N][K] (K
+// contiguous): both operands K-major.  The K range is a list of segments, each
+// pairing a K range of A with one of B (so one A segment can meet several B
+// segments without being stored twice) and carrying a power-of-two scale.
+//
+// Accumulation.  The tensor cores add into an FP32 accumulator that is not
+// rounded to nearest: over a long K loop the sum drifts towards zero (measured
+// about -1e-9 K relative), which over thousands of transforms decides the
+// error of a floating hi/lo split.  So K is cut into groups: each group
+// accumulates in its own tensor-memory partial (fresh at the group's first
+// MMA), and the epilogue warps add the finished partial, times the group's
+// scale, into FP32 registers with round-to-nearest FMAs.  A segment either
+// makes every MMA (K = 16) a group of its own -- with operands whose 16-term
+// sums are exact in FP32 (integer slices below 2^24), every partial is exact
+// and the whole product is rounded to nearest -- or opens a group that
+// following segments continue (exact integer sums over the whole group).
+//
+// One CTA computes a 128 x 128 tile: warp 0 issues the TMA loads into a ring of
+// STAGES shared-memory stages, warp 1 allocates the tensor memory and one of
+// its threads issues the MMAs, warps 2..9 drain the partials (two warps per
+// 32-lane quarter of the accumulator, each half of the columns) and write C.
+// Every wait is bounded in time; a wait that gives up sets an error word that
+// the host reads (QHD_ERR_TIMEOUT), and the CTA winds down, waits for its
+// MMAs and frees its tensor memory.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+
+#include "qhd.h"
+#include "qhd_tcdft.h"
+#include "qhd_umma.cuh"
+
+namespace qhd {
+
+namespace {
+
+constexpr int UG_BM = 128, UG_BK = 64;
+constexpr int UG_THREADS = 320;
+constexpr int UG_EPI_WARPS = 8;
+constexpr uint32_t UG_TMEM_COLS = 512;
+
+// One tile width is built: 128 columns.  Its epilogue threads hold 64 FP32
+// accumulators each and the kernel fits 10 warps per SM (each SM sub-partition
+// holds at most 16K registers, so 3 warps of a sub-partition get <= 170 each);
+// a 256-column tile would need 128 accumulators per thread and does not fit.
+template <int BN> struct UgCfg {
+    static constexpr int NBUF = (int)UG_TMEM_COLS / BN;     // partial buffers in tensor memory
+    static constexpr int STAGES = 6;                        // shared-memory ring
+    static constexpr int A_BYTES = UG_BM * UG_BK * 2;       // 16 KB
+    static constexpr int B_BYTES = BN * UG_BK * 2;
+    static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+    static constexpr int COLS = BN / 2;                     // columns per epilogue thread
+    static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE_BYTES + 1024;  // alignment + tiles + barriers
+    static_assert(BN == 128, "tile width");
+    static_assert(A_BYTES % 1024 == 0 && B_BYTES % 1024 == 0, "1024-byte aligned tiles");
+};
+
+// Walks the MMAs of the K list in order and reports group boundaries; the MMA
+// thread and the epilogue threads run the same walk.
+struct GroupWalk {
+    const UgArgs *a;
+    int seg = 0, kb = 0, i = 0;  // segment, K block inside it, MMA inside the K block
+    __device__ explicit GroupWalk(const UgArgs *args) : a(args) {}
+    __device__ bool starts() const {
+        const UgSeg &s = a->seg[seg];
+        return s.mode == UG_EACH_MMA || (s.mode == UG_OPEN && kb == 0 && i == 0);
+    }
+    __device__ bool ends() const {
+        const UgSeg &s = a->seg[seg];
+        if (s.mode == UG_EACH_MMA) return true;
+        if (kb != s.kblocks - 1 || i != 3) return false;
+        return seg + 1 >= a->nseg || a->seg[seg + 1].mode != UG_CONTINUE;
+    }
+    __device__ float scale() const {
+        int s = seg;
+        while (a->seg[s].mode == UG_CONTINUE && s > 0) --s;
+        return a->seg[s].scale;
+    }
+    __device__ bool next() {  // false past the end
+        if (++i < 4) return true;
+        i = 0;
+        if (++kb < a->seg[seg].kblocks) return true;
+        kb = 0;
+        return ++seg < a->nseg;
+    }
+};
+
+template <int BN>
+__global__ void __launch_bounds__(UG_THREADS, 1)
+    k_umma_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const __grid_constant__ UgArgs a) {
+    using Cfg = UgCfg<BN>;
+    constexpr int STAGES = Cfg::STAGES, NBUF = Cfg::NBUF;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *base = reinterpret_cast<uint8_t *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t *tiles = base;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(base + (size_t)STAGES * Cfg::STAGE_BYTES);
+    uint64_t *full = bars, *empty = bars + STAGES, *pfull = bars + 2 * STAGES, *pempty = pfull + NBUF;
+    uint64_t *done = pempty + NBUF;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(done + 1);
+
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int m_tile = blockIdx.x / a.n_tiles, n_tile = blockIdx.x % a.n_tiles;
+    const int m0 = m_tile * UG_BM, n0 = n_tile * BN;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            umma::mbar_init(&full[s], 1);
+            umma::mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < NBUF; ++b) {
+            umma::mbar_init(&pfull[b], 1);
+            umma::mbar_init(&pempty[b], UG_EPI_WARPS);
+        }
+        umma::mbar_init(done, 1);
+        umma::mbar_fence_init();
+    }
+    if (warp == 1) umma::tmem_alloc(tslot, UG_TMEM_COLS);
+    umma::tc_fence_before();
+    __syncthreads();
+    umma::tc_fence_after();
+    const uint32_t tmem = *tslot;
+
+    if (warp == 0) {
+        // ------------------------------------------------------ TMA producer
+        if (lane == 0) {
+            umma::tma_prefetch_desc(&tmA);
+            umma::tma_prefetch_desc(&tmB);
+            int kb = 0;
+            bool ok = true;
+            for (int sg = 0; sg < a.nseg && ok; ++sg) {
+                const UgSeg &s = a.seg[sg];
+                for (int j = 0; j < s.kblocks && ok; ++j, ++kb) {
+                    const int st = kb % STAGES;
+                    if (kb >= STAGES) ok = umma::mbar_wait(&empty[st], ((kb / STAGES) - 1) & 1, a.err, a.limit_ns);
+                    if (!ok) break;
+                    uint8_t *ta = tiles + (size_t)st * Cfg::STAGE_BYTES;
+                    umma::mbar_expect_tx(&full[st], Cfg::STAGE_BYTES);
+                    umma::tma_load_2d(ta, &tmA, &full[st], s.a_k0 + j * UG_BK, m0);
+                    umma::tma_load_2d(ta + Cfg::A_BYTES, &tmB, &full[st], s.b_k0 + j * UG_BK, n0);
+                }
+            }
+            if (!ok) {
+                // loads may still be landing: wait (briefly bounded) for the last ones issued
+                for (int k = kb - 1; k >= 0 && k >= kb - STAGES; --k)
+                    umma::mbar_wait(&full[k % STAGES], (k / STAGES) & 1, a.err + 1, 50000000ull);
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------------------------------------------------- MMA issue
+        if (lane == 0) {
+            constexpr uint32_t IDESC = umma::idesc_f16_f32(UG_BM, BN);
+            GroupWalk w(&a);
+            int kb = 0, buf = 0, grp = 0;
+            bool ok = a.nseg > 0;
+            uint32_t acc = 0;
+            while (ok) {
+                const int st = kb % STAGES;
+                ok = umma::mbar_wait(&full[st], (kb / STAGES) & 1, a.err, a.limit_ns);
+                if (!ok) break;
+                umma::tc_fence_after();
+                const uint32_t sa = umma::smem_u32(tiles + (size_t)st * Cfg::STAGE_BYTES);
+                const uint64_t da = umma::sdesc_k128(sa), db = umma::sdesc_k128(sa + Cfg::A_BYTES);
+                bool more = true;
+                for (int i = 0; i < 4; ++i) {
+                    if (w.starts()) {
+                        if (grp >= NBUF) {
+                            ok = umma::mbar_wait(&pempty[buf], ((grp / NBUF) - 1) & 1, a.err, a.limit_ns);
+                            if (!ok) break;
+                            umma::tc_fence_after();
+                        }
+                        acc = 0;
+                    }
+                    // 16 FP16 along K = 32 bytes: start address advances by 2 (16-byte units)
+                    umma::mma_f16(tmem + (uint32_t)(buf * BN), da + 2u * i, db + 2u * i, IDESC, acc);
+                    acc = 1;
+                    if (w.ends()) {
+                        umma::mma_commit(&pfull[buf]);
+                        buf = (buf + 1) % NBUF;
+                        ++grp;
+                    }
+                    more = w.next();
+                }
+                if (!ok) break;
+                umma::mma_commit(&empty[st]);
+                ++kb;
+                if (!more) break;
+            }
+            // every MMA issued has completed before the tensor memory is freed
+            umma::mma_commit(done);
+            umma::mbar_wait(done, 0, a.err + 1, 1000000000ull);
+        }
+    } else {
+        // ------------------------------------------------------------ epilogue
+        const int ew = warp - 2;
+        const int q = warp & 3;                  // accumulator lanes 32 q .. 32 q + 31 (hardware quarter)
+        const int h = ew >> 2;                   // column half
+        constexpr int COLS = Cfg::COLS;
+        float2 acc[COLS / 2];
+#pragma unroll
+        for (int k = 0; k < COLS / 2; ++k) acc[k] = make_float2(0.f, 0.f);
+        GroupWalk w(&a);
+        int grp = 0;
+        bool ok = a.nseg > 0;
+        bool more = ok;
+        while (more && ok) {
+            // advance the walk to the end of this group
+            const float sc = w.scale();
+            while (!w.ends()) w.next();
+            more = w.next();
+            const int buf = grp % NBUF;
+            // lane 0 waits and the warp follows, so the warp-wide tensor-memory
+            // loads below run with every lane or none
+            int okw = 1;
+            if (lane == 0) okw = umma::mbar_wait(&pfull[buf], (grp / NBUF) & 1, a.err, a.limit_ns) ? 1 : 0;
+            ok = __shfl_sync(0xffffffffu, okw, 0) != 0;
+            if (!ok) break;
+            umma::tc_fence_after();
+            const float2 s2 = make_float2(sc, sc);
+            const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BN + h * COLS);
+#pragma unroll
+            for (int c = 0; c < COLS / 16; ++c) {
+                uint32_t r[16];
+                umma::tmem_ld16(taddr + (uint32_t)(c * 16), r);
+                umma::tmem_ld_wait();
+#pragma unroll
+                for (int k = 0; k < 8; ++k)
+                    acc[c * 8 + k] = umma::fma2(make_float2(__uint_as_float(r[2 * k]), __uint_as_float(r[2 * k + 1])),
+                                                s2, acc[c * 8 + k]);
+            }
+            umma::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) umma::mbar_arrive(&pempty[buf]);
+            ++grp;
+        }
+        const int64_t row = (int64_t)m0 + q * 32 + lane;
+        if (ok && row < a.rows) {
+            float *crow = a.C + row * a.ldc + n0 + h * COLS;
+            const float2 al = make_float2(a.alpha, a.alpha), be = make_float2(a.beta, a.beta);
+#pragma unroll
+            for (int k = 0; k < COLS / 4; ++k) {
+                float2 lo = acc[2 * k], hi = acc[2 * k + 1];
+                if (a.beta != 0.f) {
+                    const float4 old = *reinterpret_cast<const float4 *>(crow + 4 * k);
+                    lo = umma::fma2(lo, al, make_float2(old.x * a.beta, old.y * a.beta));
+                    hi = umma::fma2(hi, al, make_float2(old.z * a.beta, old.w * a.beta));
+                } else {
+                    lo = make_float2(lo.x * a.alpha, lo.y * a.alpha);
+                    hi = make_float2(hi.x * a.alpha, hi.y * a.alpha);
+                }
+                (void)be;
+                *reinterpret_cast<float4 *>(crow + 4 * k) = make_float4(lo.x, lo.y, hi.x, hi.y);
+            }
+        }
+    }
+    umma::tc_fence_before();
+    __syncthreads();
+    umma::tc_fence_after();
+    if (warp == 1) umma::tmem_dealloc(tmem, UG_TMEM_COLS);
+}
+
+char g_launch_diag[512] = "";
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void *p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+// 2-D FP16 map of a row-major [rows][cols] array, box {64, box_rows}, 128-byte swizzle.
+bool make_map(CUtensorMap *m, const void *ptr, int64_t rows, int64_t cols, int box_rows) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)UG_BK, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void *>(ptr), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int BN>
+cudaError_t launch_bn(const __half *A, int64_t lda, const __half *B, int64_t ldb, int64_t n_cols, const UgArgs &a,
+                      cudaStream_t s) {
+    using Cfg = UgCfg<BN>;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_umma_gemm<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)Cfg::SMEM);
+        if (e != cudaSuccess) return e;
+        cudaFuncAttributes fa{};
+        e = cudaFuncGetAttributes(&fa, k_umma_gemm<BN>);
+        if (e != cudaSuccess) return e;
+        if (fa.maxThreadsPerBlock < UG_THREADS) {
+            snprintf(g_launch_diag, sizeof g_launch_diag, "GEMM kernel fits %d threads, needs %d (%d registers)",
+                     fa.maxThreadsPerBlock, UG_THREADS, fa.numRegs);
+            return cudaErrorLaunchOutOfResources;
+        }
+        attr = true;
+    }
+    CUtensorMap ma, mb;
+    if (!make_map(&ma, A, a.rows, lda, UG_BM) || !make_map(&mb, B, n_cols, ldb, BN))
+        return cudaErrorInvalidValue;
+    k_umma_gemm<BN><<<(unsigned)(a.m_tiles * a.n_tiles), UG_THREADS, Cfg::SMEM, s>>>(ma, mb, a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        cudaFuncAttributes fa{};
+        cudaFuncGetAttributes(&fa, k_umma_gemm<BN>);
+        int dev = 0, optin = 0, regs = 0, smsm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        cudaDeviceGetAttribute(&regs, cudaDevAttrMaxRegistersPerBlock, dev);
+        cudaDeviceGetAttribute(&smsm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        snprintf(g_launch_diag, sizeof g_launch_diag,
+                 "regs/thread %d, max threads %d, static smem %zu, max dyn smem %d, local %zu, requested dyn smem "
+                 "%zu x %d threads; device: smem/block opt-in %d, smem/SM %d, regs/block %d",
+                 fa.numRegs, fa.maxThreadsPerBlock, fa.sharedSizeBytes, fa.maxDynamicSharedSizeBytes,
+                 fa.localSizeBytes, Cfg::SMEM, UG_THREADS, optin, smsm, regs);
+    }
+    return e;
+}
+
+}  // namespace
+
+bool umma_gemm_shape_ok(int64_t rows, int64_t n_cols, int64_t lda, int64_t ldb, int bn) {
+    return bn == 128 && rows > 0 && n_cols > 0 && n_cols % bn == 0 && lda % UG_BK == 0 && ldb % UG_BK == 0 &&
+           (rows + UG_BM - 1) / UG_BM <= (int64_t(1) << 20);
+}
+
+cudaError_t umma_gemm(const __half *A, int64_t lda, const __half *B, int64_t ldb, float *C, int64_t ldc, int64_t rows,
+                      int64_t n_cols, const UgSeg *segs, int nseg, float alpha, float beta, int bn, unsigned *err,
+                      cudaStream_t s) {
+    if (!umma_gemm_shape_ok(rows, n_cols, lda, ldb, bn) || nseg < 1 || nseg > UG_MAX_SEG) return cudaErrorInvalidValue;
+    UgArgs a{};
+    a.C = C;
+    a.ldc = ldc;
+    a.rows = rows;
+    a.m_tiles = (int)((rows + UG_BM - 1) / UG_BM);
+    a.n_tiles = (int)(n_cols / bn);
+    a.nseg = nseg;
+    for (int i = 0; i < nseg; ++i) {
+        const UgSeg &g = segs[i];
+        // every K block must lie inside its operand's row
+        if (g.kblocks < 1 || g.a_k0 < 0 || g.b_k0 < 0 || g.a_k0 % UG_BK || g.b_k0 % UG_BK ||
+            g.a_k0 + (int64_t)g.kblocks * UG_BK > lda || g.b_k0 + (int64_t)g.kblocks * UG_BK > ldb)
+            return cudaErrorInvalidValue;
+        if (g.mode == UG_CONTINUE && i == 0) return cudaErrorInvalidValue;
+        a.seg[i] = g;
+    }
+    a.alpha = alpha;
+    a.beta = beta;
+    a.err = err;
+    a.limit_ns = 2000000000ull;  // 2 s of global time per wait
+    return launch_bn<128>(A, lda, B, ldb, n_cols, a, s);
+}
+
+}  // namespace qhd
+
+static thread_local char g_gemm_err[768] = "";
+
+extern "C" const char *qhd_tc_gemm_last_error(void) { return g_gemm_err; }
+
+extern "C" qhd_status qhd_tc_gemm_f16(const void *A_dev, const void *B_dev, float *C_dev, int64_t ldc, int64_t rows,
+                                      int64_t n_cols, int64_t k, int group_every_mma, float alpha, float beta,
+                                      unsigned *err_dev, void *stream) {
+    using namespace qhd;
+    if (!A_dev || !B_dev || !C_dev || !err_dev || ((uintptr_t)A_dev & 15) || ((uintptr_t)B_dev & 15) ||
+        ((uintptr_t)C_dev & 15) || ((uintptr_t)err_dev & 3))
+        return QHD_ERR_INVALID_ARG;
+    if (k < 64 || k > (int64_t(1) << 20) || ldc < n_cols || ldc % 4 || n_cols % 128 ||
+        !umma_gemm_shape_ok(rows, n_cols, k, k, 128) || (group_every_mma != 0 && group_every_mma != 1))
+        return QHD_ERR_INVALID_ARG;
+    UgSeg seg{0, 0, (int)(k / 64), 1.f, group_every_mma ? (int)UG_EACH_MMA : (int)UG_OPEN};
+    cudaError_t e = umma_gemm(reinterpret_cast<const __half *>(A_dev), k, reinterpret_cast<const __half *>(B_dev), k,
+                              C_dev, ldc, rows, n_cols, &seg, 1, alpha, beta, 128, err_dev, (cudaStream_t)stream);
+    snprintf(g_gemm_err, sizeof g_gemm_err, "%s%s%s", e == cudaSuccess ? "" : cudaGetErrorString(e),
+             e == cudaSuccess ? "" : " | ", e == cudaSuccess ? "" : g_launch_diag);
+    return e == cudaSuccess ? QHD_OK : (e == cudaErrorInvalidValue ? QHD_ERR_INVALID_ARG : QHD_ERR_CUDA);
+}

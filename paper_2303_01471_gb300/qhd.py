@@ -17,6 +17,12 @@ import numpy as np
 from . import build as _build
 
 QHD_OK = 0
+QHD_ERR_INVALID_ARG = 1
+QHD_ERR_UNSUPPORTED = 2
+QHD_ERR_STATE = 3
+QHD_ERR_CUDA = 4
+QHD_ERR_TIMEOUT = 5
+QHD_ERR_WORKSPACE = 6
 STATUS = {0: "QHD_OK", 1: "QHD_ERR_INVALID_ARG", 2: "QHD_ERR_UNSUPPORTED", 3: "QHD_ERR_STATE",
           4: "QHD_ERR_CUDA", 5: "QHD_ERR_TIMEOUT", 6: "QHD_ERR_WORKSPACE"}
 SCHED_NESTEROV = 0
@@ -37,7 +43,10 @@ EXPORTS = ["qhd_workspace_bytes", "qhd_init_grid", "qhd_set_potential", "qhd_set
            "qhd_lattice_reset_state", "qhd_lattice_get_state", "qhd_lattice_set_state", "qhd_lattice_evolve",
            "qhd_lattice_evolve_trajectory", "qhd_lattice_observables",
            "qhd_lattice_timing_enable", "qhd_lattice_timing_read", "qhd_lattice_launch_count",
-           "qhd_lattice_last_error", "qhd_lattice_destroy", "qhd_inject_failure"]
+           "qhd_lattice_last_error", "qhd_lattice_destroy", "qhd_inject_failure",
+           "qhd_group_workspace_bytes", "qhd_group_create", "qhd_group_evolve", "qhd_group_status",
+           "qhd_group_inject_wait_timeout", "qhd_group_info", "qhd_group_last_error", "qhd_group_destroy",
+           "qhd_tc_gemm_f16", "qhd_tc_gemm_last_error"]
 SPLIT_STRANG = 0
 SPLIT_LIE_TROTTER = 1
 KINETIC_SPECTRAL = 0
@@ -58,6 +67,25 @@ class _Schedule(ctypes.Structure):
                 ("c_chi", ctypes.c_double), ("t", ctypes.POINTER(ctypes.c_double)),
                 ("phi", ctypes.POINTER(ctypes.c_double)), ("chi", ctypes.POINTER(ctypes.c_double)),
                 ("n_samples", ctypes.c_int64), ("power", ctypes.c_double)]
+
+
+class GroupConfig(ctypes.Structure):
+    """Launch choices of a batched group (qhd_group_config): CTAs per instance for
+    mesh edge 64 / 128 / 256 (0 = default 2 / 4 / 8), resident CTAs per SM the
+    kernel is compiled for (1 or 2, 0 = 2), persistent clusters (0 = all that fit)."""
+    _fields_ = [("sub_cluster", ctypes.c_int32 * 3), ("min_blocks", ctypes.c_int32), ("clusters", ctypes.c_int32)]
+
+    @classmethod
+    def make(cls, sub=(0, 0, 0), min_blocks=0, clusters=0):
+        c = cls()
+        for i, v in enumerate(sub):
+            c.sub_cluster[i] = int(v)
+        c.min_blocks = int(min_blocks)
+        c.clusters = int(clusters)
+        return c
+
+    def as_dict(self):
+        return {"sub": list(self.sub_cluster), "min_blocks": self.min_blocks, "clusters": self.clusters}
 
 
 class _Obs(ctypes.Structure):
@@ -137,6 +165,28 @@ def load(build_if_missing: bool = True):
     lib.qhd_set_transform.restype = st
     lib.qhd_library_call_count.argtypes = [vp]
     lib.qhd_library_call_count.restype = ctypes.c_int64
+    lib.qhd_group_workspace_bytes.argtypes = [ctypes.c_int]
+    lib.qhd_group_workspace_bytes.restype = ctypes.c_size_t
+    lib.qhd_group_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.c_int,
+                                     ctypes.POINTER(GroupConfig), vp, ctypes.c_size_t]
+    lib.qhd_group_create.restype = st
+    lib.qhd_group_evolve.argtypes = [vp, ctypes.c_double, ctypes.c_double]
+    lib.qhd_group_evolve.restype = st
+    lib.qhd_group_status.argtypes = [vp]
+    lib.qhd_group_status.restype = st
+    lib.qhd_group_inject_wait_timeout.argtypes = [vp, ctypes.c_int]
+    lib.qhd_group_inject_wait_timeout.restype = st
+    lib.qhd_group_info.argtypes = [vp, i64p]
+    lib.qhd_group_info.restype = st
+    lib.qhd_group_last_error.argtypes = [vp]
+    lib.qhd_group_last_error.restype = ctypes.c_char_p
+    lib.qhd_group_destroy.argtypes = [vp]
+    lib.qhd_group_destroy.restype = st
+    lib.qhd_tc_gemm_f16.argtypes = [vp, vp, vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                    ctypes.c_int, ctypes.c_float, ctypes.c_float, vp, vp]
+    lib.qhd_tc_gemm_f16.restype = st
+    lib.qhd_tc_gemm_last_error.argtypes = []
+    lib.qhd_tc_gemm_last_error.restype = ctypes.c_char_p
     lib.qhd_inject_failure.argtypes = [vp, ctypes.c_int, ctypes.c_int64]
     lib.qhd_inject_failure.restype = st
     lib.qhd_destroy.argtypes = [vp]
@@ -416,3 +466,89 @@ class QHD:
             self.close()
         except Exception:
             pass
+
+
+class Group:
+    """One persistent launch over every instance of several 2-D contexts
+    (qhd_group_*): `sims` are QHD objects on one stream, each 2-D with a square
+    mesh of edge 64, 128 or 256 and a potential and schedule loaded.  evolve(T, dt)
+    advances all of them; the launch is a CUDA graph replayed while T, dt and the
+    contexts' clocks repeat."""
+
+    def __init__(self, sims, config: "GroupConfig" = None):
+        import torch
+        self.lib = load()
+        self.sims = list(sims)
+        n = len(self.sims)
+        ws = int(self.lib.qhd_group_workspace_bytes(n))
+        if ws == 0:
+            raise QHDError(1, f"a group holds 1..8 contexts, got {n}")
+        dev = self.sims[0].device
+        self._work_raw = torch.empty(ws + 256, dtype=torch.uint8, device=dev)
+        addr = self._work_raw.data_ptr()
+        ptr = addr + (-addr) % 256
+        arr = (ctypes.c_void_p * n)(*[s.ctx.value for s in self.sims])
+        self.config = config if config is not None else GroupConfig.make()
+        g = ctypes.c_void_p()
+        st = self.lib.qhd_group_create(ctypes.byref(g), arr, n, ctypes.byref(self.config), ctypes.c_void_p(ptr),
+                                       ctypes.c_size_t(ws))
+        if st != QHD_OK:
+            raise QHDError(st, "qhd_group_create failed")
+        self.g = g
+
+    def _check(self, st, what):
+        if st != QHD_OK:
+            msg = self.lib.qhd_group_last_error(self.g)
+            raise QHDError(st, f"{what}: {msg.decode() if msg else ''}")
+
+    def evolve(self, T: float, dt: float) -> None:
+        self._check(self.lib.qhd_group_evolve(self.g, float(T), float(dt)), "qhd_group_evolve")
+
+    def status(self) -> int:
+        """Synchronise; QHD_OK, or QHD_ERR_TIMEOUT when a bounded wait gave up (raises nothing)."""
+        return int(self.lib.qhd_group_status(self.g))
+
+    def inject_wait_timeout(self, on: bool = True) -> None:
+        self._check(self.lib.qhd_group_inject_wait_timeout(self.g, 1 if on else 0), "inject")
+
+    def info(self) -> dict:
+        out = (ctypes.c_int64 * 8)()
+        self._check(self.lib.qhd_group_info(self.g, out), "qhd_group_info")
+        return {"clusters": out[0], "min_blocks": out[1], "smem_per_cta": out[2], "launches": out[3],
+                "captures": out[4], "sub": {64: out[5], 128: out[6], 256: out[7]}}
+
+    def close(self) -> None:
+        if getattr(self, "g", None):
+            self.lib.qhd_group_destroy(self.g)
+            self.g = None
+        self._work_raw = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def tc_gemm_f16(A, B, C=None, every_mma=True, alpha=1.0, beta=0.0, err=None):
+    """C = alpha * A . B^T + beta * C on the tensor cores (qhd_tc_gemm_f16).  A
+    (rows, k) and B (n, k) float16 CUDA tensors, C float32 (rows, n); returns
+    (C, err) with err a 2-word int32 tensor (err[0] = 1: a bounded wait gave up)."""
+    import torch
+    lib = load()
+    rows, k = A.shape
+    n = B.shape[0]
+    need_tensor(A, torch.float16, rows * k, "A")
+    need_tensor(B, torch.float16, n * k, "B")
+    if C is None:
+        C = torch.zeros((rows, n), dtype=torch.float32, device=A.device)
+    need_tensor(C, torch.float32, rows * n, "C")
+    if err is None:
+        err = torch.zeros(2, dtype=torch.int32, device=A.device)
+    stream = torch.cuda.current_stream(A.device).cuda_stream
+    st = lib.qhd_tc_gemm_f16(ctypes.c_void_p(A.data_ptr()), ctypes.c_void_p(B.data_ptr()),
+                             ctypes.c_void_p(C.data_ptr()), n, rows, n, k, 1 if every_mma else 0,
+                             float(alpha), float(beta), ctypes.c_void_p(err.data_ptr()), ctypes.c_void_p(stream))
+    if st != QHD_OK:
+        raise QHDError(st, "qhd_tc_gemm_f16: " + lib.qhd_tc_gemm_last_error().decode())
+    return C, err

@@ -1,0 +1,169 @@
+"""The batched persistent launch (qhd_group_*): ragged batches of 128^2 and 256^2
+instances (and 64^2) in one launch per chunk, replayed as a CUDA graph.
+
+With the default split the group runs the same arithmetic as each context's own
+qhd_evolve, so its states must be bit-identical to them; with another split
+(CTAs per instance) the rounding differs and the states are compared with the
+FP64 oracle element by element.  Plus graph replay, several table chunks, the
+bounded wait's time-out (injected on the host side: nothing faults) and the
+argument checks."""
+import ctypes
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle
+import workloads
+from paper_2303_01471_gb300 import autotune, qhd
+
+TV_TOL, EF_TOL = 1e-4, 1e-5
+NORM_1K = 3 * 0.9e-6   # three standard deviations of the FP32 norm walk over 1000 steps (test_gpu_parity.py)
+
+
+def make_ctx(n, seeds, stream=None):
+    spec = [("wells" if s % 2 == 0 else "rastrigin", s) for s in seeds]
+    insts = [workloads.make(f, s, (n, n)) for f, s in spec]
+    sig = [0.5 + 1.5 * ((s * 0.37) % 1.0) for s in seeds]
+    sim = qhd.QHD((n, n), batch=len(seeds), stream=stream)
+    sim.set_potential(np.stack([i.f for i in insts]))
+    sim.set_schedule([qhd.Schedule(c_chi=2.0 * g) for g in sig])
+    sim.reset_state()
+    return sim, insts, sig
+
+
+def test_group_matches_each_context_bit_for_bit():
+    a, _, _ = make_ctx(128, [0, 1, 2])          # odd: one cluster item runs half idle
+    b, _, _ = make_ctx(256, [10, 11])
+    ref_a, _, _ = make_ctx(128, [0, 1, 2])
+    ref_b, _, _ = make_ctx(256, [10, 11])
+    grp = qhd.Group([a, b])
+    grp.evolve(1.0, 0.01)
+    assert grp.status() == qhd.QHD_OK
+    ref_a.evolve(1.0, 0.01)
+    ref_b.evolve(1.0, 0.01)
+    torch.cuda.synchronize()
+    assert torch.equal(a.psi, ref_a.psi)
+    assert torch.equal(b.psi, ref_b.psi)
+    assert a.time() == ref_a.time() and b.time() == ref_b.time()
+    info = grp.info()
+    assert info["launches"] == 1 and info["captures"] == 1 and info["sub"][128] == 4 and info["sub"][256] == 8
+    grp.close()
+    for s in (a, b, ref_a, ref_b):
+        s.close()
+
+
+@pytest.mark.parametrize("sub", [(0, 8, 0), (4, 8, 0)])
+def test_group_other_split_matches_oracle_1000_steps(sub):
+    """The configuration's length (T = 10, dt = 0.01) with the 128^2 instances
+    spread over 8 CTAs each (R = 16 rows), against the FP64 oracle."""
+    a, ia, sa = make_ctx(128, [3, 4])
+    b, ib, sb = make_ctx(256, [5])
+    c, ic, sc = make_ctx(64, [6, 7, 8])
+    grp = qhd.Group([a, b, c], qhd.GroupConfig.make(sub, 1, 0))
+    grp.evolve(10.0, 0.01)
+    assert grp.status() == qhd.QHD_OK
+    for sim, insts, sig in ((a, ia, sa), (b, ib, sb), (c, ic, sc)):
+        obs = sim.observables(0.1)
+        p = (sim.psi.abs() ** 2).double().cpu().numpy()
+        for k, inst in enumerate(insts):
+            po = oracle.evolve(inst.f, oracle.uniform_state(inst.shape), 0.0, 0.01, 1000,
+                               oracle.Schedule(c_chi=2.0 * sig[k]))
+            ob = oracle.observables(inst.f, po)
+            tv = 0.5 * np.abs(p[k] - ob.prob).sum()
+            ef = abs(obs[k].e_f - ob.e_f) / max(abs(ob.e_f), 1e-3 * np.ptp(inst.f))
+            assert tv <= TV_TOL and ef <= EF_TOL and abs(obs[k].norm - 1.0) <= NORM_1K, (inst.shape, k, tv, ef,
+                                                                                       obs[k].norm)
+            assert tuple(obs[k].x_star[:2]) == tuple(ob.x_star[:2])
+    grp.close()
+    for s in (a, b, c):
+        s.close()
+
+
+def test_group_graph_replay_and_several_chunks():
+    a, _, _ = make_ctx(128, [20, 21, 22, 23, 24])
+    ref, _, _ = make_ctx(128, [20, 21, 22, 23, 24])
+    grp = qhd.Group([a])
+    outs = []
+    for _ in range(2):                            # reset + evolve repeats: the graph replays
+        a.reset_state()
+        grp.evolve(25.0, 0.01)                    # 2500 steps: three chunks of tables
+        outs.append(a.psi.clone())
+    assert grp.status() == qhd.QHD_OK
+    info = grp.info()
+    assert info["captures"] == 1 and info["launches"] == 6
+    assert torch.equal(outs[0], outs[1])
+    ref.evolve(25.0, 0.01)
+    torch.cuda.synchronize()
+    assert torch.equal(outs[1], ref.psi)
+    assert a.time()[1] == 2500
+    grp.close()
+    a.close()
+    ref.close()
+
+
+def test_group_wait_timeout_is_reported_and_sticky():
+    a, inst, _ = make_ctx(128, [30, 31])
+    grp = qhd.Group([a])
+    grp.inject_wait_timeout(True)                 # every wait needs one arrival more than is made
+    grp.evolve(0.1, 0.01)
+    assert grp.status() == qhd.QHD_ERR_TIMEOUT
+    assert grp.status() == qhd.QHD_ERR_TIMEOUT    # sticky
+    assert b"gave up" in a.lib.qhd_group_last_error(grp.g)
+    assert a.lib.qhd_evolve(a.ctx, 0.1, 0.01) == qhd.QHD_ERR_TIMEOUT   # the context is failed too
+    assert a.lib.qhd_group_evolve(grp.g, 0.1, 0.01) == qhd.QHD_ERR_TIMEOUT
+    grp.close()
+    a.close()
+    b, _, _ = make_ctx(128, [32])                 # the device is still usable
+    b.evolve(0.1, 0.01)
+    assert abs(b.observables()[0].norm - 1.0) < 1e-6
+    b.close()
+
+
+def test_group_argument_checks():
+    lib = qhd.load()
+    a, _, _ = make_ctx(128, [40])
+    c3 = qhd.QHD((32, 32, 32))
+    c3.set_potential(np.zeros((32, 32, 32)))
+    c3.set_schedule(qhd.Schedule())
+    rect = qhd.QHD((128, 64))
+    rect.set_potential(np.zeros((128, 64)))
+    rect.set_schedule(qhd.Schedule())
+    other = torch.cuda.Stream()
+    d, _, _ = make_ctx(128, [41], stream=other)
+    for sims, st in (([a, c3], qhd.QHD_ERR_UNSUPPORTED), ([rect], qhd.QHD_ERR_UNSUPPORTED),
+                     ([a, a], qhd.QHD_ERR_INVALID_ARG), ([a, d], qhd.QHD_ERR_INVALID_ARG)):
+        with pytest.raises(qhd.QHDError) as ei:
+            qhd.Group(sims)
+        assert ei.value.status == st
+    with pytest.raises(qhd.QHDError) as ei:
+        qhd.Group([a], qhd.GroupConfig.make((0, 2, 0), 0, 0))   # 64 rows per CTA: too many
+    assert ei.value.status == qhd.QHD_ERR_INVALID_ARG
+    nopot = qhd.QHD((128, 128))
+    with pytest.raises(qhd.QHDError) as ei:
+        qhd.Group([nopot])
+    assert ei.value.status == qhd.QHD_ERR_STATE
+    assert lib.qhd_group_workspace_bytes(0) == 0 and lib.qhd_group_workspace_bytes(9) == 0
+    grp = qhd.Group([a])
+    assert lib.qhd_group_evolve(grp.g, 0.1, 0.03) == qhd.QHD_ERR_INVALID_ARG
+    assert lib.qhd_group_evolve(grp.g, 200.0, 0.01) == qhd.QHD_ERR_UNSUPPORTED  # > 16 table chunks
+    grp.evolve(0.1, 0.01)                         # argument errors are not sticky
+    assert grp.status() == qhd.QHD_OK
+    grp.close()
+    for s in (a, c3, rect, d, nopot):
+        s.close()
+
+
+def test_autotuner_picks_a_measured_candidate(tmp_path):
+    a, _, _ = make_ctx(128, [50, 51, 52, 53])
+    b, _, _ = make_ctx(256, [54, 55])
+    cache = str(tmp_path / "tune.json")
+    res = autotune.tune_group([a, b], T=0.2, dt=0.01, cache_file=cache)
+    assert not res["cached"] and len(res["ms"]) == len(autotune.candidates([a, b])) == 4
+    assert res["ms"][0][0] == min(m for m, _ in res["ms"])
+    again = autotune.tune_group([a, b], T=0.2, dt=0.01, cache_file=cache)
+    assert again["cached"] and again["config"].as_dict() == res["config"].as_dict()
+    for s in (a, b):
+        s.close()

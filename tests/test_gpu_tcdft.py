@@ -1,14 +1,15 @@
 """Parity of the tensor-core DFT transform (dense DFT GEMMs on FP16 operands,
-FP32 accumulation) with the FP64 oracle, through the C ABI.
+FP32 accumulation, the project's tcgen05 kernel) with the FP64 oracle, through
+the C ABI.  No library GEMM is called (library_call_count stays 0).
 
-The fixed-point slice form (10 products) is held to the tolerances of the FFT
-path: TV(|psi|^2) <= 1e-4, relative E[f] error <= 1e-5, and the norm within
-the FP32 floor.  The floating hi/lo forms (3 and 5 products) lose norm through
-the tensor cores' biased FP32 accumulation; their tests pin that behaviour
-(close to the oracle, a norm loss of the measured size) and keep the strict
-bound as an expected failure.  The 512^2 case is the batch shape of the
-tensor-core workload (Gaussian wells K = 16, T = 10, dt = 0.01) on 8 of its
-instances.
+Both operand forms are held to the tolerances of the FFT path: TV(|psi|^2) <=
+1e-4, relative E[f] error <= 1e-5, and the norm within the FP32 floor.  The
+floating hi/lo forms (3 and 5 products) reach them because the GEMM adds every
+16-term MMA partial to the FP32 result with round-to-nearest instead of letting
+the tensor memory accumulate the whole K (with a library GEMM's long
+accumulation they lost ~2e-4 of the norm per 100 steps).  The 512^2 case is the
+batch shape of the tensor-core workload (Gaussian wells K = 16, T = 10,
+dt = 0.01) on 8 of its instances.
 """
 import math
 
@@ -24,7 +25,7 @@ from paper_2303_01471_gb300 import qhd
 
 TV_TOL = 1e-4
 EF_TOL = 1e-5
-NORM_FP32_FLOOR_PER_1K = 1e-6
+NORM_WALK_1K = 0.9e-6   # std of the FP32 norm walk over 1000 steps (test_gpu_parity.py)
 
 
 def run_tc(fb, scheds, T, dt, products, split=qhd.SPLIT_STRANG, t0=None, pieces=1, transform=None):
@@ -61,7 +62,7 @@ def check(psi_g, obs_g, f, psi_o, steps, elementwise=True):
     tv, ef, el, ob = errors(psi_g, obs_g, f, psi_o)
     assert tv <= TV_TOL, f"TV {tv:.3e}"
     assert ef <= EF_TOL, f"E[f] rel err {ef:.3e}"
-    assert abs(obs_g.norm - 1.0) <= 4 * NORM_FP32_FLOOR_PER_1K * max(1.0, steps / 1000), \
+    assert abs(obs_g.norm - 1.0) <= 3 * NORM_WALK_1K * max(1.0, math.sqrt(steps / 1000)), \
         f"norm drift {obs_g.norm - 1:.3e}"
     assert abs(obs_g.p_succ - ob.p_succ) <= 2 * TV_TOL
     assert tuple(obs_g.x_star[: f.ndim]) == tuple(ob.x_star[: f.ndim])
@@ -84,7 +85,7 @@ def test_tc_fixed_short_runs_own_schedules(n):
     insts, fb, scheds = short_batch(n)
     dt, steps = 0.01, 100
     psi, obs, gemms, launches = run_tc(fb, scheds, steps * dt, dt, 10)
-    assert gemms == 4 * 4 * steps
+    assert gemms == 0
     for b, inst in enumerate(insts):
         psi_o = oracle.evolve(inst.f, oracle.uniform_state((n, n)), 0.0, dt, steps,
                               oracle.Schedule(c_chi=2.0 * inst.sigma))
@@ -92,32 +93,17 @@ def test_tc_fixed_short_runs_own_schedules(n):
 
 
 @pytest.mark.parametrize("products", [3, 5])
-@pytest.mark.parametrize("n", [64, 256])
-def test_tc_floating_forms_lose_norm(n, products):
-    """The floating hi/lo forms follow the oracle to ~1e-3 over 100 steps, but the
-    norm falls: the tensor cores' FP32 accumulation is biased towards zero."""
+@pytest.mark.parametrize("n", [64, 128, 256])
+def test_tc_floating_forms_strict_parity(n, products):
+    """The floating hi/lo forms over 100 steps within the strict tolerances."""
     insts, fb, scheds = short_batch(n)
     dt, steps = 0.01, 100
     psi, obs, gemms, _ = run_tc(fb, scheds, steps * dt, dt, products)
-    assert gemms == 4 * steps
+    assert gemms == 0
     for b, inst in enumerate(insts):
         psi_o = oracle.evolve(inst.f, oracle.uniform_state((n, n)), 0.0, dt, steps,
                               oracle.Schedule(c_chi=2.0 * inst.sigma))
-        tv, ef, el, _ = errors(psi[b], obs[b], inst.f, psi_o)
-        assert tv <= 2e-3 and el <= 5e-3, (tv, el)
-        assert -5e-3 < obs[b].norm - 1.0 < -1e-5, obs[b].norm - 1.0
-
-
-@pytest.mark.xfail(reason="floating hi/lo operands: biased tensor-core accumulation loses ~2e-4 of the "
-                          "norm per 100 steps", strict=False)
-@pytest.mark.parametrize("products", [3, 5])
-def test_tc_floating_forms_strict_parity(products):
-    insts, fb, scheds = short_batch(128)
-    psi, obs, _, _ = run_tc(fb, scheds, 1.0, 0.01, products)
-    for b, inst in enumerate(insts):
-        psi_o = oracle.evolve(inst.f, oracle.uniform_state((128, 128)), 0.0, 0.01, 100,
-                              oracle.Schedule(c_chi=2.0 * inst.sigma))
-        check(psi[b], obs[b], inst.f, psi_o, 100)
+        check(psi[b], obs[b], inst.f, psi_o, steps)
 
 
 def test_tc_own_kinetic_tables_and_chunks():
@@ -129,7 +115,7 @@ def test_tc_own_kinetic_tables_and_chunks():
     scheds = [qhd.Schedule(c_phi=1.5), qhd.Schedule(c_phi=2.5)]
     dt, steps = 0.01, 600
     psi, obs, gemms, _ = run_tc(fb, scheds, steps * dt, dt, 10, pieces=2)
-    assert gemms == 4 * 4 * steps
+    assert gemms == 0
     for b, inst in enumerate(insts):
         psi_o = oracle.evolve(inst.f, oracle.uniform_state((n, n)), 0.0, dt, steps,
                               oracle.Schedule(c_phi=scheds[b].c_phi))
@@ -171,14 +157,13 @@ def test_tc_fixed_512sq_wells_batch_vs_oracle():
     insts, psi_o = c4_batch()
     fb = np.stack([i.f for i in insts])
     psi, obs, gemms, _ = run_tc(fb, qhd.Schedule(), 10.0, 0.01, 10)
-    assert gemms == 16000
+    assert gemms == 0
     for b, inst in enumerate(insts):
         check(psi[b], obs[b], inst.f, psi_o[b], 1000, elementwise=False)
 
 
-@pytest.mark.xfail(reason="floating hi/lo operands: biased tensor-core accumulation (TV ~1.6e-2 after "
-                          "1000 steps at 512^2)", strict=False)
 def test_tc_3product_512sq_wells_batch_vs_oracle():
+    """The configured form (FP16 hi/lo, 3 products) on the batch shape, 1000 steps."""
     insts, psi_o = c4_batch()
     fb = np.stack([i.f for i in insts[:2]])
     psi, obs, gemms, _ = run_tc(fb, qhd.Schedule(), 10.0, 0.01, 3)
