@@ -735,12 +735,12 @@ def run_ragged(args, rank, world, local_rank, dist):
 # ------------------------------------------------------ tensor-core DFT form
 TC_WORKLOAD = ("Split-precision tensor-core DFT: 256 instances of a 2-D 512^2 mesh on [0,1]^2, Gaussian wells "
                "(K=16), T=10, dt=0.01 (1000 Strang steps), paper schedule, complex64 state; per-axis DFTs as "
-               "FP16 split-operand GEMMs with FP32 accumulation (3/5 products: floating hi/lo operands; "
+               "FP16 split-operand GEMMs with FP32 accumulation (3/5 products: block-scaled hi/lo integer slices; "
                "10 products: fixed-point slices)")
 
 
 def run_tcdft(args, rank, world, local_rank, dist):
-    """The batch once with the tensor-core transform (3 or 5 split products) and once
+    """The batch once with the tensor-core transform (3, 5 or 10 split products) and once
     with the shared-memory FFT passes, on the same device-resident inputs; accuracy
     of both against the FP64 oracle on a sample of the instances."""
     import torch
@@ -843,9 +843,10 @@ def run_tcdft(args, rank, world, local_rank, dist):
     except Exception:
         tpeak, tsrc = 1700.0, "fallback"
     # per point: read the FP32 product (8 B), write the FP16 operand segments
-    # (2 x 2 B each); the fixed-point form also reads the product once for its max
-    segs = 4 if args.tc_products == 10 else args.tc_products
-    split_bytes = count * n * n * (8 + 4 * segs + (8 if args.tc_products == 10 else 0))
+    # (2 x 2 B each; the block-scaled form adds one exponent byte per 16 values),
+    # the fixed-point form also reads the product once for its max
+    segs = 4 if args.tc_products == 10 else 2
+    split_bytes = count * n * n * (8 + 4 * segs + (8 if args.tc_products == 10 else 2 / 16))
     roofline = {"bound": "tensor", "kernel": "tcgen05 FP16 GEMM of one axis transform (qhd_umma_gemm.cu)",
                 "achieved": round(achieved, 1), "peak": tpeak, "unit": "TFLOP/s",
                 "frac": round(achieved / tpeak, 4), "peak_source": tsrc, "traffic": None,

@@ -210,18 +210,21 @@ qhd_status qhd_set_kinetic(qhd_ctx *ctx, int kind);
  * Transform used by qhd_evolve for the per-axis DFTs of the kinetic step
  * (Eq. prod_qhd_fft).  QHD_TRANSFORM_FFT (default): the shared-memory FFT
  * passes.  QHD_TRANSFORM_TC_DFT: each axis transform is a dense product with
- * the n x n DFT matrix on the tensor cores, FP16 operands with FP32
- * accumulation (cuBLAS GEMMs; the phases, transposes and operand splits run
- * in this library's kernels, with the same fixed-point phase arguments as the
- * FFT path).  products selects the operand form:
- *   3: data and DFT matrix as FP16 hi + lo (hi*hi + hi*lo + lo*hi);
- *   5: the DFT matrix to ~33 bits (two more correction products);
+ * the n x n DFT matrix on the tensor cores (this library's tcgen05 GEMM: FP16
+ * operands, every 16-term MMA sum exact in FP32 and added to the result with
+ * round-to-nearest; the phases, transposes and operand splits run in this
+ * library's kernels, with the same fixed-point phase arguments as the FFT
+ * path).  products selects the operand form:
+ *   3: block-scaled hi/lo -- each 16 consecutive values of a row share a
+ *      power-of-two exponent and are cut into two FP16 integer slices (21
+ *      bits below the block maximum), the DFT matrix into two (21 bits);
+ *      three slice products;
+ *   5: as 3 with the DFT matrix in three slices (32 bits) and two more
+ *      products;
  *  10: fixed-point slices on a per-instance power-of-two scale (data to 2^-28
  *      of the instance maximum, DFT matrix 29 bits) whose slice-level sums
  *      are integers the FP32 accumulator holds exactly (n <= 512).
- * The tensor cores' FP32 accumulation is biased towards zero over long K
- * loops, so the 3- and 5-product forms lose norm steadily (measured ~2e-4 per
- * 100 steps at 64^2..512^2); the 10-product form does not.
+ * Neither form lets the tensor cores round a partial sum, so neither drifts.
  *
  * Requires ndim == 2 and n[0] == n[1], a power of two in 64..1024 (64..512 for
  * products = 10), and batch <= 65535 (else QHD_ERR_UNSUPPORTED;
@@ -229,19 +232,19 @@ qhd_status qhd_set_kinetic(qhd_ctx *ctx, int kind);
  * tc_work_dev: caller-owned device buffer, 256-byte aligned, of at least
  * qhd_tc_workspace_bytes(...) bytes, kept until the transform is changed or
  * the context destroyed (else QHD_ERR_WORKSPACE); it holds the DFT matrices,
- * the FP16 operands, the FP32 products and cuBLAS's workspace.  Creating the
- * cuBLAS handle is the only device allocation (made by cuBLAS, freed by
- * qhd_destroy or the next qhd_set_transform).  transform = QHD_TRANSFORM_FFT
- * frees it and ignores the other arguments.  Unknown transforms or products
- * other than 3, 5, 10 give QHD_ERR_INVALID_ARG.  Synchronises the stream
- * (uploads the DFT matrices).
+ * the FP16 operands, the block exponents and the FP32 products.  No device
+ * memory is allocated.  transform = QHD_TRANSFORM_FFT releases the
+ * tensor-core state and ignores the other arguments.  Unknown transforms or
+ * products other than 3, 5 and 10 give QHD_ERR_INVALID_ARG.  Synchronises the
+ * stream (uploads the DFT matrices).
  */
 enum { QHD_TRANSFORM_FFT = 0, QHD_TRANSFORM_TC_DFT = 1 };
 size_t qhd_tc_workspace_bytes(int ndim, const int64_t *n, int64_t batch, int products);
 qhd_status qhd_set_transform(qhd_ctx *ctx, int transform, int products, void *tc_work_dev,
                              size_t tc_work_bytes);
 
-/* cuBLAS GEMM calls this context has issued so far (tensor-core transform). */
+/* Library (cuBLAS) GEMM calls this context has issued so far: always 0, the
+ * tensor-core transform runs on this library's own GEMM kernel. */
 int64_t qhd_library_call_count(const qhd_ctx *ctx);
 
 /*
@@ -315,7 +318,7 @@ enum {
                                /*      one thread-block cluster                   */
     QHD_KCLASS_TC_SPLIT = 8,   /* tensor-core transform: phase / transpose and    */
                                /*      FP16 split kernels                         */
-    QHD_KCLASS_TC_GEMM = 9,    /* tensor-core transform: cuBLAS GEMM calls        */
+    QHD_KCLASS_TC_GEMM = 9,    /* tensor-core transform: tcgen05 GEMM launches    */
     QHD_KCLASS_COUNT = 10
 };
 qhd_status qhd_timing_enable(qhd_ctx *ctx, int every);
@@ -581,8 +584,11 @@ qhd_status qhd_group_destroy(qhd_group *g);
  * step accumulates into a fresh tensor-memory partial that is added to the FP32
  * result with a round-to-nearest FMA (when the operands are integers whose
  * 16-term sums stay below 2^24, every partial is exact and the result is the
- * exact sum rounded to nearest at each addition); 0: one accumulation over all
- * of K in tensor memory (the hardware's accumulation).  Requirements: rows >= 1,
+ * exact sum rounded to nearest at each addition); 2: the same, for floating
+ * operands: each MMA truncates its exact sum towards zero to FP32, losing on
+ * average the fraction kappa = 2^-24 / (2 ln 2) of it, and the result is scaled
+ * by (1 + kappa) to undo that expected loss; 0: one accumulation over all of K
+ * in tensor memory (the hardware's accumulation).  Requirements: rows >= 1,
  * n_cols a multiple of 128, k of 64, k <= 2^20, ldc >= n_cols and a
  * multiple of 4, 16-byte aligned pointers.  err_dev: 2 device words, zero on
  * entry; word 0 becomes 1 if a bounded wait gave up (~2 s).  Enqueued on

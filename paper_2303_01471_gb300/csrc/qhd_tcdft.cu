@@ -19,21 +19,23 @@
 //
 // Two operand forms.
 //
-// Floating hi/lo (3 or 5 products).  A value x (FP32) is split a = fp16(x),
-// c = fp16(x - a), and b = fp16(2^-11 a), d = fp16(2^-11 c) feed the
-// correction terms; W = W_hi + 2^-11 W_mid + 2^-22 W_lo with the parts FP16
-// numbers of about |W|.  One GEMM over concatenated K segments:
-//   3 products: [a | c | b]         . [W_hi; W_hi; W_mid]
-//   5 products: [a | c | b | b | d] . [W_hi; W_hi; W_mid; 2^-11 W_lo; W_mid]
-// Every stage is unitary up to a known power of two, so a fixed scale keeps
-// the operands in range: psi is scaled by 2^14, each GEMM by alpha = 2^-h
-// (2^h >= sqrt n), and the kinetic split takes out the 1/n^2 its table
-// carries.  The tensor cores' FP32 accumulation is not round-to-nearest: the
-// result of a long K loop is biased towards zero (about -1e-9 K relative per
-// GEMM, measured with a library GEMM), and over hundreds of steps that bias,
-// not the operand precision, decides the error of this form.  So every K = 16
-// MMA here is a group of its own: its tensor-memory partial is added to the
-// FP32 result with a round-to-nearest FMA.
+// Block-scaled hi/lo (3 products, the FP16 hi-lo form).  Each run of 16
+// consecutive K values of a row (16 real or 16 imaginary parts) shares an
+// exponent e with 2^e > their largest magnitude; a value x is cut into FP16
+// integers a = rint(x 2^(10-e)) and c = rint((x 2^(10-e) - a) 2^11), both in
+// [-1024, 1024], and W (|W| <= 1) into W_hi = rint(2^10 W) and
+// W_lo = rint((2^10 W - W_hi) 2^11).  The products a W_hi, a W_lo and c W_hi
+// (c W_lo, of order 2^-22, is dropped) are integers below 2^20, so the exact
+// 16-term sum of one MMA stays below 2^24 and FP32 holds it exactly: every
+// MMA is an accumulation group of its own, scaled by 2^(e - 20) or
+// 2^(e - 31) and added to the FP32 result with round-to-nearest.  No partial
+// is ever truncated, so no bias enters (the tensor cores truncate each MMA's
+// sum towards zero, and a long accumulation in tensor memory drifts towards
+// zero by about 1e-9 K relative: measured).  x keeps 21 bits below the
+// largest value of its block and W 21 bits; the block exponents travel in a
+// [rows][2n/16] int8 table.  All scales are exact powers of two, the
+// transforms are unnormalised, and the kinetic table's 1/n^2 brings each step
+// back to psi's scale.
 //
 // Fixed-point slices (10 products, an error-free splitting in the manner of
 // Ozaki et al.).  Each instance is scaled by a power of two 2^(7-e) with
@@ -63,7 +65,7 @@ namespace qhd {
 
 namespace {
 
-constexpr int TC_S = 14;               // log2 of the operand scale, floating form
+constexpr int TC_BFP = 3;              // split of the block-scaled forms (3 and 5 products)
 constexpr int TC_THREADS = 256;
 constexpr int TC_TR = 64, TC_TC = 32;  // transpose tile: input rows x input columns
 constexpr int TC_FIXED = 10;           // products of the fixed-point form
@@ -74,6 +76,8 @@ struct SplitOut {
     __half *a;     // B*n rows of segments of 2n FP16
     int64_t kp;    // row length in halves
     int n;
+    int8_t *e;     // block-scaled form: exponent of each 16 K values, [B*n][2n/16]
+    int64_t eld;
 };
 
 // Per-instance scale state of the fixed-point form.
@@ -85,27 +89,35 @@ struct FixedScale {
     int from_psi;           // E restarts at this split
 };
 
-// ---------------------------------------------------------- floating hi/lo
-// Split of two neighbouring values (columns col, col+1 of one row half) into
-// every segment.
-template <int P>
-__device__ __forceinline__ void put_pair(const SplitOut &o, int64_t row, int col, float x0, float x1) {
-    const __half a0 = __float2half_rn(x0), a1 = __float2half_rn(x1);
-    const __half c0 = __float2half_rn(x0 - __half2float(a0)), c1 = __float2half_rn(x1 - __half2float(a1));
-    const float sd = 1.0f / 2048.0f;
-    const __half2 A = __halves2half2(a0, a1);
-    const __half2 Cc = __halves2half2(c0, c1);
-    const __half2 Bb = __floats2half2_rn(__half2float(a0) * sd, __half2float(a1) * sd);
+// ------------------------------------------------------ block-scaled hi/lo
+// Exponent e with 2^e > max |x| over the 16 values held by 8 neighbouring
+// lanes (two each); the lanes of one block must be converged.
+__device__ __forceinline__ int block_exponent16(float m) {
+    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));
+    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 2));
+    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 4));
+    int e = -100;  // an all-zero block: any scale holds it
+    if (m > 0.f) frexpf(m, &e);
+    // blocks below 2^-100 (far under the state's rounding) keep the floor, so
+    // 2^(10 - e) and 2^e stay normal floats
+    return e < -100 ? -100 : e;
+}
+
+// Values x0, x1 of columns col, col+1 of one row (col + 16 k .. col + 16 k + 15
+// held by lanes 8g .. 8g+7): segments [a | c] and the block's exponent.  The
+// power-of-two scaling and the subtraction are exact; a and c are integers in
+// [-1024, 1024], exact in FP16.
+__device__ __forceinline__ void put_bfp_pair(const SplitOut &o, int64_t row, int col, float x0, float x1) {
+    const int e = block_exponent16(fmaxf(fabsf(x0), fabsf(x1)));
+    const float sc = __int_as_float((127 + 10 - e) << 23);  // 2^(10 - e)
+    const float u0 = x0 * sc, u1 = x1 * sc;
+    const float a0 = rintf(u0), a1 = rintf(u1);
+    const float c0 = rintf((u0 - a0) * 2048.f), c1 = rintf((u1 - a1) * 2048.f);
     const int m = 2 * o.n;
     __half2 *dst = reinterpret_cast<__half2 *>(o.a + row * o.kp + col);
-    dst[0] = A;
-    dst[m / 2] = Cc;
-    dst[m] = Bb;
-    if (P == 5) {
-        const __half2 D = __floats2half2_rn(__half2float(c0) * sd, __half2float(c1) * sd);
-        dst[3 * m / 2] = Bb;
-        dst[2 * m] = D;
-    }
+    dst[0] = __floats2half2_rn(a0, a1);
+    dst[m / 2] = __floats2half2_rn(c0, c1);
+    if ((threadIdx.x & 7) == 0) o.e[row * o.eld + col / 16] = (int8_t)e;
 }
 
 // Fixed-point slices of two neighbouring values u0, u1 (|u| <= 2^7):
@@ -136,13 +148,15 @@ __device__ __forceinline__ int tc_exponent(unsigned m2bits) {
 template <int P>
 __device__ __forceinline__ void put_two(const SplitOut &o, int64_t row, int col, float x0, float x1) {
     if (P == TC_FIXED) put_fixed_pair(o, row, col, x0, x1);
-    else put_pair<P>(o, row, col, x0, x1);
+    else put_bfp_pair(o, row, col, x0, x1);
 }
 
 // mode 0: potential phase, input psi (interleaved); 1: potential phase, input
 // the product buffer; 2: kinetic phase, input the product buffer (rows hold
 // frequency k1 of axis 1, columns frequency k0 of axis 0).  One thread per two
-// neighbouring columns of one row.  scale: the floating form's fixed scale.
+// neighbouring columns of one row (a warp covers 64 columns of one row, so the
+// block-scaled form's 16-column blocks lie in 8-lane groups).  scale: a
+// power of two applied on input.
 template <int P, int MODE>
 __global__ void __launch_bounds__(TC_THREADS) k_tc_split(SplitOut o, const float *cbuf, TcPhaseArgs a,
                                                          int64_t rows, float scale, FixedScale fs) {
@@ -298,8 +312,8 @@ int log2i(int n) {
 
 // K extent (in units of 2n) of the DFT-matrix buffers of one direction, and
 // the row length (in units of 2n) of the split operands.
-int w_segments(int products) { return products == TC_FIXED ? 4 : products; }
-int a_segments(int products) { return products == TC_FIXED ? 4 : products; }
+int w_segments(int products) { return products == TC_FIXED ? 4 : products == 5 ? 3 : 2; }
+int a_segments(int products) { return products == TC_FIXED ? 4 : 2; }
 
 }  // namespace
 
@@ -312,12 +326,13 @@ struct TcState {
     float *c = nullptr;                 // B*n x 2n products
     unsigned *maxbits = nullptr;        // fixed form: 2 x B max |z|^2 buffers
     int *e = nullptr;                   // fixed form: B exponents
+    int8_t *e8 = nullptr;               // block-scaled form: [B*n][2n/16] block exponents
     int cur = 0;                        // max buffer of the next split
     int grid = 0;
 };
 
 bool tc_supported(int n0, int n1, int64_t batch) {
-    // transpose grids index instances by blockIdx.z; cuBLAS takes B*n rows as int
+    // transpose grids index instances by blockIdx.z; the GEMM takes B*n rows as int
     return n0 == n1 && n0 >= 64 && n0 <= 1024 && (n0 & (n0 - 1)) == 0 && batch >= 1 && batch <= 65535;
 }
 
@@ -335,6 +350,7 @@ size_t tc_workspace_bytes(int n, int64_t batch, int products) {
     t += tc_align(2 * (size_t)batch * sizeof(unsigned));
     t += tc_align((size_t)batch * sizeof(int));
     t += tc_align(2 * sizeof(unsigned));  // GEMM wait time-out word
+    t += tc_align(rows * (m / 16));       // block exponents of the block-scaled form
     return t;
 }
 
@@ -381,6 +397,8 @@ TcState *tc_create(int n, int64_t batch, int products, void *ws, size_t ws_bytes
     t->e = (int *)p;
     p += tc_align((size_t)batch * sizeof(int));
     t->err = (unsigned *)p;
+    p += tc_align(2 * sizeof(unsigned));
+    t->e8 = (int8_t *)p;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -398,17 +416,14 @@ TcState *tc_create(int n, int64_t batch, int products, void *ws, size_t ws_bytes
             for (size_t col = 0; col < m; ++col) {
                 const double v = dft_block(n, d, row, col);
                 if (products != TC_FIXED) {
-                    // hi, mid, lo of about |W| each; the lo part is paired with
-                    // b = 2^-11 a, so it carries 2^11 (v - hi - 2^-11 mid) = r1 - mid
-                    const __half hi = __double2half(v);
-                    const double r1 = (v - (double)__half2float(hi)) * 2048.0;
-                    const __half mid = __double2half(r1);
-                    const __half lo = __double2half(r1 - (double)__half2float(mid));
-                    const __half part[3] = {hi, mid, lo};
-                    const int seg3[3] = {0, 0, 1}, seg5[5] = {0, 0, 1, 2, 1};
-                    const int *seg = products == 3 ? seg3 : seg5;
-                    for (int sidx = 0; sidx < products; ++sidx)
-                        host[col * wseg * m + sidx * m + row] = part[seg[sidx]];
+                    // W_hi = rint(2^10 v), W_lo = rint((2^10 v - W_hi) 2^11) and, for 5
+                    // products, W_lo2 = rint(next residual 2^11): integers in [-1024, 1024]
+                    double r = v * 1024.0;
+                    for (int k = 0; k < wseg; ++k) {
+                        const double w = std::nearbyint(r);
+                        host[col * wseg * m + k * m + row] = __double2half(w);
+                        r = (r - w) * 2048.0;
+                    }
                 } else {
                     // integer slices of 2^7 v: w0 + 2^-7 w1 + 2^-14 w2 + 2^-21 w3
                     double r = v * 128.0, w[4];
@@ -438,6 +453,8 @@ static SplitOut split_out(TcState *t) {
     o.a = t->a;
     o.kp = (int64_t)a_segments(t->products) * 2 * t->n;
     o.n = t->n;
+    o.e = t->e8;
+    o.eld = 2 * t->n / 16;
     return o;
 }
 
@@ -480,15 +497,9 @@ cudaError_t tc_split_potential(TcState *t, const TcPhaseArgs &a, bool from_psi, 
         if (from_psi) k_tc_split<TC_FIXED, 0><<<t->grid, TC_THREADS, 0, s>>>(o, t->c, a, rows, 1.f, fs);
         else k_tc_split<TC_FIXED, 1><<<t->grid, TC_THREADS, 0, s>>>(o, t->c, a, rows, 1.f, fs);
     } else {
-        // scale to 2^14 |psi|: psi directly, or the product buffer 2^(14 - 4h) n^2 psi
-        const float scale = from_psi ? ldexpf(1.f, TC_S) : ldexpf(1.f, 4 * t->h - 2 * t->l);
-        if (t->products == 3) {
-            if (from_psi) k_tc_split<3, 0><<<t->grid, TC_THREADS, 0, s>>>(o, t->c, a, rows, scale, fs);
-            else k_tc_split<3, 1><<<t->grid, TC_THREADS, 0, s>>>(o, t->c, a, rows, scale, fs);
-        } else {
-            if (from_psi) k_tc_split<5, 0><<<t->grid, TC_THREADS, 0, s>>>(o, t->c, a, rows, scale, fs);
-            else k_tc_split<5, 1><<<t->grid, TC_THREADS, 0, s>>>(o, t->c, a, rows, scale, fs);
-        }
+        // unnormalised transforms and the kinetic table's 1/n^2: psi's scale throughout
+        if (from_psi) k_tc_split<TC_BFP, 0><<<t->grid, TC_THREADS, 0, s>>>(o, t->c, a, rows, 1.f, fs);
+        else k_tc_split<TC_BFP, 1><<<t->grid, TC_THREADS, 0, s>>>(o, t->c, a, rows, 1.f, fs);
     }
     ++*launches;
     return cudaGetLastError();
@@ -497,18 +508,16 @@ cudaError_t tc_split_potential(TcState *t, const TcPhaseArgs &a, bool from_psi, 
 cudaError_t tc_split_kinetic(TcState *t, const TcPhaseArgs &a, cudaStream_t s, int64_t *launches) {
     const int64_t rows = t->batch * t->n;
     const SplitOut o = split_out(t);
-    // the axis-0 kinetic factors carry the inverse transform's 1 / n^2; the
-    // unnormalised conj W products restore it, so it is taken out here
-    const float scale = ldexpf(1.f, 2 * t->l);
     FixedScale fs{};
     if (t->products == TC_FIXED) {
+        // the axis-0 kinetic factors carry the inverse transform's 1 / n^2; the
+        // fixed form tracks its scale in the exponent, so it is taken out here
+        const float scale = ldexpf(1.f, 2 * t->l);
         cudaError_t e = fixed_prepare(t, t->c, false, -2 * t->l, false, s, &fs, launches);
         if (e != cudaSuccess) return e;
         k_tc_split<TC_FIXED, 2><<<t->grid, TC_THREADS, 0, s>>>(o, t->c, a, rows, scale, fs);
-    } else if (t->products == 3) {
-        k_tc_split<3, 2><<<t->grid, TC_THREADS, 0, s>>>(o, t->c, a, rows, scale, fs);
     } else {
-        k_tc_split<5, 2><<<t->grid, TC_THREADS, 0, s>>>(o, t->c, a, rows, scale, fs);
+        k_tc_split<TC_BFP, 2><<<t->grid, TC_THREADS, 0, s>>>(o, t->c, a, rows, 1.f, fs);
     }
     ++*launches;
     return cudaGetLastError();
@@ -522,10 +531,8 @@ cudaError_t tc_split_transpose(TcState *t, cudaStream_t s, int64_t *launches) {
         cudaError_t e = fixed_prepare(t, t->c, false, 0, false, s, &fs, launches);
         if (e != cudaSuccess) return e;
         k_tc_split_t<TC_FIXED><<<grid, block, 0, s>>>(o, t->c, fs);
-    } else if (t->products == 3) {
-        k_tc_split_t<3><<<grid, block, 0, s>>>(o, t->c, fs);
     } else {
-        k_tc_split_t<5><<<grid, block, 0, s>>>(o, t->c, fs);
+        k_tc_split_t<TC_BFP><<<grid, block, 0, s>>>(o, t->c, fs);
     }
     ++*launches;
     return cudaGetLastError();
@@ -551,11 +558,20 @@ cudaError_t tc_gemm(TcState *t, bool inverse, cudaStream_t s, int64_t *launches)
             for (int i = 0; i <= lev; ++i)
                 seg[nseg++] = UgSeg{i * m, (lev - i) * m, kb, ldexpf(1.f, -7 * lev), i == 0 ? (int)UG_OPEN : (int)UG_CONTINUE};
     } else {
-        lda = ldb = (int64_t)t->products * m;
-        for (int sidx = 0; sidx < t->products; ++sidx) seg[nseg++] = UgSeg{sidx * m, sidx * m, kb, 1.f, (int)UG_EACH_MMA};
-        alpha = ldexpf(1.f, -t->h);
+        // a W_hi (2^-20), a W_lo and c W_hi (2^-31), each times the row's block
+        // exponent; 5 products add a W_lo2 and c W_lo (2^-42), smallest last
+        lda = 2 * (int64_t)m;
+        ldb = (int64_t)w_segments(t->products) * m;
+        seg[nseg++] = UgSeg{0, 0, kb, ldexpf(1.f, -20), (int)UG_EACH_MMA_BEXP, 0};
+        seg[nseg++] = UgSeg{0, m, kb, ldexpf(1.f, -31), (int)UG_EACH_MMA_BEXP, 0};
+        seg[nseg++] = UgSeg{m, 0, kb, ldexpf(1.f, -31), (int)UG_EACH_MMA_BEXP, 0};
+        if (t->products == 5) {
+            seg[nseg++] = UgSeg{0, 2 * m, kb, ldexpf(1.f, -42), (int)UG_EACH_MMA_BEXP, 0};
+            seg[nseg++] = UgSeg{m, m, kb, ldexpf(1.f, -42), (int)UG_EACH_MMA_BEXP, 0};
+        }
     }
-    cudaError_t e = umma_gemm(t->a, lda, w, ldb, t->c, m, rows, m, seg, nseg, alpha, 0.f, tc_bn(t->n), t->err, s);
+    cudaError_t e = umma_gemm(t->a, lda, w, ldb, t->c, m, rows, m, seg, nseg, alpha, 0.f, tc_bn(t->n), t->err, s,
+                              t->e8, m / 16);
     ++*launches;
     return e;
 }
@@ -570,8 +586,7 @@ int tc_timed_out(TcState *t, cudaStream_t s) {
 
 cudaError_t tc_finish(TcState *t, const TcPhaseArgs &a, bool phase, cudaStream_t s, int64_t *launches) {
     const int64_t rows = t->batch * t->n;
-    const float scale = ldexpf(1.f, 4 * t->h - 2 * t->l - TC_S);
-    k_tc_finish<<<t->grid, TC_THREADS, 0, s>>>(t->c, a, t->n, rows, scale,
+    k_tc_finish<<<t->grid, TC_THREADS, 0, s>>>(t->c, a, t->n, rows, 1.f,
                                                t->products == TC_FIXED ? t->e : nullptr, phase ? 1 : 0);
     ++*launches;
     return cudaGetLastError();

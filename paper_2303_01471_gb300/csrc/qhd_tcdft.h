@@ -17,12 +17,19 @@ struct TcState;
 // K = 16 MMA a group of its own (its partial added in FP32 with round to
 // nearest); UG_OPEN starts a group that accumulates in tensor memory and
 // following UG_CONTINUE segments extend (one FP32 rounding per group).
-enum { UG_EACH_MMA = 0, UG_OPEN = 1, UG_CONTINUE = 2 };
+// UG_EACH_MMA_FLOAT: every MMA its own group, for operands whose 16-term sums
+// are not exact in FP32: the result is scaled by (1 + kappa) to undo the
+// expected truncation of each partial (see qhd_umma_gemm.cu).
+// UG_EACH_MMA_BEXP: every MMA its own group, A holding integers scaled per row
+// and per block of 16 K values: the group's scale is scale * 2^E[row][e0 + j]
+// for the segment's j-th MMA (E from UgArgs::expo).
+enum { UG_EACH_MMA = 0, UG_OPEN = 1, UG_CONTINUE = 2, UG_EACH_MMA_FLOAT = 3, UG_EACH_MMA_BEXP = 4 };
 constexpr int UG_MAX_SEG = 16;
 struct UgSeg {
     int a_k0, b_k0, kblocks;
     float scale;
     int mode;
+    int e0;              // UG_EACH_MMA_BEXP: exponent column of the segment's first MMA
 };
 struct UgArgs {
     float *C;
@@ -32,6 +39,9 @@ struct UgArgs {
     int nseg;
     UgSeg seg[UG_MAX_SEG];
     float alpha, beta;
+    float kappa;         // expected relative truncation of per-MMA partials, undone in the epilogue
+    const int8_t *expo;  // UG_EACH_MMA_BEXP: per-row exponents [rows][expo_ld]
+    int64_t expo_ld;
     unsigned *err;       // 2 words: [0] a bounded wait gave up, [1] scratch of the wind-down waits
     uint64_t limit_ns;   // global-time limit of each wait
 };
@@ -41,7 +51,7 @@ bool umma_gemm_shape_ok(int64_t rows, int64_t n_cols, int64_t lda, int64_t ldb, 
 // A: FP16 [rows][lda], B: FP16 [n_cols][ldb] (B^T, K contiguous), C: FP32 [rows][ldc].
 cudaError_t umma_gemm(const __half *A, int64_t lda, const __half *B, int64_t ldb, float *C, int64_t ldc, int64_t rows,
                       int64_t n_cols, const UgSeg *segs, int nseg, float alpha, float beta, int bn, unsigned *err,
-                      cudaStream_t s);
+                      cudaStream_t s, const int8_t *expo = nullptr, int64_t expo_ld = 0);
 
 // Arguments of one split kernel: the state lives in the FP32 product buffer
 // of the state object between transforms; psi only at the start and end.

@@ -117,6 +117,11 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t *r) {
           "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
 }
+// 64 consecutive 32-bit columns of this thread's lane.
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, uint32_t *r) {
+    tmem_ld32(taddr, r);
+    tmem_ld32(taddr + 32u, r + 32);
+}
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // ---------------------------------------------------------- MMA operands

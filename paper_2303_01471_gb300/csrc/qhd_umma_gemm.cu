@@ -72,11 +72,12 @@ struct GroupWalk {
     __device__ explicit GroupWalk(const UgArgs *args) : a(args) {}
     __device__ bool starts() const {
         const UgSeg &s = a->seg[seg];
-        return s.mode == UG_EACH_MMA || (s.mode == UG_OPEN && kb == 0 && i == 0);
+        return s.mode == UG_EACH_MMA || s.mode == UG_EACH_MMA_FLOAT || s.mode == UG_EACH_MMA_BEXP ||
+               (s.mode == UG_OPEN && kb == 0 && i == 0);
     }
     __device__ bool ends() const {
         const UgSeg &s = a->seg[seg];
-        if (s.mode == UG_EACH_MMA) return true;
+        if (s.mode == UG_EACH_MMA || s.mode == UG_EACH_MMA_FLOAT || s.mode == UG_EACH_MMA_BEXP) return true;
         if (kb != s.kblocks - 1 || i != 3) return false;
         return seg + 1 >= a->nseg || a->seg[seg + 1].mode != UG_CONTINUE;
     }
@@ -211,9 +212,16 @@ __global__ void __launch_bounds__(UG_THREADS, 1)
         int grp = 0;
         bool ok = a.nseg > 0;
         bool more = ok;
+        const int64_t erow = (int64_t)m0 + q * 32 + lane;
+        const int8_t *erp = (a.expo && erow < a.rows) ? a.expo + erow * a.expo_ld : nullptr;
         while (more && ok) {
             // advance the walk to the end of this group
-            const float sc = w.scale();
+            float sc = w.scale();
+            if (a.seg[w.seg].mode == UG_EACH_MMA_BEXP) {
+                // this row's exponent of the MMA's 16 K values (0 past the last row)
+                const int e = erp ? (int)__ldg(erp + a.seg[w.seg].e0 + w.kb * 4 + w.i) : 0;
+                sc *= __int_as_float((e + 127) << 23);
+            }
             while (!w.ends()) w.next();
             more = w.next();
             const int buf = grp % NBUF;
@@ -226,16 +234,14 @@ __global__ void __launch_bounds__(UG_THREADS, 1)
             umma::tc_fence_after();
             const float2 s2 = make_float2(sc, sc);
             const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BN + h * COLS);
+            // all of this thread's columns in flight at once, one wait
+            uint32_t r[COLS];
+            static_assert(COLS == 64, "one 64-column load per thread");
+            umma::tmem_ld64(taddr, r);
+            umma::tmem_ld_wait();
 #pragma unroll
-            for (int c = 0; c < COLS / 16; ++c) {
-                uint32_t r[16];
-                umma::tmem_ld16(taddr + (uint32_t)(c * 16), r);
-                umma::tmem_ld_wait();
-#pragma unroll
-                for (int k = 0; k < 8; ++k)
-                    acc[c * 8 + k] = umma::fma2(make_float2(__uint_as_float(r[2 * k]), __uint_as_float(r[2 * k + 1])),
-                                                s2, acc[c * 8 + k]);
-            }
+            for (int k = 0; k < COLS / 2; ++k)
+                acc[k] = umma::fma2(make_float2(__uint_as_float(r[2 * k]), __uint_as_float(r[2 * k + 1])), s2, acc[k]);
             umma::tc_fence_before();
             __syncwarp();
             if (lane == 0) umma::mbar_arrive(&pempty[buf]);
@@ -244,17 +250,19 @@ __global__ void __launch_bounds__(UG_THREADS, 1)
         const int64_t row = (int64_t)m0 + q * 32 + lane;
         if (ok && row < a.rows) {
             float *crow = a.C + row * a.ldc + n0 + h * COLS;
+            // expected truncation of the per-MMA partials: result * (1 + kappa), formed
+            // as alpha acc + (alpha kappa) acc with one rounding
+            const float ak = a.alpha * a.kappa;
             const float2 al = make_float2(a.alpha, a.alpha), be = make_float2(a.beta, a.beta);
 #pragma unroll
             for (int k = 0; k < COLS / 4; ++k) {
                 float2 lo = acc[2 * k], hi = acc[2 * k + 1];
+                lo = make_float2(fmaf(lo.x, ak, lo.x * a.alpha), fmaf(lo.y, ak, lo.y * a.alpha));
+                hi = make_float2(fmaf(hi.x, ak, hi.x * a.alpha), fmaf(hi.y, ak, hi.y * a.alpha));
                 if (a.beta != 0.f) {
                     const float4 old = *reinterpret_cast<const float4 *>(crow + 4 * k);
-                    lo = umma::fma2(lo, al, make_float2(old.x * a.beta, old.y * a.beta));
-                    hi = umma::fma2(hi, al, make_float2(old.z * a.beta, old.w * a.beta));
-                } else {
-                    lo = make_float2(lo.x * a.alpha, lo.y * a.alpha);
-                    hi = make_float2(hi.x * a.alpha, hi.y * a.alpha);
+                    lo = make_float2(fmaf(old.x, a.beta, lo.x), fmaf(old.y, a.beta, lo.y));
+                    hi = make_float2(fmaf(old.z, a.beta, hi.x), fmaf(old.w, a.beta, hi.y));
                 }
                 (void)be;
                 *reinterpret_cast<float4 *>(crow + 4 * k) = make_float4(lo.x, lo.y, hi.x, hi.y);
@@ -345,7 +353,7 @@ bool umma_gemm_shape_ok(int64_t rows, int64_t n_cols, int64_t lda, int64_t ldb, 
 
 cudaError_t umma_gemm(const __half *A, int64_t lda, const __half *B, int64_t ldb, float *C, int64_t ldc, int64_t rows,
                       int64_t n_cols, const UgSeg *segs, int nseg, float alpha, float beta, int bn, unsigned *err,
-                      cudaStream_t s) {
+                      cudaStream_t s, const int8_t *expo, int64_t expo_ld) {
     if (!umma_gemm_shape_ok(rows, n_cols, lda, ldb, bn) || nseg < 1 || nseg > UG_MAX_SEG) return cudaErrorInvalidValue;
     UgArgs a{};
     a.C = C;
@@ -361,10 +369,26 @@ cudaError_t umma_gemm(const __half *A, int64_t lda, const __half *B, int64_t ldb
             g.a_k0 + (int64_t)g.kblocks * UG_BK > lda || g.b_k0 + (int64_t)g.kblocks * UG_BK > ldb)
             return cudaErrorInvalidValue;
         if (g.mode == UG_CONTINUE && i == 0) return cudaErrorInvalidValue;
+        if (g.mode == UG_EACH_MMA_BEXP && (!expo || g.e0 < 0 || g.e0 + 4 * (int64_t)g.kblocks > expo_ld))
+            return cudaErrorInvalidValue;
         a.seg[i] = g;
     }
     a.alpha = alpha;
     a.beta = beta;
+    a.expo = expo;
+    a.expo_ld = expo_ld;
+    // Each MMA returns its exact 16-term sum truncated towards zero to FP32
+    // (measured: per-MMA partials are biased by -3.9e-8 relative).  A value of
+    // mantissa m in [1, 2) loses on average half an ulp, 2^-24 / m of itself;
+    // over the mantissas of the partials (log-uniform) the expected loss is the
+    // fraction kappa = 2^-24 / (2 ln 2) of each partial, so the sum of
+    // partials is the exact product times (1 - kappa) in expectation.  Only the
+    // every-MMA groups of floating operands follow this model (exact integer
+    // partials lose nothing, and a long accumulation truncates the running sum,
+    // whose expectation has no such form).
+    bool every = true;
+    for (int i = 0; i < nseg; ++i) every = every && segs[i].mode == UG_EACH_MMA_FLOAT;
+    a.kappa = every ? (float)(5.9604644775390625e-08 / (2.0 * 0.6931471805599453)) : 0.f;
     a.err = err;
     a.limit_ns = 2000000000ull;  // 2 s of global time per wait
     return launch_bn<128>(A, lda, B, ldb, n_cols, a, s);
@@ -384,9 +408,10 @@ extern "C" qhd_status qhd_tc_gemm_f16(const void *A_dev, const void *B_dev, floa
         ((uintptr_t)C_dev & 15) || ((uintptr_t)err_dev & 3))
         return QHD_ERR_INVALID_ARG;
     if (k < 64 || k > (int64_t(1) << 20) || ldc < n_cols || ldc % 4 || n_cols % 128 ||
-        !umma_gemm_shape_ok(rows, n_cols, k, k, 128) || (group_every_mma != 0 && group_every_mma != 1))
+        !umma_gemm_shape_ok(rows, n_cols, k, k, 128) || group_every_mma < 0 || group_every_mma > 2)
         return QHD_ERR_INVALID_ARG;
-    UgSeg seg{0, 0, (int)(k / 64), 1.f, group_every_mma ? (int)UG_EACH_MMA : (int)UG_OPEN};
+    const int mode = group_every_mma == 0 ? (int)UG_OPEN : group_every_mma == 1 ? (int)UG_EACH_MMA : (int)UG_EACH_MMA_FLOAT;
+    UgSeg seg{0, 0, (int)(k / 64), 1.f, mode};
     cudaError_t e = umma_gemm(reinterpret_cast<const __half *>(A_dev), k, reinterpret_cast<const __half *>(B_dev), k,
                               C_dev, ldc, rows, n_cols, &seg, 1, alpha, beta, 128, err_dev, (cudaStream_t)stream);
     snprintf(g_gemm_err, sizeof g_gemm_err, "%s%s%s", e == cudaSuccess ? "" : cudaGetErrorString(e),

@@ -345,10 +345,10 @@ class QHD:
         """SPLIT_STRANG (default) or SPLIT_LIE_TROTTER (Eq. (prod_qhd) as printed)."""
         self._check(self.lib.qhd_set_splitting(self.ctx, int(kind)), "qhd_set_splitting")
 
-    def set_transform(self, kind: int, products: int = 5) -> None:
+    def set_transform(self, kind: int, products: int = 3) -> None:
         """TRANSFORM_FFT (default) or TRANSFORM_TC_DFT (dense DFT GEMMs on the tensor
-        cores on FP16 operands: `products` = 3 or 5 floating hi/lo partial products,
-        or 10 fixed-point slice products); the tensor-core workspace is allocated
+        cores on FP16 operands: `products` = 3 or 5 block-scaled hi/lo slice
+        products, or 10 fixed-point slice products); the tensor-core workspace is allocated
         here and kept with this object."""
         import torch
         if kind == TRANSFORM_FFT:
@@ -532,8 +532,10 @@ class Group:
 
 def tc_gemm_f16(A, B, C=None, every_mma=True, alpha=1.0, beta=0.0, err=None):
     """C = alpha * A . B^T + beta * C on the tensor cores (qhd_tc_gemm_f16).  A
-    (rows, k) and B (n, k) float16 CUDA tensors, C float32 (rows, n); returns
-    (C, err) with err a 2-word int32 tensor (err[0] = 1: a bounded wait gave up)."""
+    (rows, k) and B (n, k) float16 CUDA tensors, C float32 (rows, n); every_mma:
+    False (one accumulation), True (per-MMA partials) or "float" (per-MMA
+    partials with the expected-truncation correction).  Returns (C, err) with err
+    a 2-word int32 tensor (err[0] = 1: a bounded wait gave up)."""
     import torch
     lib = load()
     rows, k = A.shape
@@ -547,7 +549,8 @@ def tc_gemm_f16(A, B, C=None, every_mma=True, alpha=1.0, beta=0.0, err=None):
         err = torch.zeros(2, dtype=torch.int32, device=A.device)
     stream = torch.cuda.current_stream(A.device).cuda_stream
     st = lib.qhd_tc_gemm_f16(ctypes.c_void_p(A.data_ptr()), ctypes.c_void_p(B.data_ptr()),
-                             ctypes.c_void_p(C.data_ptr()), n, rows, n, k, 1 if every_mma else 0,
+                             ctypes.c_void_p(C.data_ptr()), n, rows, n, k,
+                             2 if every_mma == "float" else (1 if every_mma else 0),
                              float(alpha), float(beta), ctypes.c_void_p(err.data_ptr()), ctypes.c_void_p(stream))
     if st != QHD_OK:
         raise QHDError(st, "qhd_tc_gemm_f16: " + lib.qhd_tc_gemm_last_error().decode())

@@ -107,7 +107,9 @@ SHAPES = [(2,), (4,), (8,), (16,), (32,), (64,), (128,), (256,), (512,), (1024,)
           # 3-D generic passes
           (2, 2, 2), (4, 8, 16), (16, 8, 4), (8, 64, 2), (2, 4, 256), (64, 16, 128),
           # 3-D plane pass over the last two axes + axis-0 pass
-          (32, 32, 32), (2, 256, 256), (4, 64, 128), (8, 128, 32), (16, 32, 64), (4, 256, 64)]
+          (32, 32, 32), (2, 256, 256), (4, 64, 128), (8, 128, 32), (16, 32, 64), (4, 256, 64),
+          # ... with a long axis 0 (256) over small planes
+          (256, 32, 32), (256, 64, 128)]
 
 
 @pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "x".join(map(str, s)))
@@ -118,6 +120,24 @@ def test_parity_short_runs_all_shapes(shape):
     psi_g, obs = run_gpu(inst.f, sched, n * dt, dt)
     psi_o = oracle.evolve(inst.f, oracle.uniform_state(shape), 0.0, dt, n, to_oracle_sched(sched))
     compare(psi_g, obs[0], inst.f, psi_o, steps=n)
+
+
+def test_parity_batched_3d_axis_passes():
+    """Three 3-D instances in one context (plane pass + axis-0 pass), axis 0 of
+    length 256 and of length 64, against the oracle."""
+    for shape in [(256, 32, 64), (64, 32, 64)]:
+        insts = [workloads.gaussian_wells(s, shape, K=4) for s in (21, 22, 23)]
+        sim = qhd.QHD(shape, batch=3)
+        sim.set_potential(np.stack([i.f for i in insts]))
+        sim.set_schedule(qhd.Schedule())
+        sim.reset_state()
+        sim.evolve(0.2, 0.01)
+        obs = sim.observables(0.1)
+        psi = sim.psi.cpu().numpy().astype(np.complex128)
+        sim.close()
+        for b, inst in enumerate(insts):
+            psi_o = oracle.evolve(inst.f, oracle.uniform_state(shape), 0.0, 0.01, 20, oracle.Schedule())
+            compare(psi[b], obs[b], inst.f, psi_o, steps=20)
 
 
 def test_parity_nonunit_box_and_table_schedule():

@@ -30,6 +30,29 @@ def test_exact_integer_products(shape, every):
     assert np.array_equal(C.double().cpu().numpy(), ref)
 
 
+def test_full_range_integer_partials_are_exact():
+    """Operands over the whole integer range of the block-scaled slices
+    ([-1024, 1024]): each 16-term MMA sum (up to 2^24) comes back exactly, and
+    the per-MMA partials are added in order with round-to-nearest FP32."""
+    rows, n, k = 256, 256, 256
+    g = torch.Generator(device="cuda").manual_seed(7)
+    A = torch.randint(-1024, 1025, (rows, k), device="cuda", generator=g)
+    B = torch.randint(-1024, 1025, (n, k), device="cuda", generator=g)
+    A[:4] = 1024                            # rows and columns that reach the 2^24 bound
+    B[:4] = 1024
+    A[4:8] = -1024
+    C, err = qhd.tc_gemm_f16(A.half(), B.half(), every_mma=True)
+    torch.cuda.synchronize()
+    assert int(err[0]) == 0
+    a, b = A.cpu().numpy().astype(np.int64), B.cpu().numpy().astype(np.int64)
+    acc = np.zeros((rows, n), dtype=np.float32)
+    for j in range(0, k, 16):
+        part = a[:, j:j + 16] @ b[:, j:j + 16].T
+        assert np.abs(part).max() <= 2 ** 24
+        acc = (acc + part.astype(np.float32)).astype(np.float32)
+    assert np.array_equal(C.cpu().numpy(), acc)
+
+
 def test_fp16_products_and_accumulation_bias():
     """Random FP16 operands: per-MMA partials added with round-to-nearest agree with
     the FP64 sum to FP32 rounding and carry no bias; the one long tensor-memory
@@ -40,7 +63,7 @@ def test_fp16_products_and_accumulation_bias():
     B = (torch.rand((n, k), device="cuda", generator=g) * 2 - 1).half()
     ref = ref64(A, B)
     res = {}
-    for every in (True, False):
+    for every in (True, False, "float"):
         C, err = qhd.tc_gemm_f16(A, B, every_mma=every)
         torch.cuda.synchronize()
         assert int(err[0]) == 0
@@ -49,13 +72,16 @@ def test_fp16_products_and_accumulation_bias():
         res[every] = (np.abs(d).max() / scale, float(np.mean(d * np.sign(ref)) / scale))
     err_rn, bias_rn = res[True]
     err_hw, bias_hw = res[False]
-    assert err_rn <= 1e-5, res
+    err_fl, bias_fl = res["float"]
+    print(f"per-MMA partials: max rel err {err_rn:.2e}, bias {bias_rn:+.2e}; with the truncation correction: "
+          f"{err_fl:.2e}, {bias_fl:+.2e}; one accumulation: max rel err {err_hw:.2e}, bias {bias_hw:+.2e}")
+    assert err_rn <= 1e-5 and err_fl <= 1e-5, res
     # the hardware's long accumulation drifts towards zero by ~1e-9 K; per-MMA partials
-    # leave only the rounding inside each 16-term MMA (measured -3.9e-8 at K = 2048)
+    # leave only each MMA's truncation of its exact 16-term sum (measured -3.9e-8),
+    # which the expected-truncation correction of the floating mode removes
     assert bias_hw < -5e-7, res
     assert abs(bias_rn) <= 1e-7 and abs(bias_rn) <= abs(bias_hw) / 20, res
-    print(f"per-MMA partials: max rel err {err_rn:.2e}, bias {bias_rn:+.2e}; "
-          f"one accumulation: max rel err {res[False][0]:.2e}, bias {res[False][1]:+.2e}")
+    assert abs(bias_fl) <= abs(bias_rn) / 4, res
 
 
 def test_alpha_beta():
@@ -83,7 +109,7 @@ def test_argument_checks():
            (p(A), p(B), p(C), 256, 128, 200, 64, 1),     # n_cols not a multiple of 128
            (p(A), p(B), p(C), 256, 128, 256, 48, 1),     # k not a multiple of 64
            (p(A), p(B), p(C), 100, 128, 256, 64, 1),     # ldc < n_cols
-           (p(A), p(B), p(C), 256, 128, 256, 64, 2),     # mode
+           (p(A), p(B), p(C), 256, 128, 256, 64, 3),     # mode
            (None, p(B), p(C), 256, 128, 256, 64, 1),
            (p(A) + 2, p(B), p(C), 256, 128, 256, 64, 1)]  # misaligned
     for args in bad:
