@@ -252,6 +252,177 @@ __global__ void k_fno_layer_out(const float2 *S, const T *v, const float *Ww, co
     }
 }
 
+// ------------------------------------------- tensor-core forms (BF16 path)
+// With BF16 activations, width C = 32, M <= 16 modes and H a multiple of 8, the
+// two dense per-point contractions of the forward pass run on the tensor cores
+// (mma.sync m16n8k16, BF16 operands, FP32 accumulation): the layer output
+// (pointwise 32 x 32 map plus the inverse axis-1 DFT stage, both one product
+// per row) and the projection's 32 -> H map.  The FP32 activation path (the
+// gradient checks) keeps the SIMT kernels above.
+constexpr int TC_C = 32;       // width the tensor-core kernels are written for
+constexpr int TC_LD = 20;      // words per 16-word row of a shared B operand (conflict-free fragment loads)
+
+__device__ __forceinline__ uint32_t bf2(float lo, float hi) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&h);
+}
+
+// D (16 x 8, FP32) += A (16 x 16, BF16, row) . B (16 x 8, BF16, col)
+__device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                         uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+bool tc_layer_ok(const Dims &d) { return d.C == TC_C && d.M <= 16 && d.n % 16 == 0; }
+bool tc_proj_ok(const Dims &d) { return d.C == TC_C && d.H % 8 == 0 && d.H <= 128; }
+
+// Layer output of row bx = (b, x) on the tensor cores:
+//   a[y][o] = sum_c v[y][c] Ww[o][c] + sum_k T[y][k] U[k][o] + bw[o],
+//   T[y][k] = cos(2 pi k y / n) (k < 16), -sin(2 pi (k - 16) y / n) (k >= 16),
+//   U[k][o] = c_k Re S[k][o] / n^2, U[16 + k][o] = c_k Im S[k][o] / n^2 (zero for k >= M),
+// which is n^-2 sum_ky c_ky Re(S[ky] e^{+2 pi i ky y / n}) as in k_fno_layer_out.
+// Each warp takes 16 rows y at a time: K = 32 (channels) + 32 (spectral).
+__global__ void __launch_bounds__(FT) k_fno_layer_out_tc(const float2 *S, const __nv_bfloat16 *v, const float *Ww,
+                                                         const float *bw, Dims d, int act, __nv_bfloat16 *a_out,
+                                                         __nv_bfloat16 *v_out) {
+    __shared__ uint32_t Wb[TC_C * TC_LD], Ub[TC_C * TC_LD];  // [o][k pair]
+    __shared__ float cs[256], sn[256], bs[TC_C];
+    const int n = d.n, M = d.M;
+    const int64_t bx = blockIdx.x;
+    const float inv = 1.f / ((float)n * (float)n);
+    for (int i = threadIdx.x; i < TC_C * 16; i += blockDim.x) {
+        const int o = i / 16, j = i % 16;
+        Wb[o * TC_LD + j] = bf2(Ww[o * TC_C + 2 * j], Ww[o * TC_C + 2 * j + 1]);
+        // spectral rows 2j, 2j + 1 of U (k < 16: real parts, k >= 16: imaginary parts)
+        float u[2];
+        for (int e = 0; e < 2; ++e) {
+            const int k = 2 * j + e, ky = k & 15;
+            float val = 0.f;
+            if (ky < M) {
+                const float2 sv = S[(bx * M + ky) * (int64_t)TC_C + o];
+                val = (ky == 0 ? 1.f : 2.f) * inv * (k < 16 ? sv.x : sv.y);
+            }
+            u[e] = val;
+        }
+        Ub[o * TC_LD + j] = bf2(u[0], u[1]);
+    }
+    twiddle_table(cs, sn, n);
+    for (int i = threadIdx.x; i < TC_C; i += blockDim.x) bs[i] = bw[i];
+    __syncthreads();
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int r = lane / 4, q = 2 * (lane % 4);
+    const uint32_t *vrow = reinterpret_cast<const uint32_t *>(v + bx * (int64_t)n * TC_C);
+    for (int y0 = 16 * warp; y0 < n; y0 += 16 * (FT / 32)) {
+        float acc[4][4] = {};
+        // channels: A = v rows y0.., K = 32 in two steps
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks) {
+            const int k = 16 * ks + q;
+            const uint32_t a0 = vrow[((y0 + r) * TC_C + k) / 2], a1 = vrow[((y0 + r + 8) * TC_C + k) / 2];
+            const uint32_t a2 = vrow[((y0 + r) * TC_C + k + 8) / 2], a3 = vrow[((y0 + r + 8) * TC_C + k + 8) / 2];
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt) {
+                const int o = 8 * nt + r;
+                mma_bf16(acc[nt], a0, a1, a2, a3, Wb[o * TC_LD + k / 2], Wb[o * TC_LD + k / 2 + 4]);
+            }
+        }
+        // spectral: A = T rows y0.., K = 32 (cos | -sin) in two steps
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks) {
+            const int k = 16 * ks + q;  // k, k + 1 and k + 8, k + 9 share the cos / sin choice
+            auto tw = [&](int y, int kk) {
+                const int ky = kk & 15, idx = (ky * y) & (n - 1);
+                return kk < 16 ? cs[idx] : -sn[idx];
+            };
+            const int ya = y0 + r, yb = y0 + r + 8;
+            const uint32_t a0 = bf2(tw(ya, k), tw(ya, k + 1)), a1 = bf2(tw(yb, k), tw(yb, k + 1));
+            const uint32_t a2 = bf2(tw(ya, k + 8), tw(ya, k + 9)), a3 = bf2(tw(yb, k + 8), tw(yb, k + 9));
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt) {
+                const int o = 8 * nt + r;
+                mma_bf16(acc[nt], a0, a1, a2, a3, Ub[o * TC_LD + k / 2], Ub[o * TC_LD + k / 2 + 4]);
+            }
+        }
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt) {
+            const int o = 8 * nt + q;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int y = y0 + r + 8 * h;
+                const float x0 = acc[nt][2 * h] + bs[o], x1 = acc[nt][2 * h + 1] + bs[o + 1];
+                const int64_t idx = (bx * (int64_t)n + y) * TC_C + o;
+                if (act) {
+                    *reinterpret_cast<uint32_t *>(&a_out[idx]) = bf2(x0, x1);
+                    *reinterpret_cast<uint32_t *>(&v_out[idx]) = bf2(gelu(x0), gelu(x1));
+                } else {
+                    *reinterpret_cast<uint32_t *>(&v_out[idx]) = bf2(x0, x1);
+                }
+            }
+        }
+    }
+}
+
+// Projection on the tensor cores: per 16 points, h = W1 v + b1 (16 x H, K = 32)
+// in registers, then z = sum_k w2[k] gelu(h[k]) + b2 reduced over each row's
+// four lanes.
+__global__ void __launch_bounds__(FT) k_fno_proj_tc(const __nv_bfloat16 *v, const float *W1, const float *b1,
+                                                    const float *W2, const float *b2, Dims d, float *z) {
+    __shared__ uint32_t Wb[128 * TC_LD];  // [h][c pair]
+    __shared__ float bb[128], ww[128];
+    const int H = d.H;
+    for (int i = threadIdx.x; i < H * 16; i += blockDim.x) {
+        const int h = i / 16, j = i % 16;
+        Wb[h * TC_LD + j] = bf2(W1[h * TC_C + 2 * j], W1[h * TC_C + 2 * j + 1]);
+    }
+    for (int i = threadIdx.x; i < H; i += blockDim.x) {
+        bb[i] = b1[i];
+        ww[i] = W2[i];
+    }
+    __syncthreads();
+    const float bias2 = b2[0];
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int r = lane / 4, q = 2 * (lane % 4);
+    const int64_t P = d.P();
+    const uint32_t *vv = reinterpret_cast<const uint32_t *>(v);
+    const int64_t wstride = (int64_t)gridDim.x * (FT / 32) * 16;
+    for (int64_t p0 = ((int64_t)blockIdx.x * (FT / 32) + warp) * 16; p0 < P; p0 += wstride) {
+        uint32_t a[2][4];
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks) {
+            const int k = 16 * ks + q;
+            a[ks][0] = vv[((p0 + r) * TC_C + k) / 2];
+            a[ks][1] = vv[((p0 + r + 8) * TC_C + k) / 2];
+            a[ks][2] = vv[((p0 + r) * TC_C + k + 8) / 2];
+            a[ks][3] = vv[((p0 + r + 8) * TC_C + k + 8) / 2];
+        }
+        float t0 = 0.f, t1 = 0.f;  // rows r and r + 8
+        for (int nt = 0; nt < H / 8; ++nt) {
+            float acc[4] = {};
+            const int h = 8 * nt + r;
+#pragma unroll
+            for (int ks = 0; ks < 2; ++ks) {
+                const int k = 16 * ks + q;
+                mma_bf16(acc, a[ks][0], a[ks][1], a[ks][2], a[ks][3], Wb[h * TC_LD + k / 2], Wb[h * TC_LD + k / 2 + 4]);
+            }
+            const int hc = 8 * nt + q;
+            t0 = fmaf(ww[hc], gelu(acc[0] + bb[hc]), fmaf(ww[hc + 1], gelu(acc[1] + bb[hc + 1]), t0));
+            t1 = fmaf(ww[hc], gelu(acc[2] + bb[hc]), fmaf(ww[hc + 1], gelu(acc[3] + bb[hc + 1]), t1));
+        }
+        t0 += __shfl_xor_sync(0xffffffffu, t0, 1);
+        t0 += __shfl_xor_sync(0xffffffffu, t0, 2);
+        t1 += __shfl_xor_sync(0xffffffffu, t1, 1);
+        t1 += __shfl_xor_sync(0xffffffffu, t1, 2);
+        if ((lane & 3) == 0) {
+            z[p0 + r] = t0 + bias2;
+            z[p0 + r + 8] = t1 + bias2;
+        }
+    }
+}
+
 // ------------------------------------------------------------- projection
 template <typename T>
 __global__ void k_fno_proj(const T *v, const float *W1, const float *b1, const float *W2, const float *b2, Dims d,
@@ -689,6 +860,12 @@ qhd_status ffail(qhd_fno *f, qhd_status s, const char *msg) {
         if (e_ != cudaSuccess) return ffail((f), QHD_ERR_CUDA, cudaGetErrorString(e_)); \
     } while (0)
 
+// blocks of the tensor-core projection: 128 points per block pass, at most 16 blocks per SM
+int64_t tc_proj_grid(const Dims &d) {
+    const int64_t tiles = (d.P() + 127) / 128;
+    return tiles < 152 * 16 ? tiles : 152 * 16;
+}
+
 size_t smem_dfty(const Dims &d) { return (size_t)(d.n * d.C + 2 * d.n) * sizeof(float); }
 size_t smem_specx(const Dims &d) {
     return (size_t)(d.n * d.C + 2 * d.MX * d.C) * sizeof(float2) + 2 * d.n * sizeof(float);
@@ -726,12 +903,22 @@ qhd_status forward(qhd_fno *f, const double *fx, const float *sigma, int64_t B, 
         k_fno_specx<false><<<(unsigned)(B * d.M), FT, smem_specx(d), s>>>(
             f->tspec, reinterpret_cast<const float2 *>(W + f->off_R[l]), d, f->vhat[l], f->sspec);
         const int act = l + 1 < d.L;
-        k_fno_layer_out<T><<<(unsigned)(B * d.n), FT, smem_layer(d), s>>>(
-            f->sspec, vin, W + f->off_W[l], W + f->off_b[l], d, act, act ? (T *)f->a[l] : nullptr, (T *)f->v[l + 1]);
+        if (f->bf16 && tc_layer_ok(d))
+            k_fno_layer_out_tc<<<(unsigned)(B * d.n), FT, 0, s>>>(
+                f->sspec, (const __nv_bfloat16 *)vin, W + f->off_W[l], W + f->off_b[l], d, act,
+                act ? (__nv_bfloat16 *)f->a[l] : nullptr, (__nv_bfloat16 *)f->v[l + 1]);
+        else
+            k_fno_layer_out<T><<<(unsigned)(B * d.n), FT, smem_layer(d), s>>>(
+                f->sspec, vin, W + f->off_W[l], W + f->off_b[l], d, act, act ? (T *)f->a[l] : nullptr,
+                (T *)f->v[l + 1]);
         f->launches += 3;
     }
-    k_fno_proj<T><<<grid_for(d.P()), FT, smem_proj(d), s>>>((const T *)f->v[d.L], W + f->off_p1, W + f->off_p1b,
-                                                          W + f->off_p2, W + f->off_p2b, d, f->z);
+    if (f->bf16 && tc_proj_ok(d))
+        k_fno_proj_tc<<<(unsigned)tc_proj_grid(d), FT, 0, s>>>((const __nv_bfloat16 *)f->v[d.L], W + f->off_p1,
+                                                              W + f->off_p1b, W + f->off_p2, W + f->off_p2b, d, f->z);
+    else
+        k_fno_proj<T><<<grid_for(d.P()), FT, smem_proj(d), s>>>((const T *)f->v[d.L], W + f->off_p1, W + f->off_p1b,
+                                                              W + f->off_p2, W + f->off_p2b, d, f->z);
     k_fno_softmax<<<(unsigned)B, FT, 0, s>>>(f->z, d.G(), p_out ? p_out : f->p, f->lse);
     f->launches += 2;
     FNO_CHECK(f);

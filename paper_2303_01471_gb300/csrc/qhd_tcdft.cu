@@ -314,6 +314,10 @@ int log2i(int n) {
 // the row length (in units of 2n) of the split operands.
 int w_segments(int products) { return products == TC_FIXED ? 4 : products == 5 ? 3 : 2; }
 int a_segments(int products) { return products == TC_FIXED ? 4 : 2; }
+// Row pitch (halves) of an operand of `segs` segments of m values: 128 bytes more
+// than the segments need, so consecutive rows of a TMA box (a power-of-two
+// number of bytes apart otherwise) spread over the L2 slices.
+int64_t tc_pitch(int segs, size_t m) { return (int64_t)segs * (int64_t)m + 64; }
 
 }  // namespace
 
@@ -344,8 +348,8 @@ bool tc_products_ok(int n, int products) {
 size_t tc_workspace_bytes(int n, int64_t batch, int products) {
     const size_t m = 2 * (size_t)n, rows = (size_t)batch * (size_t)n;
     size_t t = 0;
-    t += 2 * tc_align((size_t)w_segments(products) * m * m * sizeof(__half));
-    t += tc_align(rows * (size_t)a_segments(products) * m * sizeof(__half));
+    t += 2 * tc_align((size_t)tc_pitch(w_segments(products), m) * m * sizeof(__half));
+    t += tc_align(rows * (size_t)tc_pitch(a_segments(products), m) * sizeof(__half));
     t += tc_align(rows * m * sizeof(float));
     t += tc_align(2 * (size_t)batch * sizeof(unsigned));
     t += tc_align((size_t)batch * sizeof(int));
@@ -384,12 +388,13 @@ TcState *tc_create(int n, int64_t batch, int products, void *ws, size_t ws_bytes
     const size_t m = 2 * (size_t)n, rows = (size_t)batch * (size_t)n;
     const size_t wseg = (size_t)w_segments(products);
     char *p = (char *)ws;
+    const size_t wp = (size_t)tc_pitch((int)wseg, m);
     t->w[0] = (__half *)p;
-    p += tc_align(wseg * m * m * sizeof(__half));
+    p += tc_align(wp * m * sizeof(__half));
     t->w[1] = (__half *)p;
-    p += tc_align(wseg * m * m * sizeof(__half));
+    p += tc_align(wp * m * sizeof(__half));
     t->a = (__half *)p;
-    p += tc_align(rows * (size_t)a_segments(products) * m * sizeof(__half));
+    p += tc_align(rows * (size_t)tc_pitch(a_segments(products), m) * sizeof(__half));
     t->c = (float *)p;
     p += tc_align(rows * m * sizeof(float));
     t->maxbits = (unsigned *)p;
@@ -410,7 +415,7 @@ TcState *tc_create(int n, int64_t batch, int products, void *ws, size_t ws_bytes
     }
 
     // W and conj W from FP64, split on the host
-    std::vector<__half> host(wseg * m * m);
+    std::vector<__half> host(wp * m, __float2half(0.f));
     for (int d = 0; d < 2; ++d) {
         for (size_t row = 0; row < m; ++row)
             for (size_t col = 0; col < m; ++col) {
@@ -421,7 +426,7 @@ TcState *tc_create(int n, int64_t batch, int products, void *ws, size_t ws_bytes
                     double r = v * 1024.0;
                     for (int k = 0; k < wseg; ++k) {
                         const double w = std::nearbyint(r);
-                        host[col * wseg * m + k * m + row] = __double2half(w);
+                        host[col * wp + k * m + row] = __double2half(w);
                         r = (r - w) * 2048.0;
                     }
                 } else {
@@ -432,7 +437,7 @@ TcState *tc_create(int n, int64_t batch, int products, void *ws, size_t ws_bytes
                         r = (r - w[k]) * 128.0;
                     }
                     // segments w0 | w1 | w2 | w3 along K; level L pairs a_i with w_(L-i)
-                    for (int k = 0; k < 4; ++k) host[col * wseg * m + k * m + row] = __double2half(w[k]);
+                    for (int k = 0; k < 4; ++k) host[col * wp + k * m + row] = __double2half(w[k]);
                 }
             }
         if (cudaMemcpyAsync(t->w[d], host.data(), host.size() * sizeof(__half), cudaMemcpyHostToDevice, s) !=
@@ -451,7 +456,7 @@ void tc_destroy(TcState *t) { delete t; }
 static SplitOut split_out(TcState *t) {
     SplitOut o;
     o.a = t->a;
-    o.kp = (int64_t)a_segments(t->products) * 2 * t->n;
+    o.kp = tc_pitch(a_segments(t->products), 2 * (size_t)t->n);
     o.n = t->n;
     o.e = t->e8;
     o.eld = 2 * t->n / 16;
@@ -552,16 +557,16 @@ cudaError_t tc_gemm(TcState *t, bool inverse, cudaStream_t s, int64_t *launches)
     float alpha = 1.f;
     int64_t lda, ldb;
     if (t->products == TC_FIXED) {
-        lda = 4 * (int64_t)m;
-        ldb = 4 * (int64_t)m;
+        lda = tc_pitch(4, m);
+        ldb = tc_pitch(4, m);
         for (int lev = 0; lev < 4; ++lev)
             for (int i = 0; i <= lev; ++i)
                 seg[nseg++] = UgSeg{i * m, (lev - i) * m, kb, ldexpf(1.f, -7 * lev), i == 0 ? (int)UG_OPEN : (int)UG_CONTINUE};
     } else {
         // a W_hi (2^-20), a W_lo and c W_hi (2^-31), each times the row's block
         // exponent; 5 products add a W_lo2 and c W_lo (2^-42), smallest last
-        lda = 2 * (int64_t)m;
-        ldb = (int64_t)w_segments(t->products) * m;
+        lda = tc_pitch(2, m);
+        ldb = tc_pitch(w_segments(t->products), m);
         seg[nseg++] = UgSeg{0, 0, kb, ldexpf(1.f, -20), (int)UG_EACH_MMA_BEXP, 0};
         seg[nseg++] = UgSeg{0, m, kb, ldexpf(1.f, -31), (int)UG_EACH_MMA_BEXP, 0};
         seg[nseg++] = UgSeg{m, 0, kb, ldexpf(1.f, -31), (int)UG_EACH_MMA_BEXP, 0};

@@ -95,6 +95,30 @@ def test_bf16_activations_stay_close():
     assert (tv <= 5e-3).all(), tv
 
 
+def test_tensor_core_forward_matches_reference():
+    """Width 32 with BF16 activations runs the layer outputs and the projection on
+    the tensor cores (BF16 MMA, FP32 accumulation); against the FP64 reference and
+    against the FP32-activation (SIMT) path on the same parameters."""
+    n = 64
+    cfg = fno.FNOConfig(n=n, width=32, modes=16, layers=4, hidden=128, act_bf16=True)
+    shape = ref.Shape(n, 32, 16, 4, 128)
+    f, sigma, _ = tiny_batch(5, B=3, n=n)
+    params = perturbed_params(cfg, 6)
+    p_ref, _ = ref.forward(params.astype(np.float64), shape, f, sigma)
+    out = {}
+    for bf16 in (True, False):
+        net = fno.FNO(fno.FNOConfig(**{**cfg.__dict__, "act_bf16": bf16}), batch_max=4,
+                      params=torch.from_numpy(params))
+        out[bf16] = net.forward(dev(f, torch.float64), dev(sigma, torch.float32)).cpu().numpy()
+        net.close()
+    tv_tc = 0.5 * np.abs(out[True] - p_ref).sum(axis=(1, 2))
+    tv_32 = 0.5 * np.abs(out[False] - p_ref).sum(axis=(1, 2))
+    print(f"TV vs FP64 reference: tensor-core BF16 {tv_tc}, FP32 SIMT {tv_32}")
+    assert (tv_32 <= 1e-5).all(), tv_32
+    assert (tv_tc <= 1e-2).all(), tv_tc
+    assert np.allclose(out[True].sum(axis=(1, 2)), 1.0, atol=1e-5)
+
+
 def test_adam_steps_reduce_the_loss():
     f, sigma, pt = tiny_batch(3, B=4)
     net = fno.FNO(CFG, batch_max=4, train=True, seed=4)
