@@ -278,7 +278,7 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1
 }
 
 bool tc_layer_ok(const Dims &d) { return d.C == TC_C && d.M <= 16 && d.n % 16 == 0; }
-bool tc_proj_ok(const Dims &d) { return d.C == TC_C && d.H % 8 == 0 && d.H <= 128; }
+bool tc_proj_ok(const Dims &d) { return d.C == TC_C && d.H % 16 == 0 && d.H <= 128; }
 
 // Layer output of row bx = (b, x) on the tensor cores:
 //   a[y][o] = sum_c v[y][c] Ww[o][c] + sum_k T[y][k] U[k][o] + bw[o],
@@ -421,6 +421,220 @@ __global__ void __launch_bounds__(FT) k_fno_proj_tc(const __nv_bfloat16 *v, cons
             z[p0 + r + 8] = t1 + bias2;
         }
     }
+}
+
+// Axis-1 truncated DFT stage of row bx on the tensor cores (BF16 path):
+//   D[k][c] = sum_y T[k][y] V[y][c],  T[k][y] = cos(2 pi k y / n) (k < 16), -sin(2 pi (k - 16) y / n) (k >= 16),
+// so out[bx][ky][c] = s(ky) (D[ky][c], D[16 + ky][c]) as k_fno_dfty.  V (bf16 activations or FP32
+// gradients) is staged transposed in shared memory as BF16 pairs; each warp owns one 16 x 8 tile of D.
+template <typename T>
+__global__ void __launch_bounds__(FT) k_fno_dfty_tc(const T *in, Dims d, float s0, float s1, float2 *out) {
+    __shared__ uint32_t Vt[TC_C * (128 + 4)];  // [c][y pair], n <= 256
+    __shared__ float cs[256], sn[256], Ds[32 * 33];
+    const int n = d.n, M = d.M, LDV = n / 2 + 4;
+    const int64_t bx = blockIdx.x;
+    const T *src = in + bx * (int64_t)n * TC_C;
+    for (int i = threadIdx.x; i < TC_C * (n / 2); i += blockDim.x) {
+        const int c = i % TC_C, j = i / TC_C;
+        Vt[c * LDV + j] = bf2(ldv(&src[(2 * j) * TC_C + c]), ldv(&src[(2 * j + 1) * TC_C + c]));
+    }
+    twiddle_table(cs, sn, n);
+    __syncthreads();
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int r = lane / 4, q = 2 * (lane % 4);
+    const int mt = warp / 4, nt = warp % 4;  // 2 x 4 tiles of 16 x 8
+    auto tw = [&](int k, int y) {
+        const int idx = ((k & 15) * y) & (n - 1);
+        return k < 16 ? cs[idx] : -sn[idx];
+    };
+    float acc[4] = {};
+    const int ka = 16 * mt + r, kb = ka + 8, c = 8 * nt + r;
+    for (int y0 = 0; y0 < n; y0 += 16) {
+        const int y = y0 + q;
+        const uint32_t a0 = bf2(tw(ka, y), tw(ka, y + 1)), a1 = bf2(tw(kb, y), tw(kb, y + 1));
+        const uint32_t a2 = bf2(tw(ka, y + 8), tw(ka, y + 9)), a3 = bf2(tw(kb, y + 8), tw(kb, y + 9));
+        mma_bf16(acc, a0, a1, a2, a3, Vt[c * LDV + y / 2], Vt[c * LDV + y / 2 + 4]);
+    }
+    const int co = 8 * nt + q;
+    Ds[ka * 33 + co] = acc[0];
+    Ds[ka * 33 + co + 1] = acc[1];
+    Ds[kb * 33 + co] = acc[2];
+    Ds[kb * 33 + co + 1] = acc[3];
+    __syncthreads();
+    for (int o = threadIdx.x; o < M * TC_C; o += blockDim.x) {
+        const int ky = o / TC_C, cc = o % TC_C;
+        const float sc = ky == 0 ? s0 : s1;
+        out[bx * (int64_t)M * TC_C + o] = make_float2(Ds[ky * 33 + cc] * sc, Ds[(16 + ky) * 33 + cc] * sc);
+    }
+}
+
+// Backward of the layer input on the tensor cores (BF16 path), as k_fno_layer_in_bwd:
+//   dv[y][c] = sum_o Ww[o][c] da[y][o] + sum_k T[y][k] U[k][c],  U = [Re dT ; Im dT] (zero past M).
+__global__ void __launch_bounds__(FT) k_fno_layer_in_bwd_tc(const float2 *dT, const float *da, const float *Ww, Dims d,
+                                                            float *dv) {
+    __shared__ uint32_t Wt[TC_C * TC_LD], Ub[TC_C * TC_LD];  // [c][k pair]
+    __shared__ float cs[256], sn[256];
+    const int n = d.n, M = d.M;
+    const int64_t bx = blockIdx.x;
+    for (int i = threadIdx.x; i < TC_C * 16; i += blockDim.x) {
+        const int c = i / 16, j = i % 16;
+        Wt[c * TC_LD + j] = bf2(Ww[(2 * j) * TC_C + c], Ww[(2 * j + 1) * TC_C + c]);
+        float u[2];
+        for (int e = 0; e < 2; ++e) {
+            const int k = 2 * j + e, ky = k & 15;
+            float val = 0.f;
+            if (ky < M) {
+                const float2 t = dT[(bx * M + ky) * (int64_t)TC_C + c];
+                val = k < 16 ? t.x : t.y;
+            }
+            u[e] = val;
+        }
+        Ub[c * TC_LD + j] = bf2(u[0], u[1]);
+    }
+    twiddle_table(cs, sn, n);
+    __syncthreads();
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int r = lane / 4, q = 2 * (lane % 4);
+    const float *drow = da + bx * (int64_t)n * TC_C;
+    for (int y0 = 16 * warp; y0 < n; y0 += 16 * (FT / 32)) {
+        float acc[4][4] = {};
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks) {
+            const int k = 16 * ks + q;
+            auto pr = [&](int y, int kk) {
+                const float2 t = *reinterpret_cast<const float2 *>(&drow[y * TC_C + kk]);
+                return bf2(t.x, t.y);
+            };
+            const uint32_t a0 = pr(y0 + r, k), a1 = pr(y0 + r + 8, k), a2 = pr(y0 + r, k + 8), a3 = pr(y0 + r + 8, k + 8);
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt) {
+                const int c = 8 * nt + r;
+                mma_bf16(acc[nt], a0, a1, a2, a3, Wt[c * TC_LD + k / 2], Wt[c * TC_LD + k / 2 + 4]);
+            }
+        }
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks) {
+            const int k = 16 * ks + q;
+            auto tw = [&](int y, int kk) {
+                const int idx = ((kk & 15) * y) & (n - 1);
+                return kk < 16 ? cs[idx] : -sn[idx];
+            };
+            const int ya = y0 + r, yb = y0 + r + 8;
+            const uint32_t a0 = bf2(tw(ya, k), tw(ya, k + 1)), a1 = bf2(tw(yb, k), tw(yb, k + 1));
+            const uint32_t a2 = bf2(tw(ya, k + 8), tw(ya, k + 9)), a3 = bf2(tw(yb, k + 8), tw(yb, k + 9));
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt) {
+                const int c = 8 * nt + r;
+                mma_bf16(acc[nt], a0, a1, a2, a3, Ub[c * TC_LD + k / 2], Ub[c * TC_LD + k / 2 + 4]);
+            }
+        }
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt) {
+            const int c = 8 * nt + q;
+            float *out = dv + bx * (int64_t)n * TC_C;
+            *reinterpret_cast<float2 *>(&out[(y0 + r) * TC_C + c]) = make_float2(acc[nt][0], acc[nt][1]);
+            *reinterpret_cast<float2 *>(&out[(y0 + r + 8) * TC_C + c]) = make_float2(acc[nt][2], acc[nt][3]);
+        }
+    }
+}
+
+// Projection backward on the tensor cores (BF16 path), as k_fno_proj_bwd: per 16
+// points, h = W1 v + b1 (MMA), q = dz w2 gelu'(h) (stored to dh for the W1
+// gradient), dv = W1^T q (a second MMA whose A operand is q in registers), and
+// block partial sums of dz gelu(h) (W2 gradient) and dz (b2 gradient).
+__global__ void __launch_bounds__(FT) k_fno_proj_bwd_tc(const __nv_bfloat16 *v, const float *dz, const float *W1,
+                                                        const float *b1, const float *W2, Dims d, float *dh, float *dv,
+                                                        double *part) {
+    constexpr int LDT = 64 + 4;                   // words per row of W1^T pairs (H <= 128)
+    __shared__ uint32_t Wb[128 * TC_LD];          // [h][c pair]
+    __shared__ uint32_t Wt[TC_C * LDT];           // [c][h pair]
+    __shared__ float bb[128], ww[128], acc_s[129];
+    const int H = d.H;
+    for (int i = threadIdx.x; i < H * 16; i += blockDim.x) {
+        const int h = i / 16, j = i % 16;
+        Wb[h * TC_LD + j] = bf2(W1[h * TC_C + 2 * j], W1[h * TC_C + 2 * j + 1]);
+    }
+    for (int i = threadIdx.x; i < TC_C * (H / 2); i += blockDim.x) {
+        const int c = i % TC_C, j = i / TC_C;
+        Wt[c * LDT + j] = bf2(W1[(2 * j) * TC_C + c], W1[(2 * j + 1) * TC_C + c]);
+    }
+    for (int i = threadIdx.x; i < H; i += blockDim.x) {
+        bb[i] = b1[i];
+        ww[i] = W2[i];
+    }
+    for (int i = threadIdx.x; i <= H; i += blockDim.x) acc_s[i] = 0.f;
+    __syncthreads();
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int r = lane / 4, q = 2 * (lane % 4);
+    const int64_t P = d.P();
+    const uint32_t *vv = reinterpret_cast<const uint32_t *>(v);
+    const int64_t wstride = (int64_t)gridDim.x * (FT / 32) * 16;
+    for (int64_t p0 = ((int64_t)blockIdx.x * (FT / 32) + warp) * 16; p0 < P; p0 += wstride) {
+        uint32_t a[2][4];
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks) {
+            const int k = 16 * ks + q;
+            a[ks][0] = vv[((p0 + r) * TC_C + k) / 2];
+            a[ks][1] = vv[((p0 + r + 8) * TC_C + k) / 2];
+            a[ks][2] = vv[((p0 + r) * TC_C + k + 8) / 2];
+            a[ks][3] = vv[((p0 + r + 8) * TC_C + k + 8) / 2];
+        }
+        const float e0 = dz[p0 + r], e1 = dz[p0 + r + 8];
+        float dva[4][4] = {};
+        for (int nt2 = 0; nt2 < H / 16; ++nt2) {
+            uint32_t qa[4];
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                float acc[4] = {};
+                const int hr = 16 * nt2 + 8 * half + r;
+#pragma unroll
+                for (int ks = 0; ks < 2; ++ks) {
+                    const int k = 16 * ks + q;
+                    mma_bf16(acc, a[ks][0], a[ks][1], a[ks][2], a[ks][3], Wb[hr * TC_LD + k / 2],
+                             Wb[hr * TC_LD + k / 2 + 4]);
+                }
+                const int hc = 16 * nt2 + 8 * half + q;
+                const float h0 = acc[0] + bb[hc], h1 = acc[1] + bb[hc + 1];
+                const float h2 = acc[2] + bb[hc], h3 = acc[3] + bb[hc + 1];
+                // W2 gradient: sum over the warp's 16 points of dz gelu(h)
+                float g0 = fmaf(e0, gelu(h0), e1 * gelu(h2)), g1 = fmaf(e0, gelu(h1), e1 * gelu(h3));
+#pragma unroll
+                for (int o = 4; o < 32; o <<= 1) {
+                    g0 += __shfl_xor_sync(0xffffffffu, g0, o);
+                    g1 += __shfl_xor_sync(0xffffffffu, g1, o);
+                }
+                if (lane < 4) {
+                    atomicAdd(&acc_s[hc], g0);
+                    atomicAdd(&acc_s[hc + 1], g1);
+                }
+                const float q0 = e0 * ww[hc] * gelu_d(h0), q1 = e0 * ww[hc + 1] * gelu_d(h1);
+                const float q2 = e1 * ww[hc] * gelu_d(h2), q3 = e1 * ww[hc + 1] * gelu_d(h3);
+                *reinterpret_cast<float2 *>(&dh[(p0 + r) * H + hc]) = make_float2(q0, q1);
+                *reinterpret_cast<float2 *>(&dh[(p0 + r + 8) * H + hc]) = make_float2(q2, q3);
+                qa[2 * half] = bf2(q0, q1);      // rows r: k = hc, hc + 1 of this 16-wide step
+                qa[2 * half + 1] = bf2(q2, q3);  // rows r + 8
+            }
+            // dv[p][c] += sum_h q[p][h] W1[h][c] over this step's 16 h
+            const int kh = 16 * nt2 + q;
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt) {
+                const int c = 8 * nt + r;
+                mma_bf16(dva[nt], qa[0], qa[1], qa[2], qa[3], Wt[c * LDT + kh / 2], Wt[c * LDT + kh / 2 + 4]);
+            }
+        }
+        float t = e0 + e1;
+#pragma unroll
+        for (int o = 4; o < 32; o <<= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) atomicAdd(&acc_s[H], t);
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt) {
+            const int c = 8 * nt + q;
+            *reinterpret_cast<float2 *>(&dv[(p0 + r) * TC_C + c]) = make_float2(dva[nt][0], dva[nt][1]);
+            *reinterpret_cast<float2 *>(&dv[(p0 + r + 8) * TC_C + c]) = make_float2(dva[nt][2], dva[nt][3]);
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i <= H; i += blockDim.x) part[(int64_t)blockIdx.x * (H + 1) + i] = acc_s[i];
 }
 
 // ------------------------------------------------------------- projection
@@ -899,7 +1113,10 @@ qhd_status forward(qhd_fno *f, const double *fx, const float *sigma, int64_t B, 
     f->launches += 2;
     for (int l = 0; l < d.L; ++l) {
         const T *vin = (const T *)f->v[l];
-        k_fno_dfty<T><<<(unsigned)(B * d.n), FT, smem_dfty(d), s>>>(vin, d, 1.f, 1.f, f->tspec);
+        if (f->bf16 && tc_layer_ok(d))
+            k_fno_dfty_tc<T><<<(unsigned)(B * d.n), FT, 0, s>>>(vin, d, 1.f, 1.f, f->tspec);
+        else
+            k_fno_dfty<T><<<(unsigned)(B * d.n), FT, smem_dfty(d), s>>>(vin, d, 1.f, 1.f, f->tspec);
         k_fno_specx<false><<<(unsigned)(B * d.M), FT, smem_specx(d), s>>>(
             f->tspec, reinterpret_cast<const float2 *>(W + f->off_R[l]), d, f->vhat[l], f->sspec);
         const int act = l + 1 < d.L;
@@ -936,8 +1153,12 @@ qhd_status backward(qhd_fno *f, const float *p_true, int64_t B, float *grad, dou
     k_fno_loss<<<(unsigned)B, FT, 0, s>>>(f->z, f->lse, f->p, p_true, d.G(), 1.f / (float)B, f->dz, f->loss);
     // projection
     const size_t sp = smem_proj(d) + (size_t)(d.H + 1) * sizeof(float);
-    k_fno_proj_bwd<T><<<nb, FT, sp, s>>>((const T *)f->v[d.L], f->dz, W + f->off_p1, W + f->off_p1b, W + f->off_p2,
-                                          d, f->dh, f->dv, f->part);
+    if (f->bf16 && tc_proj_ok(d))
+        k_fno_proj_bwd_tc<<<nb, FT, 0, s>>>((const __nv_bfloat16 *)f->v[d.L], f->dz, W + f->off_p1, W + f->off_p1b,
+                                             W + f->off_p2, d, f->dh, f->dv, f->part);
+    else
+        k_fno_proj_bwd<T><<<nb, FT, sp, s>>>((const T *)f->v[d.L], f->dz, W + f->off_p1, W + f->off_p1b, W + f->off_p2,
+                                              d, f->dh, f->dv, f->part);
     k_fno_reduce<<<1, FT, 0, s>>>(f->part, nb, d.H + 1, grad + f->off_p2);
     k_fno_wgrad<T><<<nb, FT, 0, s>>>(f->dh, (const T *)f->v[d.L], P, d.H, d.C, f->part);
     k_fno_reduce<<<grid_for((int64_t)d.H * d.C + d.H), FT, 0, s>>>(f->part, nb, d.H * d.C + d.H, grad + f->off_p1);
@@ -952,12 +1173,19 @@ qhd_status backward(qhd_fno *f, const float *p_true, int64_t B, float *grad, dou
                                                                       grad + f->off_W[l]);
         // spectral path: adjoint of the inverse axis-1 stage, then of the axis-0 stages
         const float inv = 1.f / ((float)d.n * (float)d.n);
-        k_fno_dfty<float><<<(unsigned)(B * d.n), FT, smem_dfty(d), s>>>(f->da, d, inv, 2.f * inv, f->dspec);
+        if (f->bf16 && tc_layer_ok(d))
+            k_fno_dfty_tc<float><<<(unsigned)(B * d.n), FT, 0, s>>>(f->da, d, inv, 2.f * inv, f->dspec);
+        else
+            k_fno_dfty<float><<<(unsigned)(B * d.n), FT, smem_dfty(d), s>>>(f->da, d, inv, 2.f * inv, f->dspec);
         k_fno_specx<true><<<(unsigned)(B * d.M), FT, smem_specx(d), s>>>(
             f->dspec, reinterpret_cast<const float2 *>(W + f->off_R[l]), d, f->dwhat, f->tspec);
         k_fno_dR<<<(unsigned)(d.MX * d.M), FT, 2 * d.C * sizeof(float2), s>>>(
             f->dwhat, f->vhat[l], d, reinterpret_cast<float2 *>(grad + f->off_R[l]));
-        k_fno_layer_in_bwd<<<(unsigned)(B * d.n), FT, smem_layer(d), s>>>(f->tspec, f->da, W + f->off_W[l], d, f->dv);
+        if (f->bf16 && tc_layer_ok(d))
+            k_fno_layer_in_bwd_tc<<<(unsigned)(B * d.n), FT, 0, s>>>(f->tspec, f->da, W + f->off_W[l], d, f->dv);
+        else
+            k_fno_layer_in_bwd<<<(unsigned)(B * d.n), FT, smem_layer(d), s>>>(f->tspec, f->da, W + f->off_W[l], d,
+                                                                               f->dv);
         f->launches += 7;
     }
     // lift: sum over points of dv0 (x) features

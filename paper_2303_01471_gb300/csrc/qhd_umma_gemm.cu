@@ -64,17 +64,12 @@ template <int BN> struct UgCfg {
     static_assert(A_BYTES % 1024 == 0 && B_BYTES % 1024 == 0, "1024-byte aligned tiles");
 };
 
-// Walks the MMAs of the K list in order and reports group boundaries; the MMA
-// thread and the epilogue threads run the same walk.
+// Walks the MMAs of the K list in order and reports group boundaries for the
+// epilogue threads (the MMA thread decides the same boundaries per segment).
 struct GroupWalk {
     const UgArgs *a;
     int seg = 0, kb = 0, i = 0;  // segment, K block inside it, MMA inside the K block
     __device__ explicit GroupWalk(const UgArgs *args) : a(args) {}
-    __device__ bool starts() const {
-        const UgSeg &s = a->seg[seg];
-        return s.mode == UG_EACH_MMA || s.mode == UG_EACH_MMA_FLOAT || s.mode == UG_EACH_MMA_BEXP ||
-               (s.mode == UG_OPEN && kb == 0 && i == 0);
-    }
     __device__ bool ends() const {
         const UgSeg &s = a->seg[seg];
         if (s.mode == UG_EACH_MMA || s.mode == UG_EACH_MMA_FLOAT || s.mode == UG_EACH_MMA_BEXP) return true;
@@ -159,41 +154,57 @@ __global__ void __launch_bounds__(UG_THREADS, 1)
         // ---------------------------------------------------------- MMA issue
         if (lane == 0) {
             constexpr uint32_t IDESC = umma::idesc_f16_f32(UG_BM, BN);
-            GroupWalk w(&a);
+            // The group structure is decided per segment in registers: the issue
+            // rate of this one thread bounds the tensor pipe, so the per-MMA path
+            // carries no parameter-space lookups.
             int kb = 0, buf = 0, grp = 0;
             bool ok = a.nseg > 0;
-            uint32_t acc = 0;
-            while (ok) {
-                const int st = kb % STAGES;
-                ok = umma::mbar_wait(&full[st], (kb / STAGES) & 1, a.err, a.limit_ns);
-                if (!ok) break;
+            auto open_group = [&]() -> bool {
+                if (grp < NBUF) return true;
+                if (!umma::mbar_wait(&pempty[buf], ((grp / NBUF) - 1) & 1, a.err, a.limit_ns)) return false;
                 umma::tc_fence_after();
-                const uint32_t sa = umma::smem_u32(tiles + (size_t)st * Cfg::STAGE_BYTES);
-                const uint64_t da = umma::sdesc_k128(sa), db = umma::sdesc_k128(sa + Cfg::A_BYTES);
-                bool more = true;
-                for (int i = 0; i < 4; ++i) {
-                    if (w.starts()) {
-                        if (grp >= NBUF) {
-                            ok = umma::mbar_wait(&pempty[buf], ((grp / NBUF) - 1) & 1, a.err, a.limit_ns);
-                            if (!ok) break;
-                            umma::tc_fence_after();
-                        }
-                        acc = 0;
-                    }
+                return true;
+            };
+            auto close_group = [&]() {
+                umma::mma_commit(&pfull[buf]);
+                buf = (buf + 1) % NBUF;
+                ++grp;
+            };
+            for (int sg = 0; sg < a.nseg && ok; ++sg) {
+                const int mode = a.seg[sg].mode, kbs = a.seg[sg].kblocks;
+                const bool each = mode == UG_EACH_MMA || mode == UG_EACH_MMA_FLOAT || mode == UG_EACH_MMA_BEXP;
+                const bool opens = mode == UG_OPEN;
+                const bool closes = sg + 1 >= a.nseg || a.seg[sg + 1].mode != UG_CONTINUE;
+                for (int j = 0; j < kbs; ++j, ++kb) {
+                    const int st = kb % STAGES;
+                    ok = umma::mbar_wait(&full[st], (kb / STAGES) & 1, a.err, a.limit_ns);
+                    if (!ok) break;
+                    umma::tc_fence_after();
+                    const uint32_t sa = umma::smem_u32(tiles + (size_t)st * Cfg::STAGE_BYTES);
+                    const uint64_t da = umma::sdesc_k128(sa), db = umma::sdesc_k128(sa + Cfg::A_BYTES);
                     // 16 FP16 along K = 32 bytes: start address advances by 2 (16-byte units)
-                    umma::mma_f16(tmem + (uint32_t)(buf * BN), da + 2u * i, db + 2u * i, IDESC, acc);
-                    acc = 1;
-                    if (w.ends()) {
-                        umma::mma_commit(&pfull[buf]);
-                        buf = (buf + 1) % NBUF;
-                        ++grp;
+                    if (each) {
+                        for (int i = 0; i < 4 && ok; ++i) {
+                            ok = open_group();
+                            if (!ok) break;
+                            umma::mma_f16(tmem + (uint32_t)(buf * BN), da + 2u * i, db + 2u * i, IDESC, 0u);
+                            close_group();
+                        }
+                        if (!ok) break;
+                    } else {
+                        const bool first = opens && j == 0;
+                        if (first) {
+                            ok = open_group();
+                            if (!ok) break;
+                        }
+                        const uint32_t d = tmem + (uint32_t)(buf * BN);
+                        umma::mma_f16(d, da, db, IDESC, first ? 0u : 1u);
+#pragma unroll
+                        for (int i = 1; i < 4; ++i) umma::mma_f16(d, da + 2u * i, db + 2u * i, IDESC, 1u);
+                        if (closes && j == kbs - 1) close_group();
                     }
-                    more = w.next();
+                    umma::mma_commit(&empty[st]);
                 }
-                if (!ok) break;
-                umma::mma_commit(&empty[st]);
-                ++kb;
-                if (!more) break;
             }
             // every MMA issued has completed before the tensor memory is freed
             umma::mma_commit(done);

@@ -119,6 +119,37 @@ def test_tensor_core_forward_matches_reference():
     assert np.allclose(out[True].sum(axis=(1, 2)), 1.0, atol=1e-5)
 
 
+def test_tensor_core_gradients_match_the_fp32_path():
+    """The BF16 training path (tensor-core forward, layer-input and projection
+    backward, axis-1 DFT stages) against the FP32-activation SIMT path on the same
+    parameters and data: every parameter block's gradient agrees to BF16 accuracy."""
+    n = 32
+    cfg = fno.FNOConfig(n=n, width=32, modes=16, layers=2, hidden=128, act_bf16=True)
+    f, sigma, pt = tiny_batch(7, B=3, n=n)
+    params = perturbed_params(cfg, 8)
+    grads = {}
+    for bf16 in (True, False):
+        net = fno.FNO(fno.FNOConfig(**{**cfg.__dict__, "act_bf16": bf16}), batch_max=4, train=True,
+                      params=torch.from_numpy(params))
+        net.loss_grad(dev(f, torch.float64), dev(sigma, torch.float32), dev(pt, torch.float32))
+        grads[bf16] = net.grad.cpu().numpy().astype(np.float64)
+        net.close()
+    worst = {}
+    total = np.linalg.norm(grads[False])
+    for name, (o, k) in fno.param_layout(cfg).items():
+        if k == 0:
+            continue
+        g16, g32 = grads[True][o:o + k], grads[False][o:o + k]
+        if name == "p2_b":
+            # the output bias shifts every logit alike and the softmax ignores such a
+            # shift: its exact gradient is zero, both paths leave only rounding
+            assert np.abs(g16).max() <= 1e-4 * total and np.abs(g32).max() <= 1e-4 * total, (g16, g32)
+            continue
+        worst[name] = np.linalg.norm(g16 - g32) / max(np.linalg.norm(g32), 1e-30)
+    print("relative gradient difference, BF16 tensor-core vs FP32:", {k: f"{v:.1e}" for k, v in worst.items()})
+    assert max(worst.values()) <= 5e-2, worst
+
+
 def test_adam_steps_reduce_the_loss():
     f, sigma, pt = tiny_batch(3, B=4)
     net = fno.FNO(CFG, batch_max=4, train=True, seed=4)
