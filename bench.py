@@ -989,8 +989,25 @@ def run_fno(args, rank, world, local_rank, dist):
     mac = L * (g * C * M * 2 + M * (2 * M * C * n * 4 * 2 + 2 * M * C * C * 4) + g * C * (2 * (M - 1) + C)) \
         + g * (H * C + H + 4 * C)
     flop = 2.0 * mac
+    # forward bytes per instance, what the kernel sequence must move (BF16 activations
+    # of C channels = 2C bytes per point; spectra FP32 complex): lift reads f (8) and
+    # writes the features (16) and v0; per layer the axis-1 stage reads v and writes
+    # its M-mode spectrum, the axis-0 stage reads it and writes the mixed spectrum
+    # and the retained modes, the layer output reads the spectrum and v and writes
+    # v (and the pre-activation a, except after the last layer); the projection
+    # reads v and writes z, the softmax reads z and writes p
+    act, spec = 2 * C, 8 * M * C / n
+    vhat = 8 * 2 * M * M * C / g
+    per_layer = act + spec + spec + vhat + spec + spec + act + act + act
+    bytes_pt = (8 + 16 + act) + L * per_layer - act + (act + 4) + 8
+    bytes_inst = bytes_pt * g
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            hpeak, hsrc = float(json.load(fh)["hbm_gbs"]), "measured (STREAM-style copy)"
+    except Exception:
+        hpeak, hsrc = 6800.0, "fallback"
+    achieved = bytes_inst * nte / inf_s / 1e9
     fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12
-    achieved = flop * nte / inf_s / 1e12
     return {
         "metric": "instances/s", "value": inf_rate * world, "unit": "instances/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": inf_s * 1e3, "higher_is_better": True,
@@ -1010,10 +1027,12 @@ def run_fno(args, rank, world, local_rank, dist):
                   "seconds": t_train, "instances_per_s": nsteps * args.fno_batch / t_train},
         "data_generation_s": {"inputs": t_inputs, "solver_targets": t_data},
         "gpu_launches": launches,
-        "roofline": {"bound": "alu", "kernel": "FNO forward (all kernels)", "achieved": round(achieved, 2),
-                     "peak": round(fp32_peak, 1), "unit": "TFLOP/s", "frac": round(achieved / fp32_peak, 4),
-                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz", "traffic": None,
-                     "flop_per_instance": flop},
+        "roofline": {"bound": "hbm", "kernel": "FNO forward (all kernels; dense parts on BF16 MMA)",
+                     "achieved": round(achieved, 1), "peak": hpeak, "unit": "GB/s",
+                     "frac": round(achieved / hpeak, 4), "peak_source": hsrc, "traffic": None,
+                     "algorithmic_bytes_per_instance": bytes_inst, "flop_per_instance": flop,
+                     "flop_rate_tflops": round(flop * nte / inf_s / 1e12, 2),
+                     "fp32_simt_peak_tflops": round(fp32_peak, 1)},
         "clocks": clk.summary(),
     }
 

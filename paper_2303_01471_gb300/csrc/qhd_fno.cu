@@ -278,6 +278,8 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1
 }
 
 bool tc_layer_ok(const Dims &d) { return d.C == TC_C && d.M <= 16 && d.n % 16 == 0; }
+// the axis-0 stages: 2 MX = 4 M retained axis-0 modes in tiles of 16 (M = 8 or 16)
+bool tc_specx_ok(const Dims &d) { return tc_layer_ok(d) && d.MX % 16 == 0; }
 bool tc_proj_ok(const Dims &d) { return d.C == TC_C && d.H % 16 == 0 && d.H <= 128; }
 
 // Layer output of row bx = (b, x) on the tensor cores:
@@ -635,6 +637,154 @@ __global__ void __launch_bounds__(FT) k_fno_proj_bwd_tc(const __nv_bfloat16 *v, 
     }
     __syncthreads();
     for (int i = threadIdx.x; i <= H; i += blockDim.x) part[(int64_t)blockIdx.x * (H + 1) + i] = acc_s[i];
+}
+
+// Axis-0 stages with the mode mixing on the tensor cores (BF16 path), as
+// k_fno_specx: one block per (b, ky).  With theta = 2 pi f(kx) x / n,
+//   Y1[kx][c] = sum_x X[x][c] e^{-i theta}:  [Re; Im] Y1 = [[cos, sin], [-sin, cos]] . [Re X; Im X]
+//   (a 2 MX x 2n by 2n x C product, K over (x, re|im)),
+//   the per-mode mixing in FP32 as k_fno_specx,
+//   out[x][c] = sum_kx Y2[kx][c] e^{+i theta}:  [Re; Im] out = [[cos, -sin], [sin, cos]] . [Re Y2; Im Y2]
+//   (2n x 2 MX by 2 MX x C, K over (kx, re|im)).
+// X and Y2 enter the products as BF16, transposed into shared memory; each
+// warp computes the real and the imaginary tile of the same rows, so it writes
+// complex outputs directly.
+template <bool ADJ>
+__global__ void __launch_bounds__(FT) k_fno_specx_tc(const float2 *in, const float2 *R, Dims d, float2 *mid,
+                                                     float2 *out) {
+    extern __shared__ __align__(16) uint32_t sm32[];
+    const int n = d.n, M = d.M, MX = d.MX;
+    const int LDX = n + 4;                         // words per row of Xt: n (re) pairs then n (im) pairs... (2n / 2 = n)
+    uint32_t *Xt = sm32;                           // [c][k pair], k over (re x | im x), 2n values
+    float2 *Y1 = reinterpret_cast<float2 *>(Xt + TC_C * LDX);  // [kx][c]
+    float2 *Y2 = Y1 + MX * TC_C;                   // [kx][c]
+    uint32_t *Yt = reinterpret_cast<uint32_t *>(Y2 + MX * TC_C);  // [c][k pair], k over (re kx | im kx), 2 MX values
+    constexpr int LDY = 32 + 4;
+    float *cs = reinterpret_cast<float *>(Yt + TC_C * LDY), *sn = cs + n;
+    const int64_t b = blockIdx.x / M;
+    const int ky = blockIdx.x - (int)(b * M);
+    for (int i = threadIdx.x; i < TC_C * (n / 2); i += blockDim.x) {
+        const int c = i % TC_C, j = i / TC_C;  // x pair (2j, 2j + 1)
+        const float2 v0 = in[((b * n + 2 * j) * M + ky) * (int64_t)TC_C + c];
+        const float2 v1 = in[((b * n + 2 * j + 1) * M + ky) * (int64_t)TC_C + c];
+        Xt[c * LDX + j] = bf2(v0.x, v1.x);
+        Xt[c * LDX + n / 2 + j] = bf2(v0.y, v1.y);
+    }
+    twiddle_table(cs, sn, n);
+    __syncthreads();
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int r = lane / 4, q = 2 * (lane % 4);
+    auto fr = [&](int kx) { return kx_freq(kx, M, n); };
+    // ---- Y1: warp -> (kx tile kt, column tile nt); real and imaginary rows together
+    for (int t = warp; t < (MX / 16) * 4; t += FT / 32) {
+        const int kt = t / 4, nt = t % 4;
+        const int ka = 16 * kt + r, kb = ka + 8;
+        const int fa = fr(ka), fb = fr(kb);
+        float re[4] = {}, im[4] = {};
+        const int c = 8 * nt + r;
+        for (int k0 = 0; k0 < 2 * n; k0 += 16) {
+            // K index k = x (k < n: Re X) or x + n (Im X); this step's k0 .. k0 + 15 lie in one half
+            const bool imx = k0 >= n;
+            const int x = (imx ? k0 - n : k0) + q;
+            auto cth = [&](int f, int xx) { return cs[(f * xx) & (n - 1)]; };
+            auto sth = [&](int f, int xx) { return sn[(f * xx) & (n - 1)]; };
+            // real rows: cos . Re X + sin . Im X;  imaginary rows: -sin . Re X + cos . Im X
+            uint32_t ar[4], ai[4];
+            if (!imx) {
+                ar[0] = bf2(cth(fa, x), cth(fa, x + 1)); ar[1] = bf2(cth(fb, x), cth(fb, x + 1));
+                ar[2] = bf2(cth(fa, x + 8), cth(fa, x + 9)); ar[3] = bf2(cth(fb, x + 8), cth(fb, x + 9));
+                ai[0] = bf2(-sth(fa, x), -sth(fa, x + 1)); ai[1] = bf2(-sth(fb, x), -sth(fb, x + 1));
+                ai[2] = bf2(-sth(fa, x + 8), -sth(fa, x + 9)); ai[3] = bf2(-sth(fb, x + 8), -sth(fb, x + 9));
+            } else {
+                ar[0] = bf2(sth(fa, x), sth(fa, x + 1)); ar[1] = bf2(sth(fb, x), sth(fb, x + 1));
+                ar[2] = bf2(sth(fa, x + 8), sth(fa, x + 9)); ar[3] = bf2(sth(fb, x + 8), sth(fb, x + 9));
+                ai[0] = bf2(cth(fa, x), cth(fa, x + 1)); ai[1] = bf2(cth(fb, x), cth(fb, x + 1));
+                ai[2] = bf2(cth(fa, x + 8), cth(fa, x + 9)); ai[3] = bf2(cth(fb, x + 8), cth(fb, x + 9));
+            }
+            const int kw = (k0 + q) / 2;
+            const uint32_t b0 = Xt[c * LDX + kw], b1 = Xt[c * LDX + kw + 4];
+            mma_bf16(re, ar[0], ar[1], ar[2], ar[3], b0, b1);
+            mma_bf16(im, ai[0], ai[1], ai[2], ai[3], b0, b1);
+        }
+        const int co = 8 * nt + q;
+        const float2 ya0 = make_float2(re[0], im[0]), ya1 = make_float2(re[1], im[1]);
+        const float2 yb0 = make_float2(re[2], im[2]), yb1 = make_float2(re[3], im[3]);
+        Y1[ka * TC_C + co] = ya0;
+        Y1[ka * TC_C + co + 1] = ya1;
+        Y1[kb * TC_C + co] = yb0;
+        Y1[kb * TC_C + co + 1] = yb1;
+        mid[((b * MX + ka) * M + ky) * (int64_t)TC_C + co] = ya0;
+        mid[((b * MX + ka) * M + ky) * (int64_t)TC_C + co + 1] = ya1;
+        mid[((b * MX + kb) * M + ky) * (int64_t)TC_C + co] = yb0;
+        mid[((b * MX + kb) * M + ky) * (int64_t)TC_C + co + 1] = yb1;
+    }
+    __syncthreads();
+    // ---- mode mixing (FP32), then Y2 as BF16 pairs over (re kx | im kx)
+    for (int o = threadIdx.x; o < MX * TC_C; o += blockDim.x) {
+        const int kx = o / TC_C, c = o - kx * TC_C;
+        const float2 *Rm = R + ((int64_t)(kx * M + ky) * TC_C) * TC_C;  // [i][o]
+        float re = 0.f, im = 0.f;
+        for (int j = 0; j < TC_C; ++j) {
+            const float2 y = Y1[kx * TC_C + j];
+            if (!ADJ) {
+                const float2 rr = Rm[j * TC_C + c];
+                re += rr.x * y.x - rr.y * y.y;
+                im += rr.x * y.y + rr.y * y.x;
+            } else {
+                const float2 rr = Rm[c * TC_C + j];
+                re += rr.x * y.x + rr.y * y.y;
+                im += rr.x * y.y - rr.y * y.x;
+            }
+        }
+        Y2[o] = make_float2(re, im);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < TC_C * (MX / 2); i += blockDim.x) {
+        const int c = i % TC_C, j = i / TC_C;  // kx pair (2j, 2j + 1)
+        const float2 v0 = Y2[(2 * j) * TC_C + c], v1 = Y2[(2 * j + 1) * TC_C + c];
+        Yt[c * LDY + j] = bf2(v0.x, v1.x);
+        Yt[c * LDY + MX / 2 + j] = bf2(v0.y, v1.y);
+    }
+    __syncthreads();
+    // ---- out: warp -> (x tile, column tile); real and imaginary rows together
+    for (int t = warp; t < (n / 16) * 4; t += FT / 32) {
+        const int xt = t / 4, nt = t % 4;
+        const int xa = 16 * xt + r, xb = xa + 8;
+        float re[4] = {}, im[4] = {};
+        const int c = 8 * nt + r;
+        for (int k0 = 0; k0 < 2 * MX; k0 += 16) {
+            const bool imk = k0 >= MX;
+            const int kx = (imk ? k0 - MX : k0) + q;
+            auto cth = [&](int xx, int kk) { return cs[(fr(kk) * xx) & (n - 1)]; };
+            auto sth = [&](int xx, int kk) { return sn[(fr(kk) * xx) & (n - 1)]; };
+            // real rows: cos . Re Y2 - sin . Im Y2;  imaginary rows: sin . Re Y2 + cos . Im Y2
+            uint32_t ar[4], ai[4];
+            if (!imk) {
+                ar[0] = bf2(cth(xa, kx), cth(xa, kx + 1)); ar[1] = bf2(cth(xb, kx), cth(xb, kx + 1));
+                ar[2] = bf2(cth(xa, kx + 8), cth(xa, kx + 9)); ar[3] = bf2(cth(xb, kx + 8), cth(xb, kx + 9));
+                ai[0] = bf2(sth(xa, kx), sth(xa, kx + 1)); ai[1] = bf2(sth(xb, kx), sth(xb, kx + 1));
+                ai[2] = bf2(sth(xa, kx + 8), sth(xa, kx + 9)); ai[3] = bf2(sth(xb, kx + 8), sth(xb, kx + 9));
+            } else {
+                ar[0] = bf2(-sth(xa, kx), -sth(xa, kx + 1)); ar[1] = bf2(-sth(xb, kx), -sth(xb, kx + 1));
+                ar[2] = bf2(-sth(xa, kx + 8), -sth(xa, kx + 9)); ar[3] = bf2(-sth(xb, kx + 8), -sth(xb, kx + 9));
+                ai[0] = bf2(cth(xa, kx), cth(xa, kx + 1)); ai[1] = bf2(cth(xb, kx), cth(xb, kx + 1));
+                ai[2] = bf2(cth(xa, kx + 8), cth(xa, kx + 9)); ai[3] = bf2(cth(xb, kx + 8), cth(xb, kx + 9));
+            }
+            const int kw = (k0 + q) / 2;
+            const uint32_t b0 = Yt[c * LDY + kw], b1 = Yt[c * LDY + kw + 4];
+            mma_bf16(re, ar[0], ar[1], ar[2], ar[3], b0, b1);
+            mma_bf16(im, ai[0], ai[1], ai[2], ai[3], b0, b1);
+        }
+        const int co = 8 * nt + q;
+        out[((b * n + xa) * M + ky) * (int64_t)TC_C + co] = make_float2(re[0], im[0]);
+        out[((b * n + xa) * M + ky) * (int64_t)TC_C + co + 1] = make_float2(re[1], im[1]);
+        out[((b * n + xb) * M + ky) * (int64_t)TC_C + co] = make_float2(re[2], im[2]);
+        out[((b * n + xb) * M + ky) * (int64_t)TC_C + co + 1] = make_float2(re[3], im[3]);
+    }
+}
+
+size_t smem_specx_tc(const Dims &d) {
+    return (size_t)TC_C * (d.n + 4) * 4 + 2 * (size_t)d.MX * TC_C * 8 + (size_t)TC_C * 36 * 4 + 2 * (size_t)d.n * 4;
 }
 
 // ------------------------------------------------------------- projection
@@ -1096,6 +1246,8 @@ void set_smem_limits() {
     cudaFuncSetAttribute(k_fno_dfty<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_fno_specx<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_fno_specx<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_fno_specx_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_fno_specx_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_fno_layer_out<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_fno_layer_in_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
 }
@@ -1117,8 +1269,12 @@ qhd_status forward(qhd_fno *f, const double *fx, const float *sigma, int64_t B, 
             k_fno_dfty_tc<T><<<(unsigned)(B * d.n), FT, 0, s>>>(vin, d, 1.f, 1.f, f->tspec);
         else
             k_fno_dfty<T><<<(unsigned)(B * d.n), FT, smem_dfty(d), s>>>(vin, d, 1.f, 1.f, f->tspec);
-        k_fno_specx<false><<<(unsigned)(B * d.M), FT, smem_specx(d), s>>>(
-            f->tspec, reinterpret_cast<const float2 *>(W + f->off_R[l]), d, f->vhat[l], f->sspec);
+        if (f->bf16 && tc_specx_ok(d))
+            k_fno_specx_tc<false><<<(unsigned)(B * d.M), FT, smem_specx_tc(d), s>>>(
+                f->tspec, reinterpret_cast<const float2 *>(W + f->off_R[l]), d, f->vhat[l], f->sspec);
+        else
+            k_fno_specx<false><<<(unsigned)(B * d.M), FT, smem_specx(d), s>>>(
+                f->tspec, reinterpret_cast<const float2 *>(W + f->off_R[l]), d, f->vhat[l], f->sspec);
         const int act = l + 1 < d.L;
         if (f->bf16 && tc_layer_ok(d))
             k_fno_layer_out_tc<<<(unsigned)(B * d.n), FT, 0, s>>>(
@@ -1177,8 +1333,12 @@ qhd_status backward(qhd_fno *f, const float *p_true, int64_t B, float *grad, dou
             k_fno_dfty_tc<float><<<(unsigned)(B * d.n), FT, 0, s>>>(f->da, d, inv, 2.f * inv, f->dspec);
         else
             k_fno_dfty<float><<<(unsigned)(B * d.n), FT, smem_dfty(d), s>>>(f->da, d, inv, 2.f * inv, f->dspec);
-        k_fno_specx<true><<<(unsigned)(B * d.M), FT, smem_specx(d), s>>>(
-            f->dspec, reinterpret_cast<const float2 *>(W + f->off_R[l]), d, f->dwhat, f->tspec);
+        if (f->bf16 && tc_specx_ok(d))
+            k_fno_specx_tc<true><<<(unsigned)(B * d.M), FT, smem_specx_tc(d), s>>>(
+                f->dspec, reinterpret_cast<const float2 *>(W + f->off_R[l]), d, f->dwhat, f->tspec);
+        else
+            k_fno_specx<true><<<(unsigned)(B * d.M), FT, smem_specx(d), s>>>(
+                f->dspec, reinterpret_cast<const float2 *>(W + f->off_R[l]), d, f->dwhat, f->tspec);
         k_fno_dR<<<(unsigned)(d.MX * d.M), FT, 2 * d.C * sizeof(float2), s>>>(
             f->dwhat, f->vhat[l], d, reinterpret_cast<float2 *>(grad + f->off_R[l]));
         if (f->bf16 && tc_layer_ok(d))
