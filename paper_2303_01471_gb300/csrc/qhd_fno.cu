@@ -108,11 +108,30 @@ __global__ void k_fno_lift(const double *f, const float *sigma, const double2 *s
         q[1] = sigma[b];
         q[2] = (float)(g / d.n) / (float)d.n;
         q[3] = (float)(g % d.n) / (float)d.n;
-        for (int j = 0; j < 4; ++j) feat[p * 4 + j] = q[j];
-        for (int c = 0; c < d.C; ++c) {
-            float a = bias[c];
-            for (int j = 0; j < 4; ++j) a = fmaf(W[c * 4 + j], q[j], a);
-            stv(&v0[p * d.C + c], a);
+        *reinterpret_cast<float4 *>(&feat[p * 4]) = make_float4(q[0], q[1], q[2], q[3]);
+        if (sizeof(T) == 2 && d.C == 32) {
+            // BF16 at width 32: the point's 64 bytes as four 16-byte stores
+            uint32_t w[16];
+#pragma unroll
+            for (int c = 0; c < 32; c += 2) {
+                float a0 = bias[c], a1 = bias[c + 1];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    a0 = fmaf(W[c * 4 + j], q[j], a0);
+                    a1 = fmaf(W[(c + 1) * 4 + j], q[j], a1);
+                }
+                const __nv_bfloat162 h = __floats2bfloat162_rn(a0, a1);
+                w[c / 2] = *reinterpret_cast<const uint32_t *>(&h);
+            }
+            uint4 *dst = reinterpret_cast<uint4 *>(&v0[p * d.C]);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) dst[k] = make_uint4(w[4 * k], w[4 * k + 1], w[4 * k + 2], w[4 * k + 3]);
+        } else {
+            for (int c = 0; c < d.C; ++c) {
+                float a = bias[c];
+                for (int j = 0; j < 4; ++j) a = fmaf(W[c * 4 + j], q[j], a);
+                stv(&v0[p * d.C + c], a);
+            }
         }
     }
 }
