@@ -301,6 +301,85 @@ bool tc_layer_ok(const Dims &d) { return d.C == TC_C && d.M <= 16 && d.n % 16 ==
 bool tc_specx_ok(const Dims &d) { return tc_layer_ok(d) && d.MX % 16 == 0; }
 bool tc_proj_ok(const Dims &d) { return d.C == TC_C && d.H % 16 == 0 && d.H <= 128; }
 
+// A-operand fragments of the DFT products (the same for every row and mode),
+// built once per network by k_fno_frags from the same cos/sin table the
+// SIMT kernels use; entry (tile, k step, lane) holds the lane's four BF16 pairs
+// of mma.m16n8k16's A operand.
+struct TcFrags {
+    const uint4 *dfty;  // [2][n/16][32]: T[k][y] (k < 16 cos, else -sin) for the axis-1 stage
+    const uint4 *lay;   // [n/16][2][32]: T[y][k] for the layer output / layer-input backward
+    const uint4 *sx1;   // [MX/16][2n/16][2][32]: axis-0 forward rows (re, im)
+    const uint4 *sx2;   // [n/16][2 MX/16][2][32]: axis-0 inverse rows (re, im)
+};
+
+__host__ __device__ size_t frag_count(const Dims &d, int which) {
+    const int n = d.n, MX = d.MX;
+    switch (which) {
+    case 0: return 2 * (size_t)(n / 16) * 32;
+    case 1: return (size_t)(n / 16) * 2 * 32;
+    case 2: return (size_t)(MX / 16) * (2 * n / 16) * 2 * 32;
+    default: return (size_t)(n / 16) * (2 * MX / 16) * 2 * 32;
+    }
+}
+
+__global__ void __launch_bounds__(FT) k_fno_frags(uint4 *dfty, uint4 *lay, uint4 *sx1, uint4 *sx2, Dims d) {
+    __shared__ float cs[256], sn[256];
+    const int n = d.n, M = d.M, MX = d.MX;
+    twiddle_table(cs, sn, n);
+    __syncthreads();
+    auto twk = [&](int k, int y) {  // k < 16: cos, else -sin of 2 pi (k & 15) y / n
+        const int idx = ((k & 15) * y) & (n - 1);
+        return k < 16 ? cs[idx] : -sn[idx];
+    };
+    auto cth = [&](int f, int x) { return cs[(f * x) & (n - 1)]; };
+    auto sth = [&](int f, int x) { return sn[(f * x) & (n - 1)]; };
+    const size_t c0 = frag_count(d, 0), c1 = frag_count(d, 1);
+    const size_t c2 = sx1 ? frag_count(d, 2) : 0, c3 = sx2 ? frag_count(d, 3) : 0;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < c0 + c1 + c2 + c3;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const int lane = (int)(e % 32), r = lane / 4, q = 2 * (lane % 4);
+        if (e < c0) {
+            const int t = (int)(e / 32), KS = n / 16, mt = t / KS, ks = t % KS;
+            const int y = 16 * ks + q, ka = 16 * mt + r, kb = ka + 8;
+            dfty[e] = make_uint4(bf2(twk(ka, y), twk(ka, y + 1)), bf2(twk(kb, y), twk(kb, y + 1)),
+                                 bf2(twk(ka, y + 8), twk(ka, y + 9)), bf2(twk(kb, y + 8), twk(kb, y + 9)));
+        } else if (e < c0 + c1) {
+            const size_t e1 = e - c0;
+            const int t = (int)(e1 / 32), yt = t / 2, ks = t % 2;
+            const int k = 16 * ks + q, ya = 16 * yt + r, yb = ya + 8;
+            lay[e1] = make_uint4(bf2(twk(k, ya), twk(k + 1, ya)), bf2(twk(k, yb), twk(k + 1, yb)),
+                                 bf2(twk(k + 8, ya), twk(k + 9, ya)), bf2(twk(k + 8, yb), twk(k + 9, yb)));
+        } else if (e < c0 + c1 + c2) {
+            const size_t e2 = e - c0 - c1;
+            const int t = (int)(e2 / 32), kind = t % 2, t2 = t / 2, S1 = 2 * n / 16, st = t2 % S1, kt = t2 / S1;
+            const int k0 = 16 * st;
+            const bool imx = k0 >= n;
+            const int x = (imx ? k0 - n : k0) + q;
+            const int fa = kx_freq(16 * kt + r, M, n), fb = kx_freq(16 * kt + r + 8, M, n);
+            // real rows: [cos | sin] over (Re X | Im X); imaginary rows: [-sin | cos]
+            auto v = [&](int f, int xx) {
+                return kind == 0 ? (imx ? sth(f, xx) : cth(f, xx)) : (imx ? cth(f, xx) : -sth(f, xx));
+            };
+            sx1[e2] = make_uint4(bf2(v(fa, x), v(fa, x + 1)), bf2(v(fb, x), v(fb, x + 1)),
+                                 bf2(v(fa, x + 8), v(fa, x + 9)), bf2(v(fb, x + 8), v(fb, x + 9)));
+        } else {
+            const size_t e3 = e - c0 - c1 - c2;
+            const int t = (int)(e3 / 32), kind = t % 2, t2 = t / 2, S2 = 2 * MX / 16, st = t2 % S2, xt = t2 / S2;
+            const int k0 = 16 * st;
+            const bool imk = k0 >= MX;
+            const int kx = (imk ? k0 - MX : k0) + q;
+            const int xa = 16 * xt + r, xb = xa + 8;
+            // real rows: [cos | -sin] over (Re Y2 | Im Y2); imaginary rows: [sin | cos]
+            auto v = [&](int xx, int kk) {
+                const int f = kx_freq(kk, M, n);
+                return kind == 0 ? (imk ? -sth(f, xx) : cth(f, xx)) : (imk ? cth(f, xx) : sth(f, xx));
+            };
+            sx2[e3] = make_uint4(bf2(v(xa, kx), v(xa, kx + 1)), bf2(v(xb, kx), v(xb, kx + 1)),
+                                 bf2(v(xa, kx + 8), v(xa, kx + 9)), bf2(v(xb, kx + 8), v(xb, kx + 9)));
+        }
+    }
+}
+
 // Layer output of row bx = (b, x) on the tensor cores:
 //   a[y][o] = sum_c v[y][c] Ww[o][c] + sum_k T[y][k] U[k][o] + bw[o],
 //   T[y][k] = cos(2 pi k y / n) (k < 16), -sin(2 pi (k - 16) y / n) (k >= 16),
@@ -309,9 +388,9 @@ bool tc_proj_ok(const Dims &d) { return d.C == TC_C && d.H % 16 == 0 && d.H <= 1
 // Each warp takes 16 rows y at a time: K = 32 (channels) + 32 (spectral).
 __global__ void __launch_bounds__(FT) k_fno_layer_out_tc(const float2 *S, const __nv_bfloat16 *v, const float *Ww,
                                                          const float *bw, Dims d, int act, __nv_bfloat16 *a_out,
-                                                         __nv_bfloat16 *v_out) {
+                                                         __nv_bfloat16 *v_out, const uint4 *lay) {
     __shared__ uint32_t Wb[TC_C * TC_LD], Ub[TC_C * TC_LD];  // [o][k pair]
-    __shared__ float cs[256], sn[256], bs[TC_C];
+    __shared__ float bs[TC_C];
     const int n = d.n, M = d.M;
     const int64_t bx = blockIdx.x;
     const float inv = 1.f / ((float)n * (float)n);
@@ -331,7 +410,6 @@ __global__ void __launch_bounds__(FT) k_fno_layer_out_tc(const float2 *S, const 
         }
         Ub[o * TC_LD + j] = bf2(u[0], u[1]);
     }
-    twiddle_table(cs, sn, n);
     for (int i = threadIdx.x; i < TC_C; i += blockDim.x) bs[i] = bw[i];
     __syncthreads();
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -354,18 +432,12 @@ __global__ void __launch_bounds__(FT) k_fno_layer_out_tc(const float2 *S, const 
         // spectral: A = T rows y0.., K = 32 (cos | -sin) in two steps
 #pragma unroll
         for (int ks = 0; ks < 2; ++ks) {
-            const int k = 16 * ks + q;  // k, k + 1 and k + 8, k + 9 share the cos / sin choice
-            auto tw = [&](int y, int kk) {
-                const int ky = kk & 15, idx = (ky * y) & (n - 1);
-                return kk < 16 ? cs[idx] : -sn[idx];
-            };
-            const int ya = y0 + r, yb = y0 + r + 8;
-            const uint32_t a0 = bf2(tw(ya, k), tw(ya, k + 1)), a1 = bf2(tw(yb, k), tw(yb, k + 1));
-            const uint32_t a2 = bf2(tw(ya, k + 8), tw(ya, k + 9)), a3 = bf2(tw(yb, k + 8), tw(yb, k + 9));
+            const int k = 16 * ks + q;
+            const uint4 A = __ldg(&lay[((y0 / 16) * 2 + ks) * 32 + lane]);
 #pragma unroll
             for (int nt = 0; nt < 4; ++nt) {
                 const int o = 8 * nt + r;
-                mma_bf16(acc[nt], a0, a1, a2, a3, Ub[o * TC_LD + k / 2], Ub[o * TC_LD + k / 2 + 4]);
+                mma_bf16(acc[nt], A.x, A.y, A.z, A.w, Ub[o * TC_LD + k / 2], Ub[o * TC_LD + k / 2 + 4]);
             }
         }
 #pragma unroll
@@ -449,9 +521,10 @@ __global__ void __launch_bounds__(FT) k_fno_proj_tc(const __nv_bfloat16 *v, cons
 // so out[bx][ky][c] = s(ky) (D[ky][c], D[16 + ky][c]) as k_fno_dfty.  V (bf16 activations or FP32
 // gradients) is staged transposed in shared memory as BF16 pairs; each warp owns one 16 x 8 tile of D.
 template <typename T>
-__global__ void __launch_bounds__(FT) k_fno_dfty_tc(const T *in, Dims d, float s0, float s1, float2 *out) {
+__global__ void __launch_bounds__(FT) k_fno_dfty_tc(const T *in, Dims d, float s0, float s1, float2 *out,
+                                                    const uint4 *fr) {
     __shared__ uint32_t Vt[TC_C * (128 + 4)];  // [c][y pair], n <= 256
-    __shared__ float cs[256], sn[256], Ds[32 * 33];
+    __shared__ float Ds[32 * 33];
     const int n = d.n, M = d.M, LDV = n / 2 + 4;
     const int64_t bx = blockIdx.x;
     const T *src = in + bx * (int64_t)n * TC_C;
@@ -459,22 +532,17 @@ __global__ void __launch_bounds__(FT) k_fno_dfty_tc(const T *in, Dims d, float s
         const int c = i % TC_C, j = i / TC_C;
         Vt[c * LDV + j] = bf2(ldv(&src[(2 * j) * TC_C + c]), ldv(&src[(2 * j + 1) * TC_C + c]));
     }
-    twiddle_table(cs, sn, n);
     __syncthreads();
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int r = lane / 4, q = 2 * (lane % 4);
     const int mt = warp / 4, nt = warp % 4;  // 2 x 4 tiles of 16 x 8
-    auto tw = [&](int k, int y) {
-        const int idx = ((k & 15) * y) & (n - 1);
-        return k < 16 ? cs[idx] : -sn[idx];
-    };
     float acc[4] = {};
     const int ka = 16 * mt + r, kb = ka + 8, c = 8 * nt + r;
+    const uint4 *frm = fr + (size_t)mt * (n / 16) * 32 + lane;
     for (int y0 = 0; y0 < n; y0 += 16) {
         const int y = y0 + q;
-        const uint32_t a0 = bf2(tw(ka, y), tw(ka, y + 1)), a1 = bf2(tw(kb, y), tw(kb, y + 1));
-        const uint32_t a2 = bf2(tw(ka, y + 8), tw(ka, y + 9)), a3 = bf2(tw(kb, y + 8), tw(kb, y + 9));
-        mma_bf16(acc, a0, a1, a2, a3, Vt[c * LDV + y / 2], Vt[c * LDV + y / 2 + 4]);
+        const uint4 A = __ldg(&frm[(y0 / 16) * 32]);
+        mma_bf16(acc, A.x, A.y, A.z, A.w, Vt[c * LDV + y / 2], Vt[c * LDV + y / 2 + 4]);
     }
     const int co = 8 * nt + q;
     Ds[ka * 33 + co] = acc[0];
@@ -492,9 +560,8 @@ __global__ void __launch_bounds__(FT) k_fno_dfty_tc(const T *in, Dims d, float s
 // Backward of the layer input on the tensor cores (BF16 path), as k_fno_layer_in_bwd:
 //   dv[y][c] = sum_o Ww[o][c] da[y][o] + sum_k T[y][k] U[k][c],  U = [Re dT ; Im dT] (zero past M).
 __global__ void __launch_bounds__(FT) k_fno_layer_in_bwd_tc(const float2 *dT, const float *da, const float *Ww, Dims d,
-                                                            float *dv) {
+                                                            float *dv, const uint4 *lay) {
     __shared__ uint32_t Wt[TC_C * TC_LD], Ub[TC_C * TC_LD];  // [c][k pair]
-    __shared__ float cs[256], sn[256];
     const int n = d.n, M = d.M;
     const int64_t bx = blockIdx.x;
     for (int i = threadIdx.x; i < TC_C * 16; i += blockDim.x) {
@@ -512,7 +579,6 @@ __global__ void __launch_bounds__(FT) k_fno_layer_in_bwd_tc(const float2 *dT, co
         }
         Ub[c * TC_LD + j] = bf2(u[0], u[1]);
     }
-    twiddle_table(cs, sn, n);
     __syncthreads();
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int r = lane / 4, q = 2 * (lane % 4);
@@ -536,17 +602,11 @@ __global__ void __launch_bounds__(FT) k_fno_layer_in_bwd_tc(const float2 *dT, co
 #pragma unroll
         for (int ks = 0; ks < 2; ++ks) {
             const int k = 16 * ks + q;
-            auto tw = [&](int y, int kk) {
-                const int idx = ((kk & 15) * y) & (n - 1);
-                return kk < 16 ? cs[idx] : -sn[idx];
-            };
-            const int ya = y0 + r, yb = y0 + r + 8;
-            const uint32_t a0 = bf2(tw(ya, k), tw(ya, k + 1)), a1 = bf2(tw(yb, k), tw(yb, k + 1));
-            const uint32_t a2 = bf2(tw(ya, k + 8), tw(ya, k + 9)), a3 = bf2(tw(yb, k + 8), tw(yb, k + 9));
+            const uint4 A = __ldg(&lay[((y0 / 16) * 2 + ks) * 32 + lane]);
 #pragma unroll
             for (int nt = 0; nt < 4; ++nt) {
                 const int c = 8 * nt + r;
-                mma_bf16(acc[nt], a0, a1, a2, a3, Ub[c * TC_LD + k / 2], Ub[c * TC_LD + k / 2 + 4]);
+                mma_bf16(acc[nt], A.x, A.y, A.z, A.w, Ub[c * TC_LD + k / 2], Ub[c * TC_LD + k / 2 + 4]);
             }
         }
 #pragma unroll
@@ -670,16 +730,15 @@ __global__ void __launch_bounds__(FT) k_fno_proj_bwd_tc(const __nv_bfloat16 *v, 
 // complex outputs directly.
 template <bool ADJ>
 __global__ void __launch_bounds__(FT) k_fno_specx_tc(const float2 *in, const float2 *R, Dims d, float2 *mid,
-                                                     float2 *out) {
+                                                     float2 *out, const uint4 *sx1, const uint4 *sx2) {
     extern __shared__ __align__(16) uint32_t sm32[];
     const int n = d.n, M = d.M, MX = d.MX;
-    const int LDX = n + 4;                         // words per row of Xt: n (re) pairs then n (im) pairs... (2n / 2 = n)
+    const int LDX = n + 4;                         // words per row of Xt: n/2 (re) pairs, n/2 (im) pairs, padding
     uint32_t *Xt = sm32;                           // [c][k pair], k over (re x | im x), 2n values
     float2 *Y1 = reinterpret_cast<float2 *>(Xt + TC_C * LDX);  // [kx][c]
     float2 *Y2 = Y1 + MX * TC_C;                   // [kx][c]
     uint32_t *Yt = reinterpret_cast<uint32_t *>(Y2 + MX * TC_C);  // [c][k pair], k over (re kx | im kx), 2 MX values
     constexpr int LDY = 32 + 4;
-    float *cs = reinterpret_cast<float *>(Yt + TC_C * LDY), *sn = cs + n;
     const int64_t b = blockIdx.x / M;
     const int ky = blockIdx.x - (int)(b * M);
     for (int i = threadIdx.x; i < TC_C * (n / 2); i += blockDim.x) {
@@ -689,37 +748,21 @@ __global__ void __launch_bounds__(FT) k_fno_specx_tc(const float2 *in, const flo
         Xt[c * LDX + j] = bf2(v0.x, v1.x);
         Xt[c * LDX + n / 2 + j] = bf2(v0.y, v1.y);
     }
-    twiddle_table(cs, sn, n);
     __syncthreads();
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int r = lane / 4, q = 2 * (lane % 4);
-    auto fr = [&](int kx) { return kx_freq(kx, M, n); };
+    const int S1 = 2 * n / 16, S2 = 2 * MX / 16;
     // ---- Y1: warp -> (kx tile kt, column tile nt); real and imaginary rows together
     for (int t = warp; t < (MX / 16) * 4; t += FT / 32) {
         const int kt = t / 4, nt = t % 4;
         const int ka = 16 * kt + r, kb = ka + 8;
-        const int fa = fr(ka), fb = fr(kb);
         float re[4] = {}, im[4] = {};
         const int c = 8 * nt + r;
         for (int k0 = 0; k0 < 2 * n; k0 += 16) {
-            // K index k = x (k < n: Re X) or x + n (Im X); this step's k0 .. k0 + 15 lie in one half
-            const bool imx = k0 >= n;
-            const int x = (imx ? k0 - n : k0) + q;
-            auto cth = [&](int f, int xx) { return cs[(f * xx) & (n - 1)]; };
-            auto sth = [&](int f, int xx) { return sn[(f * xx) & (n - 1)]; };
             // real rows: cos . Re X + sin . Im X;  imaginary rows: -sin . Re X + cos . Im X
-            uint32_t ar[4], ai[4];
-            if (!imx) {
-                ar[0] = bf2(cth(fa, x), cth(fa, x + 1)); ar[1] = bf2(cth(fb, x), cth(fb, x + 1));
-                ar[2] = bf2(cth(fa, x + 8), cth(fa, x + 9)); ar[3] = bf2(cth(fb, x + 8), cth(fb, x + 9));
-                ai[0] = bf2(-sth(fa, x), -sth(fa, x + 1)); ai[1] = bf2(-sth(fb, x), -sth(fb, x + 1));
-                ai[2] = bf2(-sth(fa, x + 8), -sth(fa, x + 9)); ai[3] = bf2(-sth(fb, x + 8), -sth(fb, x + 9));
-            } else {
-                ar[0] = bf2(sth(fa, x), sth(fa, x + 1)); ar[1] = bf2(sth(fb, x), sth(fb, x + 1));
-                ar[2] = bf2(sth(fa, x + 8), sth(fa, x + 9)); ar[3] = bf2(sth(fb, x + 8), sth(fb, x + 9));
-                ai[0] = bf2(cth(fa, x), cth(fa, x + 1)); ai[1] = bf2(cth(fb, x), cth(fb, x + 1));
-                ai[2] = bf2(cth(fa, x + 8), cth(fa, x + 9)); ai[3] = bf2(cth(fb, x + 8), cth(fb, x + 9));
-            }
+            const uint4 *fa = &sx1[(((size_t)kt * S1 + k0 / 16) * 2) * 32 + lane];
+            const uint4 A = __ldg(fa), B = __ldg(fa + 32);
+            const uint32_t ar[4] = {A.x, A.y, A.z, A.w}, ai[4] = {B.x, B.y, B.z, B.w};
             const int kw = (k0 + q) / 2;
             const uint32_t b0 = Xt[c * LDX + kw], b1 = Xt[c * LDX + kw + 4];
             mma_bf16(re, ar[0], ar[1], ar[2], ar[3], b0, b1);
@@ -772,23 +815,10 @@ __global__ void __launch_bounds__(FT) k_fno_specx_tc(const float2 *in, const flo
         float re[4] = {}, im[4] = {};
         const int c = 8 * nt + r;
         for (int k0 = 0; k0 < 2 * MX; k0 += 16) {
-            const bool imk = k0 >= MX;
-            const int kx = (imk ? k0 - MX : k0) + q;
-            auto cth = [&](int xx, int kk) { return cs[(fr(kk) * xx) & (n - 1)]; };
-            auto sth = [&](int xx, int kk) { return sn[(fr(kk) * xx) & (n - 1)]; };
             // real rows: cos . Re Y2 - sin . Im Y2;  imaginary rows: sin . Re Y2 + cos . Im Y2
-            uint32_t ar[4], ai[4];
-            if (!imk) {
-                ar[0] = bf2(cth(xa, kx), cth(xa, kx + 1)); ar[1] = bf2(cth(xb, kx), cth(xb, kx + 1));
-                ar[2] = bf2(cth(xa, kx + 8), cth(xa, kx + 9)); ar[3] = bf2(cth(xb, kx + 8), cth(xb, kx + 9));
-                ai[0] = bf2(sth(xa, kx), sth(xa, kx + 1)); ai[1] = bf2(sth(xb, kx), sth(xb, kx + 1));
-                ai[2] = bf2(sth(xa, kx + 8), sth(xa, kx + 9)); ai[3] = bf2(sth(xb, kx + 8), sth(xb, kx + 9));
-            } else {
-                ar[0] = bf2(-sth(xa, kx), -sth(xa, kx + 1)); ar[1] = bf2(-sth(xb, kx), -sth(xb, kx + 1));
-                ar[2] = bf2(-sth(xa, kx + 8), -sth(xa, kx + 9)); ar[3] = bf2(-sth(xb, kx + 8), -sth(xb, kx + 9));
-                ai[0] = bf2(cth(xa, kx), cth(xa, kx + 1)); ai[1] = bf2(cth(xb, kx), cth(xb, kx + 1));
-                ai[2] = bf2(cth(xa, kx + 8), cth(xa, kx + 9)); ai[3] = bf2(cth(xb, kx + 8), cth(xb, kx + 9));
-            }
+            const uint4 *fa = &sx2[(((size_t)xt * S2 + k0 / 16) * 2) * 32 + lane];
+            const uint4 A = __ldg(fa), B = __ldg(fa + 32);
+            const uint32_t ar[4] = {A.x, A.y, A.z, A.w}, ai[4] = {B.x, B.y, B.z, B.w};
             const int kw = (k0 + q) / 2;
             const uint32_t b0 = Yt[c * LDY + kw], b1 = Yt[c * LDY + kw + 4];
             mma_bf16(re, ar[0], ar[1], ar[2], ar[3], b0, b1);
@@ -803,7 +833,7 @@ __global__ void __launch_bounds__(FT) k_fno_specx_tc(const float2 *in, const flo
 }
 
 size_t smem_specx_tc(const Dims &d) {
-    return (size_t)TC_C * (d.n + 4) * 4 + 2 * (size_t)d.MX * TC_C * 8 + (size_t)TC_C * 36 * 4 + 2 * (size_t)d.n * 4;
+    return (size_t)TC_C * (d.n + 4) * 4 + 2 * (size_t)d.MX * TC_C * 8 + (size_t)TC_C * 36 * 4;
 }
 
 // ------------------------------------------------------------- projection
@@ -1095,6 +1125,7 @@ struct qhd_fno {
     float *z = nullptr, *p = nullptr, *lse = nullptr;
     float *dz = nullptr, *dh = nullptr, *dv = nullptr, *da = nullptr;
     float2 *dspec = nullptr, *dwhat = nullptr;
+    uint4 *fr[4] = {};  // A-operand fragment tables of the tensor-core path (k_fno_frags)
     double *part = nullptr, *loss = nullptr;
     float *m = nullptr, *vv = nullptr;
     int64_t launches = 0;
@@ -1180,6 +1211,10 @@ size_t workspace(const qhd_fno_config *c, int64_t B, int train, qhd_fno *f) {
     const size_t o_t = take(spec), o_s = take(spec);
     for (int l = 0; l < c->layers; ++l) o_vh[l] = take(vh);
     const size_t o_z = take(P * sizeof(float)), o_p = take(P * sizeof(float)), o_lse = take(B * sizeof(float));
+    size_t o_fr[4] = {0, 0, 0, 0};
+    const bool frl = c->act_bf16 && tc_layer_ok(d), frs = frl && tc_specx_ok(d);
+    for (int k = 0; k < 4; ++k)
+        if (k < 2 ? frl : frs) o_fr[k] = take(frag_count(d, k) * sizeof(uint4));
     size_t o_dz = 0, o_dh = 0, o_dv = 0, o_da = 0, o_ds = 0, o_dw = 0, o_part = 0, o_loss = 0, o_m = 0, o_vv = 0;
     if (train) {
         o_dz = take(P * sizeof(float));
@@ -1210,6 +1245,7 @@ size_t workspace(const qhd_fno_config *c, int64_t B, int train, qhd_fno *f) {
         f->z = (float *)(w + o_z);
         f->p = (float *)(w + o_p);
         f->lse = (float *)(w + o_lse);
+        for (int k = 0; k < 4; ++k) f->fr[k] = (k < 2 ? frl : frs) ? (uint4 *)(w + o_fr[k]) : nullptr;
         if (train) {
             f->dz = (float *)(w + o_dz);
             f->dh = (float *)(w + o_dh);
@@ -1285,12 +1321,13 @@ qhd_status forward(qhd_fno *f, const double *fx, const float *sigma, int64_t B, 
     for (int l = 0; l < d.L; ++l) {
         const T *vin = (const T *)f->v[l];
         if (f->bf16 && tc_layer_ok(d))
-            k_fno_dfty_tc<T><<<(unsigned)(B * d.n), FT, 0, s>>>(vin, d, 1.f, 1.f, f->tspec);
+            k_fno_dfty_tc<T><<<(unsigned)(B * d.n), FT, 0, s>>>(vin, d, 1.f, 1.f, f->tspec, f->fr[0]);
         else
             k_fno_dfty<T><<<(unsigned)(B * d.n), FT, smem_dfty(d), s>>>(vin, d, 1.f, 1.f, f->tspec);
         if (f->bf16 && tc_specx_ok(d))
             k_fno_specx_tc<false><<<(unsigned)(B * d.M), FT, smem_specx_tc(d), s>>>(
-                f->tspec, reinterpret_cast<const float2 *>(W + f->off_R[l]), d, f->vhat[l], f->sspec);
+                f->tspec, reinterpret_cast<const float2 *>(W + f->off_R[l]), d, f->vhat[l], f->sspec, f->fr[2],
+                f->fr[3]);
         else
             k_fno_specx<false><<<(unsigned)(B * d.M), FT, smem_specx(d), s>>>(
                 f->tspec, reinterpret_cast<const float2 *>(W + f->off_R[l]), d, f->vhat[l], f->sspec);
@@ -1298,7 +1335,7 @@ qhd_status forward(qhd_fno *f, const double *fx, const float *sigma, int64_t B, 
         if (f->bf16 && tc_layer_ok(d))
             k_fno_layer_out_tc<<<(unsigned)(B * d.n), FT, 0, s>>>(
                 f->sspec, (const __nv_bfloat16 *)vin, W + f->off_W[l], W + f->off_b[l], d, act,
-                act ? (__nv_bfloat16 *)f->a[l] : nullptr, (__nv_bfloat16 *)f->v[l + 1]);
+                act ? (__nv_bfloat16 *)f->a[l] : nullptr, (__nv_bfloat16 *)f->v[l + 1], f->fr[1]);
         else
             k_fno_layer_out<T><<<(unsigned)(B * d.n), FT, smem_layer(d), s>>>(
                 f->sspec, vin, W + f->off_W[l], W + f->off_b[l], d, act, act ? (T *)f->a[l] : nullptr,
@@ -1349,19 +1386,21 @@ qhd_status backward(qhd_fno *f, const float *p_true, int64_t B, float *grad, dou
         // spectral path: adjoint of the inverse axis-1 stage, then of the axis-0 stages
         const float inv = 1.f / ((float)d.n * (float)d.n);
         if (f->bf16 && tc_layer_ok(d))
-            k_fno_dfty_tc<float><<<(unsigned)(B * d.n), FT, 0, s>>>(f->da, d, inv, 2.f * inv, f->dspec);
+            k_fno_dfty_tc<float><<<(unsigned)(B * d.n), FT, 0, s>>>(f->da, d, inv, 2.f * inv, f->dspec, f->fr[0]);
         else
             k_fno_dfty<float><<<(unsigned)(B * d.n), FT, smem_dfty(d), s>>>(f->da, d, inv, 2.f * inv, f->dspec);
         if (f->bf16 && tc_specx_ok(d))
             k_fno_specx_tc<true><<<(unsigned)(B * d.M), FT, smem_specx_tc(d), s>>>(
-                f->dspec, reinterpret_cast<const float2 *>(W + f->off_R[l]), d, f->dwhat, f->tspec);
+                f->dspec, reinterpret_cast<const float2 *>(W + f->off_R[l]), d, f->dwhat, f->tspec, f->fr[2],
+                f->fr[3]);
         else
             k_fno_specx<true><<<(unsigned)(B * d.M), FT, smem_specx(d), s>>>(
                 f->dspec, reinterpret_cast<const float2 *>(W + f->off_R[l]), d, f->dwhat, f->tspec);
         k_fno_dR<<<(unsigned)(d.MX * d.M), FT, 2 * d.C * sizeof(float2), s>>>(
             f->dwhat, f->vhat[l], d, reinterpret_cast<float2 *>(grad + f->off_R[l]));
         if (f->bf16 && tc_layer_ok(d))
-            k_fno_layer_in_bwd_tc<<<(unsigned)(B * d.n), FT, 0, s>>>(f->tspec, f->da, W + f->off_W[l], d, f->dv);
+            k_fno_layer_in_bwd_tc<<<(unsigned)(B * d.n), FT, 0, s>>>(f->tspec, f->da, W + f->off_W[l], d, f->dv,
+                                                                      f->fr[1]);
         else
             k_fno_layer_in_bwd<<<(unsigned)(B * d.n), FT, smem_layer(d), s>>>(f->tspec, f->da, W + f->off_W[l], d,
                                                                                f->dv);
@@ -1413,6 +1452,13 @@ qhd_status qhd_fno_create(qhd_fno **out, const qhd_fno_config *cfg, int64_t batc
     workspace(cfg, batch_max, f->train, f);
     if (f->bf16) set_smem_limits<__nv_bfloat16>();
     else set_smem_limits<float>();
+    if (f->fr[0]) {
+        k_fno_frags<<<64, FT, 0, f->stream>>>(f->fr[0], f->fr[1], f->fr[2], f->fr[3], f->d);
+        if (cudaGetLastError() != cudaSuccess) {
+            delete f;
+            return QHD_ERR_CUDA;
+        }
+    }
     if (f->train) {
         if (cudaMemsetAsync(f->m, 0, f->nparam * sizeof(float), f->stream) != cudaSuccess ||
             cudaMemsetAsync(f->vv, 0, f->nparam * sizeof(float), f->stream) != cudaSuccess) {
