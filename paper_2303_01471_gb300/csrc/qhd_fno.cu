@@ -836,6 +836,91 @@ size_t smem_specx_tc(const Dims &d) {
     return (size_t)TC_C * (d.n + 4) * 4 + 2 * (size_t)d.MX * TC_C * 8 + (size_t)TC_C * 36 * 4;
 }
 
+// Weight-gradient partials on the tensor cores (BF16 path, Cc = 32 columns of
+// BF16 activations Y, O a multiple of 16 up to 128 rows of FP32 gradients X):
+//   part[blk][o * 32 + c] = sum_p X[p][o] Y[p][c],  part[blk][O * 32 + o] = sum_p X[p][o]
+// over the block's range of points, as k_fno_wgrad.  Each warp takes 16 points
+// at a time: A = X^T (O x 16, X rounded to BF16), B = Y (16 x 32); the warps'
+// FP32 tiles and the FP32 column sums of X meet in shared memory.
+__global__ void __launch_bounds__(FT) k_fno_wgrad_tc(const float *X, const __nv_bfloat16 *Y, int64_t P, int O,
+                                                     double *part) {
+    __shared__ float Dsum[128 * TC_C], bsum[128];
+    for (int i = threadIdx.x; i < O * TC_C; i += blockDim.x) Dsum[i] = 0.f;
+    for (int i = threadIdx.x; i < O; i += blockDim.x) bsum[i] = 0.f;
+    __syncthreads();
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int r = lane / 4, q = 2 * (lane % 4);
+    const int64_t per_blk = ((P + gridDim.x - 1) / gridDim.x + 15) / 16 * 16;
+    const int64_t p0 = (int64_t)blockIdx.x * per_blk;
+    const int64_t p1 = p0 + per_blk < P ? p0 + per_blk : P;
+    const int MT = O / 16;
+    float acc[8][4][4];
+    float bacc[8][2];
+#pragma unroll
+    for (int mt = 0; mt < 8; ++mt) {
+        bacc[mt][0] = bacc[mt][1] = 0.f;
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[mt][nt][e] = 0.f;
+    }
+    const unsigned short *Yh = reinterpret_cast<const unsigned short *>(Y);
+    for (int64_t t = p0 + 16 * warp; t < p1; t += 16 * (FT / 32)) {
+        // B fragments: rows (points) t + q, t + q + 1 (and + 8), column c = 8 nt + r
+        uint32_t b[4][2];
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt) {
+            const int c = 8 * nt + r;
+            const uint32_t y0 = Yh[(t + q) * TC_C + c], y1 = Yh[(t + q + 1) * TC_C + c];
+            const uint32_t y8 = Yh[(t + q + 8) * TC_C + c], y9 = Yh[(t + q + 9) * TC_C + c];
+            b[nt][0] = y0 | (y1 << 16);
+            b[nt][1] = y8 | (y9 << 16);
+        }
+#pragma unroll
+        for (int mt = 0; mt < 8; ++mt) {
+            if (mt >= MT) break;
+            const int oa = 16 * mt + r, ob = oa + 8;
+            const float xa0 = X[(t + q) * O + oa], xa1 = X[(t + q + 1) * O + oa];
+            const float xb0 = X[(t + q) * O + ob], xb1 = X[(t + q + 1) * O + ob];
+            const float xa8 = X[(t + q + 8) * O + oa], xa9 = X[(t + q + 9) * O + oa];
+            const float xb8 = X[(t + q + 8) * O + ob], xb9 = X[(t + q + 9) * O + ob];
+            bacc[mt][0] += (xa0 + xa1) + (xa8 + xa9);
+            bacc[mt][1] += (xb0 + xb1) + (xb8 + xb9);
+            const uint32_t a0 = bf2(xa0, xa1), a1 = bf2(xb0, xb1), a2 = bf2(xa8, xa9), a3 = bf2(xb8, xb9);
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt) mma_bf16(acc[mt][nt], a0, a1, a2, a3, b[nt][0], b[nt][1]);
+        }
+    }
+#pragma unroll
+    for (int mt = 0; mt < 8; ++mt) {
+        if (mt >= MT) break;
+        const int oa = 16 * mt + r, ob = oa + 8;
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt) {
+            const int c = 8 * nt + q;
+            atomicAdd(&Dsum[oa * TC_C + c], acc[mt][nt][0]);
+            atomicAdd(&Dsum[oa * TC_C + c + 1], acc[mt][nt][1]);
+            atomicAdd(&Dsum[ob * TC_C + c], acc[mt][nt][2]);
+            atomicAdd(&Dsum[ob * TC_C + c + 1], acc[mt][nt][3]);
+        }
+        float s0 = bacc[mt][0], s1 = bacc[mt][1];
+        s0 += __shfl_xor_sync(0xffffffffu, s0, 1);
+        s0 += __shfl_xor_sync(0xffffffffu, s0, 2);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, 1);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, 2);
+        if ((lane & 3) == 0) {
+            atomicAdd(&bsum[oa], s0);
+            atomicAdd(&bsum[ob], s1);
+        }
+    }
+    __syncthreads();
+    double *dst = part + (int64_t)blockIdx.x * (O * TC_C + O);
+    for (int i = threadIdx.x; i < O * TC_C; i += blockDim.x) dst[i] = Dsum[i];
+    for (int i = threadIdx.x; i < O; i += blockDim.x) dst[O * TC_C + i] = bsum[i];
+}
+
+bool tc_wgrad_ok(const Dims &d, int O) { return d.C == TC_C && O % 16 == 0 && O <= 128; }
+
 // ------------------------------------------------------------- projection
 template <typename T>
 __global__ void k_fno_proj(const T *v, const float *W1, const float *b1, const float *W2, const float *b2, Dims d,
@@ -1372,7 +1457,10 @@ qhd_status backward(qhd_fno *f, const float *p_true, int64_t B, float *grad, dou
         k_fno_proj_bwd<T><<<nb, FT, sp, s>>>((const T *)f->v[d.L], f->dz, W + f->off_p1, W + f->off_p1b, W + f->off_p2,
                                               d, f->dh, f->dv, f->part);
     k_fno_reduce<<<1, FT, 0, s>>>(f->part, nb, d.H + 1, grad + f->off_p2);
-    k_fno_wgrad<T><<<nb, FT, 0, s>>>(f->dh, (const T *)f->v[d.L], P, d.H, d.C, f->part);
+    if (f->bf16 && tc_wgrad_ok(d, d.H))
+        k_fno_wgrad_tc<<<nb, FT, 0, s>>>(f->dh, (const __nv_bfloat16 *)f->v[d.L], P, d.H, f->part);
+    else
+        k_fno_wgrad<T><<<nb, FT, 0, s>>>(f->dh, (const T *)f->v[d.L], P, d.H, d.C, f->part);
     k_fno_reduce<<<grid_for((int64_t)d.H * d.C + d.H), FT, 0, s>>>(f->part, nb, d.H * d.C + d.H, grad + f->off_p1);
     f->launches += 5;
     for (int l = d.L - 1; l >= 0; --l) {
@@ -1380,7 +1468,10 @@ qhd_status backward(qhd_fno *f, const float *p_true, int64_t B, float *grad, dou
         k_fno_act_bwd<T><<<grid_for(P * d.C), FT, 0, s>>>(f->dv, act ? (const T *)f->a[l] : nullptr, P * d.C, act,
                                                         f->da);
         // pointwise weights and bias: sum over points of da (x) v_l
-        k_fno_wgrad<T><<<nb, FT, 0, s>>>(f->da, (const T *)f->v[l], P, d.C, d.C, f->part);
+        if (f->bf16 && tc_wgrad_ok(d, d.C))
+            k_fno_wgrad_tc<<<nb, FT, 0, s>>>(f->da, (const __nv_bfloat16 *)f->v[l], P, d.C, f->part);
+        else
+            k_fno_wgrad<T><<<nb, FT, 0, s>>>(f->da, (const T *)f->v[l], P, d.C, d.C, f->part);
         k_fno_reduce<<<grid_for((int64_t)d.C * d.C + d.C), FT, 0, s>>>(f->part, nb, d.C * d.C + d.C,
                                                                       grad + f->off_W[l]);
         // spectral path: adjoint of the inverse axis-1 stage, then of the axis-0 stages
