@@ -69,8 +69,9 @@ constexpr int TC_BFP = 3;              // split of the block-scaled forms (3 and
 constexpr int TC_THREADS = 256;
 constexpr int TC_TR = 64, TC_TC = 32;  // transpose tile: input rows x input columns
 constexpr int TC_FIXED = 10;           // products of the fixed-point form
-// GEMM tile width (columns of C per CTA)
-int tc_bn(int) { return 128; }
+// GEMM tile width (columns of C per CTA) requested: 256 where the 2n columns allow
+// it (the GEMM keeps 128 for per-MMA groups)
+int tc_bn(int n) { return (2 * n) % 256 == 0 ? 256 : 128; }
 
 struct SplitOut {
     __half *a;     // B*n rows of segments of 2n FP16

@@ -48,19 +48,23 @@ constexpr int UG_THREADS = 320;
 constexpr int UG_EPI_WARPS = 8;
 constexpr uint32_t UG_TMEM_COLS = 512;
 
-// One tile width is built: 128 columns.  Its epilogue threads hold 64 FP32
-// accumulators each and the kernel fits 10 warps per SM (each SM sub-partition
-// holds at most 16K registers, so 3 warps of a sub-partition get <= 170 each);
-// a 256-column tile would need 128 accumulators per thread and does not fit.
+// Two tile widths.  128 columns: the epilogue threads hold 64 FP32 accumulators
+// each across groups (each SM sub-partition holds at most 16K registers, so 3
+// warps of a sub-partition get <= 170 each), which the per-MMA groups need.
+// 256 columns (long tensor-memory accumulations only): 128 columns per
+// epilogue thread do not fit in registers, so each finished group is added to
+// C in global memory (read-modify-write, FP32 round-to-nearest, the same
+// arithmetic as the register path); one MMA instruction does twice the work and
+// the operands cost 3/4 of the bytes per flop.
 template <int BN> struct UgCfg {
     static constexpr int NBUF = (int)UG_TMEM_COLS / BN;     // partial buffers in tensor memory
-    static constexpr int STAGES = 6;                        // shared-memory ring
+    static constexpr int STAGES = BN == 256 ? 4 : 6;        // shared-memory ring
     static constexpr int A_BYTES = UG_BM * UG_BK * 2;       // 16 KB
     static constexpr int B_BYTES = BN * UG_BK * 2;
     static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
     static constexpr int COLS = BN / 2;                     // columns per epilogue thread
     static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE_BYTES + 1024;  // alignment + tiles + barriers
-    static_assert(BN == 128, "tile width");
+    static_assert(BN == 128 || BN == 256, "tile width");
     static_assert(A_BYTES % 1024 == 0 && B_BYTES % 1024 == 0, "1024-byte aligned tiles");
 };
 
@@ -216,6 +220,53 @@ __global__ void __launch_bounds__(UG_THREADS, 1)
         const int q = warp & 3;                  // accumulator lanes 32 q .. 32 q + 31 (hardware quarter)
         const int h = ew >> 2;                   // column half
         constexpr int COLS = Cfg::COLS;
+        if constexpr (BN == 256) {
+            GroupWalk w(&a);
+            int grp = 0;
+            bool ok = a.nseg > 0;
+            bool more = ok;
+            const int64_t row = (int64_t)m0 + q * 32 + lane;
+            float *crow = row < a.rows ? a.C + row * a.ldc + n0 + h * COLS : nullptr;
+            while (more && ok) {
+                const float sc = w.scale() * a.alpha;
+                while (!w.ends()) w.next();
+                more = w.next();
+                const int buf = grp % NBUF;
+                int okw = 1;
+                if (lane == 0) okw = umma::mbar_wait(&pfull[buf], (grp / NBUF) & 1, a.err, a.limit_ns) ? 1 : 0;
+                ok = __shfl_sync(0xffffffffu, okw, 0) != 0;
+                if (!ok) break;
+                umma::tc_fence_after();
+                const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BN + h * COLS);
+#pragma unroll 1
+                for (int ch = 0; ch < COLS / 32; ++ch) {
+                    uint32_t r[32];
+                    umma::tmem_ld32(taddr + (uint32_t)(ch * 32), r);
+                    umma::tmem_ld_wait();
+                    if (crow) {
+                        float4 *cp = reinterpret_cast<float4 *>(crow + ch * 32);
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) {
+                            float4 base = make_float4(0.f, 0.f, 0.f, 0.f);
+                            if (grp > 0) {
+                                base = cp[k];
+                            } else if (a.beta != 0.f) {
+                                const float4 old = cp[k];
+                                base = make_float4(old.x * a.beta, old.y * a.beta, old.z * a.beta, old.w * a.beta);
+                            }
+                            cp[k] = make_float4(fmaf(__uint_as_float(r[4 * k]), sc, base.x),
+                                                fmaf(__uint_as_float(r[4 * k + 1]), sc, base.y),
+                                                fmaf(__uint_as_float(r[4 * k + 2]), sc, base.z),
+                                                fmaf(__uint_as_float(r[4 * k + 3]), sc, base.w));
+                        }
+                    }
+                }
+                umma::tc_fence_before();
+                __syncwarp();
+                if (lane == 0) umma::mbar_arrive(&pempty[buf]);
+                ++grp;
+            }
+        } else {
         float2 acc[COLS / 2];
 #pragma unroll
         for (int k = 0; k < COLS / 2; ++k) acc[k] = make_float2(0.f, 0.f);
@@ -278,6 +329,7 @@ __global__ void __launch_bounds__(UG_THREADS, 1)
                 (void)be;
                 *reinterpret_cast<float4 *>(crow + 4 * k) = make_float4(lo.x, lo.y, hi.x, hi.y);
             }
+        }
         }
     }
     umma::tc_fence_before();
@@ -358,20 +410,24 @@ cudaError_t launch_bn(const __half *A, int64_t lda, const __half *B, int64_t ldb
 }  // namespace
 
 bool umma_gemm_shape_ok(int64_t rows, int64_t n_cols, int64_t lda, int64_t ldb, int bn) {
-    return bn == 128 && rows > 0 && n_cols > 0 && n_cols % bn == 0 && lda % UG_BK == 0 && ldb % UG_BK == 0 &&
-           (rows + UG_BM - 1) / UG_BM <= (int64_t(1) << 20);
+    return (bn == 128 || bn == 256) && rows > 0 && n_cols > 0 && n_cols % bn == 0 && lda % UG_BK == 0 &&
+           ldb % UG_BK == 0 && (rows + UG_BM - 1) / UG_BM <= (int64_t(1) << 20);
 }
 
 cudaError_t umma_gemm(const __half *A, int64_t lda, const __half *B, int64_t ldb, float *C, int64_t ldc, int64_t rows,
                       int64_t n_cols, const UgSeg *segs, int nseg, float alpha, float beta, int bn, unsigned *err,
                       cudaStream_t s, const int8_t *expo, int64_t expo_ld) {
     if (!umma_gemm_shape_ok(rows, n_cols, lda, ldb, bn) || nseg < 1 || nseg > UG_MAX_SEG) return cudaErrorInvalidValue;
+    // 256-column tiles when every group is a long tensor-memory accumulation
+    bool long_groups = true;
+    for (int i = 0; i < nseg; ++i) long_groups = long_groups && (segs[i].mode == UG_OPEN || segs[i].mode == UG_CONTINUE);
+    const int tile = (bn == 256 && long_groups && n_cols % 256 == 0) ? 256 : 128;
     UgArgs a{};
     a.C = C;
     a.ldc = ldc;
     a.rows = rows;
     a.m_tiles = (int)((rows + UG_BM - 1) / UG_BM);
-    a.n_tiles = (int)(n_cols / bn);
+    a.n_tiles = (int)(n_cols / tile);
     a.nseg = nseg;
     for (int i = 0; i < nseg; ++i) {
         const UgSeg &g = segs[i];
@@ -402,7 +458,7 @@ cudaError_t umma_gemm(const __half *A, int64_t lda, const __half *B, int64_t ldb
     a.kappa = every ? (float)(5.9604644775390625e-08 / (2.0 * 0.6931471805599453)) : 0.f;
     a.err = err;
     a.limit_ns = 2000000000ull;  // 2 s of global time per wait
-    return launch_bn<128>(A, lda, B, ldb, n_cols, a, s);
+    return tile == 256 ? launch_bn<256>(A, lda, B, ldb, n_cols, a, s) : launch_bn<128>(A, lda, B, ldb, n_cols, a, s);
 }
 
 }  // namespace qhd
@@ -424,7 +480,8 @@ extern "C" qhd_status qhd_tc_gemm_f16(const void *A_dev, const void *B_dev, floa
     const int mode = group_every_mma == 0 ? (int)UG_OPEN : group_every_mma == 1 ? (int)UG_EACH_MMA : (int)UG_EACH_MMA_FLOAT;
     UgSeg seg{0, 0, (int)(k / 64), 1.f, mode};
     cudaError_t e = umma_gemm(reinterpret_cast<const __half *>(A_dev), k, reinterpret_cast<const __half *>(B_dev), k,
-                              C_dev, ldc, rows, n_cols, &seg, 1, alpha, beta, 128, err_dev, (cudaStream_t)stream);
+                              C_dev, ldc, rows, n_cols, &seg, 1, alpha, beta, n_cols % 256 == 0 ? 256 : 128, err_dev,
+                              (cudaStream_t)stream);
     snprintf(g_gemm_err, sizeof g_gemm_err, "%s%s%s", e == cudaSuccess ? "" : cudaGetErrorString(e),
              e == cudaSuccess ? "" : " | ", e == cudaSuccess ? "" : g_launch_diag);
     return e == cudaSuccess ? QHD_OK : (e == cudaErrorInvalidValue ? QHD_ERR_INVALID_ARG : QHD_ERR_CUDA);

@@ -16,7 +16,9 @@ def ref64(A, B):
     return A.double().cpu().numpy() @ B.double().cpu().numpy().T
 
 
-@pytest.mark.parametrize("shape", [(128, 128, 64), (256, 256, 128), (384, 512, 1024), (192, 128, 128), (1, 128, 64)])
+# one accumulation with 256 columns (or a multiple) runs the 256-wide tile, everything else the 128-wide one
+@pytest.mark.parametrize("shape", [(128, 128, 64), (256, 256, 128), (384, 512, 1024), (192, 128, 128), (1, 128, 64),
+                                   (200, 768, 192)])
 @pytest.mark.parametrize("every", [True, False])
 def test_exact_integer_products(shape, every):
     rows, n, k = shape
@@ -84,13 +86,14 @@ def test_fp16_products_and_accumulation_bias():
     assert abs(bias_fl) <= abs(bias_rn) / 4, res
 
 
-def test_alpha_beta():
+@pytest.mark.parametrize("every", [True, False])   # per-MMA groups: 128-wide tiles; one accumulation: 256-wide
+def test_alpha_beta(every):
     rows, n, k = 256, 256, 256
     g = torch.Generator(device="cuda").manual_seed(3)
     A = torch.randint(-4, 5, (rows, k), device="cuda", generator=g).half()
     B = torch.randint(-4, 5, (n, k), device="cuda", generator=g).half()
     C0 = torch.randint(-100, 101, (rows, n), device="cuda", generator=g).float()
-    C, err = qhd.tc_gemm_f16(A, B, C=C0.clone(), alpha=0.5, beta=2.0)
+    C, err = qhd.tc_gemm_f16(A, B, C=C0.clone(), every_mma=every, alpha=0.5, beta=2.0)
     torch.cuda.synchronize()
     assert int(err[0]) == 0
     assert np.array_equal(C.double().cpu().numpy(), 0.5 * ref64(A, B) + 2.0 * C0.double().cpu().numpy())
