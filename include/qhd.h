@@ -588,7 +588,8 @@ qhd_status qhd_group_destroy(qhd_group *g);
  * operands: each MMA truncates its exact sum towards zero to FP32, losing on
  * average the fraction kappa = 2^-24 / (2 ln 2) of it, and the result is scaled
  * by (1 + kappa) to undo that expected loss; 0: one accumulation over all of K
- * in tensor memory (the hardware's accumulation).  Requirements: rows >= 1,
+ * in tensor memory (the hardware's accumulation; 128 x 256 tiles when n_cols
+ * is a multiple of 256, each finished tile added to C in place).  Requirements: rows >= 1,
  * n_cols a multiple of 128, k of 64, k <= 2^20, ldc >= n_cols and a
  * multiple of 4, 16-byte aligned pointers.  err_dev: 2 device words, zero on
  * entry; word 0 becomes 1 if a bounded wait gave up (~2 s).  Enqueued on

@@ -277,7 +277,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_absmax(const float *in, int n
 }
 
 // Product buffer (natural layout) -> psi, with the final potential phase.
-// Floating form: a fixed scale; fixed-point form: 2^E per instance.
+// Block-scaled forms: a fixed scale (1); fixed-point form: 2^E per instance.
 __global__ void __launch_bounds__(TC_THREADS) k_tc_finish(const float *cbuf, TcPhaseArgs a, int n, int64_t rows,
                                                          float scale, const int *e, int phase) {
     __shared__ float4 ptab[PHASE_TAB];
@@ -323,11 +323,11 @@ int64_t tc_pitch(int segs, size_t m) { return (int64_t)segs * (int64_t)m + 64; }
 }  // namespace
 
 struct TcState {
-    int n = 0, products = 5, h = 0, l = 0;
+    int n = 0, products = 3, l = 0;
     int64_t batch = 0;
     unsigned *err = nullptr;            // GEMM wait time-out word (2 words)
-    __half *w[2] = {nullptr, nullptr};  // forward, inverse DFT matrix, stored transposed [2n][K]: K-major
-    __half *a = nullptr;                // B*n rows of split operands
+    __half *w[2] = {nullptr, nullptr};  // forward, inverse DFT matrix, stored transposed [2n][pitch]: K-major
+    __half *a = nullptr;                // B*n rows of split operands (padded pitch, tc_pitch)
     float *c = nullptr;                 // B*n x 2n products
     unsigned *maxbits = nullptr;        // fixed form: 2 x B max |z|^2 buffers
     int *e = nullptr;                   // fixed form: B exponents
@@ -385,7 +385,6 @@ TcState *tc_create(int n, int64_t batch, int products, void *ws, size_t ws_bytes
     t->batch = batch;
     t->products = products;
     t->l = log2i(n);
-    t->h = (t->l + 1) / 2;
     const size_t m = 2 * (size_t)n, rows = (size_t)batch * (size_t)n;
     const size_t wseg = (size_t)w_segments(products);
     char *p = (char *)ws;
@@ -545,9 +544,9 @@ cudaError_t tc_split_transpose(TcState *t, cudaStream_t s, int64_t *launches) {
 }
 
 // One axis transform: C[rows][2n] = products of the split rows with the block
-// DFT matrix.  Floating forms: every K = 16 MMA its own accumulation group,
-// alpha = 2^-h.  Fixed form: level L = segments (a_i, w_(L-i)), i = 0..L, one
-// exact group scaled by 2^-7L.
+// DFT matrix.  Block-scaled forms: every K = 16 MMA its own exact group, scaled
+// by the row's block exponent.  Fixed form: level L = segments (a_i, w_(L-i)),
+// i = 0..L, one exact group scaled by 2^-7L.
 cudaError_t tc_gemm(TcState *t, bool inverse, cudaStream_t s, int64_t *launches) {
     const int m = 2 * t->n;
     const int kb = m / 64;

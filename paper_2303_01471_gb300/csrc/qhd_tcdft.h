@@ -67,7 +67,7 @@ struct TcPhaseArgs {
 };
 
 bool tc_supported(int n0, int n1, int64_t batch);
-// products: 3 or 5 (floating FP16 hi/lo operands), 10 (fixed-point slices, n <= 512)
+// products: 3 or 5 (block-scaled FP16 hi/lo integer slices), 10 (fixed-point slices, n <= 512)
 bool tc_products_ok(int n, int products);
 size_t tc_workspace_bytes(int n, int64_t batch, int products);
 // Returns nullptr with *why set when the workspace is short or a CUDA call fails.
