@@ -553,7 +553,8 @@ def fp32_peak_flops():
 
 def c1_plain(args, dev, rank):
     """C1: one 128^2 Gaussian-well instance (K=8) at a time, T=10, dt=0.01 (1000
-    Strang steps), seeds 0..9: the whole run is one launch of one cluster (4 CTAs).
+    Strang steps), seeds 0..9: the whole run is one launch of one cluster (8 CTAs:
+    a lone instance takes the wide split).
     Device-timed per seed (set f on the device, reset, evolve, observables),
     median reported, parity of each seed against the FP64 oracle."""
     import torch
@@ -583,11 +584,11 @@ def c1_plain(args, dev, rank):
             parity.append({"seed": 1000 * rank + seeds[k], "tv": float(0.5 * np.abs(p - ob.prob).sum()),
                            "ef_rel": abs(obs.e_f - ob.e_f) / max(abs(ob.e_f), 1e-3 * np.ptp(inst.f)),
                            "norm_drift": obs.norm - 1.0})
+    sms_used = sim.cluster_ctas()
     sim.close()
     med = statistics.median(ms)
     pts = n * n * nsteps
     flops = pts * FLOP_PER_POINT_STEP_2D[n]
-    sms_used = qhd_plane_cluster(n)
     peak_sms = fp32_peak_flops() * sms_used / torch.cuda.get_device_properties(dev).multi_processor_count
     return {"workload": "128^2 Gaussian wells (K=8), T=10, dt=0.01 (1000 Strang steps), one instance per run, "
                         "seeds 0..9 (median)",
@@ -601,10 +602,6 @@ def c1_plain(args, dev, rank):
                          "algorithmic_flop_per_point_step": FLOP_PER_POINT_STEP_2D[n]},
             "timing": "CUDA events on the context's stream, median of 5 runs per seed after a warm-up",
             "clocks": clk.summary()}
-
-
-def qhd_plane_cluster(n):
-    return {32: 2, 64: 2, 128: 4, 256: 8}[n]
 
 
 RAGGED_WORKLOAD = ("Batched QHD: 4096 instances, 2048 x 128^2 + 2048 x 256^2 on [0,1]^2, families alternating "

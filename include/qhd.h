@@ -247,6 +247,15 @@ qhd_status qhd_set_transform(qhd_ctx *ctx, int transform, int products, void *tc
  * tensor-core transform runs on this library's own GEMM kernel. */
 int64_t qhd_library_call_count(const qhd_ctx *ctx);
 
+/* CTAs per instance (2-D grids held in one thread-block cluster for a whole
+ * chunk of steps) or per plane (3-D plane passes) of the cluster engine; 0 for
+ * the generic passes or a NULL context.  For 2-D grids whose axis 0 has 64 or
+ * 128 points, a batch with at most (SM count / wide split) instances runs on
+ * twice the default CTAs per instance (4 for 64, 8 for 128: half the rows per
+ * CTA), fixed at qhd_init_grid.  A batched group (qhd_group_*) uses the same
+ * split by default. */
+int qhd_cluster_ctas(const qhd_ctx *ctx);
+
 /*
  * Observables of every instance: out_host[batch] receives qhd_obs; prob_dev
  * (optional, NULL to skip) receives |psi|^2 as float32, batch*G values.

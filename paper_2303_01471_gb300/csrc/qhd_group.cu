@@ -338,7 +338,8 @@ qhd_status qhd_group_create(qhd_group **out, qhd_ctx *const *ctxs, int n_ctx, co
             return QHD_ERR_INVALID_ARG;
         }
         const int idx = v.n[0] == 64 ? 0 : v.n[0] == 128 ? 1 : 2;
-        const int sub = c.sub_cluster[idx] ? c.sub_cluster[idx] : default_sub(v.n[0]);
+        // default: the context's own split, so the group runs its arithmetic
+        const int sub = c.sub_cluster[idx] ? c.sub_cluster[idx] : (v.plane_c ? v.plane_c : default_sub(v.n[0]));
         if (!sub_ok(v.n[0], sub)) {
             delete g;
             return QHD_ERR_INVALID_ARG;

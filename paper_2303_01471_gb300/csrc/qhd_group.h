@@ -30,6 +30,7 @@ struct GroupCtxView {
     int64_t steps_done;
     cudaStream_t stream;
     bool whole_run;          // 2-D grid held in one cluster per instance (FFT transform)
+    int plane_c;             // CTAs per instance of the context's own whole-run launch (0: none)
 };
 
 // Fills v; QHD_ERR_STATE without a potential and a schedule.

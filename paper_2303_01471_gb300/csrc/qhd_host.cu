@@ -127,6 +127,7 @@ struct qhd_ctx {
     float4 *twx = nullptr;  // exchange twiddles of the cluster-distributed axis
     float4 *ptab = nullptr; // potential phase table exp(-2 pi i (k + 1/2) / PHASE_TAB), hi/lo
     int plane_mode = 0;     // 0 generic passes, 2 whole-run 2-D clusters, 3 3-D plane pass
+    int plane_c = 0;        // CTAs per instance (2-D) or per plane (3-D) of the cluster engine
     double *coord = nullptr;
     double *obs_part = nullptr, *obs_res = nullptr;
     MinMaxPart *mm = nullptr;
@@ -281,6 +282,10 @@ const char *qhd_last_error(const qhd_ctx *c) { return c ? c->err.c_str() : ""; }
 
 int64_t qhd_launch_count(const qhd_ctx *c) { return c ? c->launches : 0; }
 
+int qhd_cluster_ctas(const qhd_ctx *c) {
+    return c && (c->plane_mode == 2 || c->plane_mode == 3) ? c->plane_c : 0;
+}
+
 size_t qhd_workspace_bytes(int ndim, const int64_t *n, int64_t batch) {
     if (!shape_ok(ndim, n, batch)) return 0;
     return make_layout(ndim, n, batch).total;
@@ -352,14 +357,23 @@ qhd_status qhd_init_grid(qhd_ctx **out, int ndim, const int64_t *n, const double
     if (ndim == 2 && plane_supported((int)n[0], (int)n[1])) {
         c->plane_mode = 2;
         dist_axis = 0;
+        c->plane_c = plane_cluster((int)n[0]);
+        // a batch that leaves most SMs idle runs each instance on twice the CTAs
+        int dev = 0, sms = 0;
+        const int wide = plane_cluster_wide((int)n[0]);
+        if (wide && cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+            batch * (int64_t)wide <= (int64_t)sms)
+            c->plane_c = wide;
     }
     else if (ndim == 3 && plane_supported((int)n[1], (int)n[2])) {
         c->plane_mode = 3;
         dist_axis = 1;
+        c->plane_c = plane_cluster((int)n[1]);
     }
     std::vector<float4> twx((size_t)c->ksum, make_float4(0.f, 0.f, 0.f, 0.f));
     if (dist_axis >= 0) {
-        const int n1 = (int)n[dist_axis], cc = plane_cluster(n1), rr = n1 / cc;
+        const int n1 = (int)n[dist_axis], cc = c->plane_c, rr = n1 / cc;
         for (int q = 0; q < cc; ++q)
             for (int j = 0; j < rr; ++j) {
                 const double ang = 2.0 * 3.141592653589793238462643383279502884 * (double)(((int64_t)j * q) % n1) /
@@ -686,7 +700,10 @@ qhd_status qhd_evolve(qhd_ctx *c, double T, double dt) {
             w.ptab = c->ptab;
             w.kt_batch = ktb;
             TimedScope ts(c, QHD_KCLASS_WHOLE, true);
-            QHD_LAUNCH(c, launch_plane_whole((int)c->n[0], (int)c->n[1], w, c->stream));
+            if (c->plane_c == plane_cluster((int)c->n[0]))
+                QHD_LAUNCH(c, launch_plane_whole((int)c->n[0], (int)c->n[1], w, c->stream));
+            else
+                QHD_LAUNCH(c, launch_plane_whole_wide((int)c->n[0], (int)c->n[1], w, c->stream));
             continue;
         }
         const int last_ax = ndim - 1;
@@ -1049,6 +1066,7 @@ qhd_status ctx_group_view(qhd_ctx *c, GroupCtxView *v) {
     v->steps_done = c->steps_done;
     v->stream = c->stream;
     v->whole_run = c->plane_mode == 2 && c->tc == nullptr;
+    v->plane_c = c->plane_mode == 2 ? c->plane_c : 0;
     return QHD_OK;
 }
 

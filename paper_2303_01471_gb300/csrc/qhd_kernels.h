@@ -146,6 +146,9 @@ cudaError_t launch_plane_pass(int n1, int n2, const PlaneArgs &a, cudaStream_t s
 cudaError_t launch_plane_whole(int n1, int n2, const PlaneArgs &a, cudaStream_t s);
 bool plane_supported(int n1, int n2);
 int plane_cluster(int n1);
+// Whole-run kernel with twice the CTAs per instance (distributed axis 64 or 128; 0: none).
+int plane_cluster_wide(int n1);
+cudaError_t launch_plane_whole_wide(int n1, int n2, const PlaneArgs &a, cudaStream_t s);
 
 // Plans shared with the host (twiddle tables are built on the host).
 void plan_of(int n, int *r1, int *r2);

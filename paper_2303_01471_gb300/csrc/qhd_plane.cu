@@ -59,8 +59,10 @@ __global__ void __launch_bounds__(PLANE_THREADS, plane_min_blocks<N1, N2, C>()) 
     plane_copy<N1, N2, C, false>(tile, g);
 }
 
-template <int N1, int N2, int C>
-__global__ void __launch_bounds__(PLANE_THREADS, 2) k_plane_whole(PlaneArgs a) {
+// MINB: CTAs per SM the kernel is compiled for (2 for batches; 1 for the wide
+// split, which runs only when every CTA has an SM of its own).
+template <int N1, int N2, int C, int MINB>
+__global__ void __launch_bounds__(PLANE_THREADS, MINB) k_plane_whole(PlaneArgs a) {
     extern __shared__ __align__(16) float4 smem4[];
     float4 *ptab = smem4;
     float2 *tile = reinterpret_cast<float2 *>(smem4 + PHASE_TAB);
@@ -104,10 +106,10 @@ static cudaError_t plane_pass_impl(const PlaneArgs &a, cudaStream_t s) {
     return launch_cluster(k_plane_pass<N1, N2, C>, a.planes, C, PlaneCfg<N1, N2, C>::SMEM, a, s, attr_done);
 }
 
-template <int N1, int N2, int C>
+template <int N1, int N2, int C, int MINB = 2>
 static cudaError_t plane_whole_impl(const PlaneArgs &a, cudaStream_t s) {
     static bool attr_done = false;
-    return launch_cluster(k_plane_whole<N1, N2, C>, a.batch, C, PlaneCfg<N1, N2, C>::SMEM, a, s, attr_done);
+    return launch_cluster(k_plane_whole<N1, N2, C, MINB>, a.batch, C, PlaneCfg<N1, N2, C>::SMEM, a, s, attr_done);
 }
 
 // Cluster size per distributed-axis length: R = 32 rows per CTA (16 for 32).
@@ -146,6 +148,27 @@ cudaError_t launch_plane_pass(int n1, int n2, const PlaneArgs &a, cudaStream_t s
 
 cudaError_t launch_plane_whole(int n1, int n2, const PlaneArgs &a, cudaStream_t s) {
     QHD_PLANE_DISPATCH(plane_whole_impl)
+}
+
+// The whole-run kernel with twice the CTAs per instance (half the rows each) for
+// distributed axes of 64 and 128: a batch too small to fill the GPU then runs on
+// twice the SMs.
+__host__ __device__ constexpr int plane_c_wide(int n1) { return n1 == 128 ? 8 : n1 == 64 ? 4 : 0; }
+
+int plane_cluster_wide(int n1) { return plane_c_wide(n1); }
+
+cudaError_t launch_plane_whole_wide(int n1, int n2, const PlaneArgs &a, cudaStream_t s) {
+    switch (n1 * 1000 + n2) {
+    case 64032: return plane_whole_impl<64, 32, plane_c_wide(64), 1>(a, s);
+    case 64064: return plane_whole_impl<64, 64, plane_c_wide(64), 1>(a, s);
+    case 64128: return plane_whole_impl<64, 128, plane_c_wide(64), 1>(a, s);
+    case 64256: return plane_whole_impl<64, 256, plane_c_wide(64), 1>(a, s);
+    case 128032: return plane_whole_impl<128, 32, plane_c_wide(128), 1>(a, s);
+    case 128064: return plane_whole_impl<128, 64, plane_c_wide(128), 1>(a, s);
+    case 128128: return plane_whole_impl<128, 128, plane_c_wide(128), 1>(a, s);
+    case 128256: return plane_whole_impl<128, 256, plane_c_wide(128), 1>(a, s);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace qhd

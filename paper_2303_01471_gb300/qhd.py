@@ -35,7 +35,7 @@ EXPORTS = ["qhd_workspace_bytes", "qhd_init_grid", "qhd_set_potential", "qhd_set
            "qhd_observables", "qhd_launch_count", "qhd_timing_enable", "qhd_timing_read",
            "qhd_destroy", "qhd_status_string", "qhd_last_error", "qhd_observables_static",
            "qhd_set_splitting", "qhd_evolve_trajectory", "qhd_tc_workspace_bytes", "qhd_set_transform",
-           "qhd_library_call_count", "qhd_set_kinetic", "qhd_spectrum_workspace_bytes",
+           "qhd_library_call_count", "qhd_cluster_ctas", "qhd_set_kinetic", "qhd_spectrum_workspace_bytes",
            "qhd_apply_hamiltonian", "qhd_lowest_eigenpairs", "qhd_fno_param_count", "qhd_fno_workspace_bytes", "qhd_fno_create",
            "qhd_fno_forward", "qhd_fno_loss_grad", "qhd_fno_adam_step", "qhd_fno_launch_count",
            "qhd_fno_last_error", "qhd_fno_destroy", "qhd_lattice_workspace_bytes", "qhd_lattice_init",
@@ -165,6 +165,8 @@ def load(build_if_missing: bool = True):
     lib.qhd_set_transform.restype = st
     lib.qhd_library_call_count.argtypes = [vp]
     lib.qhd_library_call_count.restype = ctypes.c_int64
+    lib.qhd_cluster_ctas.argtypes = [vp]
+    lib.qhd_cluster_ctas.restype = ctypes.c_int
     lib.qhd_group_workspace_bytes.argtypes = [ctypes.c_int]
     lib.qhd_group_workspace_bytes.restype = ctypes.c_size_t
     lib.qhd_group_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.c_int,
@@ -370,6 +372,10 @@ class QHD:
 
     def library_call_count(self) -> int:
         return int(self.lib.qhd_library_call_count(self.ctx))
+
+    def cluster_ctas(self) -> int:
+        """CTAs per instance (2-D) or per plane (3-D) of the cluster engine, 0 if unused."""
+        return int(self.lib.qhd_cluster_ctas(self.ctx))
 
     def set_kinetic(self, kind: int) -> None:
         """KINETIC_SPECTRAL (default) or KINETIC_FD2 (central second difference of

@@ -35,7 +35,7 @@ def make_ctx(n, seeds, stream=None):
 
 
 def test_group_matches_each_context_bit_for_bit():
-    a, _, _ = make_ctx(128, [0, 1, 2])          # odd: one cluster item runs half idle
+    a, _, _ = make_ctx(128, [0, 1, 2])          # a small batch: each context keeps its wide 8-CTA split
     b, _, _ = make_ctx(256, [10, 11])
     ref_a, _, _ = make_ctx(128, [0, 1, 2])
     ref_b, _, _ = make_ctx(256, [10, 11])
@@ -49,7 +49,9 @@ def test_group_matches_each_context_bit_for_bit():
     assert torch.equal(b.psi, ref_b.psi)
     assert a.time() == ref_a.time() and b.time() == ref_b.time()
     info = grp.info()
-    assert info["launches"] == 1 and info["captures"] == 1 and info["sub"][128] == 4 and info["sub"][256] == 8
+    # default split: each context's own (a small batch of 128^2 takes the wide 8-CTA split)
+    assert a.cluster_ctas() == 8 and b.cluster_ctas() == 8
+    assert info["launches"] == 1 and info["captures"] == 1 and info["sub"][128] == 8 and info["sub"][256] == 8
     grp.close()
     for s in (a, b, ref_a, ref_b):
         s.close()

@@ -140,6 +140,29 @@ def test_parity_batched_3d_axis_passes():
             compare(psi[b], obs[b], inst.f, psi_o, steps=20)
 
 
+@pytest.mark.parametrize("n", [64, 128])
+def test_wide_and_default_cluster_splits_match_oracle(n):
+    """A lone instance runs on twice the default CTAs per instance (4 for 64^2, 8 for
+    128^2); a batch too large for that keeps the default split.  Both against the
+    oracle on the same instance."""
+    inst = workloads.gaussian_wells(41, (n, n), K=8)
+    psi_o = oracle.evolve(inst.f, oracle.uniform_state((n, n)), 0.0, 0.01, 100, oracle.Schedule())
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    wide = {64: 4, 128: 8}[n]
+    for batch, ctas in ((1, wide), (sms // wide + 1, wide // 2)):
+        sim = qhd.QHD((n, n), batch=batch)
+        sim.set_potential(np.broadcast_to(inst.f, (batch, n, n)).copy())
+        sim.set_schedule(qhd.Schedule())
+        sim.reset_state()
+        sim.evolve(1.0, 0.01)
+        assert sim.cluster_ctas() == ctas, (batch, sim.cluster_ctas())
+        obs = sim.observables(0.1)
+        psi = sim.psi.cpu().numpy().astype(np.complex128)
+        sim.close()
+        compare(psi[0], obs[0], inst.f, psi_o, steps=100)
+        assert np.array_equal(psi[-1], psi[0])   # every instance of the batch is the same run
+
+
 def test_parity_nonunit_box_and_table_schedule():
     shape = (64, 32)
     lo, hi = (-2.0, -1.0), (3.0, 1.5)
