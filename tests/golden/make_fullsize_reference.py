@@ -7,8 +7,9 @@ workload (10^4 Strang steps, T = 10, dt = 1e-3, the paper's schedule):
 This calls only the oracle and the seeded input generator.  For each instance it
 stores, in tests/golden/fullsize_<name>.npz: the observables (norm, E[f], P_succ,
 x*), the probability mass p = |psi|^2 on the smallest set of mesh points that
-holds all but MASS_LEFT of it, at most KEEP_MAX points (flat indices and FP64
-values, largest first), and the mass outside that set.  A test then bounds the total-variation distance of
+holds all but MASS_LEFT of it, at most keep_max points per case (flat indices and
+FP64 values, largest first), the mass outside that set, and the mass outside the
+top 2^k points for k = 10..24.  A test then bounds the total-variation distance of
 any other p from above without the full array:
   TV <= 1/2 [ sum_{i in S} |p_i - q_i| + (mass of p outside S) + (mass of q outside S) ].
 
@@ -38,10 +39,11 @@ import workloads  # noqa: E402
 T_END, DT = 10.0, 1e-3
 NSTEPS = 10000
 MASS_LEFT = 1e-7
-KEEP_MAX = 32768   # at most this many points per file (the rest is stored as one mass)
+# at most this many points per file (the rest is stored as one mass): the 2-D state
+# is concentrated, the 3-D one is spread over a ball of ~10^5 points and a long tail
 CASES = {
-    "1024sq_rastrigin": dict(family="rastrigin", seed=0, shape=(1024, 1024), kw={}),
-    "256cube_wells": dict(family="wells", seed=1, shape=(256, 256, 256), kw={"K": 32}),
+    "1024sq_rastrigin": dict(family="rastrigin", seed=0, shape=(1024, 1024), kw={}, keep_max=32768),
+    "256cube_wells": dict(family="wells", seed=1, shape=(256, 256, 256), kw={"K": 32}, keep_max=262144),
 }
 
 
@@ -70,13 +72,16 @@ def make(name: str) -> str:
     p = ob.prob.ravel()
     order = np.argsort(p)[::-1]
     cum = np.cumsum(p[order])
-    keep = min(int(np.searchsorted(cum, cum[-1] - MASS_LEFT)) + 1, KEEP_MAX)
-    idx = order[:keep].astype(np.int64)
+    keep = min(int(np.searchsorted(cum, cum[-1] - MASS_LEFT)) + 1, c["keep_max"])
+    idx = order[:keep].astype(np.int64 if p.size >= 2 ** 31 else np.int32)
+    # mass outside the top 2^k points, for k = 10 .. 24 (how spread the state is)
+    profile = np.array([[2 ** k, float(cum[-1] - cum[min(2 ** k, p.size) - 1])] for k in range(10, 25)
+                        if 2 ** k <= p.size])
     out = path_of(name)
     np.savez_compressed(out, key=case_key(name), norm=ob.norm, e_f=ob.e_f, p_succ=ob.p_succ,
                         x_star=np.asarray(ob.x_star, dtype=np.float64), idx=idx, p=p[idx],
                         mass_outside=float(p.sum() - p[idx].sum()), f_ptp=float(np.ptp(inst.f)),
-                        seconds=time.time() - t0, threads=oracle.max_threads())
+                        mass_profile=profile, seconds=time.time() - t0, threads=oracle.max_threads())
     return out
 
 
