@@ -68,31 +68,39 @@ template <int BN> struct UgCfg {
     static_assert(A_BYTES % 1024 == 0 && B_BYTES % 1024 == 0, "1024-byte aligned tiles");
 };
 
-// Walks the MMAs of the K list in order and reports group boundaries for the
-// epilogue threads (the MMA thread decides the same boundaries per segment).
-struct GroupWalk {
-    const UgArgs *a;
-    int seg = 0, kb = 0, i = 0;  // segment, K block inside it, MMA inside the K block
-    __device__ explicit GroupWalk(const UgArgs *args) : a(args) {}
-    __device__ bool ends() const {
-        const UgSeg &s = a->seg[seg];
-        if (s.mode == UG_EACH_MMA || s.mode == UG_EACH_MMA_FLOAT || s.mode == UG_EACH_MMA_BEXP) return true;
-        if (kb != s.kblocks - 1 || i != 3) return false;
-        return seg + 1 >= a->nseg || a->seg[seg + 1].mode != UG_CONTINUE;
+// Visits the accumulation groups of the K list in order with their scales,
+// deciding the boundaries per segment in registers (the MMA thread's walk):
+// every MMA of a per-MMA segment is a group (scaled, for the block-scaled mode,
+// by this row's exponent of the MMA's 16 K values, 1 past the last row), and a
+// run of UG_OPEN + UG_CONTINUE segments is one group with the opening
+// segment's scale.  f(scale) handles one group; false stops the walk.
+template <typename F>
+__device__ __forceinline__ bool for_each_group(const UgArgs &a, const int8_t *erp, F &&f) {
+    float open_scale = 1.f;
+    for (int sg = 0; sg < a.nseg; ++sg) {
+        const int mode = a.seg[sg].mode, kbs = a.seg[sg].kblocks;
+        const float scale = a.seg[sg].scale;
+        if (mode == UG_EACH_MMA || mode == UG_EACH_MMA_FLOAT || mode == UG_EACH_MMA_BEXP) {
+            const bool bexp = mode == UG_EACH_MMA_BEXP;
+            const int e0 = a.seg[sg].e0;
+            for (int kb = 0; kb < kbs; ++kb) {
+                // the four MMAs' exponents of this K block in one load (0 past the last row)
+                const uint32_t e4 = bexp && erp ? __ldg(reinterpret_cast<const uint32_t *>(erp + e0 + kb * 4)) : 0u;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    float sc = scale;
+                    if (bexp) sc *= __int_as_float(((int)(int8_t)(e4 >> (8 * i)) + 127) << 23);
+                    if (!f(sc)) return false;
+                }
+            }
+        } else {
+            if (mode == UG_OPEN) open_scale = scale;
+            const bool closes = sg + 1 >= a.nseg || a.seg[sg + 1].mode != UG_CONTINUE;
+            if (closes && !f(open_scale)) return false;
+        }
     }
-    __device__ float scale() const {
-        int s = seg;
-        while (a->seg[s].mode == UG_CONTINUE && s > 0) --s;
-        return a->seg[s].scale;
-    }
-    __device__ bool next() {  // false past the end
-        if (++i < 4) return true;
-        i = 0;
-        if (++kb < a->seg[seg].kblocks) return true;
-        kb = 0;
-        return ++seg < a->nseg;
-    }
-};
+    return true;
+}
 
 template <int BN>
 __global__ void __launch_bounds__(UG_THREADS, 1)
@@ -221,21 +229,15 @@ __global__ void __launch_bounds__(UG_THREADS, 1)
         const int h = ew >> 2;                   // column half
         constexpr int COLS = Cfg::COLS;
         if constexpr (BN == 256) {
-            GroupWalk w(&a);
             int grp = 0;
-            bool ok = a.nseg > 0;
-            bool more = ok;
             const int64_t row = (int64_t)m0 + q * 32 + lane;
             float *crow = row < a.rows ? a.C + row * a.ldc + n0 + h * COLS : nullptr;
-            while (more && ok) {
-                const float sc = w.scale() * a.alpha;
-                while (!w.ends()) w.next();
-                more = w.next();
+            auto group = [&](float scale) -> bool {
+                const float sc = scale * a.alpha;
                 const int buf = grp % NBUF;
                 int okw = 1;
                 if (lane == 0) okw = umma::mbar_wait(&pfull[buf], (grp / NBUF) & 1, a.err, a.limit_ns) ? 1 : 0;
-                ok = __shfl_sync(0xffffffffu, okw, 0) != 0;
-                if (!ok) break;
+                if (__shfl_sync(0xffffffffu, okw, 0) == 0) return false;
                 umma::tc_fence_after();
                 const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BN + h * COLS);
 #pragma unroll 1
@@ -265,34 +267,23 @@ __global__ void __launch_bounds__(UG_THREADS, 1)
                 __syncwarp();
                 if (lane == 0) umma::mbar_arrive(&pempty[buf]);
                 ++grp;
-            }
+                return true;
+            };
+            if (a.nseg > 0) for_each_group(a, nullptr, group);
         } else {
         float2 acc[COLS / 2];
 #pragma unroll
         for (int k = 0; k < COLS / 2; ++k) acc[k] = make_float2(0.f, 0.f);
-        GroupWalk w(&a);
         int grp = 0;
-        bool ok = a.nseg > 0;
-        bool more = ok;
         const int64_t erow = (int64_t)m0 + q * 32 + lane;
         const int8_t *erp = (a.expo && erow < a.rows) ? a.expo + erow * a.expo_ld : nullptr;
-        while (more && ok) {
-            // advance the walk to the end of this group
-            float sc = w.scale();
-            if (a.seg[w.seg].mode == UG_EACH_MMA_BEXP) {
-                // this row's exponent of the MMA's 16 K values (0 past the last row)
-                const int e = erp ? (int)__ldg(erp + a.seg[w.seg].e0 + w.kb * 4 + w.i) : 0;
-                sc *= __int_as_float((e + 127) << 23);
-            }
-            while (!w.ends()) w.next();
-            more = w.next();
+        auto group = [&](float sc) -> bool {
             const int buf = grp % NBUF;
             // lane 0 waits and the warp follows, so the warp-wide tensor-memory
             // loads below run with every lane or none
             int okw = 1;
             if (lane == 0) okw = umma::mbar_wait(&pfull[buf], (grp / NBUF) & 1, a.err, a.limit_ns) ? 1 : 0;
-            ok = __shfl_sync(0xffffffffu, okw, 0) != 0;
-            if (!ok) break;
+            if (__shfl_sync(0xffffffffu, okw, 0) == 0) return false;
             umma::tc_fence_after();
             const float2 s2 = make_float2(sc, sc);
             const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BN + h * COLS);
@@ -308,7 +299,9 @@ __global__ void __launch_bounds__(UG_THREADS, 1)
             __syncwarp();
             if (lane == 0) umma::mbar_arrive(&pempty[buf]);
             ++grp;
-        }
+            return true;
+        };
+        const bool ok = a.nseg > 0 && for_each_group(a, erp, group);
         const int64_t row = (int64_t)m0 + q * 32 + lane;
         if (ok && row < a.rows) {
             float *crow = a.C + row * a.ldc + n0 + h * COLS;
@@ -436,7 +429,9 @@ cudaError_t umma_gemm(const __half *A, int64_t lda, const __half *B, int64_t ldb
             g.a_k0 + (int64_t)g.kblocks * UG_BK > lda || g.b_k0 + (int64_t)g.kblocks * UG_BK > ldb)
             return cudaErrorInvalidValue;
         if (g.mode == UG_CONTINUE && i == 0) return cudaErrorInvalidValue;
-        if (g.mode == UG_EACH_MMA_BEXP && (!expo || g.e0 < 0 || g.e0 + 4 * (int64_t)g.kblocks > expo_ld))
+        // the epilogue reads a K block's four exponents as one aligned 32-bit word
+        if (g.mode == UG_EACH_MMA_BEXP && (!expo || ((uintptr_t)expo & 3) || expo_ld % 4 || g.e0 < 0 || g.e0 % 4 ||
+                                           g.e0 + 4 * (int64_t)g.kblocks > expo_ld))
             return cudaErrorInvalidValue;
         a.seg[i] = g;
     }
