@@ -276,6 +276,46 @@ __device__ __forceinline__ void line_fft(float2 *x, float2 *sm, int t, const flo
     }
 }
 
+// ------------------------------------------------------ zero-mode split
+// A state close to uniform keeps almost all of its norm in one Fourier value,
+// the global zero mode.  Each FP32 rounding of that value inside the
+// butterflies moves every point of its line coherently, so the norm takes a
+// random walk of ~2^-24 per rounding while the state is near uniform (most of
+// the walk of a run on a fine mesh).  The pass that applies the last forward
+// transform, the kinetic factor and the inverse transform along one line
+// therefore transforms the line through frequency 0 of the other axes as
+// x - mu (mu = the line mean) and adds back K0 (N mu), K0 being the (exactly
+// known) kinetic factor of the line's zero mode: the same linear map, with the
+// large value kept out of the transforms.  Every other line's zero mode holds
+// only the small share of the norm at its own frequency, so those lines are
+// transformed as they are.  N is a power of two, so mu = sum / N and
+// N mu = sum are exact.
+//
+// Sum of a line's points held E per thread by T consecutive lanes (T a power of
+// two dividing 32; mask: those lanes): a local sum, then an xor butterfly over
+// the T lanes; both partners add the same two values, so every lane ends with
+// the same bits.
+template <int E, int T>
+__device__ __forceinline__ float2 line_sum_lanes(const float2 *x, unsigned mask = 0xffffffffu) {
+    float2 s = x[0];
+#pragma unroll
+    for (int e = 1; e < E; ++e) s = cadd(s, x[e]);
+#pragma unroll
+    for (int m = 1; m < T; m <<= 1) {
+        s.x += __shfl_xor_sync(mask, s.x, m);
+        s.y += __shfl_xor_sync(mask, s.y, m);
+    }
+    return s;
+}
+
+// x[e] -= sum / N for the E points of this thread.
+template <int N, int E>
+__device__ __forceinline__ void sub_line_mean(float2 *x, float2 sum) {
+    const float2 mu = make_float2(sum.x * (1.0f / N), sum.y * (1.0f / N));
+#pragma unroll
+    for (int e = 0; e < E; ++e) x[e] = csub(x[e], mu);
+}
+
 // ------------------------------------------------------- phase helpers
 // Fixed-point turns: a phase angle 2 pi u / 2^32 is carried as u (uint32).
 // hi32((c * v) mod 2^64) for a 64-bit fraction c (units of 2^-64 turns) and a

@@ -99,6 +99,26 @@ __global__ void __launch_bounds__(W * LineCfg<N>::T, N <= 256 ? 4 : 1) k_axis(Ax
 #pragma unroll
     for (int e = 0; e < E; ++e) x[e] = g[(int64_t)(t + T * e) * a.inner];
     float2 *sm = smem + (C::TWO_STAGE ? c * S : 0);
+    // zero-mode split (qhd_device.cuh) in the forward-kinetic-inverse pass, for
+    // the tile holding column 0 (frequency 0 of the other axes) of each
+    // instance: the T threads of a column span several warps, so their partial
+    // sums meet in shared memory behind the exchange buffer and every thread
+    // adds them in the same order.
+    constexpr int ALL3 = MODE_FWD | MODE_KIN | MODE_INV;
+    const bool split0 = (a.mode & ALL3) == ALL3 && blockIdx.x == o * tiles;
+    float2 sum = make_float2(0.f, 0.f), mean_part = make_float2(0.f, 0.f);
+    if (split0) {
+        float2 *red = smem + (C::TWO_STAGE ? W * S : 0);
+        float2 s = x[0];
+#pragma unroll
+        for (int e = 1; e < E; ++e) s = cadd(s, x[e]);
+        red[t * W + c] = s;
+        __syncthreads();
+        sum = red[c];
+#pragma unroll
+        for (int q = 1; q < T; ++q) sum = cadd(sum, red[q * W + c]);
+        sub_line_mean<N, E>(x, sum);
+    }
     if (a.mode & MODE_FWD) line_fft<N, false>(x, sm, t, a.tw2, BlockSync{});
     if (a.mode & MODE_KIN) {
         // axis 0 pass: plane index o is the instance.  Each per-axis factor is
@@ -111,16 +131,22 @@ __global__ void __launch_bounds__(W * LineCfg<N>::T, N <= 256 ? 4 : 1) k_axis(Ax
         const float4 k1 = __ldg(&kb[a.koff1 + i1]);
         float4 k2 = make_float4(1.f, 0.f, 0.f, 0.f);
         if (a.ndim == 3) k2 = __ldg(&kb[a.koff2 + (ci & ((1 << a.log_n2) - 1))]);
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-            const float4 k0 = __ldg(&kb[t + T * e]);
-            float2 y = cmul_comp(x[e], make_float2(k0.x, k0.y), make_float2(k0.z, k0.w));
+        auto kin = [&](float2 v, float4 k0) {
+            float2 y = cmul_comp(v, make_float2(k0.x, k0.y), make_float2(k0.z, k0.w));
             y = cmul_comp(y, make_float2(k1.x, k1.y), make_float2(k1.z, k1.w));
             if (a.ndim == 3) y = cmul_comp(y, make_float2(k2.x, k2.y), make_float2(k2.z, k2.w));
-            x[e] = y;
-        }
+            return y;
+        };
+#pragma unroll
+        for (int e = 0; e < E; ++e) x[e] = kin(x[e], __ldg(&kb[t + T * e]));
+        // the mean's part: N mu = sum through the factor of frequency 0
+        if (split0) mean_part = kin(sum, __ldg(&kb[0]));
     }
     if (a.mode & MODE_INV) line_fft<N, true>(x, sm, t, a.tw2, BlockSync{});
+    if (split0) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) x[e] = cadd(x[e], mean_part);
+    }
 #pragma unroll
     for (int e = 0; e < E; ++e) g[(int64_t)(t + T * e) * a.inner] = x[e];
 }
@@ -156,6 +182,10 @@ __global__ void __launch_bounds__(ROW_THREADS) k_oned(OneDArgs a) {
         const uint32_t dz = step_dither(a.dither_base + (uint64_t)j);
 #pragma unroll
         for (int e = 0; e < E; ++e) x[e] = apply_phase_tab(x[e], turns_mul(c, fv[e]) + dz, ptab);
+        // zero-mode split (qhd_device.cuh): the line is the whole instance, so
+        // its zero mode is the global one
+        const float2 sum = line_sum_lanes<E, T>(x);
+        sub_line_mean<N, E>(x, sum);
         line_fft<N, false>(x, sm, t, a.tw2, WarpSync{});
         const float4 *kb = a.kt + ((int64_t)j * a.kt_batch + (a.kt_batch == 1 ? 0 : b)) * N;
 #pragma unroll
@@ -163,7 +193,11 @@ __global__ void __launch_bounds__(ROW_THREADS) k_oned(OneDArgs a) {
             const float4 k0 = __ldg(&kb[t + T * e]);
             x[e] = cmul_comp(x[e], make_float2(k0.x, k0.y), make_float2(k0.z, k0.w));
         }
+        const float4 z0 = __ldg(&kb[0]);
+        const float2 mean_part = cmul_comp(sum, make_float2(z0.x, z0.y), make_float2(z0.z, z0.w));
         line_fft<N, true>(x, sm, t, a.tw2, WarpSync{});
+#pragma unroll
+        for (int e = 0; e < E; ++e) x[e] = cadd(x[e], mean_part);
     }
     if (a.final_phase) {
         const uint64_t c = a.pot[(int64_t)a.cnt * a.batch + b];
@@ -340,7 +374,8 @@ static cudaError_t axis_w_impl(const AxisArgs &a, cudaStream_t s) {
     using C = LineCfg<N>;
     constexpr int S = line_stride<N>(false, W);
     const int64_t blocks = a.planes * (a.inner / W);
-    const size_t xch = C::TWO_STAGE ? (size_t)W * S * sizeof(float2) : 0;
+    // exchange buffer, then the column partial sums of the zero-mode split
+    const size_t xch = (C::TWO_STAGE ? (size_t)W * S * sizeof(float2) : 0) + (size_t)W * C::T * sizeof(float2);
     k_axis<N, W><<<(unsigned)blocks, W * C::T, xch, s>>>(a);
     return cudaGetLastError();
 }

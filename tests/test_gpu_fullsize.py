@@ -26,10 +26,14 @@ TV_TOL = 1e-4
 EF_TOL = 1e-5
 NORM_TOL = 1e-6
 # FP32 rounding of the state is a random walk of the norm once the systematic part
-# is removed (the compensated product's order, qhd_device.cuh): 32 instances of 128^2
-# wells and 12 of 1024^2 Rastrigin over 10^4 steps give a spread (std) of 2.1-2.4e-6
-# with a mean within one standard error of 0 (test_norm_drift_is_unbiased_over_seeds).
-NORM_WALK_10K = 2.5e-6
+# is removed (the compensated product's order, qhd_device.cuh), and the zero-mode
+# split (qhd_device.cuh) keeps the near-uniform early state's dominant Fourier value
+# out of the butterflies, which removes most of the walk on fine meshes.  Measured
+# spread (std) over 10^4 steps of dt = 1e-3: 1024^2 Rastrigin 0.9e-6 (12 seeds),
+# 256^3 wells 0.35e-6 (3 seeds), 128^2 wells 1.8e-6 (64 seeds; a coarse mesh
+# concentrates the late state on fewer points), each mean within 1.5 standard
+# errors of 0 (test_norm_drift_is_unbiased_over_seeds).
+NORM_WALK_10K = {"1024sq_rastrigin": 0.9e-6, "256cube_wells": 0.35e-6, "128sq": 1.8e-6}
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
 CASES = {
@@ -145,12 +149,14 @@ def test_fullsize_10k_steps_match_oracle_reference(name):
 
 @pytest.mark.parametrize("name", list(CASES))
 def test_fullsize_10k_steps_norm(name):
-    """The norm after 10^4 steps (and after the 10^4 steps back) within 3 standard
-    deviations of the measured FP32 random walk."""
+    """The benchmark's instances meet the stated norm bound (1e-6) after their 10^4
+    steps; after the 10^4 steps back (twice the rounding) the norm is within 3
+    standard deviations of the measured walk, scaled by sqrt(2)."""
     obs, back, tv_back, t, steps, _ = full_run(name)
+    print(f"{name}: norm - 1 after 10^4 steps {obs.norm - 1:+.2e}, after the steps back {back.norm - 1:+.2e}")
     assert steps == 20000 and abs(t) < 1e-9
-    assert abs(obs.norm - 1.0) <= 3 * NORM_WALK_10K, obs.norm
-    assert abs(back.norm - 1.0) <= 3 * NORM_WALK_10K * np.sqrt(2), back.norm
+    assert abs(obs.norm - 1.0) <= NORM_TOL, obs.norm
+    assert abs(back.norm - 1.0) <= max(NORM_TOL, 3 * NORM_WALK_10K[name] * np.sqrt(2)), back.norm
 
 
 def test_norm_drift_is_unbiased_over_seeds():
@@ -168,7 +174,7 @@ def test_norm_drift_is_unbiased_over_seeds():
     sim.close()
     se = d.std() / np.sqrt(len(d))
     assert abs(d.mean()) <= 3 * se + 1e-7, (d.mean(), se)
-    assert np.abs(d).max() <= 4 * NORM_WALK_10K, np.abs(d).max()
+    assert np.abs(d).max() <= 4 * NORM_WALK_10K["128sq"], np.abs(d).max()
     assert 0.25 * len(d) <= (d > 0).sum() <= 0.75 * len(d), (d > 0).sum()
 
 
@@ -211,7 +217,7 @@ def test_paper_resolution_256sq_lie_trotter_and_strang():
         ef_raw = abs(obs.e_f - ob.e_f) / scale
         assert tv <= TV_TOL, (name, tv)
         assert ef_raw <= EF_TOL, (name, ef_raw)
-        assert abs(obs.norm - 1.0) <= 3 * NORM_WALK_10K, (name, obs.norm)
+        assert abs(obs.norm - 1.0) <= 3 * NORM_WALK_10K["128sq"], (name, obs.norm)
         res[name] = (p_g, ob.prob, tv)
     between = 0.5 * np.abs(res["trotter"][1] - res["strang"][1]).sum()
     assert between > 5 * max(res["trotter"][2], res["strang"][2]), (between, res["trotter"][2], res["strang"][2])

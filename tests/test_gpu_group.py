@@ -20,7 +20,9 @@ import workloads
 from paper_2303_01471_gb300 import autotune, qhd
 
 TV_TOL, EF_TOL = 1e-4, 1e-5
-NORM_1K = 3 * 0.9e-6   # three standard deviations of the FP32 norm walk over 1000 steps (test_gpu_parity.py)
+# three standard deviations of the FP32 norm walk over 1000 steps of dt = 0.01,
+# per mesh (measured over 64-256 seeds, test_gpu_parity.py), never below 1e-6
+NORM_1K = {64: 3 * 1.0e-6, 128: 3 * 0.55e-6, 256: max(1e-6, 3 * 0.42e-6)}
 
 
 def make_ctx(n, seeds, stream=None):
@@ -76,7 +78,7 @@ def test_group_other_split_matches_oracle_1000_steps(sub):
             ob = oracle.observables(inst.f, po)
             tv = 0.5 * np.abs(p[k] - ob.prob).sum()
             ef = abs(obs[k].e_f - ob.e_f) / max(abs(ob.e_f), 1e-3 * np.ptp(inst.f))
-            assert tv <= TV_TOL and ef <= EF_TOL and abs(obs[k].norm - 1.0) <= NORM_1K, (inst.shape, k, tv, ef,
+            assert tv <= TV_TOL and ef <= EF_TOL and abs(obs[k].norm - 1.0) <= NORM_1K[inst.shape[0]], (inst.shape, k, tv, ef,
                                                                                        obs[k].norm)
             assert tuple(obs[k].x_star[:2]) == tuple(ob.x_star[:2])
     grp.close()

@@ -25,23 +25,25 @@ from paper_2303_01471_gb300 import qhd
 TV_TOL = 1e-4
 EF_TOL = 1e-5
 NORM_TOL = 1e-6
-# Norm drift that FP32 arithmetic itself produces: a split-step whose every
-# product and sum is correctly rounded to FP32 (exact twiddles and phases)
-# drifts by ~1e-6 per 10^3 steps once the state concentrates on a few mesh
-# points (N_eff ~ 10), because the rounding of those few amplitudes is not
-# averaged out.  Regressions beyond 4x that floor fail outright.
-# The norm of the FP32 state is a random walk with no systematic part (the
-# rounding order of the compensated product removes the bias, qhd_device.cuh):
-# measured standard deviations over many seeds, 1000 steps of dt = 0.01 on 128^2
-# and 10^4 steps of dt = 1e-3.  The stated 1e-6 holds for most instances up to
-# 1000 steps; a test bound is 3 standard deviations, never below 1e-6.
-NORM_WALK_1K = 0.9e-6
-NORM_WALK_10K = 2.5e-6
+# Norm drift that FP32 arithmetic itself produces.  With every product and sum
+# correctly rounded the norm still takes a random walk with no systematic part
+# (the rounding order of the compensated product removes the bias,
+# qhd_device.cuh).  While the state is near uniform the global zero Fourier mode
+# holds almost all of the norm; the passes keep that value out of the
+# butterflies (the zero-mode split, qhd_device.cuh), which cut the walk of the
+# first 200 steps about 8x.  What remains comes late in a run, once the state
+# sits on a few mesh points, so it is larger on coarse meshes.  Measured
+# standard deviations of the 1000-step (dt = 0.01) drift, 64 to 256 seeds:
+# 64^2 1.0e-6, 128^2 0.55e-6, 256^2 0.42e-6; 10^4 steps of dt = 1e-3: 128^2
+# 1.8e-6, 1024^2 0.9e-6, 256^3 0.35e-6.  A test bound is 3 standard deviations,
+# never below the stated 1e-6.
+NORM_WALK_1K = 0.55e-6
+NORM_WALK_10K = 1.8e-6
 
 
 def norm_bound(nsteps):
-    # the walk is front-loaded (early on the zero Fourier mode carries almost all
-    # of the norm), so short runs get the 1000-step bound, not a scaled-down one
+    # the coarse-mesh walk is back-loaded, so short runs get the 1000-step
+    # bound, not a scaled-down one
     walk = NORM_WALK_1K if nsteps <= 1000 else NORM_WALK_10K * math.sqrt(nsteps / 1e4)
     return max(NORM_TOL, 3 * walk)
 
@@ -315,12 +317,11 @@ def test_parity_128sq_wells_1000_steps(seed):
 
 
 def test_norm_drift_128sq_wells_1000_steps_over_seeds():
-    """The norm after the configuration's 1000 steps over 32 seeds: no systematic
-    part (mean within 3 standard errors of 0, both signs), spread at the FP32
-    floor of a state whose weight sits on a few values (at first the zero Fourier
-    mode, later a few mesh points): NORM_WALK_1K is the measured standard
-    deviation."""
-    seeds = list(range(32))
+    """The norm after the configuration's 1000 steps over 256 seeds: no systematic
+    part (mean within 3 standard errors of 0, both signs), the spread at the
+    measured FP32 walk (NORM_WALK_1K), and the stated bound 1e-6 met by at least
+    90% of the instances (93% measured; 72% before the zero-mode split)."""
+    seeds = list(range(256))
     fs = np.stack([workloads.gaussian_wells(s, (128, 128), K=8).f for s in seeds])
     sim = qhd.QHD((128, 128), batch=len(seeds))
     sim.set_potential(fs)
@@ -329,11 +330,14 @@ def test_norm_drift_128sq_wells_1000_steps_over_seeds():
     sim.evolve(10.0, 0.01)
     d = np.array([o.norm - 1.0 for o in sim.observables(0.1)])
     sim.close()
-    print(f"1000-step norm drift over 32 seeds: mean {d.mean():+.2e} std {d.std():.2e} "
-          f"max |.| {np.abs(d).max():.2e}, within 1e-6: {(np.abs(d) <= NORM_TOL).sum()}/32")
+    within = int((np.abs(d) <= NORM_TOL).sum())
+    print(f"1000-step norm drift over {len(d)} seeds: mean {d.mean():+.2e} std {d.std():.2e} "
+          f"max |.| {np.abs(d).max():.2e}, within 1e-6: {within}/{len(d)}")
     assert abs(d.mean()) <= 3 * d.std() / np.sqrt(len(d)) + 1e-8, d.mean()
-    assert 0 < (d > 0).sum() < len(d)
-    assert np.abs(d).max() <= 4 * NORM_WALK_1K, np.abs(d).max()
+    assert 0.25 * len(d) < (d > 0).sum() < 0.75 * len(d)
+    assert d.std() <= 1.2 * NORM_WALK_1K, d.std()
+    assert within >= 0.9 * len(d), within
+    assert np.abs(d).max() <= 6 * NORM_WALK_1K, np.abs(d).max()
 
 
 # ------------------------------------------------------- invariants on the GPU
