@@ -115,7 +115,9 @@ size_t qhd_workspace_bytes(int ndim, const int64_t *n, int64_t batch);
  * lo[k] < hi[k], both finite; 1 <= batch <= 65535 independent instances
  * sharing the mesh (each with its own f and schedule); G <= 2^30 and
  * batch * G <= 2^34.  psi_dev: caller-owned device
- * buffer of batch*G complex64, 8-byte aligned.  work_dev: caller-owned device
+ * buffer of batch*G complex64, 16-byte aligned (the passes move two points per
+ * 16-byte copy; an 8-byte aligned pointer is refused with
+ * QHD_ERR_INVALID_ARG).  work_dev: caller-owned device
  * buffer of work_bytes >= qhd_workspace_bytes(...), 256-byte aligned.
  * stream: a cudaStream_t (NULL = legacy default stream).  Both buffers must
  * outlive the context.  *out is set only on QHD_OK.

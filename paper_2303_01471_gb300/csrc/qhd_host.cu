@@ -297,7 +297,8 @@ qhd_status qhd_init_grid(qhd_ctx **out, int ndim, const int64_t *n, const double
     if (!shape_ok(ndim, n, batch)) return QHD_ERR_INVALID_ARG;
     for (int d = 0; d < ndim; ++d)
         if (!std::isfinite(lo[d]) || !std::isfinite(hi[d]) || !(lo[d] < hi[d])) return QHD_ERR_INVALID_ARG;
-    if (!psi_dev || ((uintptr_t)psi_dev & 7)) return QHD_ERR_INVALID_ARG;
+    // 16-byte aligned: the passes move psi in 16-byte (two-point) copies
+    if (!psi_dev || ((uintptr_t)psi_dev & 15)) return QHD_ERR_INVALID_ARG;
     Layout L = make_layout(ndim, n, batch);
     if (!work_dev || ((uintptr_t)work_dev & 255) || work_bytes < L.total) return QHD_ERR_WORKSPACE;
 

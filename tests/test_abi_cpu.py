@@ -59,6 +59,8 @@ def test_init_rejects_bad_arguments_without_a_device(lib):
     assert lib.qhd_init_grid(None, 2, n, lo, hi, 1, fake, fake, ws, None) == 1
     assert lib.qhd_init_grid(ctypes.byref(ctx), 2, n, lo, bad_hi, 1, fake, fake, ws, None) == 1
     assert lib.qhd_init_grid(ctypes.byref(ctx), 2, n, lo, hi, 1, None, fake, ws, None) == 1
+    # psi 8-byte but not 16-byte aligned: the passes copy it 16 bytes at a time
+    assert lib.qhd_init_grid(ctypes.byref(ctx), 2, n, lo, hi, 1, ctypes.c_void_p(0x10000008), fake, ws, None) == 1
     assert lib.qhd_init_grid(ctypes.byref(ctx), 2, n, lo, hi, 1, fake, None, ws, None) == 6
     assert lib.qhd_init_grid(ctypes.byref(ctx), 2, n, lo, hi, 1, fake, fake, ws - 1, None) == 6
     assert lib.qhd_init_grid(ctypes.byref(ctx), 2, n, lo, hi, 1, fake,
