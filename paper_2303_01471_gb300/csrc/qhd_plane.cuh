@@ -99,6 +99,26 @@ __device__ __forceinline__ void plane_rows(float2 *tile, const float4 *__restric
     using P = PlaneCfg<N1, N2, C>;
     constexpr int T2 = P::T2, E2 = P::E2;
     const int t = threadIdx.x % T2;
+    // zero-mode split (qhd_device.cuh): the row transform is the last forward
+    // transform before the kinetic factor, and local row 0 of rank 0 (frequency
+    // 0 along the distributed axis) holds the global zero mode.  Its T2 threads
+    // (lanes 0..T2-1 of warp 0, the ones that transform it below) take the mean
+    // out of the shared-memory row before the row loop and add the mean's part
+    // back after it, so the loop itself is the same for every row.
+    const bool zrow = DIR == 2 && rank == 0 && (int)threadIdx.x < T2;
+    float2 mean_part = make_float2(0.f, 0.f);
+    if (zrow) {
+        float2 v[E2];
+#pragma unroll
+        for (int e = 0; e < E2; ++e) v[e] = tile[t + T2 * e];
+        const float2 sum = line_sum_lanes<E2, T2>(v, T2 >= 32 ? 0xffffffffu : (1u << T2) - 1u);
+        sub_line_mean<N2, E2>(v, sum);
+#pragma unroll
+        for (int e = 0; e < E2; ++e) tile[t + T2 * e] = v[e];
+        const float4 k0 = kt0[0], k1 = kt1[0];
+        const float2 y = cmul_comp(sum, make_float2(k0.x, k0.y), make_float2(k0.z, k0.w));
+        mean_part = cmul_comp(y, make_float2(k1.x, k1.y), make_float2(k1.z, k1.w));
+    }
 #pragma unroll 1
     for (int base = 0; base < P::R; base += P::ROWS_PER_ITER) {
         const int row = base + threadIdx.x / T2;
@@ -111,39 +131,28 @@ __device__ __forceinline__ void plane_rows(float2 *tile, const float4 *__restric
             if (DIR == 1) {
                 line_fft<N2, true>(x, rp, t, tw_row, WarpSyncP{});
             } else {
-                // zero-mode split (qhd_device.cuh): the row transform is the last
-                // forward transform before the kinetic factor, and the row of
-                // distributed-axis frequency 0 (rank 0, local row 0: lanes
-                // 0..T2-1 of warp 0) holds the global zero mode
-                float2 sum = make_float2(0.f, 0.f);
-                const bool zrow = DIR == 2 && rank == 0 && row == 0;
-                if (zrow) {
-                    sum = line_sum_lanes<E2, T2>(x, T2 >= 32 ? 0xffffffffu : (1u << T2) - 1u);
-                    sub_line_mean<N2, E2>(x, sum);
-                }
                 line_fft<N2, false>(x, rp, t, tw_row, WarpSyncP{});
                 if (DIR == 2) {
                     // this local row holds frequency rank + C * row along the distributed axis
                     // plain (coherent) loads: the batched persistent kernel writes
                     // these tables earlier in the same launch
                     const float4 k0 = kt0[rank + C * row];
-                    auto kin = [&](float2 v, float4 k1) {
-                        const float2 y = cmul_comp(v, make_float2(k0.x, k0.y), make_float2(k0.z, k0.w));
-                        return cmul_comp(y, make_float2(k1.x, k1.y), make_float2(k1.z, k1.w));
-                    };
 #pragma unroll
-                    for (int e = 0; e < E2; ++e) x[e] = kin(x[e], kt1[t + T2 * e]);
-                    const float2 mean_part = zrow ? kin(sum, kt1[0]) : make_float2(0.f, 0.f);
-                    line_fft<N2, true>(x, rp, t, tw_row, WarpSyncP{});
-                    if (zrow) {
-#pragma unroll
-                        for (int e = 0; e < E2; ++e) x[e] = cadd(x[e], mean_part);
+                    for (int e = 0; e < E2; ++e) {
+                        const float4 k1 = kt1[t + T2 * e];
+                        float2 y = cmul_comp(x[e], make_float2(k0.x, k0.y), make_float2(k0.z, k0.w));
+                        x[e] = cmul_comp(y, make_float2(k1.x, k1.y), make_float2(k1.z, k1.w));
                     }
+                    line_fft<N2, true>(x, rp, t, tw_row, WarpSyncP{});
                 }
             }
 #pragma unroll
             for (int e = 0; e < E2; ++e) rp[t + T2 * e] = x[e];
         }
+    }
+    if (zrow) {
+#pragma unroll
+        for (int e = 0; e < E2; ++e) tile[t + T2 * e] = cadd(tile[t + T2 * e], mean_part);
     }
 }
 
