@@ -47,7 +47,7 @@ BYTES_PER_POINT = {"row": 20, "axis1_fwd": 16, "axis0": 16, "axis1_inv": 16, "pl
 # DRAM bytes (read + write) of one launch from an ncu capture (not measured by
 # this run), with the SHA-256 (first 16 hex digits) of the kernel sources it was
 # taken on; bench lines carry the figure only while those sources are unchanged.
-TRAFFIC_PER_LAUNCH = {("plane", "256x256x256"): {"bytes": 201422848 + 77155072, "sources_sha16": "f2d1a1a1f17ff082",
+TRAFFIC_PER_LAUNCH = {("plane", "256x256x256"): {"bytes": 201427968 + 77629696, "sources_sha16": "d0e447d7b574d27d",
                                                   "captured": "ncu --metrics dram__bytes_read.sum,"
                                                               "dram__bytes_write.sum, one launch, 256^3 wells"}}
 TRAFFIC_SOURCES = ["paper_2303_01471_gb300/csrc/qhd_plane.cu", "paper_2303_01471_gb300/csrc/qhd_plane.cuh",

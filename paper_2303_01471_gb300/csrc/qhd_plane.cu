@@ -38,8 +38,19 @@ __global__ void __launch_bounds__(PLANE_THREADS, plane_min_blocks<N1, N2, C>()) 
     const bool inv = a.mode & MODE_INV, fwd = a.mode & MODE_FWD;
 
     plane_copy<N1, N2, C, true>(tile, g);
-    load_phase_tab(ptab, a.ptab);
     const uint32_t *fqr = a.fq + plane * (int64_t)N1 * N2;
+    {
+        // the potential rows this CTA's exchange positions read (R / C rows in
+        // each of the C row blocks) go to L2 now, during the tile load and the
+        // inverse transforms, so the exchange's potential loads hit L2
+        // (measured: 163.2 -> 160.5 us per 256^3 pass)
+        constexpr uint32_t FQB = (uint32_t)((P::R / C) * N2 * sizeof(uint32_t));
+        if (FQB % 16 == 0 && (int)threadIdx.x < C) {
+            const uint32_t *src = fqr + (int64_t)(P::R * threadIdx.x + rank * (P::R / C)) * N2;
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(FQB) : "memory");
+        }
+    }
+    load_phase_tab(ptab, a.ptab);
     const uint64_t coef = a.pot[plane / a.planes_per_inst];
     plane_copy_wait();
     if (inv) {
