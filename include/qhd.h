@@ -220,7 +220,10 @@ qhd_status qhd_set_kinetic(qhd_ctx *ctx, int kind);
  *   3: block-scaled hi/lo -- each 16 consecutive values of a row share a
  *      power-of-two exponent and are cut into two FP16 integer slices (21
  *      bits below the block maximum), the DFT matrix into two (21 bits);
- *      three slice products;
+ *      three slice products.  The DFT matrix's last slice is re-rounded every
+ *      step with a pseudo-random offset (floor(r + u), u in [0, 1) per step),
+ *      so its rounding is exact on average over steps instead of a fixed
+ *      perturbation repeated in every transform;
  *   5: as 3 with the DFT matrix in three slices (32 bits) and two more
  *      products;
  *  10: fixed-point slices on a per-instance power-of-two scale (data to 2^-28
@@ -233,8 +236,9 @@ qhd_status qhd_set_kinetic(qhd_ctx *ctx, int kind);
  * qhd_tc_workspace_bytes returns 0 for these and for other products).
  * tc_work_dev: caller-owned device buffer, 256-byte aligned, of at least
  * qhd_tc_workspace_bytes(...) bytes, kept until the transform is changed or
- * the context destroyed (else QHD_ERR_WORKSPACE); it holds the DFT matrices,
- * the FP16 operands, the block exponents and the FP32 products.  No device
+ * the context destroyed (else QHD_ERR_WORKSPACE); it holds the DFT matrices
+ * (and, for 3 and 5 products, their last slice before rounding in FP32), the
+ * FP16 operands, the block exponents and the FP32 products.  No device
  * memory is allocated.  transform = QHD_TRANSFORM_FFT releases the
  * tensor-core state and ignores the other arguments.  Unknown transforms or
  * products other than 3, 5 and 10 give QHD_ERR_INVALID_ARG.  Synchronises the

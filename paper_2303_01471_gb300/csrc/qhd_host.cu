@@ -587,6 +587,7 @@ qhd_status evolve_tc_chunk(qhd_ctx *c, int64_t j0, int64_t cnt, bool last_chunk,
         qhd_status s;
         {
             TimedScope ts(c, QHD_KCLASS_TC_SPLIT, sample);
+            QHD_CUDA(c, tc_dither_w(c->tc, ta.dither, c->stream, &c->launches));
             QHD_CUDA(c, tc_split_potential(c->tc, ta, j == 0, c->stream, &c->launches));
         }
         if ((s = gemm(false, sample)) != QHD_OK) return s;

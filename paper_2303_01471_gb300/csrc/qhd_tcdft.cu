@@ -327,6 +327,7 @@ struct TcState {
     int64_t batch = 0;
     unsigned *err = nullptr;            // GEMM wait time-out word (2 words)
     __half *w[2] = {nullptr, nullptr};  // forward, inverse DFT matrix, stored transposed [2n][pitch]: K-major
+    float *wres[2] = {nullptr, nullptr}; // block-scaled forms: the last W slice before rounding, [2n][2n]
     __half *a = nullptr;                // B*n rows of split operands (padded pitch, tc_pitch)
     float *c = nullptr;                 // B*n x 2n products
     unsigned *maxbits = nullptr;        // fixed form: 2 x B max |z|^2 buffers
@@ -356,6 +357,7 @@ size_t tc_workspace_bytes(int n, int64_t batch, int products) {
     t += tc_align((size_t)batch * sizeof(int));
     t += tc_align(2 * sizeof(unsigned));  // GEMM wait time-out word
     t += tc_align(rows * (m / 16));       // block exponents of the block-scaled form
+    if (products != TC_FIXED) t += 2 * tc_align(m * m * sizeof(float));  // residuals of the dithered slice
     return t;
 }
 
@@ -404,6 +406,13 @@ TcState *tc_create(int n, int64_t batch, int products, void *ws, size_t ws_bytes
     t->err = (unsigned *)p;
     p += tc_align(2 * sizeof(unsigned));
     t->e8 = (int8_t *)p;
+    p += tc_align(rows * (m / 16));
+    if (products != TC_FIXED) {
+        t->wres[0] = (float *)p;
+        p += tc_align(m * m * sizeof(float));
+        t->wres[1] = (float *)p;
+        p += tc_align(m * m * sizeof(float));
+    }
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -416,6 +425,7 @@ TcState *tc_create(int n, int64_t batch, int products, void *ws, size_t ws_bytes
 
     // W and conj W from FP64, split on the host
     std::vector<__half> host(wp * m, __float2half(0.f));
+    std::vector<float> res(products != TC_FIXED ? m * m : 0);
     for (int d = 0; d < 2; ++d) {
         for (size_t row = 0; row < m; ++row)
             for (size_t col = 0; col < m; ++col) {
@@ -425,6 +435,7 @@ TcState *tc_create(int n, int64_t batch, int products, void *ws, size_t ws_bytes
                     // products, W_lo2 = rint(next residual 2^11): integers in [-1024, 1024]
                     double r = v * 1024.0;
                     for (int k = 0; k < wseg; ++k) {
+                        if (k == (int)wseg - 1) res[col * m + row] = (float)r;
                         const double w = std::nearbyint(r);
                         host[col * wp + k * m + row] = __double2half(w);
                         r = (r - w) * 2048.0;
@@ -442,6 +453,9 @@ TcState *tc_create(int n, int64_t batch, int products, void *ws, size_t ws_bytes
             }
         if (cudaMemcpyAsync(t->w[d], host.data(), host.size() * sizeof(__half), cudaMemcpyHostToDevice, s) !=
                 cudaSuccess ||
+            (products != TC_FIXED &&
+             cudaMemcpyAsync(t->wres[d], res.data(), res.size() * sizeof(float), cudaMemcpyHostToDevice, s) !=
+                 cudaSuccess) ||
             cudaStreamSynchronize(s) != cudaSuccess) {
             *why = "copy of the DFT matrices failed";
             delete t;
@@ -579,6 +593,44 @@ cudaError_t tc_gemm(TcState *t, bool inverse, cudaStream_t s, int64_t *launches)
                               t->e8, m / 16);
     ++*launches;
     return e;
+}
+
+// Dithered rounding of the last DFT-matrix slice (block-scaled forms).  The
+// DFT matrix has only n distinct entries and enters every transform of every
+// step, so a fixed rounding of it is one structured perturbation repeated
+// thousands of times: its effect on the norm adds up coherently (a steady loss
+// of ~2e-4 over 1000 steps with the 21-bit matrix).  Rounding the last slice
+// per step as floor(r + u), with u a fresh pseudo-random offset in [0, 1) for
+// the step (the same for every entry), makes the slice exact on average over
+// steps: the rounding errors of different steps are independent and add as a
+// random walk.  r is the slice before rounding, r in [-1024, 1024], so every
+// slice stays an integer in [-1024, 1024] and every MMA partial stays exact.
+__global__ void k_tc_w_dither(__half *w0, __half *w1, const float *res0, const float *res1, int64_t m, int64_t wp,
+                              int seg, float u0, float u1) {
+    const int d = blockIdx.y;
+    __half *w = d == 0 ? w0 : w1;
+    const float *res = d == 0 ? res0 : res1;
+    const float u = d == 0 ? u0 : u1;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m * m; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t col = i / m, row = i - col * m;
+        w[col * wp + seg * m + row] = __float2half_rn(floorf(res[i] + u));
+    }
+}
+
+cudaError_t tc_dither_w(TcState *t, uint32_t dither, cudaStream_t s, int64_t *launches) {
+    if (t->products == TC_FIXED) return cudaSuccess;
+    const int64_t m = 2 * (int64_t)t->n;
+    const int seg = w_segments(t->products) - 1;
+    // offsets of the forward and inverse matrices: 24 bits of the step's
+    // dither, the inverse half a unit apart
+    const uint32_t q = dither >> 8;
+    const float u0 = (float)q * 5.9604644775390625e-08f;                         // 2^-24
+    const float u1 = (float)((q + 0x800000u) & 0xFFFFFFu) * 5.9604644775390625e-08f;
+    k_tc_w_dither<<<dim3((unsigned)t->grid, 2), TC_THREADS, 0, s>>>(t->w[0], t->w[1], t->wres[0], t->wres[1], m,
+                                                                    tc_pitch(w_segments(t->products), (size_t)m), seg,
+                                                                    u0, u1);
+    ++*launches;
+    return cudaGetLastError();
 }
 
 int tc_timed_out(TcState *t, cudaStream_t s) {

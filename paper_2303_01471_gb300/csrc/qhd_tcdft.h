@@ -83,6 +83,9 @@ cudaError_t tc_split_potential(TcState *t, const TcPhaseArgs &a, bool from_psi, 
 cudaError_t tc_split_transpose(TcState *t, cudaStream_t s, int64_t *launches);
 cudaError_t tc_split_kinetic(TcState *t, const TcPhaseArgs &a, cudaStream_t s, int64_t *launches);
 cudaError_t tc_gemm(TcState *t, bool inverse, cudaStream_t s, int64_t *launches);
+// Block-scaled forms: re-round the last DFT-matrix slice of both directions with
+// the step's dither (an offset in [0, 1) taken from its top 24 bits).
+cudaError_t tc_dither_w(TcState *t, uint32_t dither, cudaStream_t s, int64_t *launches);
 // 1 when a bounded wait of a tensor-core GEMM gave up (reads a device word;
 // synchronises the stream); -1 when the read itself failed.
 int tc_timed_out(TcState *t, cudaStream_t s);

@@ -8,20 +8,20 @@ floor.  Its integer slices have level sums FP32 holds exactly, so the
 truncation of the tensor cores' own accumulation never enters.
 
 The block-scaled FP16 hi/lo forms (3 products: the configured "hi-lo" form;
-5 products: the DFT matrix to 32 bits) are exact per MMA as well, yet they do
-not meet those tolerances over 1000 steps, and the tests state what they do
-reach.  The DFT matrix has only n distinct entries, so its rounding error is
-the same structured perturbation in every transform of every step and its
-effect on the norm adds up coherently instead of as a random walk: with 21-bit
-entries (3 products) the norm falls by 1.4-2.6e-4 over 1000 steps, E[f] moves
-with it, TV reaches 1.0-1.3e-4.  A CPU emulation of the whole step (64^2,
-exact slices and FP32 round-to-nearest accumulation in the kernel's order)
-reproduces this and splits it: the 21-bit matrix alone loses 2.4e-4, a 32-bit
-one 5e-7; the FP32 accumulation of the per-MMA partials, whose running sums in
-the inverse transforms are far larger than their results, loses 3.6e-5.  So
-the 5-product form halves TV but its norm still falls by 1e-4.  The 512^2
-case is the batch shape of the tensor-core workload (Gaussian wells K = 16,
-T = 10, dt = 0.01) on 8 of its instances.
+5 products: the DFT matrix to 32 bits) are exact per MMA as well; the tests
+state what they reach over 1000 steps.  The DFT matrix has only n distinct
+entries, so a fixed rounding of it is the same structured perturbation in every
+transform of every step and its effect on the norm adds up coherently instead
+of as a random walk: with 21-bit entries rounded once the norm fell by
+1.4-2.6e-4 over 1000 steps, E[f] moved with it, TV reached 1.0-1.3e-4 (a CPU
+emulation of the step split this into 2.4e-4 from the 21-bit matrix, 5e-7 from
+a 32-bit one, 3.6e-5 from the FP32 accumulation of the per-MMA partials).  The
+last slice is therefore re-rounded every step as floor(r + u) with a fresh
+offset u: exact on average over steps, so its errors add as a random walk; the
+3-product form then reaches TV 1.1-2.6e-5 and E[f] 0.4-1.05e-5.  The 5-product
+form keeps a steady loss of ~1e-4 that the matrix's last slice does not
+explain.  The 512^2 case is the batch shape of the tensor-core workload
+(Gaussian wells K = 16, T = 10, dt = 0.01) on 8 of its instances.
 """
 import math
 
@@ -108,10 +108,20 @@ def test_tc_fixed_short_runs_own_schedules(n):
 
 
 # What the block-scaled forms reach (measured on GB300, see the module docstring):
-# over 100 steps TV <= 1e-4 and |norm - 1| <= 9e-6, E[f] <= 1.2e-5; over 1000
-# steps a steady norm loss of at most 2.6e-4 (3 products) / 1.4e-4 (5 products).
+# over 100 steps TV <= 1e-4 and |norm - 1| <= 9e-6, E[f] <= 1.2e-5.  Over 1000
+# steps the 3-product form, whose last DFT-matrix slice is re-rounded with a fresh
+# offset every step, reaches TV 1.1-2.6e-5, E[f] 0.4-1.05e-5 and a norm drift of
+# either sign up to 1e-5 (128^2 and 512^2, two instances each; 1.1-1.3e-4, 1.4-2.6e-4
+# and a steady loss of 1.4-2.6e-4 with the fixed rounding); the 5-product form
+# keeps a steady loss of at most 1.4e-4.
 BS_100 = {"tv": 1e-4, "ef": 2e-5, "norm": 1.5e-5}
-BS_1K = {3: {"tv": 1.5e-4, "ef": 3.5e-4, "loss": 3.5e-4}, 5: {"tv": 1e-4, "ef": 2e-4, "loss": 2e-4}}
+# Pointwise error per sqrt(step) over 100 steps, relative to the largest amplitude.
+# The 3-product form's re-rounded slice is a fresh perturbation every step; at
+# n = 1024 (K = 2048) its pointwise effect after 100 steps measured 3.3e-4 (2e-4
+# with the fixed rounding, whose coherent part instead grows to TV 1e-4 by 1000
+# steps), while TV, E[f] and the norm stay within the bounds above.
+BS_EL = {3: 4e-5, 5: 2e-5}
+BS_1K = {3: {"tv": 5e-5, "ef": 3e-5, "norm": 3e-5}, 5: {"tv": 1e-4, "ef": 2e-4, "loss": 2e-4}}
 
 
 @pytest.mark.parametrize("products", [3, 5])
@@ -129,7 +139,7 @@ def test_tc_block_scaled_forms_100_steps(n, products):
         tv, ef, el, ob = errors(psi[b], obs[b], inst.f, psi_o)
         assert tv <= BS_100["tv"] and ef <= BS_100["ef"], (tv, ef)
         assert abs(obs[b].norm - 1.0) <= BS_100["norm"], obs[b].norm - 1.0
-        assert el <= 2e-5 * math.sqrt(steps + 1), el
+        assert el <= BS_EL[products] * math.sqrt(steps + 1), el
         assert tuple(obs[b].x_star[:2]) == tuple(ob.x_star[:2])
 
 
@@ -138,8 +148,12 @@ def block_scaled_1k(products, psi, obs, insts, psi_o):
     for b, inst in enumerate(insts):
         tv, ef, _, ob = errors(psi[b], obs[b], inst.f, psi_o[b])
         drift = obs[b].norm - 1.0
-        # the coherent loss of the rounded DFT matrix: always a loss, bounded
-        assert -lim["loss"] <= drift < 0.0, drift
+        print(f"{products} products, instance {b}: TV {tv:.2e} E[f] {ef:.2e} norm - 1 {drift:+.2e}")
+        if "loss" in lim:
+            # the steady loss of the 5-product form: always a loss, bounded
+            assert -lim["loss"] <= drift < 0.0, drift
+        else:
+            assert abs(drift) <= lim["norm"], drift
         assert tv <= lim["tv"] and ef <= lim["ef"], (tv, ef)
         assert tuple(obs[b].x_star[:2]) == tuple(ob.x_star[:2])
 
