@@ -24,7 +24,7 @@ SOURCES = ["qhd_kernels.cu", "qhd_plane.cu", "qhd_host.cu", "qhd_static.cu", "qh
 PROBE_SOURCE = "qhd_probe.cu"
 PROBE_LIB = os.path.join(LIBDIR, "libqhd_probe.so")
 HEADERS = ["qhd_device.cuh", "qhd_kernels.h", "qhd_plane.cuh", "qhd_tcdft.h", "qhd_spectrum.h", "qhd_sched.cuh",
-           "qhd_prep.cuh", "qhd_group.h", "qhd_umma.cuh"]
+           "qhd_prep.cuh", "qhd_group.h", "qhd_umma.cuh", "qhd_trace.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -27,6 +27,7 @@
 #include "qhd.h"
 #include "qhd_group.h"
 #include "qhd_spectrum.h"
+#include "qhd_trace.h"
 #include "qhd_kernels.h"
 #include "qhd_plane.cuh"
 #include "qhd_prep.cuh"
@@ -402,6 +403,7 @@ qhd_status qhd_group_create(qhd_group **out, qhd_ctx *const *ctxs, int n_ctx, co
 }
 
 qhd_status qhd_group_evolve(qhd_group *g, double T, double dt) {
+    qhd::TraceRange trace("qhd_group_evolve");
     if (!g) return QHD_ERR_INVALID_ARG;
     if (g->sticky != QHD_OK) return g->sticky;
     if (!std::isfinite(T) || !std::isfinite(dt) || dt == 0.0)

@@ -14,6 +14,7 @@
 #include "qhd_device.cuh"
 #include "qhd_group.h"
 #include "qhd_kernels.h"
+#include "qhd_trace.h"
 #include "qhd_sched.cuh"
 #include "qhd_spectrum.h"
 #include "qhd_tcdft.h"
@@ -479,6 +480,7 @@ static qhd_status set_potential_common(qhd_ctx *c) {
 }
 
 qhd_status qhd_set_potential(qhd_ctx *c, const double *f_host) {
+    TraceRange trace("qhd_set_potential");
     qhd_status s = check_ctx(c);
     if (s != QHD_OK) return s;
     if (!f_host) return fail(c, QHD_ERR_INVALID_ARG, "f_host is NULL");
@@ -618,6 +620,7 @@ qhd_status evolve_tc_chunk(qhd_ctx *c, int64_t j0, int64_t cnt, bool last_chunk,
 }  // namespace
 
 qhd_status qhd_evolve(qhd_ctx *c, double T, double dt) {
+    TraceRange trace("qhd_evolve");
     qhd_status s = check_ctx(c);
     if (s != QHD_OK) return s;
     if (!std::isfinite(T) || !std::isfinite(dt) || dt == 0.0)
@@ -658,6 +661,7 @@ qhd_status qhd_evolve(qhd_ctx *c, double T, double dt) {
     for (int64_t j0 = 0; j0 < nsteps; j0 += ch) {
         const int64_t cnt = nsteps - j0 < ch ? nsteps - j0 : ch;
         const bool last_chunk = j0 + cnt == nsteps;
+        TraceRange trace_chunk("qhd_evolve chunk");
         pa.j0 = j0;
         pa.cnt = cnt;
         {
@@ -813,6 +817,7 @@ qhd_status qhd_evolve(qhd_ctx *c, double T, double dt) {
 }
 
 qhd_status qhd_observables(qhd_ctx *c, qhd_obs *out, float *prob_dev, double radius) {
+    TraceRange trace("qhd_observables");
     qhd_status s = check_ctx(c);
     if (s != QHD_OK) return s;
     if (!out) return fail(c, QHD_ERR_INVALID_ARG, "out is NULL");

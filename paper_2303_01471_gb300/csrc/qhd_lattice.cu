@@ -35,6 +35,7 @@
 #include "qhd_device.cuh"
 #include "qhd_kernels.h"
 #include "qhd_sched.cuh"
+#include "qhd_trace.h"
 
 using namespace qhd;
 
@@ -1114,6 +1115,7 @@ qhd_status qhd_lattice_reset_state(qhd_lattice *c, int init) {
 }
 
 qhd_status qhd_lattice_evolve(qhd_lattice *c, double T, double dt) {
+    qhd::TraceRange trace("qhd_lattice_evolve");
     qhd_status s = lcheck(c);
     if (s != QHD_OK) return s;
     if (!std::isfinite(T) || !std::isfinite(dt) || dt == 0.0)
